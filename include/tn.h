@@ -1,0 +1,141 @@
+/*
+ * tn.h -- C ABI of the GB300 tensor-network contraction library (libtn.so).
+ *
+ * The library contracts tensor networks edge by edge on one NVIDIA GB300
+ * (sm_103a): a pairwise tensordot of two nodes over their shared legs
+ * (TensorNetwork paper, Sec. III.A.3 "Standard Edges" and III.B.4
+ * "contract_between", which flattens all edges between two nodes into one
+ * before contracting, Sec. III.B.2), driven along matrix product state (MPS)
+ * chains (Sec. II, Fig. 3a) as environment sweeps, and the MPS image
+ * classifier of Sec. IV.A.
+ *
+ * Conventions shared by every entry point
+ *  - All tensor data pointers are DEVICE pointers owned by the caller; the
+ *    library never frees or keeps them. Scalars documented as "device" are
+ *    device pointers too. Host arrays (shapes, leg lists, pointer tables) are
+ *    read during the call only.
+ *  - Dense float32 tensors, strides in elements. A tensor whose strides are
+ *    all zero is read as row-major contiguous.
+ *  - Legs are 0-based (the paper's a[0], get_edge(0)).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream). A nonzero return means nothing was launched. Errors
+ *    raised inside a kernel (a bounded wait that expired) are recorded in a
+ *    device status word, read and cleared by tn_sync_status().
+ *  - No entry point allocates device memory: scratch space is a caller
+ *    buffer whose size the matching *_workspace_bytes call returns.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TN_MAX_RANK 8
+
+/* Status codes. */
+enum {
+  TN_OK = 0,
+  TN_ERR_ARG = 1,         /* null pointer, rank > 8, leg out of range or repeated, bad count */
+  TN_ERR_SHAPE = 2,       /* paired legs differ in dimension (the paper's "if the dimensions
+                             match", Sec. II), or an output shape that is not the result's */
+  TN_ERR_UNSUPPORTED = 3, /* valid request outside what the kernels implement (dtype, layout) */
+  TN_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  TN_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired (kernel returned early) */
+  TN_ERR_WORKSPACE = 6    /* workspace missing, misaligned (256 B) or too small */
+};
+
+/* Element types. */
+enum { TN_F32 = 0 };
+
+/* Arithmetic of a contraction. Inputs and outputs stay float32 in memory. */
+enum {
+  TN_PREC_FP32 = 0,  /* float32 FMA on the CUDA cores */
+  TN_PREC_BF16 = 1,  /* operands rounded to bfloat16 (nearest-even), float32
+                        accumulation on the tcgen05 tensor cores */
+  TN_PREC_BF16X3 = 2 /* split bfloat16: x = hi + lo with hi = bf16(x),
+                        lo = bf16(x - hi); A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi,
+                        all three on tcgen05 into one float32 accumulator */
+};
+
+/* A dense tensor (a node's array, Sec. III.A.2). */
+typedef struct tn_tensor {
+  void* data;                     /* device pointer */
+  int32_t rank;                   /* 0 .. TN_MAX_RANK; rank 0 is a scalar */
+  int32_t dtype;                  /* TN_F32 */
+  int64_t shape[TN_MAX_RANK];     /* dims; entries past rank ignored */
+  int64_t stride[TN_MAX_RANK];    /* element strides, or all zero for row-major */
+} tn_tensor;
+
+/* Fills t as a row-major float32 tensor. Returns TN_OK or TN_ERR_ARG. */
+int tn_tensor_init(tn_tensor* t, void* data, int rank, const int64_t* shape);
+
+/* ------------------------------------------------------------------------ */
+/* Pairwise tensordot (Sec. III.A.3, III.B.4; numpy tensordot semantics)     */
+/* ------------------------------------------------------------------------ */
+/*
+ * C[f_A..., f_B...] = sum over the shared legs of A[...] * B[...], where leg
+ * legsA[j] of A is connected to leg legsB[j] of B (j < nshared). The result's
+ * legs are A's free legs in A's order followed by B's free legs in B's order;
+ * nshared = 0 is the outer product (Sec. III.B.5). All shared legs are merged
+ * into one contraction index (edge flattening, Sec. III.B.2) without moving
+ * data: leg permutations are folded into the kernels' operand gathers, so no
+ * transposed copy is ever made.
+ *   A, B   input tensors (float32, any strides)
+ *   legsA, legsB  host arrays of nshared leg indices (may be NULL if nshared = 0)
+ *   C      output tensor: float32, row-major contiguous, shape as above; it
+ *          must not overlap A or B
+ *   prec   TN_PREC_FP32 / TN_PREC_BF16 / TN_PREC_BF16X3
+ * Errors: TN_ERR_ARG, TN_ERR_SHAPE, TN_ERR_UNSUPPORTED, TN_ERR_CUDA.
+ */
+int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                int nshared, const tn_tensor* C, int prec, void* stream);
+
+/* One pairwise contraction of a grouped launch. */
+typedef struct tn_contract_spec {
+  tn_tensor A, B, C;
+  int32_t nshared;
+  int32_t legsA[TN_MAX_RANK];
+  int32_t legsB[TN_MAX_RANK];
+} tn_contract_spec;
+
+/*
+ * Grouped contraction: many tensordots of uneven shapes in one persistent
+ * launch. A plan validates and lays out the specs once (host), its device
+ * work list is uploaded into a caller workspace, and each run launches one
+ * kernel over all output tiles, largest contractions first.
+ *   tn_group_plan_create: specs (host array, read during the call), prec;
+ *     returns TN_OK and *plan, or the first spec's error (*plan = NULL).
+ *   tn_group_plan_workspace_bytes: device bytes the plan's work list needs.
+ *   tn_group_plan_upload: copies the work list into `workspace` (device,
+ *     256-byte aligned, at least the size above) on `stream`.
+ *   tn_group_plan_run: launches the contractions; `workspace` must hold the
+ *     uploaded work list (uploads and runs are ordered on the stream).
+ *   tn_group_plan_destroy: frees the host plan (never device memory).
+ * Errors: as tn_contract, plus TN_ERR_WORKSPACE.
+ */
+typedef struct tn_group_plan tn_group_plan;
+int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn_group_plan** plan);
+size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan);
+int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
+int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
+void tn_group_plan_destroy(tn_group_plan* plan);
+/* Total floating-point work (2 M N K summed over specs) and algorithmic bytes
+ * (|A| + |B| + |C| float32 elements summed over specs) of a plan. */
+double tn_group_plan_flops(const tn_group_plan* plan);
+double tn_group_plan_bytes(const tn_group_plan* plan);
+
+/* Device status word: returns the first kernel-side error since the last
+ * call (TN_OK if none) after synchronising `stream`, and clears it. */
+int tn_sync_status(void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* tn_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

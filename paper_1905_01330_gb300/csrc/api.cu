@@ -1,0 +1,187 @@
+// extern "C" entry points of libtn.so for pairwise and grouped contractions.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+__device__ int g_status;
+
+int* status_word() {
+  static int* ptrs[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int*>(p);
+  }
+  return ptrs[dev];
+}
+
+static void set_tiles(ContractDesc* d) {
+  d->tiles_m = (int32_t)((d->M + TC_BM - 1) / TC_BM);
+  d->tiles_n = (int32_t)((d->N + TC_BN - 1) / TC_BN);
+}
+
+static int launch_one(const ContractDesc& d, int prec, cudaStream_t stream) {
+  const int64_t tiles = (int64_t)d.tiles_m * d.tiles_n;
+  if (prec == TN_PREC_FP32) return launch_contract_simt(d, nullptr, 1, tiles, stream);
+  return launch_contract_tc(d, nullptr, 1, tiles, prec, stream);
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+struct tn_group_plan {
+  std::vector<ContractDesc> descs;  // launched specs, largest first, tile_begin set
+  std::vector<ContractDesc> zeros;  // specs with an empty shared index (K = 0): C = 0
+  int prec = TN_PREC_FP32;
+  int64_t total_tiles = 0;
+  double flops = 0.0, bytes = 0.0;
+};
+
+extern "C" {
+
+int tn_tensor_init(tn_tensor* t, void* data, int rank, const int64_t* shape) {
+  if (!t || rank < 0 || rank > TN_MAX_RANK || (rank > 0 && !shape)) return TN_ERR_ARG;
+  memset(t, 0, sizeof(*t));
+  t->data = data;
+  t->rank = rank;
+  t->dtype = TN_F32;
+  for (int i = 0; i < rank; ++i) t->shape[i] = shape[i];
+  return TN_OK;
+}
+
+const char* tn_status_string(int status) {
+  switch (status) {
+    case TN_OK: return "ok";
+    case TN_ERR_ARG: return "invalid argument";
+    case TN_ERR_SHAPE: return "shape mismatch";
+    case TN_ERR_UNSUPPORTED: return "unsupported";
+    case TN_ERR_CUDA: return "CUDA error";
+    case TN_ERR_TIMEOUT: return "device wait timed out";
+    case TN_ERR_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+int tn_sync_status(void* stream) {
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return TN_ERR_CUDA;
+  int* w = status_word();
+  if (!w) return TN_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TN_ERR_CUDA;
+  if (h != 0) {
+    const int zero = 0;
+    if (cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return TN_ERR_CUDA;
+  }
+  return h;
+}
+
+int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                int nshared, const tn_tensor* C, int prec, void* stream) {
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  ContractDesc d;
+  int rc = plan_contract(A, legsA, B, legsB, nshared, C, &d);
+  if (rc != TN_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.M == 0 || d.N == 0) return TN_OK;
+  if (d.K == 0)
+    return cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) == cudaSuccess ? TN_OK
+                                                                                          : TN_ERR_CUDA;
+  set_tiles(&d);
+  return launch_one(d, prec, s);
+}
+
+int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn_group_plan** plan) {
+  if (!plan) return TN_ERR_ARG;
+  *plan = nullptr;
+  if (nspecs < 0 || (nspecs > 0 && !specs)) return TN_ERR_ARG;
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  tn_group_plan* p = new (std::nothrow) tn_group_plan();
+  if (!p) return TN_ERR_ARG;
+  p->prec = prec;
+  p->descs.reserve((size_t)nspecs);
+  for (int i = 0; i < nspecs; ++i) {
+    const tn_contract_spec& sp = specs[i];
+    if (sp.nshared < 0 || sp.nshared > TN_MAX_RANK) { delete p; return TN_ERR_ARG; }
+    int la[TN_MAX_RANK], lb[TN_MAX_RANK];
+    for (int j = 0; j < sp.nshared; ++j) { la[j] = sp.legsA[j]; lb[j] = sp.legsB[j]; }
+    ContractDesc d;
+    int rc = plan_contract(&sp.A, la, &sp.B, lb, sp.nshared, &sp.C, &d);
+    if (rc != TN_OK) { delete p; return rc; }
+    if (d.M == 0 || d.N == 0) continue;
+    p->bytes += 4.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
+    if (d.K == 0) { p->zeros.push_back(d); continue; }
+    p->flops += 2.0 * (double)d.M * (double)d.N * (double)d.K;
+    set_tiles(&d);
+    p->descs.push_back(d);
+  }
+  // largest contractions first, so the tail of the launch is made of small tiles
+  std::stable_sort(p->descs.begin(), p->descs.end(), [](const ContractDesc& a, const ContractDesc& b) {
+    return (double)a.M * a.N * a.K > (double)b.M * b.N * b.K;
+  });
+  int64_t t = 0;
+  for (auto& d : p->descs) {
+    d.tile_begin = t;
+    t += (int64_t)d.tiles_m * d.tiles_n;
+  }
+  p->total_tiles = t;
+  if (t > 0x7FFFFFFF) { delete p; return TN_ERR_UNSUPPORTED; }
+  *plan = p;
+  return TN_OK;
+}
+
+size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
+  if (!plan) return 0;
+  return sizeof(ContractDesc) * plan->descs.size();
+}
+
+double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
+double tn_group_plan_bytes(const tn_group_plan* plan) { return plan ? plan->bytes : 0.0; }
+
+static int check_ws(const tn_group_plan* plan, void* ws, size_t bytes) {
+  const size_t need = tn_group_plan_workspace_bytes(plan);
+  if (need == 0) return TN_OK;
+  if (!ws || bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return TN_ERR_WORKSPACE;
+  return TN_OK;
+}
+
+int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws(plan, workspace, bytes);
+  if (rc != TN_OK) return rc;
+  const size_t need = tn_group_plan_workspace_bytes(plan);
+  if (need == 0) return TN_OK;
+  // pageable source: the call returns once the bytes are staged, so the plan
+  // may be destroyed right after it
+  return cudaMemcpyAsync(workspace, plan->descs.data(), need, cudaMemcpyHostToDevice,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? TN_OK
+             : TN_ERR_CUDA;
+}
+
+int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws(plan, workspace, bytes);
+  if (rc != TN_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const auto& z : plan->zeros)
+    if (cudaMemsetAsync(z.C, 0, sizeof(float) * (size_t)(z.M * z.N), s) != cudaSuccess) return TN_ERR_CUDA;
+  if (plan->total_tiles == 0) return TN_OK;
+  const ContractDesc* g = static_cast<const ContractDesc*>(workspace);
+  const int n = (int)plan->descs.size();
+  if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, n, plan->total_tiles, s);
+  return launch_contract_tc(plan->descs[0], g, n, plan->total_tiles, plan->prec, s);
+}
+
+void tn_group_plan_destroy(tn_group_plan* plan) { delete plan; }
+
+}  // extern "C"

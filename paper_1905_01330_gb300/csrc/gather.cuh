@@ -1,0 +1,49 @@
+// Device helpers shared by the contraction kernels: locating a tile in a
+// grouped launch and turning composite GEMM indices into element offsets.
+#pragma once
+
+#include "tn_internal.h"
+
+namespace tn {
+
+// Offset of composite index `idx` over legs (dims, strides), last leg fastest.
+__device__ __forceinline__ int64_t leg_offset(uint32_t idx, int n, const int32_t* dims,
+                                              const int64_t* strides) {
+  int64_t off = 0;
+  for (int q = n - 1; q >= 0; --q) {
+    const uint32_t d = (uint32_t)dims[q];
+    off += (int64_t)(idx % d) * strides[q];
+    idx /= d;
+  }
+  return off;
+}
+
+// Copies the descriptor that owns global tile `tile` into shared memory and
+// returns the tile's index within it. `group` is sorted by tile_begin.
+__device__ __forceinline__ int64_t fetch_desc(const ContractDesc& single, const ContractDesc* group,
+                                              int ndesc, int64_t tile, ContractDesc* sd,
+                                              int* s_idx) {
+  if (threadIdx.x == 0) {
+    int idx = 0;
+    if (group) {
+      int lo = 0, hi = ndesc - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (group[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+      }
+      idx = lo;
+    }
+    *s_idx = idx;
+  }
+  __syncthreads();
+  const ContractDesc* src = group ? group + *s_idx : &single;
+  const int nwords = (int)(sizeof(ContractDesc) / sizeof(int32_t));
+  const int32_t* s = reinterpret_cast<const int32_t*>(src);
+  int32_t* dst = reinterpret_cast<int32_t*>(sd);
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = s[i];
+  __syncthreads();
+  return tile - sd->tile_begin;
+}
+
+}  // namespace tn

@@ -1,0 +1,56 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tn.h"
+
+namespace tn {
+
+// GEMM view of one pairwise contraction (edge flattening, Sec. III.B.2):
+//   C[m, n] = sum_k A(m, k) B(k, n)
+// m runs over A's free legs (A's order, last fastest), n over B's free legs,
+// k over the shared legs in `kdim` order (last fastest). Element addresses are
+// sums of per-leg index * stride, so any leg permutation or stride pattern of
+// the inputs is read in place.
+struct ContractDesc {
+  const float* A;
+  const float* B;
+  float* C;
+  int64_t M, N, K;
+  int32_t nm, nn, nk;
+  int32_t a_kfast;   // 1: A's unit-stride direction is k (else m)
+  int32_t b_kfast;   // 1: B's unit-stride direction is k (else n)
+  int32_t tiles_m, tiles_n;
+  int32_t pad0;
+  int64_t tile_begin;  // first global tile index of this spec in a grouped launch
+  int32_t mdim[TN_MAX_RANK];
+  int32_t ndim[TN_MAX_RANK];
+  int32_t kdim[TN_MAX_RANK];
+  int64_t mstr[TN_MAX_RANK];
+  int64_t nstr[TN_MAX_RANK];
+  int64_t kstrA[TN_MAX_RANK];
+  int64_t kstrB[TN_MAX_RANK];
+};
+
+// Validates one contraction and fills its descriptor (tile counts for the
+// given tile shape). Returns a TN_* status.
+int plan_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                  int nshared, const tn_tensor* C, ContractDesc* d);
+
+// Launchers. `group` (device array of ndesc descriptors sorted by decreasing
+// work, tile_begin filled) is used when non-null; otherwise `single` is.
+int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, int ndesc,
+                         int64_t total_tiles, cudaStream_t stream);
+int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, int ndesc,
+                       int64_t total_tiles, int prec, cudaStream_t stream);
+
+// Tile shapes of the kernels (used by the planner to count tiles).
+constexpr int SIMT_BM = 128, SIMT_BN = 128;
+constexpr int TC_BM = 128, TC_BN = 128;
+
+// Device status word (first error wins); defined in api.cu.
+int* status_word();
+
+}  // namespace tn

@@ -1,0 +1,178 @@
+"""Python binding of libtn.so (include/tn.h): argument marshalling only.
+
+PyTorch provides device memory and streams; every step of the computation
+runs in the library's CUDA kernels. There is no fallback: if libtn.so is not
+built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+TN_MAX_RANK = 8
+PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+STATUS = {0: "TN_OK", 1: "TN_ERR_ARG", 2: "TN_ERR_SHAPE", 3: "TN_ERR_UNSUPPORTED", 4: "TN_ERR_CUDA",
+          5: "TN_ERR_TIMEOUT", 6: "TN_ERR_WORKSPACE"}
+
+
+class TnError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s: %s (%d)" % (what, STATUS.get(code, "?"), code))
+        self.code = code
+
+
+class TnTensor(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("rank", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("shape", ctypes.c_int64 * TN_MAX_RANK), ("stride", ctypes.c_int64 * TN_MAX_RANK)]
+
+
+class TnContractSpec(ctypes.Structure):
+    _fields_ = [("A", TnTensor), ("B", TnTensor), ("C", TnTensor), ("nshared", ctypes.c_int32),
+                ("legsA", ctypes.c_int32 * TN_MAX_RANK), ("legsB", ctypes.c_int32 * TN_MAX_RANK)]
+
+
+_lib = None
+_EXPORTS = None
+
+
+def exported_symbols():
+    """Names of the entry points declared in include/tn.h that the binding uses."""
+    return list(_signatures().keys())
+
+
+def _signatures():
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    tp = ctypes.POINTER(TnTensor)
+    ip = ctypes.POINTER(ctypes.c_int)
+    return {
+        "tn_tensor_init": (i32, [tp, vp, i32, ctypes.POINTER(i64)]),
+        "tn_contract": (i32, [tp, ip, tp, ip, i32, tp, i32, vp]),
+        "tn_group_plan_create": (i32, [ctypes.POINTER(TnContractSpec), i32, i32, ctypes.POINTER(vp)]),
+        "tn_group_plan_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "tn_group_plan_upload": (i32, [vp, vp, ctypes.c_size_t, vp]),
+        "tn_group_plan_run": (i32, [vp, vp, ctypes.c_size_t, vp]),
+        "tn_group_plan_destroy": (None, [vp]),
+        "tn_group_plan_flops": (ctypes.c_double, [vp]),
+        "tn_group_plan_bytes": (ctypes.c_double, [vp]),
+        "tn_sync_status": (i32, [vp]),
+        "tn_status_string": (ctypes.c_char_p, [i32]),
+    }
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(require_gpu: bool = True):
+    """Loads libtn.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libtn.so is not built (run paper_1905_01330_gb300.build.build()); "
+                           "there is no CPU fallback")
+    if require_gpu and not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: libtn.so runs on the GPU only")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _signatures().items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise TnError(code, what)
+
+
+def tensor_desc(t: torch.Tensor) -> TnTensor:
+    if t.dtype != torch.float32:
+        raise TypeError("libtn contracts float32 tensors")
+    if t.dim() > TN_MAX_RANK:
+        raise ValueError("rank > 8")
+    d = TnTensor()
+    d.data = t.data_ptr() if t.numel() > 0 else None
+    d.rank = t.dim()
+    d.dtype = 0
+    for i, (n, s) in enumerate(zip(t.shape, t.stride())):
+        d.shape[i] = n
+        d.stride[i] = s
+    return d
+
+
+def result_shape(A: torch.Tensor, legsA, B: torch.Tensor, legsB):
+    return [A.shape[p] for p in range(A.dim()) if p not in legsA] + \
+           [B.shape[p] for p in range(B.dim()) if p not in legsB]
+
+
+def contract(A: torch.Tensor, legsA, B: torch.Tensor, legsB, prec: str = "bf16",
+             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """tensordot of A and B over legsA[j] <-> legsB[j] (tn_contract)."""
+    lib = load()
+    legsA, legsB = list(legsA), list(legsB)
+    if len(legsA) != len(legsB):
+        raise ValueError("legsA and legsB differ in length")
+    if out is None:
+        shape = result_shape(A, legsA, B, legsB)
+        out = torch.empty(shape, dtype=torch.float32, device=A.device)
+    da, db, dc = tensor_desc(A), tensor_desc(B), tensor_desc(out)
+    k = len(legsA)
+    la = (ctypes.c_int * max(k, 1))(*legsA)
+    lb = (ctypes.c_int * max(k, 1))(*legsB)
+    _check(lib.tn_contract(ctypes.byref(da), la, ctypes.byref(db), lb, k, ctypes.byref(dc),
+                           PREC[prec], _stream(stream)), "tn_contract")
+    return out
+
+
+def sync_status(stream=None) -> int:
+    return load().tn_sync_status(_stream(stream))
+
+
+class GroupPlan:
+    """A grouped contraction (tn_group_plan_*): specs = [(A, legsA, B, legsB, C), ...]."""
+
+    def __init__(self, specs, prec: str = "bf16", stream=None):
+        lib = load()
+        arr = (TnContractSpec * max(len(specs), 1))()
+        for i, (A, la, B, lb, C) in enumerate(specs):
+            arr[i].A = tensor_desc(A)
+            arr[i].B = tensor_desc(B)
+            arr[i].C = tensor_desc(C)
+            arr[i].nshared = len(la)
+            for j in range(len(la)):
+                arr[i].legsA[j] = la[j]
+                arr[i].legsB[j] = lb[j]
+        self._keep = specs
+        h = ctypes.c_void_p()
+        _check(lib.tn_group_plan_create(arr, len(specs), PREC[prec], ctypes.byref(h)), "tn_group_plan_create")
+        self._h = h
+        self.prec = prec
+        nbytes = lib.tn_group_plan_workspace_bytes(h)
+        dev = specs[0][0].device if specs else torch.device("cuda")
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        self.ws_bytes = self.workspace.numel()
+        self.flops = lib.tn_group_plan_flops(h)
+        self.bytes = lib.tn_group_plan_bytes(h)
+        _check(lib.tn_group_plan_upload(h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                        _stream(stream)), "tn_group_plan_upload")
+
+    def run(self, stream=None):
+        _check(load().tn_group_plan_run(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                        _stream(stream)), "tn_group_plan_run")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.tn_group_plan_destroy(h)
+            self._h = None
