@@ -1,0 +1,316 @@
+"""Benchmark: grouped pairwise tensordot on GB300 (tcgen05, bf16 operands,
+float32 accumulation), 2048 random contraction specs in one launch.
+
+Workload: 2048 specs from the seeded spec generator (seed 2): ranks 3-5,
+dims uniform in {8,16,24,32,48,64}, 1-3 shared legs in random leg order,
+every operand and result capped at 2^24 elements; float32 N(0,1) entries
+drawn on the device (torch Philox, seeded). 2.01 TFLOP and 31.9 GB of
+float32 operands and results per step, far larger than L2 (129 MB), so no
+L2 flush is needed between steps.
+
+One step = one tn_group_plan_run (a single kernel launch). The line also
+reports the split-bf16x3 and plain-fp32 paths on the same workload, the
+end-to-end rate through the C ABI with pinned host buffers, the roofline of
+the dominant kernel, SM clocks sampled during the timed region, and the FP64
+CPU oracle timed on a bounded sample (first 16 specs) on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contraction TFLOP/s & % tensor peak; MPS fwd+bwd samples/s vs plain FP32 at tol"
+N_SPECS = 2048
+SEED = 2
+CPU_SAMPLE_SPECS = 16     # cpu_baseline: first 16 specs (6.2 GFLOP)
+REF_STEP_SPECS = 4        # --impl reference: first 4 specs per step
+
+
+def workload_config():
+    return {"workload": "grouped tensordot: 2048 random specs (rank 3-5, dims {8,16,24,32,48,64}, "
+                        "1-3 shared legs in random order, 2^24-element cap), fp32 in/out, one launch",
+            "specs": N_SPECS, "seed": SEED, "precision": "bf16 operands, fp32 accumulate (tcgen05)",
+            "l2": "inputs and results (31.9 GB) larger than L2; no flush needed"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_sample(specs_h, count):
+    """Times the FP64 oracle on the first `count` specs; returns (flop/s, seconds, flops, cores)."""
+    import oracle
+    from paper_1905_01330_gb300 import synth
+    oracle.lib()
+    data = []
+    flops = 0.0
+    for i, (sa, la, sb, lb) in enumerate(specs_h[:count]):
+        A = synth.normal_f32(synth.substream(SEED, 2 * i), sa)
+        B = synth.normal_f32(synth.substream(SEED, 2 * i + 1), sb)
+        data.append((A, la, B, lb))
+        flops += 2.0 * np.prod(synth.spec_sizes((sa, la, sb, lb)))
+    t0 = time.perf_counter()
+    for A, la, B, lb in data:
+        oracle.tensordot(A, la, B, lb)
+    dt = time.perf_counter() - t0
+    return flops / dt, dt, flops, len(os.sched_getaffinity(0))
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores (rank 0 only), same metric and unit."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1905_01330_gb300 import synth
+    specs_h = synth.contraction_specs(N_SPECS, seed=SEED)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(specs_h, REF_STEP_SPECS)
+    times, flops = [], 0.0
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(args.steps):
+        r, dt, fl, cores = cpu_oracle_sample(specs_h, REF_STEP_SPECS)
+        times.append(dt)
+        flops = fl
+    total = sum(times)
+    value = flops * args.steps / total / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "first %d of the 2048 specs per step (%.2f GFLOP)" % (REF_STEP_SPECS, flops / 1e9)},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--specs", type=int, default=N_SPECS,
+                    help="first N specs only (smaller case for profiling; not a bench line)")
+    ap.add_argument("--variants", default="bf16x3,fp32", help="other paths to time, comma separated, or none")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1905_01330_gb300 import build, synth, tn
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    tn.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- inputs: spec shapes from SplitMix64, entries from a seeded device generator
+    specs_h = synth.contraction_specs(N_SPECS, seed=SEED)[:args.specs]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(SEED * 1000 + rank)
+    specs = []
+    for sa, la, sb, lb in specs_h:
+        At = torch.randn(sa, device=dev, generator=gen)
+        Bt = torch.randn(sb, device=dev, generator=gen)
+        Ct = torch.empty(tn.result_shape(At, la, Bt, lb), device=dev)
+        specs.append((At, list(la), Bt, list(lb), Ct))
+    stream = torch.cuda.current_stream(dev)
+    var_list = [] if args.variants == "none" else [v for v in args.variants.split(",") if v]
+    plans = {p: tn.GroupPlan(specs, prec=p) for p in ["bf16"] + var_list}
+    plan = plans["bf16"]
+    flops, nbytes = plan.flops, plan.bytes
+
+    def timed(pl, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            pl.run()
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.start()
+        start.record(stream)
+        for a, b in ev:
+            a.record(stream)
+            pl.run()
+            b.record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        barrier()
+        total_ms = start.elapsed_time(stop)
+        per = [a.elapsed_time(b) for a, b in ev]
+        return total_ms, per, clocks
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    total_ms, per, clocks = timed(plan, args.steps, args.warmup, sampler)
+    status = tn.sync_status()
+    if status != 0:
+        raise RuntimeError("kernel status %d during the timed region" % status)
+    ms_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * flops / (ms_per_step * 1e-3) / 1e12
+    launch_ms = float(np.mean(per))
+
+    # ---- same workload with the other two arithmetic paths (not the headline)
+    variants = {}
+    for p in var_list:
+        tm, pp, _ = timed(plans[p], max(2, args.steps // 2), 1)
+        variants[p] = {"ms_per_step": tm / max(2, args.steps // 2), "tflops": flops / (tm / max(2, args.steps // 2) * 1e-3) / 1e12}
+    variants["bf16"] = {"ms_per_step": ms_per_step, "tflops": flops / (ms_per_step * 1e-3) / 1e12}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = [(A.cpu().pin_memory(), B.cpu().pin_memory()) for A, _, B, _, _ in specs]
+        host_out = [torch.empty(C.shape, dtype=torch.float32, pin_memory=True) for *_, C in specs]
+        h2d = sum(a.numel() * 4 + b.numel() * 4 for a, b in host_in)
+        d2h = sum(c.numel() * 4 for c in host_out)
+        torch.cuda.synchronize(dev)
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.e2e_steps):
+            for (ha, hb), (A, _, B, _, _) in zip(host_in, specs):
+                A.copy_(ha, non_blocking=True)
+                B.copy_(hb, non_blocking=True)
+            plan.run()
+            for hc, (*_, C) in zip(host_out, specs):
+                hc.copy_(C, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = s0.elapsed_time(s1) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del host_in, host_out
+
+    hbm_peak, bf16_peak, peak_src = measured_peaks()
+    achieved_gbs = nbytes / (launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": None,
+                "kernel": "tc_contract_kernel<bf16>", "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": nbytes,
+                "tensor_tflops": flops / (launch_ms * 1e-3) / 1e12,
+                "tensor_frac": flops / (launch_ms * 1e-3) / 1e12 / bf16_peak}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt, fl, cores = cpu_oracle_sample(synth.contraction_specs(N_SPECS, seed=SEED), CPU_SAMPLE_SPECS)
+        cpu = {"value": r / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d of the 2048 specs (%.2f GFLOP, %.1f s)" % (CPU_SAMPLE_SPECS, fl / 1e9, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(),
+                "gpu_launches": args.steps, "clocks": clocks, "e2e": e2e, "roofline": roofline,
+                "cpu_baseline": cpu, "variants": variants,
+                "tensor_peak_frac": value / world / bf16_peak}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

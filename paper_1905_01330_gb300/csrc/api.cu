@@ -24,13 +24,21 @@ int* status_word() {
   return ptrs[dev];
 }
 
-static void set_tiles(ContractDesc* d) {
-  d->tiles_m = (int32_t)((d->M + TC_BM - 1) / TC_BM);
-  d->tiles_n = (int32_t)((d->N + TC_BN - 1) / TC_BN);
+// One contraction alone should still fill the GPU when its K allows: ask for
+// at least two work units per SM.
+static int64_t min_units_single() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return 2 * (int64_t)sms;
 }
 
 static int launch_one(const ContractDesc& d, int prec, cudaStream_t stream) {
-  const int64_t tiles = (int64_t)d.tiles_m * d.tiles_n;
+  const int64_t tiles = (int64_t)d.tiles_m * d.tiles_n * d.splits;
   if (prec == TN_PREC_FP32) return launch_contract_simt(d, nullptr, 1, tiles, stream);
   return launch_contract_tc(d, nullptr, 1, tiles, prec, stream);
 }
@@ -42,6 +50,7 @@ using namespace tn;
 struct tn_group_plan {
   std::vector<ContractDesc> descs;  // launched specs, largest first, tile_begin set
   std::vector<ContractDesc> zeros;  // specs with an empty shared index (K = 0): C = 0
+  std::vector<ZeroRange> zero_ranges;  // results zeroed on the device before the launch
   int prec = TN_PREC_FP32;
   int64_t total_tiles = 0;
   double flops = 0.0, bytes = 0.0;
@@ -96,7 +105,10 @@ int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const 
   if (d.K == 0)
     return cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) == cudaSuccess ? TN_OK
                                                                                           : TN_ERR_CUDA;
-  set_tiles(&d);
+  plan_units(&d, min_units_single());
+  if (d.splits > 1 &&
+      cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) != cudaSuccess)
+    return TN_ERR_CUDA;
   return launch_one(d, prec, s);
 }
 
@@ -121,17 +133,22 @@ int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn
     p->bytes += 4.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
     if (d.K == 0) { p->zeros.push_back(d); continue; }
     p->flops += 2.0 * (double)d.M * (double)d.N * (double)d.K;
-    set_tiles(&d);
+    plan_units(&d, 1);
     p->descs.push_back(d);
   }
-  // largest contractions first, so the tail of the launch is made of small tiles
-  std::stable_sort(p->descs.begin(), p->descs.end(), [](const ContractDesc& a, const ContractDesc& b) {
-    return (double)a.M * a.N * a.K > (double)b.M * b.N * b.K;
+  // largest work units first, so the tail of the launch is made of small ones
+  auto unit_work = [](const ContractDesc& d) {
+    return (double)std::min<int64_t>(d.M, TC_BM) * (double)std::min<int64_t>(d.N, TC_BN) *
+           (double)std::min<int64_t>(d.K, d.k_per_split);
+  };
+  std::stable_sort(p->descs.begin(), p->descs.end(), [&](const ContractDesc& a, const ContractDesc& b) {
+    return unit_work(a) > unit_work(b);
   });
   int64_t t = 0;
   for (auto& d : p->descs) {
     d.tile_begin = t;
-    t += (int64_t)d.tiles_m * d.tiles_n;
+    t += (int64_t)d.tiles_m * d.tiles_n * d.splits;
+    if (d.splits > 1) p->zero_ranges.push_back(ZeroRange{d.C, d.M * d.N});
   }
   p->total_tiles = t;
   if (t > 0x7FFFFFFF) { delete p; return TN_ERR_UNSUPPORTED; }
@@ -139,9 +156,14 @@ int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn
   return TN_OK;
 }
 
+// Workspace layout: descriptors, then (256-byte aligned) the zero ranges.
+static size_t zero_offset(const tn_group_plan* plan) {
+  return (sizeof(ContractDesc) * plan->descs.size() + 255) & ~size_t(255);
+}
+
 size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
   if (!plan) return 0;
-  return sizeof(ContractDesc) * plan->descs.size();
+  return zero_offset(plan) + sizeof(ZeroRange) * plan->zero_ranges.size();
 }
 
 double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
@@ -158,14 +180,18 @@ int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t byte
   if (!plan) return TN_ERR_ARG;
   int rc = check_ws(plan, workspace, bytes);
   if (rc != TN_OK) return rc;
-  const size_t need = tn_group_plan_workspace_bytes(plan);
-  if (need == 0) return TN_OK;
-  // pageable source: the call returns once the bytes are staged, so the plan
-  // may be destroyed right after it
-  return cudaMemcpyAsync(workspace, plan->descs.data(), need, cudaMemcpyHostToDevice,
-                         static_cast<cudaStream_t>(stream)) == cudaSuccess
-             ? TN_OK
-             : TN_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // pageable sources: each call returns once the bytes are staged, so the
+  // plan may be destroyed right after it
+  if (!plan->descs.empty() &&
+      cudaMemcpyAsync(workspace, plan->descs.data(), sizeof(ContractDesc) * plan->descs.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  if (!plan->zero_ranges.empty() &&
+      cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + zero_offset(plan), plan->zero_ranges.data(),
+                      sizeof(ZeroRange) * plan->zero_ranges.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  return TN_OK;
 }
 
 int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
@@ -176,6 +202,11 @@ int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, 
   for (const auto& z : plan->zeros)
     if (cudaMemsetAsync(z.C, 0, sizeof(float) * (size_t)(z.M * z.N), s) != cudaSuccess) return TN_ERR_CUDA;
   if (plan->total_tiles == 0) return TN_OK;
+  if (!plan->zero_ranges.empty()) {
+    rc = launch_zero(reinterpret_cast<const ZeroRange*>(static_cast<uint8_t*>(workspace) + zero_offset(plan)),
+                     (int)plan->zero_ranges.size(), s);
+    if (rc != TN_OK) return rc;
+  }
   const ContractDesc* g = static_cast<const ContractDesc*>(workspace);
   const int n = (int)plan->descs.size();
   if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, n, plan->total_tiles, s);

@@ -18,11 +18,12 @@ constexpr int BM = SIMT_BM, BN = SIMT_BN, BK = 16, NT = 256;
 struct SimtSmem {
   float As[2][BK][BM + 4];
   float Bs[2][BK][BN + 4];
-  int64_t rowA[BM];
-  int64_t colB[BN];
-  int64_t kA[2][BK];
-  int64_t kB[2][BK];
+  int32_t rowA[BM];
+  int32_t colB[BN];
+  int32_t kA[2][BK];
+  int32_t kB[2][BK];
   ContractDesc d;
+  UnitCoord uc;
   int idx;
 };
 
@@ -30,11 +31,11 @@ __device__ __forceinline__ void fill_k(SimtSmem& s, int buf, int64_t k0) {
   const int t = threadIdx.x;
   if (t < 2 * BK) {
     const int j = t & (BK - 1);
-    const int64_t k = k0 + j;
-    int64_t off = -1;
-    if (k < s.d.K) {
-      off = (t < BK) ? leg_offset((uint32_t)k, s.d.nk, s.d.kdim, s.d.kstrA)
-                     : leg_offset((uint32_t)k, s.d.nk, s.d.kdim, s.d.kstrB);
+    const int64_t k = s.uc.k_begin + k0 + j;
+    int32_t off = -1;
+    if (k < s.uc.k_end) {
+      off = (int32_t)((t < BK) ? leg_offset((uint32_t)k, s.d.nk, s.d.kdim, s.d.kstrA)
+                               : leg_offset((uint32_t)k, s.d.nk, s.d.kdim, s.d.kstrB));
     }
     if (t < BK) s.kA[buf][j] = off;
     else s.kB[buf][j] = off;
@@ -50,16 +51,16 @@ __device__ __forceinline__ void load_regs(const SimtSmem& s, int buf, float (&ra
     int r, k;
     if (s.d.a_kfast) { k = t & (BK - 1); r = (t >> 4) + 16 * i; }
     else { r = t & (BM - 1); k = (t >> 7) + 2 * i; }
-    const int64_t ko = s.kA[buf][k], ro = s.rowA[r];
-    ra[i] = (ko >= 0 && ro >= 0) ? __ldg(A + ro + ko) : 0.0f;
+    const int32_t ko = s.kA[buf][k], ro = s.rowA[r];
+    ra[i] = (ko >= 0 && ro >= 0) ? __ldg(A + (ro + ko)) : 0.0f;
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     int c, k;
     if (s.d.b_kfast) { k = t & (BK - 1); c = (t >> 4) + 16 * i; }
     else { c = t & (BN - 1); k = (t >> 7) + 2 * i; }
-    const int64_t ko = s.kB[buf][k], co = s.colB[c];
-    rb[i] = (ko >= 0 && co >= 0) ? __ldg(B + co + ko) : 0.0f;
+    const int32_t ko = s.kB[buf][k], co = s.colB[c];
+    rb[i] = (ko >= 0 && co >= 0) ? __ldg(B + (co + ko)) : 0.0f;
   }
 }
 
@@ -86,18 +87,19 @@ simt_contract_kernel(const __grid_constant__ ContractDesc single, const Contract
                      int ndesc) {
   __shared__ __align__(16) SimtSmem s;
   const int64_t tile = fetch_desc(single, group, ndesc, (int64_t)blockIdx.x, &s.d, &s.idx);
-  const int64_t tm = tile / s.d.tiles_n, tn = tile % s.d.tiles_n;
-  const int64_t m0 = tm * BM, n0 = tn * BN;
   const int t = threadIdx.x;
+  if (t == 0) s.uc = decode_unit(s.d, tile, BM, BN);
+  __syncthreads();
+  const int64_t m0 = s.uc.m0, n0 = s.uc.n0;
 
   if (t < BM) {
     const int64_t m = m0 + t;
-    s.rowA[t] = (m < s.d.M) ? leg_offset((uint32_t)m, s.d.nm, s.d.mdim, s.d.mstr) : -1;
+    s.rowA[t] = (m < s.d.M) ? (int32_t)leg_offset((uint32_t)m, s.d.nm, s.d.mdim, s.d.mstr) : -1;
   } else {
     const int64_t n = n0 + (t - BM);
-    s.colB[t - BM] = (n < s.d.N) ? leg_offset((uint32_t)n, s.d.nn, s.d.ndim, s.d.nstr) : -1;
+    s.colB[t - BM] = (n < s.d.N) ? (int32_t)leg_offset((uint32_t)n, s.d.nn, s.d.ndim, s.d.nstr) : -1;
   }
-  const int64_t nkt = (s.d.K + BK - 1) / BK;
+  const int64_t nkt = (s.uc.k_end - s.uc.k_begin + BK - 1) / BK;
   fill_k(s, 0, 0);
   __syncthreads();
 
@@ -143,6 +145,7 @@ simt_contract_kernel(const __grid_constant__ ContractDesc single, const Contract
   float* __restrict__ C = s.d.C;
   const int64_t N = s.d.N;
   const bool vec = ((N & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+  const bool accumulate = s.d.splits > 1;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
@@ -150,20 +153,33 @@ simt_contract_kernel(const __grid_constant__ ContractDesc single, const Contract
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t n = n0 + h * 64 + tx * 4;
-      float* dst = C + m * N + n;
-      if (vec && n + 3 < N) {
-        *reinterpret_cast<float4*>(dst) =
-            make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (n + j < N) dst[j] = acc[i][h * 4 + j];
-      }
+      if (n < N)
+        emit4(C + m * N + n, vec, N - n, accumulate, acc[i][h * 4 + 0], acc[i][h * 4 + 1],
+              acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
     }
   }
 }
 
+__global__ void zero_kernel(const ZeroRange* ranges) {
+  const ZeroRange r = ranges[blockIdx.x];
+  float* p = r.ptr;
+  int64_t n = r.count;
+  int64_t head = 0;
+  while (head < n && (reinterpret_cast<uintptr_t>(p + head) & 15) != 0) ++head;
+  for (int64_t i = threadIdx.x; i < head; i += blockDim.x) p[i] = 0.0f;
+  const int64_t nv = (n - head) / 4;
+  float4* q = reinterpret_cast<float4*>(p + head);
+  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t i = head + nv * 4 + threadIdx.x; i < n; i += blockDim.x) p[i] = 0.0f;
+}
+
 }  // namespace
+
+int launch_zero(const ZeroRange* ranges, int n, cudaStream_t stream) {
+  if (n <= 0) return TN_OK;
+  zero_kernel<<<(unsigned)n, 512, 0, stream>>>(ranges);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
 
 int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, int ndesc,
                          int64_t total_tiles, cudaStream_t stream) {

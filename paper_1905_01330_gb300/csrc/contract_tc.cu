@@ -47,10 +47,10 @@ struct TcCfg {
 
 template <int S>
 struct TcAux {
-  int64_t rowA[BM];
-  int64_t rowB[BN];
-  int64_t kA[S][BK];
-  int64_t kB[S][BK];
+  int32_t rowA[BM];
+  int32_t rowB[BN];
+  int32_t kA[S][BK];
+  int32_t kB[S][BK];
   int32_t kcA[S][BK / 8];  // 1: the 8-wide k group is unit-stride in A
   int32_t kcB[S][BK / 8];
   uint64_t full[S];
@@ -81,15 +81,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 // Loads the 8 float32 values of one (row, k group) unit of an operand.
-__device__ __forceinline__ void load_unit(const float* __restrict__ base, int64_t row_off,
-                                          const int64_t* koff, int contiguous, float (&v)[8]) {
+__device__ __forceinline__ void load_unit(const float* __restrict__ base, int32_t row_off,
+                                          const int32_t* koff, int contiguous, float (&v)[8]) {
   if (row_off < 0) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = 0.0f;
     return;
   }
   if (contiguous) {
-    const float* p = base + row_off + koff[0];
+    const float* p = base + (row_off + koff[0]);
     if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
       const float4 x = __ldg(reinterpret_cast<const float4*>(p));
       const float4 y = __ldg(reinterpret_cast<const float4*>(p) + 1);
@@ -103,8 +103,8 @@ __device__ __forceinline__ void load_unit(const float* __restrict__ base, int64_
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int64_t ko = koff[j];
-    v[j] = (ko >= 0) ? __ldg(base + row_off + ko) : 0.0f;
+    const int32_t ko = koff[j];
+    v[j] = (ko >= 0) ? __ldg(base + (row_off + ko)) : 0.0f;
   }
 }
 
@@ -131,8 +131,9 @@ __device__ __forceinline__ void store_unit(uint8_t* hi_tile, uint8_t* lo_tile, i
 
 // k-group contiguity: the 8 indices k0..k0+7 are all < K and consecutive in
 // memory (innermost shared leg has unit stride and the group does not wrap).
-__device__ __forceinline__ int group_contiguous(const ContractDesc& d, int64_t k0, const int64_t* kstr) {
-  if (d.nk == 0 || k0 + 8 > d.K) return 0;
+__device__ __forceinline__ int group_contiguous(const ContractDesc& d, int64_t k0, int64_t k_end,
+                                                const int64_t* kstr) {
+  if (d.nk == 0 || k0 + 8 > k_end) return 0;
   const int last = d.nk - 1;
   if (kstr[last] != 1) return 0;
   const int64_t dl = d.kdim[last];
@@ -174,19 +175,19 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
   ptx::tc_fence_after();
   const uint32_t tmem = x.tmem_base;
   const ContractDesc& d = x.d;
-  const int64_t tm = tile / d.tiles_n, tn = tile % d.tiles_n;
-  const int64_t m0 = tm * BM, n0 = tn * BN;
-  const int64_t nkt = (d.K + BK - 1) / BK;
+  const UnitCoord uc = decode_unit(d, tile, BM, BN);
+  const int64_t m0 = uc.m0, n0 = uc.n0;
+  const int64_t nkt = (uc.k_end - uc.k_begin + BK - 1) / BK;
   const uint32_t stage0 = ptx::smem_addr(smem);
 
   if (warp < 8) {
     // ------------------------------------------------------------ converters
     if (t < BM) {
       const int64_t m = m0 + t;
-      x.rowA[t] = (m < d.M) ? leg_offset((uint32_t)m, d.nm, d.mdim, d.mstr) : -1;
+      x.rowA[t] = (m < d.M) ? (int32_t)leg_offset((uint32_t)m, d.nm, d.mdim, d.mstr) : -1;
     } else {
       const int64_t n = n0 + (t - BM);
-      x.rowB[t - BM] = (n < d.N) ? leg_offset((uint32_t)n, d.nn, d.ndim, d.nstr) : -1;
+      x.rowB[t - BM] = (n < d.N) ? (int32_t)leg_offset((uint32_t)n, d.nn, d.ndim, d.nstr) : -1;
     }
     bool ok = true;
     const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant and column half of this warp
@@ -226,13 +227,13 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
       // is written after the collective check below)
       if (t < 2 * BK) {
         const int j = t & (BK - 1);
-        const int64_t k = kt * BK + j;
+        const int64_t k = uc.k_begin + kt * BK + j;
         const bool isA = t < BK;
         const int64_t* kstr = isA ? d.kstrA : d.kstrB;
-        const int64_t off = (k < d.K) ? leg_offset((uint32_t)k, d.nk, d.kdim, kstr) : -1;
+        const int32_t off = (k < uc.k_end) ? (int32_t)leg_offset((uint32_t)k, d.nk, d.kdim, kstr) : -1;
         if (isA) x.kA[s][j] = off; else x.kB[s][j] = off;
         if ((j & 7) == 0) {
-          const int c = group_contiguous(d, k, kstr);
+          const int c = group_contiguous(d, k, uc.k_end, kstr);
           if (isA) x.kcA[s][j >> 3] = c; else x.kcB[s][j >> 3] = c;
         }
       }
@@ -299,17 +300,12 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
         if (m < d.M) {
           float* dst = C + m * N + n0 + col;
           const int64_t nrem = N - (n0 + col);
-          if (vec && nrem >= 32) {
+          const bool accumulate = d.splits > 1;
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(dst + j) =
-                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                              __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < nrem) dst[j] = __uint_as_float(r[j]);
-          }
+          for (int j = 0; j < 32; j += 4)
+            if (j < nrem)
+              emit4(dst + j, vec, nrem - j, accumulate, __uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                    __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
         }
       }
     }

@@ -46,4 +46,40 @@ __device__ __forceinline__ int64_t fetch_desc(const ContractDesc& single, const 
   return tile - sd->tile_begin;
 }
 
+struct UnitCoord {
+  int64_t m0, n0, k_begin, k_end;
+};
+
+__device__ __forceinline__ UnitCoord decode_unit(const ContractDesc& d, int64_t u, int bm, int bn) {
+  UnitCoord c;
+  const int64_t tn = u % d.tiles_n;
+  const int64_t rest = u / d.tiles_n;
+  const int64_t tm = rest % d.tiles_m;
+  const int64_t split = rest / d.tiles_m;
+  c.m0 = tm * bm;
+  c.n0 = tn * bn;
+  c.k_begin = split * d.k_per_split;
+  c.k_end = min(d.K, c.k_begin + d.k_per_split);
+  return c;
+}
+
+// Writes (splits == 1) or accumulates (splits > 1, C pre-zeroed) four
+// consecutive results; `vec` means 16-byte aligned with all four in range.
+__device__ __forceinline__ void emit4(float* dst, bool vec, int64_t nrem, bool accumulate, float a,
+                                      float b, float c, float e) {
+  if (vec && nrem >= 4) {
+    if (accumulate) atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a, b, c, e));
+    else *reinterpret_cast<float4*>(dst) = make_float4(a, b, c, e);
+    return;
+  }
+  const float v[4] = {a, b, c, e};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j < nrem) {
+      if (accumulate) atomicAdd(dst + j, v[j]);
+      else dst[j] = v[j];
+    }
+  }
+}
+
 }  // namespace tn

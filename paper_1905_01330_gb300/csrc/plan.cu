@@ -134,7 +134,32 @@ int plan_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, cons
   const int64_t b_n = d->nn ? d->nstr[d->nn - 1] : big;
   d->a_kfast = (a_k < a_m) ? 1 : 0;
   d->b_kfast = (b_k < b_n) ? 1 : 0;
+
+  // the kernels address operands with 32-bit element offsets
+  int64_t span_a = 0, span_b = 0;
+  for (int p = 0; p < A->rank; ++p) span_a += (A->shape[p] > 0 ? A->shape[p] - 1 : 0) * sa[p];
+  for (int p = 0; p < B->rank; ++p) span_b += (B->shape[p] > 0 ? B->shape[p] - 1 : 0) * sb[p];
+  if (span_a >= (1ll << 31) || span_b >= (1ll << 31)) return TN_ERR_UNSUPPORTED;
+  d->splits = 1;
+  d->k_per_split = K;
   return TN_OK;
+}
+
+void plan_units(ContractDesc* d, int64_t min_units) {
+  d->tiles_m = (int32_t)((d->M + TC_BM - 1) / TC_BM);
+  d->tiles_n = (int32_t)((d->N + TC_BN - 1) / TC_BN);
+  const int64_t slabs = (d->K + 63) / 64;
+  const int64_t tiles = (int64_t)d->tiles_m * d->tiles_n;
+  int64_t splits = (slabs + MAX_SLABS_PER_UNIT - 1) / MAX_SLABS_PER_UNIT;
+  if (min_units > tiles * splits) {
+    const int64_t want = (min_units + tiles - 1) / tiles;
+    const int64_t cap = slabs / 4 > 1 ? slabs / 4 : 1;
+    if (want > splits) splits = want < cap ? want : cap;
+  }
+  if (splits < 1) splits = 1;
+  const int64_t per = (slabs + splits - 1) / splits;
+  d->splits = (int32_t)((slabs + per - 1) / per);
+  d->k_per_split = per * 64;
 }
 
 }  // namespace tn

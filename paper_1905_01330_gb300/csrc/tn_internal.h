@@ -23,8 +23,11 @@ struct ContractDesc {
   int32_t a_kfast;   // 1: A's unit-stride direction is k (else m)
   int32_t b_kfast;   // 1: B's unit-stride direction is k (else n)
   int32_t tiles_m, tiles_n;
+  int32_t splits;      // k ranges the shared index is cut into (split-K); results are summed
+                       // into C with float32 atomic adds when > 1, so C is zeroed first
   int32_t pad0;
-  int64_t tile_begin;  // first global tile index of this spec in a grouped launch
+  int64_t k_per_split; // shared indices per k range (a multiple of 64)
+  int64_t tile_begin;  // first global work unit of this spec in a grouped launch
   int32_t mdim[TN_MAX_RANK];
   int32_t ndim[TN_MAX_RANK];
   int32_t kdim[TN_MAX_RANK];
@@ -40,7 +43,9 @@ int plan_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, cons
                   int nshared, const tn_tensor* C, ContractDesc* d);
 
 // Launchers. `group` (device array of ndesc descriptors sorted by decreasing
-// work, tile_begin filled) is used when non-null; otherwise `single` is.
+// unit work, tile_begin filled) is used when non-null; otherwise `single` is.
+// Work unit u of a spec: tn = u % tiles_n, tm = (u / tiles_n) % tiles_m,
+// split = u / (tiles_n * tiles_m).
 int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, int ndesc,
                          int64_t total_tiles, cudaStream_t stream);
 int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, int ndesc,
@@ -49,6 +54,20 @@ int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, in
 // Tile shapes of the kernels (used by the planner to count tiles).
 constexpr int SIMT_BM = 128, SIMT_BN = 128;
 constexpr int TC_BM = 128, TC_BN = 128;
+// Longest k range of one work unit, in 64-wide slabs: a spec whose shared
+// index is longer is split so no single CTA serialises a huge K.
+constexpr int MAX_SLABS_PER_UNIT = 32;
+
+// Sets tiles_m/n, splits and k_per_split; `min_units` asks for at least that
+// many work units when K is long enough to split (keeping >= 4 slabs per unit).
+void plan_units(ContractDesc* d, int64_t min_units);
+
+// Zeroes the results of split specs: list of (pointer, element count).
+struct ZeroRange {
+  float* ptr;
+  int64_t count;
+};
+int launch_zero(const ZeroRange* ranges, int n, cudaStream_t stream);
 
 // Device status word (first error wins); defined in api.cu.
 int* status_word();
