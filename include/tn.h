@@ -128,6 +128,72 @@ void tn_group_plan_destroy(tn_group_plan* plan);
 double tn_group_plan_flops(const tn_group_plan* plan);
 double tn_group_plan_bytes(const tn_group_plan* plan);
 
+/* ------------------------------------------------------------------------ */
+/* Matrix product states and operators (Sec. II, Fig. 3a)                    */
+/* ------------------------------------------------------------------------ */
+/* An open-boundary MPS: n rank-3 cores, core i of shape (bond[i], d,
+ * bond[i+1]) row-major float32 on the device, bond[0] = bond[n] = 1. The
+ * bond array and the pointer table are host memory. */
+typedef struct tn_mps {
+  int32_t n;
+  int32_t d;
+  const int64_t* bond;
+  float* const* cores;
+} tn_mps;
+
+/* An MPO: n rank-4 cores W_i of shape (w[i], w[i+1], d, d) row-major float32
+ * on the device, index order (left bond, right bond, bra s, ket s'),
+ * w[0] = w[n] = 1. */
+typedef struct tn_mpo {
+  int32_t n;
+  int32_t d;
+  const int64_t* bond;
+  float* const* cores;
+} tn_mpo;
+
+/*
+ * <bra|ket> of two MPS with the same n and d, by the left-to-right transfer
+ * sweep E_i[b,b'] = sum_{a,a',s} E_{i-1}[a,a'] bra_i[a,s,b] ket_i[a',s,b'],
+ * done per site as two contractions (T = E.ket_i over a', then
+ * E' = bra_i.T over a and s). After every site E is divided by its
+ * largest magnitude and the natural log of that factor is added, in float64,
+ * to a running log-scale, so long chains neither overflow nor underflow.
+ *   result: DEVICE pointer to 2 doubles, written as {value, log_scale} with
+ *           <bra|ket> = value * exp(log_scale).
+ *   prec:   arithmetic of the two contractions per site. Chains whose bonds
+ *           are all <= 64 run in one CTA in float32 (environment kept in
+ *           shared memory across sites) whatever prec says; longer bonds run
+ *           each contraction through the tcgen05 (BF16, BF16X3) or float32
+ *           kernels of tn_contract.
+ *   workspace: DEVICE scratch of tn_mps_inner_workspace_bytes() bytes,
+ *           256-byte aligned (may be NULL when that size is 0).
+ * Errors: TN_ERR_ARG (null, n < 1, bonds not matching, edge bonds != 1,
+ * cores missing), TN_ERR_WORKSPACE, TN_ERR_CUDA.
+ */
+size_t tn_mps_inner_workspace_bytes(const tn_mps* bra, const tn_mps* ket);
+int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace, size_t ws_bytes,
+                 double* result, void* stream);
+
+/*
+ * <psi|H|psi> and <psi|psi> for an MPS psi and an MPO H (same n and d), by the
+ * left environment sweep L[w, a, a'] (w the MPO bond, a the bra bond, a' the
+ * ket bond), three contractions per site:
+ *   (i)   T1[w, a', s, b]   = sum_a      L[w, a, a'] psi_i[a, s, b]
+ *   (ii)  T2[w', s', a', b] = sum_{w, s} W_i[w, w', s, s'] T1[w, a', s, b]
+ *   (iii) L'[w', b, b']     = sum_{a',s'} T2[w', s', a', b] psi_i[a', s', b']
+ * with the same per-site rescaling and float64 log-scale as tn_mps_inner;
+ * (i) and (iii) use `prec`, (ii) (contraction length w*d) runs in float32.
+ *   result: DEVICE pointer to 4 doubles {e_value, e_log_scale, n_value,
+ *           n_log_scale}: <psi|H|psi> = e_value * exp(e_log_scale) and
+ *           <psi|psi> = n_value * exp(n_log_scale); the energy per the
+ *           normalised state is their ratio.
+ *   workspace: DEVICE scratch of tn_mps_expect_workspace_bytes() bytes.
+ * Errors: as tn_mps_inner.
+ */
+size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H);
+int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace, size_t ws_bytes,
+                  double* result, void* stream);
+
 /* Device status word: returns the first kernel-side error since the last
  * call (TN_OK if none) after synchronising `stream`, and clears it. */
 int tn_sync_status(void* stream);

@@ -96,11 +96,17 @@ int tn_sync_status(void* stream) {
 
 int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
                 int nshared, const tn_tensor* C, int prec, void* stream) {
+  return tn::contract_internal(A, legsA, B, legsB, nshared, C, prec, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+int tn::contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                          int nshared, const tn_tensor* C, int prec, cudaStream_t s) {
   if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
   ContractDesc d;
   int rc = plan_contract(A, legsA, B, legsB, nshared, C, &d);
   if (rc != TN_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (d.M == 0 || d.N == 0) return TN_OK;
   if (d.K == 0)
     return cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) == cudaSuccess ? TN_OK
@@ -111,6 +117,8 @@ int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const 
     return TN_ERR_CUDA;
   return launch_one(d, prec, s);
 }
+
+extern "C" {
 
 int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn_group_plan** plan) {
   if (!plan) return TN_ERR_ARG;

@@ -1,0 +1,371 @@
+// Matrix product state sweeps: <bra|ket> (transfer sweep) and <psi|H|psi>
+// (MPO left-environment sweep), with per-site rescaling and a float64
+// running log-scale (Sec. II, Fig. 3a; MPS as a sparse 2^N vector, Sec. IV.A).
+//
+// Chains with every bond <= 64 run the whole inner-product sweep in one CTA:
+// the environment and the per-site intermediate stay in shared memory from
+// site to site. Larger bonds run each per-site contraction through
+// tn_contract's kernels (tcgen05 for BF16/BF16X3), with the environment in a
+// caller workspace, followed by a two-kernel rescale.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tn_internal.h"
+
+namespace tn {
+namespace {
+
+constexpr int SMALL_D = 64;      // largest bond of the one-CTA sweep
+constexpr int SMALL_PHYS = 4;    // largest physical dim of the one-CTA sweep
+constexpr int SMALL_MAXN = 1024; // sites passed by value to the one-CTA sweep
+constexpr int SMALL_THREADS = 256;
+
+struct SmallChain {
+  int32_t n, d;
+  int32_t bb[SMALL_MAXN + 1];
+  int32_t bk[SMALL_MAXN + 1];
+  const float* bra[SMALL_MAXN];
+  const float* ket[SMALL_MAXN];
+};
+
+__device__ float block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float m = 0.0f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+
+// One CTA: E (Da x Dak) -> T[a,s,bk] = sum_ak E[a,ak] ket[ak,s,bk]
+//                       -> E'[b,bk] = sum_{a,s} bra[a,s,b] T[a,s,bk]
+// -> divide by max|E'| and add its log to the float64 log-scale.
+__global__ void __launch_bounds__(SMALL_THREADS)
+mps_inner_small_kernel(const __grid_constant__ SmallChain c, double* result) {
+  extern __shared__ float sm[];
+  float* E = sm;
+  float* E2 = E + SMALL_D * SMALL_D;
+  float* T = E2 + SMALL_D * SMALL_D;
+  __shared__ float red[SMALL_THREADS / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) E[0] = 1.0f;
+  double lg = 0.0;
+  __syncthreads();
+  const int d = c.d;
+  for (int i = 0; i < c.n; ++i) {
+    const int Da = c.bb[i], Db = c.bb[i + 1], Dak = c.bk[i], Dbk = c.bk[i + 1];
+    const float* __restrict__ K = c.ket[i];
+    const float* __restrict__ Br = c.bra[i];
+    const int nt = Da * d * Dbk;
+    for (int idx = tid; idx < nt; idx += SMALL_THREADS) {
+      const int bk = idx % Dbk, rest = idx / Dbk, s = rest % d, a = rest / d;
+      float acc = 0.0f;
+      for (int ak = 0; ak < Dak; ++ak) acc = fmaf(E[a * Dak + ak], __ldg(K + (ak * d + s) * Dbk + bk), acc);
+      T[idx] = acc;
+    }
+    __syncthreads();
+    const int ne = Db * Dbk;
+    float mx = 0.0f;
+    for (int idx = tid; idx < ne; idx += SMALL_THREADS) {
+      const int bk = idx % Dbk, b = idx / Dbk;
+      float acc = 0.0f;
+      for (int as = 0; as < Da * d; ++as) acc = fmaf(__ldg(Br + as * Db + b), T[as * Dbk + bk], acc);
+      E2[idx] = acc;
+      mx = fmaxf(mx, fabsf(acc));
+    }
+    const float m = block_max(mx, red);
+    const float sc = m > 0.0f ? m : 1.0f;
+    for (int idx = tid; idx < ne; idx += SMALL_THREADS) E[idx] = E2[idx] / sc;
+    lg += log((double)sc);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    result[0] = (double)E[0];
+    result[1] = lg;
+  }
+}
+
+// ------------------------------------------------------------ rescale pair
+// Largest |x| of x[0..n) into *bits (float bits; nonnegative floats order as
+// unsigned integers). *bits starts at 0.
+__global__ void absmax_kernel(const float* __restrict__ x, int64_t n, unsigned* bits) {
+  __shared__ float red[32];
+  float m = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(bits, __float_as_uint(m));
+}
+
+// x /= max (if nonzero); one thread adds log(max) to *log_acc.
+__global__ void scale_kernel(float* __restrict__ x, int64_t n, const unsigned* bits, double* log_acc) {
+  const float m = __uint_as_float(*bits);
+  const float sc = m > 0.0f ? m : 1.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = x[i] / sc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *log_acc += log((double)sc);
+}
+
+// E[0] = 1 (a 1x1 or 1x1x1 environment), log-scales and max slots zeroed.
+__global__ void init_sweep_kernel(float* E, double* log_acc, int nlog, unsigned* bits, int nbits) {
+  for (int i = threadIdx.x; i < nbits; i += blockDim.x) bits[i] = 0u;
+  if (threadIdx.x < nlog) log_acc[threadIdx.x] = 0.0;
+  if (threadIdx.x == 0) E[0] = 1.0f;
+}
+
+// result[2j] = (double)env_j[0], result[2j+1] = log_acc[j].
+__global__ void finish_kernel(const float* e0, const double* l0, const float* e1, const double* l1,
+                              double* result) {
+  if (threadIdx.x == 0) {
+    result[0] = (double)e0[0];
+    result[1] = l0[0];
+    if (e1) {
+      result[2] = (double)e1[0];
+      result[3] = l1[0];
+    }
+  }
+}
+
+int rescale(float* x, int64_t n, unsigned* bits, double* log_acc, cudaStream_t s) {
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 1024);
+  absmax_kernel<<<blocks, threads, 0, s>>>(x, n, bits);
+  scale_kernel<<<blocks, threads, 0, s>>>(x, n, bits, log_acc);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+int check_chain(const tn_mps* m) {
+  if (!m || m->n < 1 || m->d < 1 || !m->bond || !m->cores) return TN_ERR_ARG;
+  if (m->bond[0] != 1 || m->bond[m->n] != 1) return TN_ERR_ARG;
+  for (int i = 0; i < m->n; ++i) {
+    if (m->bond[i + 1] < 1 || !m->cores[i]) return TN_ERR_ARG;
+  }
+  return TN_OK;
+}
+
+int64_t max_bond(const tn_mps* m) {
+  int64_t x = 1;
+  for (int i = 0; i <= m->n; ++i) x = std::max(x, m->bond[i]);
+  return x;
+}
+
+tn_tensor tensor3(float* p, int64_t a, int64_t b, int64_t c) {
+  tn_tensor t;
+  const int64_t sh[3] = {a, b, c};
+  tn_tensor_init(&t, p, 3, sh);
+  return t;
+}
+tn_tensor tensor2(float* p, int64_t a, int64_t b) {
+  tn_tensor t;
+  const int64_t sh[2] = {a, b};
+  tn_tensor_init(&t, p, 2, sh);
+  return t;
+}
+tn_tensor tensor4(float* p, int64_t a, int64_t b, int64_t c, int64_t d) {
+  tn_tensor t;
+  const int64_t sh[4] = {a, b, c, d};
+  tn_tensor_init(&t, p, 4, sh);
+  return t;
+}
+
+bool small_ok(const tn_mps* bra, const tn_mps* ket) {
+  return bra->n <= SMALL_MAXN && bra->d <= SMALL_PHYS && max_bond(bra) <= SMALL_D && max_bond(ket) <= SMALL_D;
+}
+
+// Workspace of the contraction-kernel inner sweep: E0, E1 (Dmax^2 each),
+// T (Dmax d Dmax), n max slots, one log-scale.
+struct InnerWs {
+  float *E0, *E1, *T;
+  unsigned* bits;
+  double* lg;
+  size_t bytes;
+};
+
+InnerWs inner_layout(uint8_t* base, int64_t D, int64_t d, int n) {
+  InnerWs w;
+  size_t off = 0;
+  auto take = [&](size_t b) { uint8_t* p = base ? base + off : nullptr; off += align256(b); return p; };
+  w.E0 = reinterpret_cast<float*>(take(sizeof(float) * D * D));
+  w.E1 = reinterpret_cast<float*>(take(sizeof(float) * D * D));
+  w.T = reinterpret_cast<float*>(take(sizeof(float) * D * d * D));
+  w.bits = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)n));
+  w.lg = reinterpret_cast<double*>(take(sizeof(double) * 2));
+  w.bytes = off;
+  return w;
+}
+
+// Inner-product sweep through the contraction kernels. Leaves the final 1x1
+// environment in *final_env and the log-scale in w.lg[0].
+int inner_sweep(const tn_mps* bra, const tn_mps* ket, int prec, const InnerWs& w, float** final_env,
+                cudaStream_t s) {
+  init_sweep_kernel<<<1, 256, 0, s>>>(w.E0, w.lg, 1, w.bits, bra->n);
+  if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  float* E = w.E0;
+  float* E2 = w.E1;
+  const int64_t d = bra->d;
+  for (int i = 0; i < bra->n; ++i) {
+    const int64_t Da = bra->bond[i], Db = bra->bond[i + 1], Dak = ket->bond[i], Dbk = ket->bond[i + 1];
+    tn_tensor tE = tensor2(E, Da, Dak);
+    tn_tensor tK = tensor3(ket->cores[i], Dak, d, Dbk);
+    tn_tensor tT = tensor3(w.T, Da, d, Dbk);
+    const int l1a[1] = {1}, l1b[1] = {0};
+    int rc = contract_internal(&tE, l1a, &tK, l1b, 1, &tT, prec, s);
+    if (rc != TN_OK) return rc;
+    tn_tensor tB = tensor3(bra->cores[i], Da, d, Db);
+    tn_tensor tE2 = tensor2(E2, Db, Dbk);
+    const int l2a[2] = {0, 1}, l2b[2] = {0, 1};
+    rc = contract_internal(&tB, l2a, &tT, l2b, 2, &tE2, prec, s);
+    if (rc != TN_OK) return rc;
+    rc = rescale(E2, Db * Dbk, w.bits + i, w.lg, s);
+    if (rc != TN_OK) return rc;
+    std::swap(E, E2);
+  }
+  *final_env = E;
+  return TN_OK;
+}
+
+// Workspace of the MPO sweep: L0, L1 (wmax Dmax^2), T1, T2 (wmax Dmax d Dmax),
+// n max slots, one log-scale; the inner sweep reuses the front of it.
+struct ExpectWs {
+  float *L0, *L1, *T1, *T2;
+  unsigned* bits;
+  double* lg;
+  size_t bytes;
+};
+
+ExpectWs expect_layout(uint8_t* base, int64_t D, int64_t W, int64_t d, int n) {
+  ExpectWs w;
+  size_t off = 0;
+  auto take = [&](size_t b) { uint8_t* p = base ? base + off : nullptr; off += align256(b); return p; };
+  w.L0 = reinterpret_cast<float*>(take(sizeof(float) * W * D * D));
+  w.L1 = reinterpret_cast<float*>(take(sizeof(float) * W * D * D));
+  w.T1 = reinterpret_cast<float*>(take(sizeof(float) * W * D * d * D));
+  w.T2 = reinterpret_cast<float*>(take(sizeof(float) * W * D * d * D));
+  w.bits = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)n));
+  w.lg = reinterpret_cast<double*>(take(sizeof(double) * 2));
+  w.bytes = off;
+  return w;
+}
+
+}  // namespace
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+size_t tn_mps_inner_workspace_bytes(const tn_mps* bra, const tn_mps* ket) {
+  if (check_chain(bra) != TN_OK || check_chain(ket) != TN_OK) return 0;
+  if (small_ok(bra, ket)) return 0;
+  const int64_t D = std::max(max_bond(bra), max_bond(ket));
+  return inner_layout(nullptr, D, bra->d, bra->n).bytes;
+}
+
+int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace, size_t ws_bytes,
+                 double* result, void* stream) {
+  int rc;
+  if ((rc = check_chain(bra)) != TN_OK || (rc = check_chain(ket)) != TN_OK) return rc;
+  if (bra->n != ket->n || bra->d != ket->d || !result) return TN_ERR_ARG;
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (small_ok(bra, ket)) {
+    SmallChain c;
+    c.n = bra->n;
+    c.d = bra->d;
+    for (int i = 0; i <= bra->n; ++i) {
+      c.bb[i] = (int32_t)bra->bond[i];
+      c.bk[i] = (int32_t)ket->bond[i];
+    }
+    for (int i = 0; i < bra->n; ++i) {
+      c.bra[i] = bra->cores[i];
+      c.ket[i] = ket->cores[i];
+    }
+    const size_t smem = sizeof(float) * (2 * SMALL_D * SMALL_D + SMALL_D * SMALL_PHYS * SMALL_D);
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(mps_inner_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess)
+        return TN_ERR_CUDA;
+      attr = true;
+    }
+    mps_inner_small_kernel<<<1, SMALL_THREADS, smem, s>>>(c, result);
+    return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+  }
+  const int64_t D = std::max(max_bond(bra), max_bond(ket));
+  InnerWs w = inner_layout(static_cast<uint8_t*>(workspace), D, bra->d, bra->n);
+  if (!workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
+  float* env = nullptr;
+  rc = inner_sweep(bra, ket, prec, w, &env, s);
+  if (rc != TN_OK) return rc;
+  finish_kernel<<<1, 32, 0, s>>>(env, w.lg, nullptr, nullptr, result);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H) {
+  if (check_chain(psi) != TN_OK || !H || !H->bond) return 0;
+  int64_t W = 1;
+  for (int i = 0; i <= H->n; ++i) W = std::max(W, H->bond[i]);
+  const int64_t D = max_bond(psi);
+  const size_t a = expect_layout(nullptr, D, W, psi->d, psi->n).bytes;
+  const size_t b = inner_layout(nullptr, D, psi->d, psi->n).bytes;
+  return a + b;
+}
+
+int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace, size_t ws_bytes,
+                  double* result, void* stream) {
+  int rc;
+  if ((rc = check_chain(psi)) != TN_OK) return rc;
+  if (!H || !H->bond || !H->cores || H->n != psi->n || H->d != psi->d || !result) return TN_ERR_ARG;
+  if (H->bond[0] != 1 || H->bond[H->n] != 1) return TN_ERR_ARG;
+  for (int i = 0; i < H->n; ++i)
+    if (H->bond[i + 1] < 1 || !H->cores[i]) return TN_ERR_ARG;
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t Wm = 1;
+  for (int i = 0; i <= H->n; ++i) Wm = std::max(Wm, H->bond[i]);
+  const int64_t D = max_bond(psi), d = psi->d;
+  const size_t need = tn_mps_expect_workspace_bytes(psi, H);
+  if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  ExpectWs w = expect_layout(base, D, Wm, d, psi->n);
+  InnerWs wi = inner_layout(base + w.bytes, D, d, psi->n);
+
+  // <psi|psi>
+  float* env = nullptr;
+  rc = inner_sweep(psi, psi, prec, wi, &env, s);
+  if (rc != TN_OK) return rc;
+
+  // <psi|H|psi>
+  init_sweep_kernel<<<1, 256, 0, s>>>(w.L0, w.lg, 1, w.bits, psi->n);
+  if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  float* L = w.L0;
+  float* L2 = w.L1;
+  for (int i = 0; i < psi->n; ++i) {
+    const int64_t Da = psi->bond[i], Db = psi->bond[i + 1], wa = H->bond[i], wb = H->bond[i + 1];
+    // (i) T1[w, a', s, b] = sum_a L[w, a, a'] A[a, s, b]
+    tn_tensor tL = tensor3(L, wa, Da, Da);
+    tn_tensor tA = tensor3(psi->cores[i], Da, d, Db);
+    tn_tensor tT1 = tensor4(w.T1, wa, Da, d, Db);
+    const int la1[1] = {1}, lb1[1] = {0};
+    if ((rc = contract_internal(&tL, la1, &tA, lb1, 1, &tT1, prec, s)) != TN_OK) return rc;
+    // (ii) T2[w', s', a', b] = sum_{w,s} W[w, w', s, s'] T1[w, a', s, b]
+    tn_tensor tW = tensor4(H->cores[i], wa, wb, d, d);
+    tn_tensor tT2 = tensor4(w.T2, wb, d, Da, Db);
+    const int la2[2] = {0, 2}, lb2[2] = {0, 2};
+    if ((rc = contract_internal(&tW, la2, &tT1, lb2, 2, &tT2, TN_PREC_FP32, s)) != TN_OK) return rc;
+    // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] A[a', s', b']
+    tn_tensor tL2 = tensor3(L2, wb, Db, Db);
+    const int la3[2] = {1, 2}, lb3[2] = {1, 0};
+    if ((rc = contract_internal(&tT2, la3, &tA, lb3, 2, &tL2, prec, s)) != TN_OK) return rc;
+    if ((rc = rescale(L2, wb * Db * Db, w.bits + i, w.lg, s)) != TN_OK) return rc;
+    std::swap(L, L2);
+  }
+  finish_kernel<<<1, 32, 0, s>>>(L, w.lg, env, wi.lg, result);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+}  // extern "C"

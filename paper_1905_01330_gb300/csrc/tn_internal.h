@@ -69,7 +69,14 @@ struct ZeroRange {
 };
 int launch_zero(const ZeroRange* ranges, int n, cudaStream_t stream);
 
+// tn_contract without the C-ABI wrapper (used by the chain sweeps).
+int contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                      int nshared, const tn_tensor* C, int prec, cudaStream_t stream);
+
 // Device status word (first error wins); defined in api.cu.
 int* status_word();
+
+// Bytes rounded up to the 256-byte alignment every workspace region keeps.
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace tn

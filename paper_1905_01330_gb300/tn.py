@@ -35,6 +35,31 @@ class TnContractSpec(ctypes.Structure):
                 ("legsA", ctypes.c_int32 * TN_MAX_RANK), ("legsB", ctypes.c_int32 * TN_MAX_RANK)]
 
 
+class TnChain(ctypes.Structure):
+    """tn_mps / tn_mpo: n cores, physical dim d, host bond array, host table of device pointers."""
+    _fields_ = [("n", ctypes.c_int32), ("d", ctypes.c_int32), ("bond", ctypes.POINTER(ctypes.c_int64)),
+                ("cores", ctypes.POINTER(ctypes.c_void_p))]
+
+
+def chain_desc(cores, phys_axis: int = 1):
+    """(TnChain, keepalive) for a list of contiguous float32 CUDA tensors; bonds
+    are the first axis of each core plus the last core's second bond axis."""
+    for c in cores:
+        if c.dtype != torch.float32 or not c.is_cuda or not c.is_contiguous():
+            raise TypeError("MPS/MPO cores must be contiguous float32 CUDA tensors")
+    n = len(cores)
+    right_axis = 2 if cores[-1].dim() == 3 else 1
+    bonds = [c.shape[0] for c in cores] + [cores[-1].shape[right_axis]]
+    bond_arr = (ctypes.c_int64 * (n + 1))(*bonds)
+    ptr_arr = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cores])
+    ch = TnChain()
+    ch.n = n
+    ch.d = cores[0].shape[phys_axis]
+    ch.bond = ctypes.cast(bond_arr, ctypes.POINTER(ctypes.c_int64))
+    ch.cores = ctypes.cast(ptr_arr, ctypes.POINTER(ctypes.c_void_p))
+    return ch, (bond_arr, ptr_arr, cores)
+
+
 _lib = None
 _EXPORTS = None
 
@@ -58,6 +83,10 @@ def _signatures():
         "tn_group_plan_destroy": (None, [vp]),
         "tn_group_plan_flops": (ctypes.c_double, [vp]),
         "tn_group_plan_bytes": (ctypes.c_double, [vp]),
+        "tn_mps_inner_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
+        "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
+        "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
+        "tn_mps_expect": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
     }
@@ -137,6 +166,40 @@ def contract(A: torch.Tensor, legsA, B: torch.Tensor, legsB, prec: str = "bf16",
 
 def sync_status(stream=None) -> int:
     return load().tn_sync_status(_stream(stream))
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def mps_inner(bra, ket, prec: str = "fp32", stream=None, out: torch.Tensor | None = None):
+    """<bra|ket> of two MPS (lists of (D, d, D') cores) as a float64 CUDA tensor
+    [value, log_scale]: <bra|ket> = value * exp(log_scale) (tn_mps_inner)."""
+    lib = load()
+    cb, kb = chain_desc(bra)
+    ck, kk = chain_desc(ket)
+    dev = bra[0].device
+    ws = _workspace(lib.tn_mps_inner_workspace_bytes(ctypes.byref(cb), ctypes.byref(ck)), dev)
+    res = out if out is not None else torch.empty(2, dtype=torch.float64, device=dev)
+    _check(lib.tn_mps_inner(ctypes.byref(cb), ctypes.byref(ck), PREC[prec], ctypes.c_void_p(ws.data_ptr()),
+                            ws.numel(), ctypes.c_void_p(res.data_ptr()), _stream(stream)), "tn_mps_inner")
+    res._tn_keep = (ws, kb, kk)
+    return res
+
+
+def mps_expect(psi, mpo, prec: str = "fp32", stream=None, out: torch.Tensor | None = None):
+    """<psi|H|psi> and <psi|psi> (tn_mps_expect) as a float64 CUDA tensor
+    [e_value, e_log_scale, n_value, n_log_scale]. mpo cores are (w, w', d, d)."""
+    lib = load()
+    cp, kp = chain_desc(psi)
+    ch, kh = chain_desc(mpo, phys_axis=2)
+    dev = psi[0].device
+    ws = _workspace(lib.tn_mps_expect_workspace_bytes(ctypes.byref(cp), ctypes.byref(ch)), dev)
+    res = out if out is not None else torch.empty(4, dtype=torch.float64, device=dev)
+    _check(lib.tn_mps_expect(ctypes.byref(cp), ctypes.byref(ch), PREC[prec], ctypes.c_void_p(ws.data_ptr()),
+                             ws.numel(), ctypes.c_void_p(res.data_ptr()), _stream(stream)), "tn_mps_expect")
+    res._tn_keep = (ws, kp, kh)
+    return res
 
 
 class GroupPlan:

@@ -1,0 +1,130 @@
+"""GPU parity of the MPS inner-product and MPO-energy sweeps against the oracle.
+
+Scalars are compared as value * exp(log_scale) on both sides, relative error
+|x - x*| / |x*|. Tolerance of a sweep result made of c tensor-core
+contractions: fp32 1e-5; bf16x3 2 * 2^-16 * sqrt(c); bf16 2 * 2^-8 * sqrt(c).
+2^-16 is the per-contraction relative error of the three-term split (the
+dropped lo*lo term and the rounding of lo), 2^-8 that of two bf16 roundings;
+independent per-site errors add up like a random walk over the c steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_01330_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+UNIT = {"bf16x3": 2.0 ** -16, "bf16": 2.0 ** -8}
+
+
+def tol(prec, contractions):
+    if prec == "fp32":
+        return 1e-5
+    return 2.0 * UNIT[prec] * math.sqrt(contractions)
+
+
+@pytest.fixture(scope="module")
+def tn():
+    from paper_1905_01330_gb300 import build, tn as tnmod
+    build.build()
+    tnmod.load()
+    return tnmod
+
+
+def to_dev(cores):
+    return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cores]
+
+
+def rel(got, ref):
+    return abs(got - ref) / abs(ref)
+
+
+def val(r, j=0):
+    r = r.cpu().numpy()
+    return r[2 * j] * math.exp(r[2 * j + 1])
+
+
+def test_config1_inner_product_small_chain(tn):
+    # N=20, d=2, chi=32, cores N(0, 1/chi): the one-CTA float32 sweep
+    cores = synth.random_mps(20, 2, 32, seed=1)
+    v, lg = oracle.mps_inner(cores, cores)
+    ref = v * math.exp(lg)
+    # brute force over the 2^20 amplitudes pins the oracle here as well
+    psi = oracle.mps_state(cores)
+    assert rel(float(psi @ psi), ref) < 1e-10
+    for prec in ("fp32", "bf16", "bf16x3"):
+        r = tn.mps_inner(to_dev(cores), to_dev(cores), prec=prec)
+        assert tn.sync_status() == 0
+        assert rel(val(r), ref) <= 1e-5, prec
+
+
+def test_overlap_of_different_states_small(tn):
+    a = synth.random_mps(14, 2, 16, seed=3)
+    b = synth.random_mps(14, 2, 24, seed=4)
+    v, lg = oracle.mps_inner(a, b)
+    r = tn.mps_inner(to_dev(a), to_dev(b), prec="fp32")
+    assert rel(val(r), v * math.exp(lg)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_inner_product_large_bond_contraction_path(tn, prec):
+    # bonds above 64 run through the tensordot kernels with a workspace
+    cores = synth.random_mps(16, 2, 96, seed=5)
+    v, lg = oracle.mps_inner(cores, cores)
+    r = tn.mps_inner(to_dev(cores), to_dev(cores), prec=prec)
+    assert tn.sync_status() == 0
+    assert rel(val(r), v * math.exp(lg)) <= tol(prec, 2 * 16)
+
+
+def test_long_chain_log_scale(tn):
+    # 400 sites of N(0,1) cores: the raw norm is far outside float32 range
+    cores = synth.random_mps(400, 2, 8, seed=6, std=1.0)
+    v, lg = oracle.mps_inner(cores, cores)
+    r = tn.mps_inner(to_dev(cores), to_dev(cores), prec="fp32").cpu().numpy()
+    assert lg > 200.0
+    assert abs((math.log(r[0]) + r[1]) - (math.log(v) + lg)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_tfim_energy_random_mps(tn, prec):
+    n = 10
+    cores = synth.random_mps(n, 2, 8, seed=7)
+    W = synth.tfim_mpo(n)
+    e, le = oracle.mpo_expect(cores, W)
+    nv, ln = oracle.mps_inner(cores, cores)
+    r = tn.mps_expect(to_dev(cores), to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    # the energy per normalised state
+    E_ref = e * math.exp(le) / (nv * math.exp(ln))
+    E = val(r, 0) / val(r, 1)
+    assert rel(val(r, 0), e * math.exp(le)) <= tol(prec, 2 * n), (E, E_ref)
+    assert rel(val(r, 1), nv * math.exp(ln)) <= tol(prec, 2 * n)
+
+
+def test_tfim_closed_forms_on_gpu(tn):
+    n = 12
+    W = synth.tfim_mpo(n)
+    r2 = 1.0 / math.sqrt(2.0)
+    for vec, E_exact in (([1.0, 0.0], -(n - 1)), ([r2, r2], -n)):
+        cores = [np.asarray(vec, dtype=np.float32).reshape(1, 2, 1) for _ in range(n)]
+        r = tn.mps_expect(to_dev(cores), to_dev(W), prec="fp32")
+        assert abs(val(r, 0) / val(r, 1) - E_exact) <= 1e-5 * abs(E_exact)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_left_canonical_energy_large_bond(tn, prec):
+    # config-5 shape at reduced length and bond: left-canonical, chi = 128
+    n, chi = 16, 128
+    cores = synth.left_canonical_mps(n, 2, chi, seed=5)
+    W = synth.tfim_mpo(n)
+    e, le = oracle.mpo_expect(cores, W)
+    nv, ln = oracle.mps_inner(cores, cores)
+    assert abs(nv * math.exp(ln) - 1.0) < n * 1e-6
+    r = tn.mps_expect(to_dev(cores), to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    assert rel(val(r, 0), e * math.exp(le)) <= tol(prec, 2 * n)
+    assert abs(val(r, 1) - 1.0) <= tol(prec, 2 * n) + n * 1e-6
