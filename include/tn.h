@@ -194,6 +194,78 @@ size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H);
 int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace, size_t ws_bytes,
                   double* result, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* MPS image classifier (Sec. IV.A)                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * Scores of a batch of greyscale images under one MPS W with a label leg:
+ * pixel p of image b is encoded by the local feature map
+ * Phi(p) = (cos(pi p / 2), sin(pi p / 2)), and score_l(b) is the inner
+ * product of the product state of the n encoded pixels with W_l, the MPS
+ * obtained by fixing the label leg to l. W has n cores of shape
+ * (bond[i], 2, bond[i+1]) except the label core at `label_site`, of shape
+ * (bond[ls], 2, n_labels, bond[ls+1]); every bond <= 128, d = 2.
+ * The sweep runs from both ends towards the label core: the left vector after
+ * sites 0..ls-1 and the right vector after sites n-1..ls+1 (each step
+ * v' = sum_s Phi_s(x_i) v.W_i[:, s, :]) are divided per sample by their
+ * largest magnitude after every site, the logs of those factors summed in
+ * float64, and met at the label core.
+ *   pixels:  DEVICE [batch, n] float32, row-major.
+ *   ftilde:  DEVICE [batch, n_labels] float32; log_scale: DEVICE [batch]
+ *            float64. score_l(b) = ftilde[b, l] * exp(log_scale[b]).
+ *   prec:    TN_PREC_FP32 (float32 on the CUDA cores) or TN_PREC_BF16 (bf16
+ *            operands, float32 accumulation on tcgen05, when every inner
+ *            bond is the same chi in {32, 64, 128}).
+ *   ckpt_every: the forward keeps the per-sample sweep vector every
+ *            ckpt_every sites (1 = every site) for the backward pass, which
+ *            recomputes the vectors in between; 0 keeps none (no backward).
+ *   workspace: DEVICE scratch of tn_mps_classify_workspace_bytes(); it holds
+ *            the forward's state for tn_mps_classify_backward.
+ * Errors: TN_ERR_ARG, TN_ERR_SHAPE (bonds or label core inconsistent),
+ * TN_ERR_UNSUPPORTED (bond > 128, d != 2, BF16 on uneven bonds),
+ * TN_ERR_WORKSPACE, TN_ERR_CUDA.
+ */
+size_t tn_mps_classify_workspace_bytes(const tn_mps* W, int label_site, int n_labels, int batch,
+                                       int ckpt_every);
+int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* pixels, int batch,
+                    int prec, int ckpt_every, float* ftilde, double* log_scale, void* workspace,
+                    size_t ws_bytes, void* stream);
+
+/*
+ * Gradient of a loss with respect to every core, given dLoss/dftilde
+ * (DEVICE [batch, n_labels] float32) for a loss that depends on the scores
+ * only through their direction f / ||f|| (so log_scale carries no gradient),
+ * e.g. cross-entropy of softmax(f / ||f||). Must follow tn_mps_classify on
+ * the same W, pixels, batch and workspace with ckpt_every >= 1. Per site i,
+ * with v the normalised sweep vector entering i and g the adjoint of the
+ * vector leaving it,
+ *   dW_i[a, s, c] = sum_b v_b[a] Phi_s(x_bi) g_b[c] / scale_bi,
+ *   g_b <- sum_{s,c} W_i[a, s, c] Phi_s(x_bi) g_b[c] / scale_bi,
+ * done as one adjoint sweep per half-chain and, per checkpoint segment, one
+ * grouped tensordot over the batch for the segment's cores.
+ *   dcores: host table of n DEVICE pointers, each shaped like its core
+ *           (overwritten).
+ *   prec:   arithmetic of the sweeps and of the batch contractions.
+ * Errors: as tn_mps_classify.
+ */
+int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, const float* pixels,
+                             int batch, int prec, int ckpt_every, const float* dftilde,
+                             float* const* dcores, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Loss head of the classifier: with z_b = ftilde_b / ||ftilde_b||_2 (equal
+ * to f_b / ||f_b||, so the log-scale drops out),
+ *   loss = (1 / batch) sum_b [ logsumexp(z_b) - z_b[label_b] ],
+ *   dftilde_b = (g_b - z_b (z_b . g_b)) / (batch ||ftilde_b||),
+ *   g_b = softmax(z_b) - onehot(label_b).
+ *   ftilde: DEVICE [batch, n_labels] float32; labels: DEVICE [batch] int64 in
+ *   [0, n_labels); loss: DEVICE float64 scalar; dftilde: DEVICE [batch,
+ *   n_labels] float32 (may be NULL). The mean is reduced in a fixed order
+ *   (deterministic). Errors: TN_ERR_ARG, TN_ERR_CUDA.
+ */
+int tn_mps_classify_loss(const float* ftilde, const int64_t* labels, int batch, int n_labels,
+                         double* loss, float* dftilde, void* stream);
+
 /* Device status word: returns the first kernel-side error since the last
  * call (TN_OK if none) after synchronising `stream`, and clears it. */
 int tn_sync_status(void* stream);

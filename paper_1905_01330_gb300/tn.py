@@ -87,6 +87,12 @@ def _signatures():
         "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
         "tn_mps_expect": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
+        "tn_mps_classify_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), i32, i32, i32, i32]),
+        "tn_mps_classify": (i32, [ctypes.POINTER(TnChain), i32, i32, vp, i32, i32, i32, vp, vp, vp,
+                                  ctypes.c_size_t, vp]),
+        "tn_mps_classify_backward": (i32, [ctypes.POINTER(TnChain), i32, i32, vp, i32, i32, i32, vp,
+                                           ctypes.POINTER(ctypes.c_void_p), vp, ctypes.c_size_t, vp]),
+        "tn_mps_classify_loss": (i32, [vp, vp, i32, i32, vp, vp, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
     }
@@ -239,3 +245,108 @@ class GroupPlan:
         if h is not None and _lib is not None:
             _lib.tn_group_plan_destroy(h)
             self._h = None
+
+
+# ---------------------------------------------------------------------------
+# MPS classifier (Sec. IV.A)
+# ---------------------------------------------------------------------------
+
+def classifier_workspace(cores, label_site: int, n_labels: int, batch: int, ckpt_every: int) -> torch.Tensor:
+    lib = load()
+    ch, keep = chain_desc_classifier(cores, label_site)
+    nbytes = lib.tn_mps_classify_workspace_bytes(ctypes.byref(ch), label_site, n_labels, batch, ckpt_every)
+    return _workspace(nbytes, cores[0].device)
+
+
+def chain_desc_classifier(cores, label_site: int):
+    """tn_mps of a classifier MPS: the label core (D, 2, L, D') keeps its bonds."""
+    for c in cores:
+        if c.dtype != torch.float32 or not c.is_cuda or not c.is_contiguous():
+            raise TypeError("classifier cores must be contiguous float32 CUDA tensors")
+    n = len(cores)
+    bonds = [c.shape[0] for c in cores] + [cores[-1].shape[-1]]
+    bond_arr = (ctypes.c_int64 * (n + 1))(*bonds)
+    ptr_arr = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cores])
+    ch = TnChain()
+    ch.n = n
+    ch.d = cores[0].shape[1]
+    ch.bond = ctypes.cast(bond_arr, ctypes.POINTER(ctypes.c_int64))
+    ch.cores = ctypes.cast(ptr_arr, ctypes.POINTER(ctypes.c_void_p))
+    return ch, (bond_arr, ptr_arr, cores)
+
+
+def mps_classify(cores, label_site: int, pixels: torch.Tensor, prec: str = "fp32", ckpt_every: int = 1,
+                 workspace: torch.Tensor | None = None, stream=None):
+    """(ftilde [B, L] float32, log_scale [B] float64, workspace): scores = ftilde * exp(log_scale)."""
+    lib = load()
+    L = cores[label_site].shape[2]
+    B = pixels.shape[0]
+    if pixels.dtype != torch.float32 or not pixels.is_contiguous():
+        raise TypeError("pixels must be a contiguous float32 CUDA tensor [batch, n]")
+    ch, keep = chain_desc_classifier(cores, label_site)
+    if workspace is None:
+        workspace = classifier_workspace(cores, label_site, L, B, ckpt_every)
+    ft = torch.empty((B, L), dtype=torch.float32, device=pixels.device)
+    lam = torch.empty((B,), dtype=torch.float64, device=pixels.device)
+    _check(lib.tn_mps_classify(ctypes.byref(ch), label_site, L, ctypes.c_void_p(pixels.data_ptr()), B, PREC[prec],
+                               ckpt_every, ctypes.c_void_p(ft.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                               ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream)),
+           "tn_mps_classify")
+    return ft, lam, workspace
+
+
+def mps_classify_backward(cores, label_site: int, pixels: torch.Tensor, dftilde: torch.Tensor,
+                          workspace: torch.Tensor, prec: str = "fp32", ckpt_every: int = 1, stream=None):
+    """Core gradients (list shaped like cores) from dLoss/dftilde; needs the forward's workspace."""
+    lib = load()
+    L = cores[label_site].shape[2]
+    B = pixels.shape[0]
+    ch, keep = chain_desc_classifier(cores, label_site)
+    dft = dftilde.contiguous().float()
+    grads = [torch.empty_like(c) for c in cores]
+    table = (ctypes.c_void_p * len(grads))(*[g.data_ptr() for g in grads])
+    _check(lib.tn_mps_classify_backward(ctypes.byref(ch), label_site, L, ctypes.c_void_p(pixels.data_ptr()), B,
+                                        PREC[prec], ckpt_every, ctypes.c_void_p(dft.data_ptr()), table,
+                                        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream)),
+           "tn_mps_classify_backward")
+    return grads
+
+
+def mps_classify_loss(ftilde: torch.Tensor, labels: torch.Tensor, stream=None):
+    """(loss float64 scalar tensor, dLoss/dftilde) of mean CE(softmax(f/||f||), y) (tn_mps_classify_loss)."""
+    lib = load()
+    B, L = ftilde.shape
+    ft = ftilde.contiguous()
+    y = labels.to(torch.int64).contiguous()
+    loss = torch.empty((), dtype=torch.float64, device=ft.device)
+    dft = torch.empty_like(ft)
+    _check(lib.tn_mps_classify_loss(ctypes.c_void_p(ft.data_ptr()), ctypes.c_void_p(y.data_ptr()), B, L,
+                                    ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(dft.data_ptr()),
+                                    _stream(stream)), "tn_mps_classify_loss")
+    return loss, dft
+
+
+class MPSClassifierFn(torch.autograd.Function):
+    """ftilde, log_scale = MPSClassifierFn.apply(pixels, label_site, prec, ckpt_every, *cores).
+
+    The backward is the library's hand-written adjoint (tn_mps_classify_backward)
+    with checkpointed sweep vectors. log_scale is returned without a gradient:
+    losses must depend on the scores only through f / ||f|| (as the
+    normalised cross-entropy of the classifier does)."""
+
+    @staticmethod
+    def forward(ctx, pixels, label_site, prec, ckpt_every, *cores):
+        ft, lam, ws = mps_classify(list(cores), label_site, pixels, prec=prec, ckpt_every=ckpt_every)
+        ctx.save_for_backward(pixels, *cores)
+        ctx.ws = ws
+        ctx.meta = (label_site, prec, ckpt_every)
+        ctx.mark_non_differentiable(lam)
+        return ft, lam
+
+    @staticmethod
+    def backward(ctx, dft, dlam):
+        pixels, *cores = ctx.saved_tensors
+        label_site, prec, ckpt_every = ctx.meta
+        grads = mps_classify_backward(cores, label_site, pixels, dft, ctx.ws, prec=prec, ckpt_every=ckpt_every)
+        ctx.ws = None
+        return (None, None, None, None, *grads)

@@ -1,0 +1,124 @@
+"""GPU parity of the MPS classifier: forward scores, loss head and the adjoint
+backward against the FP64 oracle.
+
+Scores are compared per sample as vectors over labels, on the true scale
+f = ftilde * exp(log_scale): ||f - f*|| / ||f*||. Gradients per core:
+||dW - dW*||_F / ||dW*||_F. float32 path tolerances: 1e-5 * sqrt(sites) for
+scores (independent float32 roundings per site), 1e-4 for gradients (sums of
+products over the batch on top of the sweep).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_01330_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    from paper_1905_01330_gb300 import build, tn as tnmod
+    build.build()
+    tnmod.load()
+    return tnmod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def score_err(ft, lam, ft_ref, lam_ref):
+    """Per-sample normwise relative error of the scores, computed in the log domain."""
+    ft = ft.double().cpu().numpy()
+    lam = lam.cpu().numpy()
+    shift = lam - lam_ref  # f = ft e^lam; f* = ft_ref e^lam_ref
+    got = ft * np.exp(shift)[:, None]
+    return np.linalg.norm(got - ft_ref, axis=1) / np.linalg.norm(ft_ref, axis=1)
+
+
+@pytest.mark.parametrize("n,chi,ls,L,B", [(12, 8, 5, 3, 40), (50, 16, 25, 10, 70), (784, 32, 392, 10, 96)])
+def test_forward_fp32_parity(tn, n, chi, ls, L, B):
+    cores = synth.classifier_mps(n, chi, ls, L, seed=31, eps_std=0.1)
+    px = synth.pixels(B, n, seed=32)
+    ft_ref, lam_ref = oracle.classify(cores, ls, px)
+    ft, lam, _ = tn.mps_classify([dev(c) for c in cores], ls, dev(px), prec="fp32", ckpt_every=0)
+    assert tn.sync_status() == 0
+    err = score_err(ft, lam, ft_ref, lam_ref)
+    assert err.max() <= 1e-5 * math.sqrt(n), err.max()
+
+
+def test_identity_cores_closed_form(tn):
+    n, chi, ls, L, B = 100, 16, 40, 4, 33
+    cores = synth.classifier_mps(n, chi, ls, L, seed=1, eps_std=0.0)
+    px = synth.pixels(B, n, seed=2)
+    ft, lam, _ = tn.mps_classify([dev(c) for c in cores], ls, dev(px), prec="fp32", ckpt_every=0)
+    ref = np.sum(np.log(np.cos(np.pi * px.astype(np.float64) / 2) + np.sin(np.pi * px.astype(np.float64) / 2)), axis=1)
+    got = np.log(ft.double().cpu().numpy()) + lam.cpu().numpy()[:, None]
+    assert np.max(np.abs(got - ref[:, None])) <= 1e-5 * math.sqrt(n)
+
+
+def test_loss_head_matches_oracle(tn):
+    n, chi, ls, L, B = 20, 8, 10, 10, 64
+    cores = synth.classifier_mps(n, chi, ls, L, seed=41, eps_std=0.3)
+    px = synth.pixels(B, n, seed=42)
+    y = synth.labels(B, L, seed=43)
+    ft, lam, _ = tn.mps_classify([dev(c) for c in cores], ls, dev(px), prec="fp32", ckpt_every=0)
+    loss, dft = tn.mps_classify_loss(ft, torch.from_numpy(y).cuda())
+    ref = oracle.classify_loss(cores, ls, px, y)
+    assert abs(loss.item() - ref) <= 1e-5 * abs(ref)
+    # dLoss/dftilde is orthogonal to ftilde (the loss is scale-invariant)
+    dots = (dft.double() * ft.double()).sum(1).abs() / (dft.double().norm(dim=1) * ft.double().norm(dim=1))
+    assert dots.max().item() < 1e-4
+
+
+@pytest.mark.parametrize("ck", [1, 3, 5])
+def test_backward_fp32_parity_tiny(tn, ck):
+    n, chi, ls, L, B = 12, 8, 6, 3, 40
+    cores = synth.classifier_mps(n, chi, ls, L, seed=51, eps_std=0.3)
+    px = synth.pixels(B, n, seed=52)
+    y = synth.labels(B, L, seed=53)
+    loss_ref, g_ref = oracle.classify_grad(cores, ls, px, y)
+    dc = [dev(c) for c in cores]
+    ft, lam, ws = tn.mps_classify(dc, ls, dev(px), prec="fp32", ckpt_every=ck)
+    loss, dft = tn.mps_classify_loss(ft, torch.from_numpy(y).cuda())
+    grads = tn.mps_classify_backward(dc, ls, dev(px), dft, ws, prec="fp32", ckpt_every=ck)
+    assert tn.sync_status() == 0
+    assert abs(loss.item() - loss_ref) <= 1e-5 * abs(loss_ref)
+    for i, (g, r) in enumerate(zip(grads, g_ref)):
+        err = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
+        assert err <= 1e-4, (i, err)
+
+
+def test_backward_fp32_parity_longer_chain(tn):
+    n, chi, ls, L, B = 64, 32, 30, 10, 100
+    cores = synth.classifier_mps(n, chi, ls, L, seed=61, eps_std=0.1)
+    px = synth.pixels(B, n, seed=62)
+    y = synth.labels(B, L, seed=63)
+    _, g_ref = oracle.classify_grad(cores, ls, px, y)
+    dc = [dev(c) for c in cores]
+    ft, lam, ws = tn.mps_classify(dc, ls, dev(px), prec="fp32", ckpt_every=8)
+    _, dft = tn.mps_classify_loss(ft, torch.from_numpy(y).cuda())
+    grads = tn.mps_classify_backward(dc, ls, dev(px), dft, ws, prec="fp32", ckpt_every=8)
+    for i, (g, r) in enumerate(zip(grads, g_ref)):
+        err = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
+        assert err <= 1e-4, (i, err)
+
+
+def test_autograd_function_matches_direct_backward(tn):
+    n, chi, ls, L, B = 16, 8, 7, 4, 48
+    cores = synth.classifier_mps(n, chi, ls, L, seed=71, eps_std=0.3)
+    px = dev(synth.pixels(B, n, seed=72))
+    y = synth.labels(B, L, seed=73)
+    params = [dev(c).requires_grad_(True) for c in cores]
+    ft, lam = tn.MPSClassifierFn.apply(px, ls, "fp32", 2, *params)
+    z = ft / ft.norm(dim=1, keepdim=True)
+    loss = torch.nn.functional.cross_entropy(z, torch.from_numpy(y).cuda())
+    loss.backward()
+    _, g_ref = oracle.classify_grad(cores, ls, px.cpu().numpy(), y)
+    for i, (p, r) in enumerate(zip(params, g_ref)):
+        err = np.linalg.norm(p.grad.double().cpu().numpy() - r) / np.linalg.norm(r)
+        assert err <= 1e-4, (i, err)
