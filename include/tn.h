@@ -123,6 +123,29 @@ size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan);
 int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
 int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
 void tn_group_plan_destroy(tn_group_plan* plan);
+/*
+ * Grouped contraction that allocates nothing: the same contractions and
+ * kernels as a plan's create + upload + run, with the work list kept in a
+ * fixed 2 MiB array inside the library instead of a caller workspace. (The
+ * paper has no counterpart; this is a convenience of the library.) It is for
+ * callers that must not call cudaMalloc: code whose device memory all belongs
+ * to another framework's pool, where an extra cudaMalloc can exceed the
+ * pool's budget and synchronises the device, and code on a latency-bound path
+ * that may only launch kernels.
+ *   specs, nspecs, prec: as tn_group_plan_create; at most 4096 specs (the
+ *     work list takes 456 bytes per spec plus 16 per split result, and 4096
+ *     specs fit in the 2 MiB array); more return TN_ERR_UNSUPPORTED and
+ *     launch nothing.
+ *   The first call on a device looks up the array's device address there
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every GPU that loads libtn.so holds the array until the process exits.
+ *   All calls share the array: calls whose work overlaps on the GPU (other
+ *   streams or host threads) race on it; calls on one stream are ordered.
+ * Errors: as tn_group_plan_create, plus TN_ERR_UNSUPPORTED (too large) and
+ * TN_ERR_CUDA.
+ */
+int tn_contract_grouped_static(const tn_contract_spec* specs, int nspecs, int prec, void* stream);
+
 /* Total floating-point work (2 M N K summed over specs) and algorithmic bytes
  * (|A| + |B| + |C| float32 elements summed over specs) of a plan. */
 double tn_group_plan_flops(const tn_group_plan* plan);
