@@ -126,15 +126,16 @@ void tn_group_plan_destroy(tn_group_plan* plan);
 /*
  * Grouped contraction that allocates nothing: the same contractions and
  * kernels as a plan's create + upload + run, with the work list kept in a
- * fixed 2 MiB array inside the library instead of a caller workspace. (The
+ * fixed 4 MiB array inside the library instead of a caller workspace. (The
  * paper has no counterpart; this is a convenience of the library.) It is for
  * callers that must not call cudaMalloc: code whose device memory all belongs
  * to another framework's pool, where an extra cudaMalloc can exceed the
  * pool's budget and synchronises the device, and code on a latency-bound path
  * that may only launch kernels.
- *   specs, nspecs, prec: as tn_group_plan_create; at most 4096 specs (the
- *     work list takes 456 bytes per spec plus 16 per split result, and 4096
- *     specs fit in the 2 MiB array); more return TN_ERR_UNSUPPORTED and
+ *   specs, nspecs, prec: as tn_group_plan_create; at most 4096 specs, and
+ *     the work list (464 bytes per spec, 16 per split result, 4 per work
+ *     unit: one 128x128 output tile over at most 2048 shared indices) must
+ *     fit in the 4 MiB array; larger requests return TN_ERR_UNSUPPORTED and
  *     launch nothing.
  *   The first call on a device looks up the array's device address there
  *   (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -39,8 +39,8 @@ static int64_t min_units_single() {
 
 static int launch_one(const ContractDesc& d, int prec, cudaStream_t stream) {
   const int64_t tiles = (int64_t)d.tiles_m * d.tiles_n * d.splits;
-  if (prec == TN_PREC_FP32) return launch_contract_simt(d, nullptr, 1, tiles, stream);
-  return launch_contract_tc(d, nullptr, 1, tiles, prec, stream);
+  if (prec == TN_PREC_FP32) return launch_contract_simt(d, nullptr, nullptr, tiles, stream);
+  return launch_contract_tc(d, nullptr, nullptr, tiles, prec, stream);
 }
 
 }  // namespace tn
@@ -51,6 +51,7 @@ struct tn_group_plan {
   std::vector<ContractDesc> descs;  // launched specs, largest first, tile_begin set
   std::vector<ContractDesc> zeros;  // specs with an empty shared index (K = 0): C = 0
   std::vector<ZeroRange> zero_ranges;  // results zeroed on the device before the launch
+  std::vector<int32_t> unit_desc;      // descriptor index of every work unit
   int prec = TN_PREC_FP32;
   int64_t total_tiles = 0;
   double flops = 0.0, bytes = 0.0;
@@ -160,18 +161,28 @@ int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn
   }
   p->total_tiles = t;
   if (t > 0x7FFFFFFF) { delete p; return TN_ERR_UNSUPPORTED; }
+  p->unit_desc.resize((size_t)t);
+  for (size_t i = 0; i < p->descs.size(); ++i) {
+    const ContractDesc& d = p->descs[i];
+    const int64_t n = (int64_t)d.tiles_m * d.tiles_n * d.splits;
+    std::fill(p->unit_desc.begin() + d.tile_begin, p->unit_desc.begin() + d.tile_begin + n, (int32_t)i);
+  }
   *plan = p;
   return TN_OK;
 }
 
-// Workspace layout: descriptors, then (256-byte aligned) the zero ranges.
+// Workspace layout (each part 256-byte aligned): descriptors, zero ranges,
+// unit -> descriptor map.
 static size_t zero_offset(const tn_group_plan* plan) {
-  return (sizeof(ContractDesc) * plan->descs.size() + 255) & ~size_t(255);
+  return align256(sizeof(ContractDesc) * plan->descs.size());
+}
+static size_t map_offset(const tn_group_plan* plan) {
+  return zero_offset(plan) + align256(sizeof(ZeroRange) * plan->zero_ranges.size());
 }
 
 size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
   if (!plan) return 0;
-  return zero_offset(plan) + sizeof(ZeroRange) * plan->zero_ranges.size();
+  return map_offset(plan) + sizeof(int32_t) * plan->unit_desc.size();
 }
 
 double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
@@ -199,6 +210,10 @@ int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t byte
       cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + zero_offset(plan), plan->zero_ranges.data(),
                       sizeof(ZeroRange) * plan->zero_ranges.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return TN_ERR_CUDA;
+  if (!plan->unit_desc.empty() &&
+      cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + map_offset(plan), plan->unit_desc.data(),
+                      sizeof(int32_t) * plan->unit_desc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
   return TN_OK;
 }
 
@@ -216,9 +231,9 @@ int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, 
     if (rc != TN_OK) return rc;
   }
   const ContractDesc* g = static_cast<const ContractDesc*>(workspace);
-  const int n = (int)plan->descs.size();
-  if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, n, plan->total_tiles, s);
-  return launch_contract_tc(plan->descs[0], g, n, plan->total_tiles, plan->prec, s);
+  const int32_t* map = reinterpret_cast<const int32_t*>(static_cast<uint8_t*>(workspace) + map_offset(plan));
+  if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, map, plan->total_tiles, s);
+  return launch_contract_tc(plan->descs[0], g, map, plan->total_tiles, plan->prec, s);
 }
 
 void tn_group_plan_destroy(tn_group_plan* plan) { delete plan; }

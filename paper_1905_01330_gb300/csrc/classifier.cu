@@ -403,7 +403,13 @@ ClsLayout cls_layout(uint8_t* base, const tn_mps* W, int ls, int L, int batch, i
   w.replay = reinterpret_cast<float*>(take(bwd && ck > 1 ? vec : 0));
   w.X = reinterpret_cast<float*>(take(bwd ? 2 * vec * (size_t)w.seg_len : 0));
   w.Y = reinterpret_cast<float*>(take(bwd ? sizeof(float) * (size_t)batch * 2 * L * w.chi : 0));
-  w.plan_bytes = bwd ? align256(sizeof(ContractDesc) * (size_t)w.seg_len) + sizeof(ZeroRange) * (size_t)w.seg_len : 0;
+  // a segment's grouped plan: descriptors, split results to zero, and the
+  // unit map (each spec: at most 2 x 1 output tiles of 128 (2 chi <= 256)
+  // times ceil(batch / 2048) k ranges)
+  const size_t units_per_spec = 2 * (size_t)((batch + 64 * MAX_SLABS_PER_UNIT - 1) / (64 * MAX_SLABS_PER_UNIT));
+  w.plan_bytes = bwd ? align256(sizeof(ContractDesc) * (size_t)w.seg_len) + align256(sizeof(ZeroRange) * (size_t)w.seg_len) +
+                           sizeof(int32_t) * (size_t)w.seg_len * units_per_spec
+                     : 0;
   w.plan_ws = take(w.plan_bytes);
   w.bytes = off;
   return w;

@@ -84,9 +84,9 @@ __device__ __forceinline__ void store_regs(SimtSmem& s, int buf, const float (&r
 
 __global__ void __launch_bounds__(NT, 2)
 simt_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDesc* group,
-                     int ndesc) {
+                     const int32_t* unit_desc) {
   __shared__ __align__(16) SimtSmem s;
-  const int64_t tile = fetch_desc(single, group, ndesc, (int64_t)blockIdx.x, &s.d, &s.idx);
+  const int64_t tile = fetch_desc(single, group, unit_desc, (int64_t)blockIdx.x, &s.d, &s.idx);
   const int t = threadIdx.x;
   if (t == 0) s.uc = decode_unit(s.d, tile, BM, BN);
   __syncthreads();
@@ -181,11 +181,12 @@ int launch_zero(const ZeroRange* ranges, int n, cudaStream_t stream) {
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
-int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, int ndesc,
+int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc,
                          int64_t total_tiles, cudaStream_t stream) {
   if (total_tiles <= 0) return TN_OK;
   if (total_tiles > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
-  simt_contract_kernel<<<(unsigned)total_tiles, NT, 0, stream>>>(single, group, ndesc);
+  if (group && !unit_desc) return TN_ERR_ARG;
+  simt_contract_kernel<<<(unsigned)total_tiles, NT, 0, stream>>>(single, group, unit_desc);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 

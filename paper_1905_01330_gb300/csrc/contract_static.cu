@@ -23,14 +23,16 @@
 namespace tn {
 namespace {
 
-constexpr size_t STATIC_SCRATCH_BYTES = 2u << 20;  // 2 MiB
+constexpr size_t STATIC_SCRATCH_BYTES = 4u << 20;  // 4 MiB
 constexpr int STATIC_MAX_SPECS = 4096;
+constexpr int64_t STATIC_MAX_UNITS = 1 << 20;  // bound of the host staging map; the array bounds it further
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
 // Host staging for the work list (no heap allocation per call).
 static ContractDesc h_descs[STATIC_MAX_SPECS];
 static ZeroRange h_zero[STATIC_MAX_SPECS];
+static int32_t h_units[STATIC_MAX_UNITS];
 static std::mutex h_lock;
 
 // Device address of g_static_scratch on each device, looked up once per
@@ -97,9 +99,14 @@ extern "C" int tn_contract_grouped_static(const tn_contract_spec* specs, int nsp
     tiles += (int64_t)h_descs[i].tiles_m * h_descs[i].tiles_n * h_descs[i].splits;
     if (h_descs[i].splits > 1) h_zero[nz++] = ZeroRange{h_descs[i].C, h_descs[i].M * h_descs[i].N};
   }
-  if (tiles > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (tiles > STATIC_MAX_UNITS) return TN_ERR_UNSUPPORTED;
   const size_t desc_bytes = align256(sizeof(ContractDesc) * (size_t)nd);
-  if (desc_bytes + sizeof(ZeroRange) * (size_t)nz > STATIC_SCRATCH_BYTES) return TN_ERR_UNSUPPORTED;
+  const size_t zero_bytes = align256(sizeof(ZeroRange) * (size_t)nz);
+  if (desc_bytes + zero_bytes + sizeof(int32_t) * (size_t)tiles > STATIC_SCRATCH_BYTES) return TN_ERR_UNSUPPORTED;
+  for (int i = 0; i < nd; ++i) {
+    const int64_t n = (int64_t)h_descs[i].tiles_m * h_descs[i].tiles_n * h_descs[i].splits;
+    for (int64_t k = 0; k < n; ++k) h_units[h_descs[i].tile_begin + k] = i;
+  }
 
   // Every call rewrites the whole work list it reads; nothing in the array
   // needs to start at zero. Pageable sources: each copy returns once staged.
@@ -110,9 +117,13 @@ extern "C" int tn_contract_grouped_static(const tn_contract_spec* specs, int nsp
   if (nz > 0 && cudaMemcpyAsync(zdev, h_zero, sizeof(ZeroRange) * (size_t)nz, cudaMemcpyHostToDevice, s) !=
                     cudaSuccess)
     return TN_ERR_CUDA;
+  int32_t* map = reinterpret_cast<int32_t*>(scratch + desc_bytes + zero_bytes);
+  if (tiles > 0 && cudaMemcpyAsync(map, h_units, sizeof(int32_t) * (size_t)tiles, cudaMemcpyHostToDevice, s) !=
+                       cudaSuccess)
+    return TN_ERR_CUDA;
   if (nz > 0 && (rc = launch_zero(zdev, nz, s)) != TN_OK) return rc;
   if (tiles == 0) return TN_OK;
   const ContractDesc* g = reinterpret_cast<const ContractDesc*>(scratch);
-  if (prec == TN_PREC_FP32) return launch_contract_simt(h_descs[0], g, nd, tiles, s);
-  return launch_contract_tc(h_descs[0], g, nd, tiles, prec, s);
+  if (prec == TN_PREC_FP32) return launch_contract_simt(h_descs[0], g, map, tiles, s);
+  return launch_contract_tc(h_descs[0], g, map, tiles, prec, s);
 }

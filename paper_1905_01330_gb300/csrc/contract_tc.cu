@@ -7,17 +7,28 @@
 //   BF16X3 : x = hi + lo (hi = bf16(x), lo = bf16(x - hi)); three MMAs per
 //            k step, Ahi*Bhi + Ahi*Blo + Alo*Bhi, into the same accumulator.
 //
-// Roles in a 288-thread CTA computing one 128x128 output tile:
-//   warps 0-7 (converters): gather 128x64 float32 slabs of A and B in place
-//     through the operands' leg strides (the permutation is folded into the
-//     gather: no transposed copy exists anywhere), round to bf16 (and split),
-//     and store them into the 128-byte-swizzled K-major shared-memory layout
-//     the MMA descriptors describe; a ring of stages is handed over with
-//     mbarriers. After the k loop they drain TMEM (tcgen05.ld) and write C.
-//   warp 8 (MMA): allocates TMEM, and one lane issues tcgen05.mma for each
-//     stage, releasing stages with tcgen05.commit.
+// Persistent kernel: one 512-thread CTA per SM walks the work units
+// blockIdx.x, blockIdx.x + gridDim.x, ... (a unit is one 128x128 output tile
+// and one k range; the host sorts units largest first). Barriers and TMEM are
+// set up once per CTA; the next unit's descriptor is fetched by a 1-D bulk
+// async copy while the current unit runs.
+//
+// Every thread is a converter: the CTA gathers 128x64 float32 slabs of A and B
+// in place through the operands' leg strides (the permutation is folded into
+// the gather: no transposed copy exists anywhere), rounds them to bf16 (and
+// splits them), and stores them into the 128-byte-swizzled K-major shared-
+// memory layout the MMA descriptors describe, in a ring of stages. The offset
+// tables of the next slabs are decoded ahead, and for BF16 the loads of slab
+// k+1 stay in flight while slab k is converted. A named barrier closes each
+// slab; right after it one thread issues the slab's tcgen05.mma instructions
+// (the barrier orders every converter's fenced stores before them) and
+// commits them to the stage's `empty` barrier, which the converters wait on
+// before they reuse the stage. After a unit's k loop the 16 warps drain TMEM
+// and write C. 16 warps get 128 registers each (the register file is split
+// between the SM's four sub-partitions): two units per thread and operand,
+// twice that in flight when pipelined.
 // Every mbarrier wait is bounded (2 s of wall time); on expiry the kernel
-// records TN_ERR_TIMEOUT, stops, frees its TMEM and returns.
+// records TN_ERR_TIMEOUT, stops all units, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "gather.cuh"
@@ -27,46 +38,48 @@ namespace tn {
 namespace {
 
 constexpr int BM = TC_BM, BN = TC_BN, BK = 64;
-constexpr int NPROD = 256;             // converter threads (warps 0-7)
-constexpr int NTHREADS = NPROD + 32;   // + MMA warp
+constexpr int NTHREADS = 512;
+constexpr int UNITS = BM * (BK / 8);     // (row, 8-wide k group) units of one operand slab
+constexpr int UPT = UNITS / NTHREADS;    // units per thread and operand (2)
 constexpr int TILE_BYTES = BM * BK * 2;  // one 128x64 bf16 operand tile (16 KB)
+constexpr int TS = 3;                    // ring of shared-index offset tables
 // BF16X3 promotes the tensor-core accumulator into float32 registers every
 // KC k-slabs (KC * 64 = 256 shared indices): the tensor core's float32
 // accumulation truncates, and over long K that error (linear in the number
 // of accumulation steps) would exceed the split's own rounding error.
 constexpr int KC = 4;
-template <int SPLIT>
-constexpr uint32_t tmem_cols() { return SPLIT ? 2 * BN : BN; }  // f32 accumulators, 128 lanes each
 
 template <int SPLIT>
-struct TcCfg {
-  static constexpr int STAGES = 3;
-  static constexpr int OPS = SPLIT ? 4 : 2;  // tiles per stage: Ahi, Bhi (, Alo, Blo)
+struct Cfg {
+  static constexpr bool PIPE = !SPLIT;                       // loads of slab k+1 overlap slab k
+  static constexpr int STAGES = SPLIT ? 3 : 4;
+  static constexpr int OPS = SPLIT ? 4 : 2;                  // tiles per stage: Ahi, Bhi (, Alo, Blo)
   static constexpr int STAGE_BYTES = OPS * TILE_BYTES;
+  static constexpr uint32_t TMEM_COLS = SPLIT ? 2 * BN : BN; // f32 accumulators, 128 lanes each
 };
 
 template <int S>
 struct TcAux {
+  ContractDesc dslot[2];    // descriptors of this and the next unit (16-byte aligned)
   int32_t rowA[BM];
   int32_t rowB[BN];
-  int32_t kA[S][BK];
-  int32_t kB[S][BK];
-  int32_t kcA[S][BK / 8];  // 1: the 8-wide k group is unit-stride in A
-  int32_t kcB[S][BK / 8];
-  uint64_t full[S];
-  uint64_t empty[S];
-  uint64_t accum;
-  uint64_t chunk_full[2];  // BF16X3: accumulator buffer b holds a finished chunk
-  uint64_t drained[2];     // BF16X3: buffer b was read back and may be overwritten
+  int32_t kA[TS][BK];
+  int32_t kB[TS][BK];
+  int32_t kcA[TS][BK / 8];  // 1: the 8-wide k group is unit-stride in A
+  int32_t kcB[TS][BK / 8];
+  uint64_t empty[S];        // the MMAs reading stage s are complete
+  uint64_t accum;           // a unit's accumulator is final
+  uint64_t chunk_full[2];   // BF16X3: accumulator buffer b holds a finished chunk
+  uint64_t desc_bar[2];     // descriptor slot b has landed
+  uint64_t final_bar;       // all MMAs of the issuing thread are complete
   uint32_t tmem_base;
-  int32_t idx;
-  ContractDesc d;
+  int32_t abort;            // a bounded wait expired somewhere in the CTA
 };
 
 template <int SPLIT>
 constexpr size_t tc_smem_bytes() {
-  return 1024 /* alignment slack */ + (size_t)TcCfg<SPLIT>::STAGES * TcCfg<SPLIT>::STAGE_BYTES +
-         sizeof(TcAux<TcCfg<SPLIT>::STAGES>);
+  using C = Cfg<SPLIT>;
+  return 1024 /* alignment slack */ + (size_t)C::STAGES * C::STAGE_BYTES + sizeof(TcAux<C::STAGES>);
 }
 
 // Byte offset of the 16-byte chunk (row r, k group g) in a 128B-swizzled
@@ -129,205 +142,246 @@ __device__ __forceinline__ void store_unit(uint8_t* hi_tile, uint8_t* lo_tile, i
   }
 }
 
-// k-group contiguity: the 8 indices k0..k0+7 are all < K and consecutive in
-// memory (innermost shared leg has unit stride and the group does not wrap).
+// k-group contiguity: the 8 indices k0..k0+7 are all < k_end and consecutive
+// in memory (innermost shared leg has unit stride and the group does not wrap).
 __device__ __forceinline__ int group_contiguous(const ContractDesc& d, int64_t k0, int64_t k_end,
                                                 const int64_t* kstr) {
   if (d.nk == 0 || k0 + 8 > k_end) return 0;
   const int last = d.nk - 1;
   if (kstr[last] != 1) return 0;
-  const int64_t dl = d.kdim[last];
-  return ((k0 % dl) + 8 <= dl) ? 1 : 0;
+  const uint32_t dl = (uint32_t)d.kdim[last];
+  return (((uint32_t)k0 % dl) + 8 <= dl) ? 1 : 0;
+}
+
+// Shared-index offsets of slab kt into table slot kt % TS (threads 0-127: 64
+// for A, 64 for B; the first thread of each 8-group also records whether the
+// group is unit-stride).
+template <class Aux>
+__device__ __forceinline__ void fill_table(const ContractDesc& d, const UnitCoord& uc, int64_t kt, Aux& x) {
+  const int t = threadIdx.x;
+  if (t >= 2 * BK) return;
+  const int slot = (int)(kt % TS);
+  const int jj = t & (BK - 1);
+  const int64_t k = uc.k_begin + kt * BK + jj;
+  const bool isA = t < BK;
+  const int64_t* kstr = isA ? d.kstrA : d.kstrB;
+  const int32_t off = (k < uc.k_end) ? (int32_t)leg_offset((uint32_t)k, d.nk, d.kdim, kstr) : -1;
+  if (isA) x.kA[slot][jj] = off;
+  else x.kB[slot][jj] = off;
+  if ((jj & 7) == 0) {
+    const int c = group_contiguous(d, k, uc.k_end, kstr);
+    if (isA) x.kcA[slot][jj >> 3] = c;
+    else x.kcB[slot][jj >> 3] = c;
+  }
+}
+
+// (row, k group) of unit i of thread t: consecutive threads walk the
+// operand's unit-stride direction (k when kfast, else the row).
+__device__ __forceinline__ void unit_coord(int kfast, int t, int i, int& r, int& g) {
+  const int uu = t + NTHREADS * i;
+  r = kfast ? (uu >> 3) : (uu & (BM - 1));
+  g = kfast ? (uu & 7) : (uu >> 7);
+}
+
+template <class Aux>
+__device__ __forceinline__ void load_slab(const ContractDesc& d, const Aux& x, int slot, int t,
+                                          float (&va)[UPT][8], float (&vb)[UPT][8]) {
+#pragma unroll
+  for (int i = 0; i < UPT; ++i) {
+    int r, g;
+    unit_coord(d.a_kfast, t, i, r, g);
+    load_unit(d.A, x.rowA[r], &x.kA[slot][g * 8], x.kcA[slot][g], va[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < UPT; ++i) {
+    int r, g;
+    unit_coord(d.b_kfast, t, i, r, g);
+    load_unit(d.B, x.rowB[r], &x.kB[slot][g * 8], x.kcB[slot][g], vb[i]);
+  }
 }
 
 template <int SPLIT>
-__global__ void __launch_bounds__(NTHREADS, SPLIT ? 1 : 2)
+__device__ __forceinline__ void store_slab(const ContractDesc& d, int t, uint8_t* st, const float (&va)[UPT][8],
+                                           const float (&vb)[UPT][8]) {
+#pragma unroll
+  for (int i = 0; i < UPT; ++i) {
+    int r, g;
+    unit_coord(d.a_kfast, t, i, r, g);
+    store_unit<SPLIT>(st, st + 2 * TILE_BYTES, r, g, va[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < UPT; ++i) {
+    int r, g;
+    unit_coord(d.b_kfast, t, i, r, g);
+    store_unit<SPLIT>(st + TILE_BYTES, st + 3 * TILE_BYTES, r, g, vb[i]);
+  }
+}
+
+// Writes (splits == 1) or accumulates (split-K) 32 consecutive results of
+// row m starting at column n0 + col.
+__device__ __forceinline__ void write_row32(const ContractDesc& d, int64_t m, int64_t n0, int col,
+                                            const uint32_t (&r)[32]) {
+  if (m >= d.M) return;
+  float* __restrict__ C = d.C;
+  const int64_t N = d.N;
+  const bool vec = ((N & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+  const bool accumulate = d.splits > 1;
+  float* dst = C + m * N + n0 + col;
+  const int64_t nrem = N - (n0 + col);
+#pragma unroll
+  for (int i = 0; i < 32; i += 4)
+    if (i < nrem)
+      emit4(dst + i, vec, nrem - i, accumulate, __uint_as_float(r[i]), __uint_as_float(r[i + 1]),
+            __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(NTHREADS, 1)
 tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDesc* group,
-                   int ndesc, int* status) {
-  using Cfg = TcCfg<SPLIT>;
-  constexpr int S = Cfg::STAGES;
+                   const int32_t* unit_desc, int64_t total_units, int* status) {
+  using C = Cfg<SPLIT>;
+  constexpr int S = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  TcAux<S>& x = *reinterpret_cast<TcAux<S>*>(smem + (size_t)S * Cfg::STAGE_BYTES);
+  TcAux<S>& x = *reinterpret_cast<TcAux<S>*>(smem + (size_t)S * C::STAGE_BYTES);
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
+  const bool grouped = group != nullptr;
+  constexpr uint32_t DESC_BYTES = (uint32_t)sizeof(ContractDesc);
+  static_assert(sizeof(ContractDesc) % 16 == 0, "bulk copies move multiples of 16 bytes");
+  const bool issuer = (t == 0);    // issues the MMAs
+  const bool fetcher = (t == 32);  // prefetches descriptors
 
-  if (t == 0) {
-    for (int s = 0; s < S; ++s) {
-      ptx::mbar_init(ptx::smem_addr(&x.full[s]), NPROD);
-      ptx::mbar_init(ptx::smem_addr(&x.empty[s]), 1);
-    }
+  if (issuer) {
+    for (int s = 0; s < S; ++s) ptx::mbar_init(ptx::smem_addr(&x.empty[s]), 1);
     ptx::mbar_init(ptx::smem_addr(&x.accum), 1);
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_addr(&x.chunk_full[b]), 1);
-      ptx::mbar_init(ptx::smem_addr(&x.drained[b]), NPROD);
+      ptx::mbar_init(ptx::smem_addr(&x.desc_bar[b]), 1);
     }
+    ptx::mbar_init(ptx::smem_addr(&x.final_bar), 1);
+    x.abort = 0;
     ptx::fence_mbar_init();
+    if (grouped) {
+      ptx::mbar_arrive_expect_tx(ptx::smem_addr(&x.desc_bar[0]), DESC_BYTES);
+      ptx::bulk_copy_g2s(ptx::smem_addr(&x.dslot[0]), group + unit_desc[blockIdx.x], DESC_BYTES,
+                         ptx::smem_addr(&x.desc_bar[0]));
+    } else {
+      x.dslot[0] = single;
+      x.dslot[1] = single;
+    }
   }
-  if (warp == 8) {
-    ptx::tmem_alloc(ptx::smem_addr(&x.tmem_base), tmem_cols<SPLIT>());
+  if (warp == 0) {
+    ptx::tmem_alloc(ptx::smem_addr(&x.tmem_base), C::TMEM_COLS);
     ptx::tmem_relinquish();
-    ptx::tc_fence_before();
   }
-  const int64_t tile = fetch_desc(single, group, ndesc, (int64_t)blockIdx.x, &x.d, &x.idx);
-  // fetch_desc ends with __syncthreads(): barriers and the TMEM base are visible.
+  // the fetcher keeps the descriptor index of the unit after next in a
+  // register, so its global load overlaps a whole unit
+  int next_idx = 0;
+  if (fetcher && grouped && blockIdx.x + gridDim.x < total_units) next_idx = unit_desc[blockIdx.x + gridDim.x];
+  ptx::tc_fence_before();
+  __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = x.tmem_base;
-  const ContractDesc& d = x.d;
-  const UnitCoord uc = decode_unit(d, tile, BM, BN);
-  const int64_t m0 = uc.m0, n0 = uc.n0;
-  const int64_t nkt = (uc.k_end - uc.k_begin + BK - 1) / BK;
   const uint32_t stage0 = ptx::smem_addr(smem);
+  constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
+  const int q = warp & 3, cb = warp >> 2;  // TMEM lane quadrant and 32-column block of this warp
 
-  if (warp < 8) {
-    // ------------------------------------------------------------ converters
+  uint32_t g_slab = 0;   // slabs processed by this CTA (stage ring position)
+  uint32_t g_chunk = 0;  // BF16X3 accumulator chunks processed by this CTA
+  uint32_t j = 0;        // units processed by this CTA
+  for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x, ++j) {
+    if (x.abort) break;  // uniform: read after the barrier that ends each unit
+    const int slot = grouped ? (int)(j & 1) : 0;
+    // prefetch the next unit's descriptor into the other slot (free: every
+    // thread finished the previous unit before the barrier that ended it)
+    if (fetcher && grouped && u + gridDim.x < total_units) {
+      ptx::mbar_arrive_expect_tx(ptx::smem_addr(&x.desc_bar[slot ^ 1]), DESC_BYTES);
+      ptx::bulk_copy_g2s(ptx::smem_addr(&x.dslot[slot ^ 1]), group + next_idx, DESC_BYTES,
+                         ptx::smem_addr(&x.desc_bar[slot ^ 1]));
+      const int64_t u2 = u + 2 * (int64_t)gridDim.x;
+      if (u2 < total_units) next_idx = unit_desc[u2];
+    }
+    bool ok = true;
+    if (grouped) ok = ptx::mbar_wait(ptx::smem_addr(&x.desc_bar[slot]), (j >> 1) & 1u, status);
+    ok = __syncthreads_and(ok) != 0;  // CTA-uniform: every thread runs the same slab count
+    const ContractDesc& d = x.dslot[slot];
+    const UnitCoord uc = decode_unit(d, ok ? u - d.tile_begin : 0, BM, BN);
+    const int64_t m0 = uc.m0, n0 = uc.n0;
+    const int64_t nkt = ok ? (uc.k_end - uc.k_begin + BK - 1) / BK : 0;
+    const int64_t nchunks = (nkt + KC - 1) / KC;
+
     if (t < BM) {
       const int64_t m = m0 + t;
       x.rowA[t] = (m < d.M) ? (int32_t)leg_offset((uint32_t)m, d.nm, d.mdim, d.mstr) : -1;
-    } else {
+    } else if (t < BM + BN) {
       const int64_t n = n0 + (t - BM);
       x.rowB[t - BM] = (n < d.N) ? (int32_t)leg_offset((uint32_t)n, d.nn, d.ndim, d.nstr) : -1;
     }
-    bool ok = true;
-    const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant and column half of this warp
-    float acc[SPLIT ? 64 : 1];
+    float acc[SPLIT ? 32 : 1];
 #pragma unroll
-    for (int j = 0; j < (SPLIT ? 64 : 1); ++j) acc[j] = 0.0f;
-    const int64_t nchunks = (nkt + KC - 1) / KC;
-    int64_t next_drain = 0;
-    // BF16X3: adds finished chunk c (accumulator buffer c & 1) into acc
+    for (int i = 0; i < (SPLIT ? 32 : 1); ++i) acc[i] = 0.0f;
+    // BF16X3: adds finished chunk c of this unit (accumulator buffer c & 1)
+    // into acc; the MMAs that reuse the buffer are issued after a later
+    // barrier, so program order protects it
     auto drain = [&](int64_t c) -> bool {
-      const int b = (int)(c & 1);
-      const bool w = ptx::mbar_wait(ptx::smem_addr(&x.chunk_full[b]), (uint32_t)((c >> 1) & 1), status);
+      const uint32_t cg = g_chunk + (uint32_t)c;
+      const int b = (int)(cg & 1);
+      const bool w = ptx::mbar_wait(ptx::smem_addr(&x.chunk_full[b]), (cg >> 1) & 1u, status);
       if (!__all_sync(0xffffffffu, w)) return false;
       ptx::tc_fence_after();
+      uint32_t r[32];
+      ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + cb * 32), r);
+      ptx::tmem_ld_wait();
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t r[32];
-        ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * 64 + half * 32), r);
-        ptx::tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[half * 32 + j] += __uint_as_float(r[j]);
-      }
+      for (int i = 0; i < 32; ++i) acc[i] += __uint_as_float(r[i]);
       ptx::tc_fence_before();
-      ptx::mbar_arrive(ptx::smem_addr(&x.drained[b]));
       return true;
     };
-    for (int64_t kt = 0; kt < nkt; ++kt) {
-      const int s = (int)(kt % S);
-      const uint32_t round = (uint32_t)(kt / S);
+    int64_t next_drain = 0;
+
+    // two register sets used in turn (the loop below is unrolled by two), so
+    // the loads of slab k+1 are consumed only in the next slab's step
+    float ra0[UPT][8], rb0[UPT][8], ra1[UPT][8], rb1[UPT][8];
+    // One slab: decode tables ahead, gather (pipelined: the next slab into
+    // the other set), wait for the stage, convert and store the current set,
+    // close the slab with the barrier, issue its MMAs. Returns false when a
+    // bounded wait expired anywhere in the CTA.
+    auto slab = [&](int64_t kt, float (&cur_a)[UPT][8], float (&cur_b)[UPT][8], float (&nxt_a)[UPT][8],
+                    float (&nxt_b)[UPT][8]) -> bool {
+      const uint32_t gs = g_slab + (uint32_t)kt;
+      const int s = (int)(gs % S);
+      const uint32_t round = gs / S;
+      if (C::PIPE) {
+        // tables of slab kt+2 (slot last read by the loads of slab kt-1,
+        // issued before the previous barrier)
+        if (kt + 2 < nkt) fill_table(d, uc, kt + 2, x);
+        if (kt + 1 < nkt) load_slab(d, x, (int)((kt + 1) % TS), t, nxt_a, nxt_b);
+      } else {
+        if (kt + 1 < nkt) fill_table(d, uc, kt + 1, x);
+        load_slab(d, x, (int)(kt % TS), t, cur_a, cur_b);
+      }
       bool drained_ok = true;
-      if (SPLIT && (kt % KC) == 0 && kt / KC >= 2) {
-        drained_ok = drain(next_drain);
-        ++next_drain;
-      }
+      if (SPLIT && (kt % KC) == 0 && kt / KC >= 2) drained_ok = drain(next_drain++);
+      // the stage's previous MMAs must be complete before it is rewritten
       const bool waited = ptx::mbar_wait(ptx::smem_addr(&x.empty[s]), (round & 1u) ^ 1u, status) && drained_ok;
-      // decode this slab's shared-index offsets (tables only; the stage itself
-      // is written after the collective check below)
-      if (t < 2 * BK) {
-        const int j = t & (BK - 1);
-        const int64_t k = uc.k_begin + kt * BK + j;
-        const bool isA = t < BK;
-        const int64_t* kstr = isA ? d.kstrA : d.kstrB;
-        const int32_t off = (k < uc.k_end) ? (int32_t)leg_offset((uint32_t)k, d.nk, d.kdim, kstr) : -1;
-        if (isA) x.kA[s][j] = off; else x.kB[s][j] = off;
-        if ((j & 7) == 0) {
-          const int c = group_contiguous(d, k, uc.k_end, kstr);
-          if (isA) x.kcA[s][j >> 3] = c; else x.kcB[s][j >> 3] = c;
-        }
+      if (waited) {
+        store_slab<SPLIT>(d, t, smem + (size_t)s * C::STAGE_BYTES, cur_a, cur_b);
+        ptx::fence_proxy_async_smem();
       }
-      // every converter reaches this barrier once per slab; a wait that
-      // expired anywhere stops all of them together
-      if (ptx::named_barrier_or(1, NPROD, !waited)) { ok = false; break; }
-
-      uint8_t* st = smem + (size_t)s * Cfg::STAGE_BYTES;
-      float va[4][8], vb[4][8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int u = t + NPROD * i;
-        const int r = d.a_kfast ? (u >> 3) : (u & (BM - 1));
-        const int g = d.a_kfast ? (u & 7) : (u >> 7);
-        load_unit(d.A, x.rowA[r], &x.kA[s][g * 8], x.kcA[s][g], va[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int u = t + NPROD * i;
-        const int r = d.b_kfast ? (u >> 3) : (u & (BN - 1));
-        const int g = d.b_kfast ? (u & 7) : (u >> 7);
-        load_unit(d.B, x.rowB[r], &x.kB[s][g * 8], x.kcB[s][g], vb[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int u = t + NPROD * i;
-        const int r = d.a_kfast ? (u >> 3) : (u & (BM - 1));
-        const int g = d.a_kfast ? (u & 7) : (u >> 7);
-        store_unit<SPLIT>(st, st + 2 * TILE_BYTES, r, g, va[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int u = t + NPROD * i;
-        const int r = d.b_kfast ? (u >> 3) : (u & (BN - 1));
-        const int g = d.b_kfast ? (u & 7) : (u >> 7);
-        store_unit<SPLIT>(st + TILE_BYTES, st + 3 * TILE_BYTES, r, g, vb[i]);
-      }
-      ptx::fence_proxy_async_smem();
-      ptx::mbar_arrive(ptx::smem_addr(&x.full[s]));
-    }
-
-    // -------------------------------------------------------------- epilogue
-    if (SPLIT) {
-      for (; ok && next_drain < nchunks; ++next_drain) ok = drain(next_drain);
-    }
-    const bool acc_ready = ptx::mbar_wait(ptx::smem_addr(&x.accum), 0u, status) && ok;
-    if (__all_sync(0xffffffffu, acc_ready)) {  // tcgen05.ld is warp-collective
-      ptx::tc_fence_after();
-      const int64_t m = m0 + q * 32 + lane;
-      float* __restrict__ C = d.C;
-      const int64_t N = d.N;
-      const bool vec = ((N & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int col = h * 64 + half * 32;
-        uint32_t r[32];
-        if (SPLIT) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(acc[half * 32 + j]);
-        } else {
-          ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
-          ptx::tmem_ld_wait();
-        }
-        if (m < d.M) {
-          float* dst = C + m * N + n0 + col;
-          const int64_t nrem = N - (n0 + col);
-          const bool accumulate = d.splits > 1;
-#pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            if (j < nrem)
-              emit4(dst + j, vec, nrem - j, accumulate, __uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                    __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-        }
-      }
-    }
-  } else {
-    // ------------------------------------------------------------ MMA warp
-    constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
-    if (lane == 0) {
-      for (int64_t kt = 0; kt < nkt; ++kt) {
-        const int s = (int)(kt % S);
-        const uint32_t round = (uint32_t)(kt / S);
-        const int64_t c = kt / KC;
-        const bool chunk_start = (kt % KC) == 0;
-        if (SPLIT && chunk_start && c >= 2) {
-          // the converters must have read this buffer's previous chunk back
-          if (!ptx::mbar_wait(ptx::smem_addr(&x.drained[c & 1]), (uint32_t)(((c >> 1) - 1) & 1), status)) break;
-          ptx::tc_fence_after();
-        }
-        if (!ptx::mbar_wait(ptx::smem_addr(&x.full[s]), round & 1u, status)) break;
+      // every thread reaches this barrier once per slab (it also publishes
+      // the tables filled above); a wait that expired anywhere stops all of
+      // them together
+      ptx::tc_fence_before();
+      if (ptx::named_barrier_or(1, NTHREADS, !waited)) return false;
+      if (issuer) {
         ptx::tc_fence_after();
-        const uint32_t d_tmem = SPLIT ? tmem + (uint32_t)((c & 1) * BN) : tmem;
-        const bool fresh = SPLIT ? chunk_start : (kt == 0);
-        const uint32_t a_hi = stage0 + (uint32_t)(s * Cfg::STAGE_BYTES);
+        const int64_t c = kt / KC;
+        const uint32_t cg = g_chunk + (uint32_t)c;
+        const uint32_t d_tmem = SPLIT ? tmem + (uint32_t)((cg & 1) * BN) : tmem;
+        const bool fresh = SPLIT ? (kt % KC) == 0 : (kt == 0);
+        const uint32_t a_hi = stage0 + (uint32_t)(s * C::STAGE_BYTES);
         const uint32_t b_hi = a_hi + TILE_BYTES;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
@@ -342,29 +396,81 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
           }
         }
         ptx::mma_commit(ptx::smem_addr(&x.empty[s]));
-        if (SPLIT && ((kt % KC) == KC - 1 || kt == nkt - 1)) ptx::mma_commit(ptx::smem_addr(&x.chunk_full[c & 1]));
+        if (SPLIT && ((kt % KC) == KC - 1 || kt == nkt - 1)) ptx::mma_commit(ptx::smem_addr(&x.chunk_full[cg & 1]));
       }
-      if (nkt == 0) {
-        // K = 0 never reaches the kernel (the host writes zeros); keep the
-        // epilogue's wait well defined anyway.
-        ptx::mbar_arrive(ptx::smem_addr(&x.accum));
-      } else {
-        ptx::mma_commit(ptx::smem_addr(&x.accum));
-      }
+      __syncwarp();
+      return true;
+    };
+    // prologue: offset tables of the first slabs (and, pipelined, the
+    // registers of slab 0)
+    if (nkt > 0) fill_table(d, uc, 0, x);
+    if (C::PIPE && nkt > 1) fill_table(d, uc, 1, x);
+    ptx::named_barrier(1, NTHREADS);
+    if (C::PIPE && nkt > 0) load_slab(d, x, 0, t, ra0, rb0);
+    for (int64_t kt = 0; kt < nkt; kt += 2) {
+      if (!slab(kt, ra0, rb0, ra1, rb1)) { ok = false; break; }
+      if (kt + 1 < nkt && !slab(kt + 1, ra1, rb1, ra0, rb0)) { ok = false; break; }
+    }
+    // one arrival per unit on accum: a commit tracking this unit's MMAs, or a
+    // plain arrive when none were issued
+    if (issuer) {
+      if (ok && nkt > 0) ptx::mma_commit(ptx::smem_addr(&x.accum));
+      else ptx::mbar_arrive(ptx::smem_addr(&x.accum));
     }
     __syncwarp();
+
+    // -------------------------------------------------------------- epilogue
+    if (SPLIT) {
+      for (; ok && next_drain < nchunks; ++next_drain) ok = drain(next_drain);
+    }
+    const bool acc_ready = ptx::mbar_wait(ptx::smem_addr(&x.accum), j & 1u, status) && ok;
+    if (__all_sync(0xffffffffu, acc_ready) && nkt > 0) {  // tcgen05.ld is warp-collective
+      ptx::tc_fence_after();
+      const int64_t m = m0 + q * 32 + lane;
+      uint32_t r[32];
+      if (SPLIT) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(acc[i]);
+      } else {
+        ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), r);
+        ptx::tmem_ld_wait();
+      }
+      write_row32(d, m, n0, cb * 32, r);
+    }
+    if (!ok || !acc_ready) x.abort = 1;
+    g_slab += (uint32_t)nkt;
+    g_chunk += (uint32_t)nchunks;
+    // end of unit: TMEM drained, descriptor slot and offset tables free
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
   }
 
-  ptx::tc_fence_before();
-  __syncthreads();
-  if (warp == 8) {
+  // every MMA of the issuing thread has completed before TMEM is released
+  if (warp == 0) {
+    if (issuer) {
+      ptx::mma_commit(ptx::smem_addr(&x.final_bar));
+      ptx::mbar_wait(ptx::smem_addr(&x.final_bar), 0u, status);
+    }
+    __syncwarp();
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, tmem_cols<SPLIT>());
+    ptx::tmem_dealloc(tmem, C::TMEM_COLS);
   }
 }
 
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return sms;
+}
+
 template <int SPLIT>
-int launch_tc(const ContractDesc& single, const ContractDesc* group, int ndesc, int64_t tiles,
+int launch_tc(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc, int64_t units,
               cudaStream_t stream) {
   const size_t smem = tc_smem_bytes<SPLIT>();
   static bool attr_set = false;  // per process; every device gets the same attribute value
@@ -374,19 +480,21 @@ int launch_tc(const ContractDesc& single, const ContractDesc* group, int ndesc, 
       return TN_ERR_CUDA;
     attr_set = true;
   }
-  tc_contract_kernel<SPLIT><<<(unsigned)tiles, NTHREADS, smem, stream>>>(single, group, ndesc,
-                                                                         status_word());
+  const int64_t resident = (int64_t)sm_count();
+  const unsigned grid = (unsigned)(units < resident ? units : resident);
+  tc_contract_kernel<SPLIT><<<grid, NTHREADS, smem, stream>>>(single, group, unit_desc, units, status_word());
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
 }  // namespace
 
-int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, int ndesc,
+int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc,
                        int64_t total_tiles, int prec, cudaStream_t stream) {
   if (total_tiles <= 0) return TN_OK;
   if (total_tiles > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
-  if (prec == TN_PREC_BF16) return launch_tc<0>(single, group, ndesc, total_tiles, stream);
-  if (prec == TN_PREC_BF16X3) return launch_tc<1>(single, group, ndesc, total_tiles, stream);
+  if (group && !unit_desc) return TN_ERR_ARG;
+  if (prec == TN_PREC_BF16) return launch_tc<0>(single, group, unit_desc, total_tiles, stream);
+  if (prec == TN_PREC_BF16X3) return launch_tc<1>(single, group, unit_desc, total_tiles, stream);
   return TN_ERR_ARG;
 }
 

@@ -18,24 +18,13 @@ __device__ __forceinline__ int64_t leg_offset(uint32_t idx, int n, const int32_t
   return off;
 }
 
-// Copies the descriptor that owns global tile `tile` into shared memory and
-// returns the tile's index within it. `group` is sorted by tile_begin.
+// Copies the descriptor that owns global work unit `tile` (looked up in the
+// unit -> descriptor map) into shared memory and returns the unit's index
+// within its descriptor.
 __device__ __forceinline__ int64_t fetch_desc(const ContractDesc& single, const ContractDesc* group,
-                                              int ndesc, int64_t tile, ContractDesc* sd,
+                                              const int32_t* unit_desc, int64_t tile, ContractDesc* sd,
                                               int* s_idx) {
-  if (threadIdx.x == 0) {
-    int idx = 0;
-    if (group) {
-      int lo = 0, hi = ndesc - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (group[mid].tile_begin <= tile) lo = mid;
-        else hi = mid - 1;
-      }
-      idx = lo;
-    }
-    *s_idx = idx;
-  }
+  if (threadIdx.x == 0) *s_idx = group ? unit_desc[tile] : 0;
   __syncthreads();
   const ContractDesc* src = group ? group + *s_idx : &single;
   const int nwords = (int)(sizeof(ContractDesc) / sizeof(int32_t));

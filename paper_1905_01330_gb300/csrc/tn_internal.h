@@ -28,6 +28,7 @@ struct ContractDesc {
   int32_t pad0;
   int64_t k_per_split; // shared indices per k range (a multiple of 64)
   int64_t tile_begin;  // first global work unit of this spec in a grouped launch
+  int64_t pad1;        // size a multiple of 16 bytes (bulk async copies)
   int32_t mdim[TN_MAX_RANK];
   int32_t ndim[TN_MAX_RANK];
   int32_t kdim[TN_MAX_RANK];
@@ -42,13 +43,14 @@ struct ContractDesc {
 int plan_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
                   int nshared, const tn_tensor* C, ContractDesc* d);
 
-// Launchers. `group` (device array of ndesc descriptors sorted by decreasing
-// unit work, tile_begin filled) is used when non-null; otherwise `single` is.
+// Launchers. `group` (device array of descriptors sorted by decreasing unit
+// work, tile_begin filled) with `unit_desc` (device array: descriptor index of
+// every global work unit) is used when non-null; otherwise `single` is.
 // Work unit u of a spec: tn = u % tiles_n, tm = (u / tiles_n) % tiles_m,
 // split = u / (tiles_n * tiles_m).
-int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, int ndesc,
+int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc,
                          int64_t total_tiles, cudaStream_t stream);
-int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, int ndesc,
+int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc,
                        int64_t total_tiles, int prec, cudaStream_t stream);
 
 // Tile shapes of the kernels (used by the planner to count tiles).
