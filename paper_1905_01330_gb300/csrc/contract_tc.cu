@@ -7,7 +7,7 @@
 //   BF16X3 : x = hi + lo (hi = bf16(x), lo = bf16(x - hi)); three MMAs per
 //            k step, Ahi*Bhi + Ahi*Blo + Alo*Bhi, into the same accumulator.
 //
-// Persistent kernel: one 512-thread CTA per SM walks the work units
+// Persistent kernel: one 1024-thread CTA per SM walks the work units
 // blockIdx.x, blockIdx.x + gridDim.x, ... (a unit is one 128x128 output tile
 // and one k range; the host sorts units largest first). Barriers and TMEM are
 // set up once per CTA; the next unit's descriptor is fetched by a 1-D bulk
@@ -19,14 +19,14 @@
 // splits them), and stores them into the 128-byte-swizzled K-major shared-
 // memory layout the MMA descriptors describe, in a ring of stages. The offset
 // tables of the next slabs are decoded ahead, and for BF16 the loads of slab
-// k+1 stay in flight while slab k is converted. A named barrier closes each
+// k+1 can stay in flight while slab k is converted (PIPE). A named barrier closes each
 // slab; right after it one thread issues the slab's tcgen05.mma instructions
 // (the barrier orders every converter's fenced stores before them) and
 // commits them to the stage's `empty` barrier, which the converters wait on
 // before they reuse the stage. After a unit's k loop the 16 warps drain TMEM
-// and write C. 16 warps get 128 registers each (the register file is split
-// between the SM's four sub-partitions): two units per thread and operand,
-// twice that in flight when pipelined.
+// and write C. 32 warps (64 registers each; the register file is split
+// between the SM's four sub-partitions) with one unit per thread and operand:
+// the many resident warps hide the gather's latency.
 // Every mbarrier wait is bounded (2 s of wall time); on expiry the kernel
 // records TN_ERR_TIMEOUT, stops all units, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -38,20 +38,31 @@ namespace tn {
 namespace {
 
 constexpr int BM = TC_BM, BN = TC_BN, BK = 64;
-constexpr int NTHREADS = 512;
 constexpr int UNITS = BM * (BK / 8);     // (row, 8-wide k group) units of one operand slab
-constexpr int UPT = UNITS / NTHREADS;    // units per thread and operand (2)
 constexpr int TILE_BYTES = BM * BK * 2;  // one 128x64 bf16 operand tile (16 KB)
-constexpr int TS = 3;                    // ring of shared-index offset tables
+constexpr int KMAX = MAX_SLABS_PER_UNIT * BK;  // longest k range of a work unit (2048)
 // BF16X3 promotes the tensor-core accumulator into float32 registers every
 // KC k-slabs (KC * 64 = 256 shared indices): the tensor core's float32
 // accumulation truncates, and over long K that error (linear in the number
 // of accumulation steps) would exceed the split's own rounding error.
 constexpr int KC = 4;
 
+// Threads per CTA: BF16 runs 32 warps (64 registers each, one unit per
+// thread and operand; the resident warps hide the gather latency); BF16X3
+// runs 16 warps (128 registers: its promoted partial sums need them) with two
+// units per thread. (PIPE = true would keep the loads of slab k+1 in flight
+// while slab k is converted; at these register budgets it spills, so both
+// paths rely on resident warps instead.)
+template <int NT>
+struct Shape {
+  static constexpr int UPT = UNITS / NT;          // units per thread and operand
+  static constexpr int WCOLS = BN / (NT / 128);   // accumulator columns each warp drains
+};
+
 template <int SPLIT>
 struct Cfg {
-  static constexpr bool PIPE = !SPLIT;                       // loads of slab k+1 overlap slab k
+  static constexpr int NT = SPLIT ? 512 : 1024;
+  static constexpr bool PIPE = false;
   static constexpr int STAGES = SPLIT ? 3 : 4;
   static constexpr int OPS = SPLIT ? 4 : 2;                  // tiles per stage: Ahi, Bhi (, Alo, Blo)
   static constexpr int STAGE_BYTES = OPS * TILE_BYTES;
@@ -63,10 +74,10 @@ struct TcAux {
   ContractDesc dslot[2];    // descriptors of this and the next unit (16-byte aligned)
   int32_t rowA[BM];
   int32_t rowB[BN];
-  int32_t kA[TS][BK];
-  int32_t kB[TS][BK];
-  int32_t kcA[TS][BK / 8];  // 1: the 8-wide k group is unit-stride in A
-  int32_t kcB[TS][BK / 8];
+  int32_t kA[KMAX];          // shared-index offsets of the unit's k range, A
+  int32_t kB[KMAX];          // and B (-1 past the range's end)
+  int8_t kcA[KMAX / 8];      // 1: the 8-wide k group is unit-stride in A
+  int8_t kcB[KMAX / 8];
   uint64_t empty[S];        // the MMAs reading stage s are complete
   uint64_t accum;           // a unit's accumulator is final
   uint64_t chunk_full[2];   // BF16X3: accumulator buffer b holds a finished chunk
@@ -93,43 +104,185 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Loads the 8 float32 values of one (row, k group) unit of an operand.
-__device__ __forceinline__ void load_unit(const float* __restrict__ base, int32_t row_off,
-                                          const int32_t* koff, int contiguous, float (&v)[8]) {
-  if (row_off < 0) {
+// k-group contiguity: the 8 indices k0..k0+7 are all < k_end and consecutive
+// in memory (innermost shared leg has unit stride and the group does not wrap).
+__device__ __forceinline__ int group_contiguous(const ContractDesc& d, int64_t k0, int64_t k_end,
+                                                const int64_t* kstr) {
+  if (d.nk == 0 || k0 + 8 > k_end) return 0;
+  const int last = d.nk - 1;
+  if (kstr[last] != 1) return 0;
+  const uint32_t dl = (uint32_t)d.kdim[last];
+  return (((uint32_t)k0 % dl) + 8 <= dl) ? 1 : 0;
+}
+
+// Shared-index offsets of the unit's whole k range (at most KMAX), decoded
+// once per unit by all threads, and the unit-stride flag of every 8-group.
+template <int NT, class Aux>
+__device__ __forceinline__ void fill_tables(const ContractDesc& d, const UnitCoord& uc, Aux& x) {
+  const int64_t len = uc.k_end - uc.k_begin;
+  const int64_t padded = ((len + BK - 1) / BK) * BK;
+  for (int e = threadIdx.x; e < 2 * padded; e += NT) {
+    const bool isA = e < padded;
+    const int jj = isA ? e : e - (int)padded;
+    const int64_t k = uc.k_begin + jj;
+    const int64_t* kstr = isA ? d.kstrA : d.kstrB;
+    const int32_t off = (jj < len) ? (int32_t)leg_offset((uint32_t)k, d.nk, d.kdim, kstr) : -1;
+    if (isA) x.kA[jj] = off;
+    else x.kB[jj] = off;
+    if ((jj & 7) == 0) {
+      const int8_t c = (int8_t)group_contiguous(d, k, uc.k_end, kstr);
+      if (isA) x.kcA[jj >> 3] = c;
+      else x.kcB[jj >> 3] = c;
+    }
+  }
+}
+
+// Staged layouts. An operand whose unit-stride axis is a shared leg (kfast)
+// is staged K-major: a unit is 8 consecutive k of one row, stored as one
+// 16-byte chunk of a 128-byte-swizzled K-major tile. An operand whose
+// unit-stride axis is a free leg is staged MN-major: a unit is 8 consecutive
+// rows at one k, one 16-byte chunk of a 128-byte-swizzled MN-major tile
+// (atoms of 8 k-rows x 64 MN elements; the two 64-row halves 8 KB apart,
+// 8-row k groups 1 KB apart). Either way the gather reads 32 contiguous bytes
+// per unit when the memory layout allows, and consecutive threads walk the
+// unit-stride direction.
+constexpr uint32_t MN_HALF_BYTES = 8192;  // MN-major: stride between the 64-row halves
+constexpr uint32_t MN_KGROUP_BYTES = 1024;  // MN-major: stride between 8-row k groups
+
+__device__ __forceinline__ uint32_t sw128_mn_chunk(int mg, int k) {
+  return (uint32_t)((mg >> 3) * MN_HALF_BYTES + (k >> 3) * MN_KGROUP_BYTES + (k & 7) * 128 +
+                    (((mg & 7) ^ (k & 7)) << 4));
+}
+
+// Rows r0 .. r0+7 of a free-leg index are all present and consecutive in memory.
+__device__ __forceinline__ bool row_group_regular(int64_t r0, int64_t R, int n, const int32_t* dims,
+                                                  const int64_t* strides) {
+  if (n == 0 || r0 + 8 > R || strides[n - 1] != 1) return false;
+  const uint32_t dl = (uint32_t)dims[n - 1];
+  return ((uint32_t)r0 % dl) + 8 <= dl;
+}
+
+// What a thread keeps for a whole work unit, per operand and unit: the base
+// pointer of its row (K-major) or 8-row group (MN-major; null when the group
+// is not regular), its k group (K-major) or k (MN-major), its row group
+// (MN-major), and the swizzled shared-memory offset its values go to.
+template <int NT>
+struct ThreadUnits {
+  static constexpr int UPT = Shape<NT>::UPT;
+  const float* pa[UPT];
+  const float* pb[UPT];
+  uint16_t ga[UPT], gb[UPT];
+  uint8_t ma[UPT], mb[UPT];
+  uint32_t oa[UPT], ob[UPT];
+};
+
+template <int NT>
+__device__ __forceinline__ void unit_of(int kfast, const float* base, const int32_t* rows, int64_t row0, int64_t R,
+                                        int nr, const int32_t* rdims, const int64_t* rstr, int t, int i,
+                                        const float*& p, uint16_t& g, uint8_t& mg, uint32_t& off) {
+  const int uu = t + NT * i;
+  if (kfast) {
+    const int r = uu >> 3;
+    g = uu & 7;
+    mg = 0;
+    p = rows[r] >= 0 ? base + rows[r] : nullptr;
+    off = sw128_chunk(r, g);
+  } else {
+    mg = uu & 15;
+    g = uu >> 4;  // the unit's k within the slab
+    p = row_group_regular(row0 + 8 * mg, R, nr, rdims, rstr) ? base + rows[8 * mg] : nullptr;
+    off = sw128_mn_chunk(mg, g);
+  }
+}
+
+template <int NT, class Aux>
+__device__ __forceinline__ ThreadUnits<NT> thread_units(const ContractDesc& d, const Aux& x, int64_t m0, int64_t n0,
+                                                        int t) {
+  ThreadUnits<NT> u;
+#pragma unroll
+  for (int i = 0; i < Shape<NT>::UPT; ++i) {
+    unit_of<NT>(d.a_kfast, d.A, x.rowA, m0, d.M, d.nm, d.mdim, d.mstr, t, i, u.pa[i], u.ga[i], u.ma[i], u.oa[i]);
+    unit_of<NT>(d.b_kfast, d.B, x.rowB, n0, d.N, d.nn, d.ndim, d.nstr, t, i, u.pb[i], u.gb[i], u.mb[i], u.ob[i]);
+  }
+  return u;
+}
+
+__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// K-major unit: 8 consecutive k of one row.
+__device__ __forceinline__ void load_kmajor(const float* row, const int32_t* koff, int contiguous, float (&v)[8]) {
+  if (!row) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = 0.0f;
     return;
   }
-  if (contiguous) {
-    const float* p = base + (row_off + koff[0]);
-    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-      const float4 x = __ldg(reinterpret_cast<const float4*>(p));
-      const float4 y = __ldg(reinterpret_cast<const float4*>(p) + 1);
-      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-      v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = __ldg(p + j);
-    }
+  const float* p = row + koff[0];
+  if (contiguous && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    load8(p, v);
     return;
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int32_t ko = koff[j];
-    v[j] = (ko >= 0) ? __ldg(base + (row_off + ko)) : 0.0f;
+    v[j] = (ko >= 0) ? __ldg(row + ko) : 0.0f;
   }
 }
 
+// MN-major unit: 8 consecutive rows (group mg) at one shared offset ko.
+__device__ __forceinline__ void load_mnmajor(const float* base, const float* grp, const int32_t* rows, int mg,
+                                             int32_t ko, float (&v)[8]) {
+  if (ko < 0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+    return;
+  }
+  if (grp && (reinterpret_cast<uintptr_t>(grp + ko) & 15) == 0) {
+    load8(grp + ko, v);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int32_t ro = rows[8 * mg + j];
+    v[j] = (ro >= 0) ? __ldg(base + (ro + ko)) : 0.0f;
+  }
+}
+
+// Slab kt of the unit: entries kt*64 .. kt*64+63 of the unit's tables.
+template <int NT, class Aux>
+__device__ __forceinline__ void load_slab(const ContractDesc& d, const Aux& x, int kt, const ThreadUnits<NT>& tu,
+                                          float (&va)[Shape<NT>::UPT][8], float (&vb)[Shape<NT>::UPT][8]) {
+  constexpr int UPT = Shape<NT>::UPT;
+  const int k0 = kt * BK;
+#pragma unroll
+  for (int i = 0; i < UPT; ++i) {
+    if (d.a_kfast) load_kmajor(tu.pa[i], &x.kA[k0 + tu.ga[i] * 8], x.kcA[(k0 >> 3) + tu.ga[i]], va[i]);
+    else load_mnmajor(d.A, tu.pa[i], x.rowA, tu.ma[i], x.kA[k0 + tu.ga[i]], va[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < UPT; ++i) {
+    if (d.b_kfast) load_kmajor(tu.pb[i], &x.kB[k0 + tu.gb[i] * 8], x.kcB[(k0 >> 3) + tu.gb[i]], vb[i]);
+    else load_mnmajor(d.B, tu.pb[i], x.rowB, tu.mb[i], x.kB[k0 + tu.gb[i]], vb[i]);
+  }
+}
+
+// Descriptor of the 16-wide k step kk of an operand tile at `tile`.
+__device__ __forceinline__ uint64_t operand_desc(int kfast, uint32_t tile, int kk) {
+  return kfast ? ptx::sw128_kmajor_desc(tile + kk * 32)
+               : ptx::sw128_mnmajor_desc(tile + kk * 2 * MN_KGROUP_BYTES, MN_HALF_BYTES, MN_KGROUP_BYTES);
+}
+
 template <int SPLIT>
-__device__ __forceinline__ void store_unit(uint8_t* hi_tile, uint8_t* lo_tile, int r, int g,
-                                           const float (&v)[8]) {
+__device__ __forceinline__ void store_group(uint8_t* hi_tile, uint8_t* lo_tile, uint32_t off, const float (&v)[8]) {
   uint4 h;
   h.x = pack_bf16x2(v[0], v[1]);
   h.y = pack_bf16x2(v[2], v[3]);
   h.z = pack_bf16x2(v[4], v[5]);
   h.w = pack_bf16x2(v[6], v[7]);
-  const uint32_t off = sw128_chunk(r, g);
   *reinterpret_cast<uint4*>(hi_tile + off) = h;
   if (SPLIT) {
     const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
@@ -142,85 +295,28 @@ __device__ __forceinline__ void store_unit(uint8_t* hi_tile, uint8_t* lo_tile, i
   }
 }
 
-// k-group contiguity: the 8 indices k0..k0+7 are all < k_end and consecutive
-// in memory (innermost shared leg has unit stride and the group does not wrap).
-__device__ __forceinline__ int group_contiguous(const ContractDesc& d, int64_t k0, int64_t k_end,
-                                                const int64_t* kstr) {
-  if (d.nk == 0 || k0 + 8 > k_end) return 0;
-  const int last = d.nk - 1;
-  if (kstr[last] != 1) return 0;
-  const uint32_t dl = (uint32_t)d.kdim[last];
-  return (((uint32_t)k0 % dl) + 8 <= dl) ? 1 : 0;
-}
-
-// Shared-index offsets of slab kt into table slot kt % TS (threads 0-127: 64
-// for A, 64 for B; the first thread of each 8-group also records whether the
-// group is unit-stride).
-template <class Aux>
-__device__ __forceinline__ void fill_table(const ContractDesc& d, const UnitCoord& uc, int64_t kt, Aux& x) {
-  const int t = threadIdx.x;
-  if (t >= 2 * BK) return;
-  const int slot = (int)(kt % TS);
-  const int jj = t & (BK - 1);
-  const int64_t k = uc.k_begin + kt * BK + jj;
-  const bool isA = t < BK;
-  const int64_t* kstr = isA ? d.kstrA : d.kstrB;
-  const int32_t off = (k < uc.k_end) ? (int32_t)leg_offset((uint32_t)k, d.nk, d.kdim, kstr) : -1;
-  if (isA) x.kA[slot][jj] = off;
-  else x.kB[slot][jj] = off;
-  if ((jj & 7) == 0) {
-    const int c = group_contiguous(d, k, uc.k_end, kstr);
-    if (isA) x.kcA[slot][jj >> 3] = c;
-    else x.kcB[slot][jj >> 3] = c;
-  }
-}
-
-// (row, k group) of unit i of thread t: consecutive threads walk the
-// operand's unit-stride direction (k when kfast, else the row).
-__device__ __forceinline__ void unit_coord(int kfast, int t, int i, int& r, int& g) {
-  const int uu = t + NTHREADS * i;
-  r = kfast ? (uu >> 3) : (uu & (BM - 1));
-  g = kfast ? (uu & 7) : (uu >> 7);
-}
-
-template <class Aux>
-__device__ __forceinline__ void load_slab(const ContractDesc& d, const Aux& x, int slot, int t,
-                                          float (&va)[UPT][8], float (&vb)[UPT][8]) {
+template <int SPLIT, int NT>
+__device__ __forceinline__ void store_slab(uint8_t* st, const ThreadUnits<NT>& tu, const float (&va)[Shape<NT>::UPT][8],
+                                           const float (&vb)[Shape<NT>::UPT][8]) {
+  constexpr int UPT = Shape<NT>::UPT;
 #pragma unroll
-  for (int i = 0; i < UPT; ++i) {
-    int r, g;
-    unit_coord(d.a_kfast, t, i, r, g);
-    load_unit(d.A, x.rowA[r], &x.kA[slot][g * 8], x.kcA[slot][g], va[i]);
-  }
+  for (int i = 0; i < UPT; ++i) store_group<SPLIT>(st, st + 2 * TILE_BYTES, tu.oa[i], va[i]);
 #pragma unroll
-  for (int i = 0; i < UPT; ++i) {
-    int r, g;
-    unit_coord(d.b_kfast, t, i, r, g);
-    load_unit(d.B, x.rowB[r], &x.kB[slot][g * 8], x.kcB[slot][g], vb[i]);
-  }
+  for (int i = 0; i < UPT; ++i) store_group<SPLIT>(st + TILE_BYTES, st + 3 * TILE_BYTES, tu.ob[i], vb[i]);
 }
 
-template <int SPLIT>
-__device__ __forceinline__ void store_slab(const ContractDesc& d, int t, uint8_t* st, const float (&va)[UPT][8],
-                                           const float (&vb)[UPT][8]) {
-#pragma unroll
-  for (int i = 0; i < UPT; ++i) {
-    int r, g;
-    unit_coord(d.a_kfast, t, i, r, g);
-    store_unit<SPLIT>(st, st + 2 * TILE_BYTES, r, g, va[i]);
-  }
-#pragma unroll
-  for (int i = 0; i < UPT; ++i) {
-    int r, g;
-    unit_coord(d.b_kfast, t, i, r, g);
-    store_unit<SPLIT>(st + TILE_BYTES, st + 3 * TILE_BYTES, r, g, vb[i]);
-  }
-}
-
-// Writes (splits == 1) or accumulates (split-K) 32 consecutive results of
+// Writes (splits == 1) or accumulates (split-K) WCOLS consecutive results of
 // row m starting at column n0 + col.
-__device__ __forceinline__ void write_row32(const ContractDesc& d, int64_t m, int64_t n0, int col,
-                                            const uint32_t (&r)[32]) {
+// WCOLS consecutive accumulator columns of this warp's 32 lanes.
+template <int WCOLS>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[WCOLS]) {
+  if constexpr (WCOLS == 32) ptx::tmem_ld_32x32b_x32(taddr, r);
+  else ptx::tmem_ld_32x32b_x16(taddr, r);
+}
+
+template <int WCOLS>
+__device__ __forceinline__ void write_row(const ContractDesc& d, int64_t m, int64_t n0, int col,
+                                          const uint32_t (&r)[WCOLS]) {
   if (m >= d.M) return;
   float* __restrict__ C = d.C;
   const int64_t N = d.N;
@@ -229,18 +325,21 @@ __device__ __forceinline__ void write_row32(const ContractDesc& d, int64_t m, in
   float* dst = C + m * N + n0 + col;
   const int64_t nrem = N - (n0 + col);
 #pragma unroll
-  for (int i = 0; i < 32; i += 4)
+  for (int i = 0; i < WCOLS; i += 4)
     if (i < nrem)
       emit4(dst + i, vec, nrem - i, accumulate, __uint_as_float(r[i]), __uint_as_float(r[i + 1]),
             __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
 }
 
 template <int SPLIT>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(Cfg<SPLIT>::NT, 1)
 tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDesc* group,
                    const int32_t* unit_desc, int64_t total_units, int* status) {
   using C = Cfg<SPLIT>;
   constexpr int S = C::STAGES;
+  constexpr int NT = C::NT;
+  constexpr int UPT = Shape<NT>::UPT;
+  constexpr int WCOLS = Shape<NT>::WCOLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcAux<S>& x = *reinterpret_cast<TcAux<S>*>(smem + (size_t)S * C::STAGE_BYTES);
@@ -285,8 +384,7 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
   ptx::tc_fence_after();
   const uint32_t tmem = x.tmem_base;
   const uint32_t stage0 = ptx::smem_addr(smem);
-  constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
-  const int q = warp & 3, cb = warp >> 2;  // TMEM lane quadrant and 32-column block of this warp
+  const int q = warp & 3, cb = warp >> 2;  // TMEM lane quadrant and WCOLS-column block of this warp
 
   uint32_t g_slab = 0;   // slabs processed by this CTA (stage ring position)
   uint32_t g_chunk = 0;  // BF16X3 accumulator chunks processed by this CTA
@@ -319,9 +417,9 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
       const int64_t n = n0 + (t - BM);
       x.rowB[t - BM] = (n < d.N) ? (int32_t)leg_offset((uint32_t)n, d.nn, d.ndim, d.nstr) : -1;
     }
-    float acc[SPLIT ? 32 : 1];
+    float acc[SPLIT ? WCOLS : 1];
 #pragma unroll
-    for (int i = 0; i < (SPLIT ? 32 : 1); ++i) acc[i] = 0.0f;
+    for (int i = 0; i < (SPLIT ? WCOLS : 1); ++i) acc[i] = 0.0f;
     // BF16X3: adds finished chunk c of this unit (accumulator buffer c & 1)
     // into acc; the MMAs that reuse the buffer are issued after a later
     // barrier, so program order protects it
@@ -331,16 +429,17 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
       const bool w = ptx::mbar_wait(ptx::smem_addr(&x.chunk_full[b]), (cg >> 1) & 1u, status);
       if (!__all_sync(0xffffffffu, w)) return false;
       ptx::tc_fence_after();
-      uint32_t r[32];
-      ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + cb * 32), r);
+      uint32_t r[WCOLS];
+      tmem_ld_cols<WCOLS>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + cb * WCOLS), r);
       ptx::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] += __uint_as_float(r[i]);
+      for (int i = 0; i < WCOLS; ++i) acc[i] += __uint_as_float(r[i]);
       ptx::tc_fence_before();
       return true;
     };
     int64_t next_drain = 0;
 
+    ThreadUnits<NT> tu;  // filled once the row tables are published (prologue barrier)
     // two register sets used in turn (the loop below is unrolled by two), so
     // the loads of slab k+1 are consumed only in the next slab's step
     float ra0[UPT][8], rb0[UPT][8], ra1[UPT][8], rb1[UPT][8];
@@ -354,43 +453,39 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
       const int s = (int)(gs % S);
       const uint32_t round = gs / S;
       if (C::PIPE) {
-        // tables of slab kt+2 (slot last read by the loads of slab kt-1,
-        // issued before the previous barrier)
-        if (kt + 2 < nkt) fill_table(d, uc, kt + 2, x);
-        if (kt + 1 < nkt) load_slab(d, x, (int)((kt + 1) % TS), t, nxt_a, nxt_b);
+        if (kt + 1 < nkt) load_slab<NT>(d, x, (int)kt + 1, tu, nxt_a, nxt_b);
       } else {
-        if (kt + 1 < nkt) fill_table(d, uc, kt + 1, x);
-        load_slab(d, x, (int)(kt % TS), t, cur_a, cur_b);
+        load_slab<NT>(d, x, (int)kt, tu, cur_a, cur_b);
       }
       bool drained_ok = true;
       if (SPLIT && (kt % KC) == 0 && kt / KC >= 2) drained_ok = drain(next_drain++);
       // the stage's previous MMAs must be complete before it is rewritten
       const bool waited = ptx::mbar_wait(ptx::smem_addr(&x.empty[s]), (round & 1u) ^ 1u, status) && drained_ok;
       if (waited) {
-        store_slab<SPLIT>(d, t, smem + (size_t)s * C::STAGE_BYTES, cur_a, cur_b);
+        store_slab<SPLIT, NT>(smem + (size_t)s * C::STAGE_BYTES, tu, cur_a, cur_b);
         ptx::fence_proxy_async_smem();
       }
-      // every thread reaches this barrier once per slab (it also publishes
-      // the tables filled above); a wait that expired anywhere stops all of
-      // them together
+      // every thread reaches this barrier once per slab; a wait that expired
+      // anywhere stops all of them together
       ptx::tc_fence_before();
-      if (ptx::named_barrier_or(1, NTHREADS, !waited)) return false;
+      if (ptx::named_barrier_or(1, NT, !waited)) return false;
       if (issuer) {
         ptx::tc_fence_after();
         const int64_t c = kt / KC;
         const uint32_t cg = g_chunk + (uint32_t)c;
         const uint32_t d_tmem = SPLIT ? tmem + (uint32_t)((cg & 1) * BN) : tmem;
         const bool fresh = SPLIT ? (kt % KC) == 0 : (kt == 0);
+        const uint32_t idesc = ptx::idesc_bf16_f32(BM, BN, d.a_kfast ? 0 : 1, d.b_kfast ? 0 : 1);
         const uint32_t a_hi = stage0 + (uint32_t)(s * C::STAGE_BYTES);
         const uint32_t b_hi = a_hi + TILE_BYTES;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t ad = ptx::sw128_kmajor_desc(a_hi + kk * 32);
-          const uint64_t bd = ptx::sw128_kmajor_desc(b_hi + kk * 32);
+          const uint64_t ad = operand_desc(d.a_kfast, a_hi, kk);
+          const uint64_t bd = operand_desc(d.b_kfast, b_hi, kk);
           ptx::mma_bf16(d_tmem, ad, bd, idesc, (fresh && kk == 0) ? 0u : 1u);
           if (SPLIT) {
-            const uint64_t al = ptx::sw128_kmajor_desc(a_hi + 2 * TILE_BYTES + kk * 32);
-            const uint64_t bl = ptx::sw128_kmajor_desc(b_hi + 2 * TILE_BYTES + kk * 32);
+            const uint64_t al = operand_desc(d.a_kfast, a_hi + 2 * TILE_BYTES, kk);
+            const uint64_t bl = operand_desc(d.b_kfast, b_hi + 2 * TILE_BYTES, kk);
             ptx::mma_bf16(d_tmem, ad, bl, idesc, 1u);
             ptx::mma_bf16(d_tmem, al, bd, idesc, 1u);
           }
@@ -401,12 +496,12 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
       __syncwarp();
       return true;
     };
-    // prologue: offset tables of the first slabs (and, pipelined, the
-    // registers of slab 0)
-    if (nkt > 0) fill_table(d, uc, 0, x);
-    if (C::PIPE && nkt > 1) fill_table(d, uc, 1, x);
-    ptx::named_barrier(1, NTHREADS);
-    if (C::PIPE && nkt > 0) load_slab(d, x, 0, t, ra0, rb0);
+    // prologue: the unit's offset tables (and, pipelined, the registers of
+    // slab 0)
+    if (nkt > 0) fill_tables<NT>(d, uc, x);
+    ptx::named_barrier(1, NT);
+    tu = thread_units<NT>(d, x, m0, n0, t);
+    if (C::PIPE && nkt > 0) load_slab<NT>(d, x, 0, tu, ra0, rb0);
     for (int64_t kt = 0; kt < nkt; kt += 2) {
       if (!slab(kt, ra0, rb0, ra1, rb1)) { ok = false; break; }
       if (kt + 1 < nkt && !slab(kt + 1, ra1, rb1, ra0, rb0)) { ok = false; break; }
@@ -427,15 +522,15 @@ tc_contract_kernel(const __grid_constant__ ContractDesc single, const ContractDe
     if (__all_sync(0xffffffffu, acc_ready) && nkt > 0) {  // tcgen05.ld is warp-collective
       ptx::tc_fence_after();
       const int64_t m = m0 + q * 32 + lane;
-      uint32_t r[32];
+      uint32_t r[WCOLS];
       if (SPLIT) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(acc[i]);
+        for (int i = 0; i < WCOLS; ++i) r[i] = __float_as_uint(acc[i]);
       } else {
-        ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), r);
+        tmem_ld_cols<WCOLS>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * WCOLS), r);
         ptx::tmem_ld_wait();
       }
-      write_row32(d, m, n0, cb * 32, r);
+      write_row<WCOLS>(d, m, n0, cb * WCOLS, r);
     }
     if (!ok || !acc_ready) x.abort = 1;
     g_slab += (uint32_t)nkt;
@@ -482,7 +577,7 @@ int launch_tc(const ContractDesc& single, const ContractDesc* group, const int32
   }
   const int64_t resident = (int64_t)sm_count();
   const unsigned grid = (unsigned)(units < resident ? units : resident);
-  tc_contract_kernel<SPLIT><<<grid, NTHREADS, smem, stream>>>(single, group, unit_desc, units, status_word());
+  tc_contract_kernel<SPLIT><<<grid, Cfg<SPLIT>::NT, smem, stream>>>(single, group, unit_desc, units, status_word());
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
