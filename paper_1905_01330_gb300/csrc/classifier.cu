@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "classifier_tc.h"
 #include "tn_internal.h"
 
 namespace tn {
@@ -200,6 +201,14 @@ int launch_sweep_chi(const SweepParams& p, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
+int launch_sweep(int chi, const SweepParams& p, cudaStream_t s);
+
+// The tensor-core images of one mode for both half-chains.
+int pack_images(const tn_mps* W, const struct ClsLayout& w, int mode, cudaStream_t s);
+
+// A sweep on the float32 kernel (prec FP32) or the tcgen05 kernel (else).
+int run_sweep(int prec, const struct ClsLayout& w, const SweepParams& p, cudaStream_t s);
+
 int launch_sweep(int chi, const SweepParams& p, cudaStream_t s) {
   if (p.t_end <= p.t_begin) return TN_OK;
   if (chi == 32) return launch_sweep_chi<32>(p, s);
@@ -362,6 +371,8 @@ struct ClsLayout {
   float* X;        // [seg_len][batch][2 chi]
   float* Y;        // [batch][2][L][chi]
   uint8_t* plan_ws;
+  uint8_t* img[2][2];  // bf16 core images per half and mode (tensor-core sweeps)
+  size_t img_bytes;
   size_t plan_bytes;
   size_t bytes;
 };
@@ -411,8 +422,53 @@ ClsLayout cls_layout(uint8_t* base, const tn_mps* W, int ls, int L, int batch, i
                            sizeof(int32_t) * (size_t)w.seg_len * units_per_spec
                      : 0;
   w.plan_ws = take(w.plan_bytes);
+  w.img_bytes = cls_image_bytes(w.chi);
+  for (int h = 0; h < 2; ++h)
+    for (int m = 0; m < 2; ++m) w.img[h][m] = take(w.img_bytes * (size_t)w.T[h]);
   w.bytes = off;
   return w;
+}
+
+int pack_images(const tn_mps* W, const ClsLayout& w, int mode, cudaStream_t s) {
+  for (int h = 0; h < 2; ++h) {
+    ClsPackParams pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.n = W->n;
+    pp.half = h;
+    pp.mode = mode;
+    pp.chi = w.chi;
+    pp.kpad = w.chi < 64 ? 64 : w.chi;
+    pp.img_bytes = w.img_bytes;
+    for (int i = 0; i <= W->n; ++i) pp.bond[i] = (int32_t)W->bond[i];
+    for (int i = 0; i < W->n; ++i) pp.core[i] = W->cores[i];
+    pp.images = w.img[h][mode];
+    int rc = cls_pack(pp, w.T[h], s);
+    if (rc != TN_OK) return rc;
+  }
+  return TN_OK;
+}
+
+int run_sweep(int prec, const ClsLayout& w, const SweepParams& p, cudaStream_t s) {
+  if (prec == TN_PREC_FP32) return launch_sweep(w.chi, p, s);
+  ClsTcParams q;
+  memset(&q, 0, sizeof(q));
+  q.n = p.n;
+  q.batch = p.batch;
+  q.half = p.half;
+  q.mode = p.mode;
+  q.t_begin = p.t_begin;
+  q.t_end = p.t_end;
+  q.store_every = p.store_every;
+  q.store_base = p.store_base;
+  q.pixels = p.pixels;
+  q.state = p.state;
+  q.lam = p.lam;
+  q.store = p.store;
+  q.sc = p.sc;
+  q.xout = p.xout;
+  q.images = w.img[p.half][p.mode];
+  q.status = status_word();
+  return cls_sweep_tc_launch(w.chi, q, s);
 }
 
 int check_classifier(const tn_mps* W, int ls, int L, const float* pixels, int batch) {
@@ -482,12 +538,13 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
   int rc = check_classifier(W, label_site, n_labels, pixels, batch);
   if (rc != TN_OK) return rc;
   if (!ftilde || !log_scale || ckpt_every < 0) return TN_ERR_ARG;
-  if (prec != TN_PREC_FP32) return TN_ERR_UNSUPPORTED;
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16) return TN_ERR_UNSUPPORTED;
   if (batch == 0) return TN_OK;
   ClsLayout w = cls_layout(static_cast<uint8_t*>(workspace), W, label_site, n_labels, batch, ckpt_every);
   if (!workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t nvec = (int64_t)batch * w.chi;
+  if (prec != TN_PREC_FP32 && (rc = pack_images(W, w, 0, s)) != TN_OK) return rc;
   for (int h = 0; h < 2; ++h) {
     cls_init_state<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(w.state[h], w.lam[h], batch, w.chi);
     SweepParams p = sweep_params(W, w, pixels, h, 0);
@@ -498,7 +555,7 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
       p.store_every = ckpt_every;
       p.store_base = 0;
     }
-    if ((rc = launch_sweep(w.chi, p, s)) != TN_OK) return rc;
+    if ((rc = run_sweep(prec, w, p, s)) != TN_OK) return rc;
   }
   LabelParams lp;
   memset(&lp, 0, sizeof(lp));
@@ -542,6 +599,12 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
     return TN_OK;
   }
   const int dprec = prec == TN_PREC_FP32 ? TN_PREC_FP32 : prec;
+  // reduced precisions run the sweeps on the tensor cores (bf16 operands)
+  const int sprec = prec == TN_PREC_FP32 ? TN_PREC_FP32 : TN_PREC_BF16;
+  if (sprec != TN_PREC_FP32) {
+    if ((rc = pack_images(W, w, 0, s)) != TN_OK) return rc;
+    if ((rc = pack_images(W, w, 1, s)) != TN_OK) return rc;
+  }
 
   // label core: adjoints entering both half-chains, and dC = sum_b vL_b (x) Y_b
   LabelParams lp;
@@ -599,7 +662,7 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
         p.store = w.seg;
         p.store_every = 1;
         p.store_base = t0;
-        if ((rc = launch_sweep(chi, p, s)) != TN_OK) return rc;
+        if ((rc = run_sweep(sprec, w, p, s)) != TN_OK) return rc;
         vecs = w.seg;
       }
       // adjoint steps t1-1 .. t0: g <- adjoint step, X[t - t0] <- gradient operands
@@ -608,7 +671,7 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
       p.t_begin = t0;
       p.t_end = t1;
       p.xout = w.X;
-      if ((rc = launch_sweep(chi, p, s)) != TN_OK) return rc;
+      if ((rc = run_sweep(sprec, w, p, s)) != TN_OK) return rc;
       // core gradients of the segment: one grouped tensordot over the batch
       std::vector<tn_contract_spec> specs((size_t)(t1 - t0));
       for (int t = t0; t < t1; ++t) {

@@ -122,3 +122,72 @@ def test_autograd_function_matches_direct_backward(tn):
     for i, (p, r) in enumerate(zip(params, g_ref)):
         err = np.linalg.norm(p.grad.double().cpu().numpy() - r) / np.linalg.norm(r)
         assert err <= 1e-4, (i, err)
+
+
+# --------------------------------------------------------------- bf16 path
+def bf16_tol(steps):
+    """Per-sample relative score error of the bf16 sweep: two bf16 roundings
+    per product (2^-8), independent per site, so a random walk over steps;
+    factor 2 of margin."""
+    return 2.0 * 2.0 ** -8 * math.sqrt(steps)
+
+
+def round_bf16(a):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(a))
+
+
+@pytest.mark.parametrize("n,chi,ls,L,B", [(12, 8, 5, 3, 40), (60, 32, 30, 10, 200), (200, 64, 100, 10, 130),
+                                          (64, 128, 33, 10, 129)])
+def test_forward_bf16_parity(tn, n, chi, ls, L, B):
+    cores = synth.classifier_mps(n, chi, ls, L, seed=81, eps_std=0.1)
+    px = synth.pixels(B, n, seed=82)
+    ft, lam, _ = tn.mps_classify([dev(c) for c in cores], ls, dev(px), prec="bf16", ckpt_every=0)
+    assert tn.sync_status() == 0
+    # 1) against the oracle on the same bf16-rounded cores (the label core
+    #    stays float32 on both sides): what is left is the rounding of each
+    #    step's vector to bf16, 2^-9 per element times the step's conditioning
+    #    (about 4 for near-identity cores with 0.1 noise), a random walk over
+    #    sites; the tail over samples is heavier (products of random matrices)
+    rc = [c if i == ls else round_bf16(c) for i, c in enumerate(cores)]
+    ft_r, lam_r = oracle.classify(rc, ls, px)
+    err_r = score_err(ft, lam, ft_r, lam_r)
+    walk = 4.0 * 2.0 ** -9 * math.sqrt(n)
+    assert np.median(err_r) <= walk, (np.median(err_r), err_r.max())
+    assert err_r.max() <= 4.0 * walk, (err_r.max(), np.median(err_r))
+    # 2) against the exact oracle: the cores' own bf16 roundings (2^-8, shared
+    #    by every sample) add a walk of the same kind
+    ft_ref, lam_ref = oracle.classify(cores, ls, px)
+    err = score_err(ft, lam, ft_ref, lam_ref)
+    assert np.median(err) <= 2.0 * walk, (np.median(err), err.max())
+    assert err.max() <= 8.0 * walk, (err.max(), np.median(err))
+
+
+def test_forward_bf16_identity_cores(tn):
+    # identity cores are exact in bf16; only the feature values round
+    n, chi, ls, L, B = 784, 64, 392, 10, 128
+    cores = synth.classifier_mps(n, chi, ls, L, seed=1, eps_std=0.0)
+    px = synth.pixels(B, n, seed=2)
+    ft, lam, _ = tn.mps_classify([dev(c) for c in cores], ls, dev(px), prec="bf16", ckpt_every=0)
+    ref = np.sum(np.log(np.cos(np.pi * px.astype(np.float64) / 2) + np.sin(np.pi * px.astype(np.float64) / 2)), axis=1)
+    got = np.log(ft.double().cpu().numpy()) + lam.cpu().numpy()[:, None]
+    assert np.max(np.abs(got - ref[:, None])) <= bf16_tol(n)
+
+
+@pytest.mark.parametrize("ck", [1, 4])
+def test_backward_bf16_parity(tn, ck):
+    n, chi, ls, L, B = 24, 32, 12, 10, 150
+    cores = synth.classifier_mps(n, chi, ls, L, seed=91, eps_std=0.2)
+    px = synth.pixels(B, n, seed=92)
+    y = synth.labels(B, L, seed=93)
+    _, g_ref = oracle.classify_grad(cores, ls, px, y)
+    dc = [dev(c) for c in cores]
+    ft, lam, ws = tn.mps_classify(dc, ls, dev(px), prec="bf16", ckpt_every=ck)
+    _, dft = tn.mps_classify_loss(ft, torch.from_numpy(y).cuda())
+    grads = tn.mps_classify_backward(dc, ls, dev(px), dft, ws, prec="bf16", ckpt_every=ck)
+    assert tn.sync_status() == 0
+    for i, (g, r) in enumerate(zip(grads, g_ref)):
+        err = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
+        assert err <= bf16_tol(2 * n), (i, err)
