@@ -134,6 +134,146 @@ def cpu_oracle_sample(specs_h, count):
     return flops / dt, dt, flops, len(os.sched_getaffinity(0))
 
 
+def _time(fn, reps, warm, stream):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _score_err(ft, lam, ft_ref, lam_ref):
+    ft = ft.double().cpu().numpy()
+    got = ft * np.exp(lam.cpu().numpy() - lam_ref)[:, None]
+    e = np.linalg.norm(got - ft_ref, axis=1) / np.linalg.norm(ft_ref, axis=1)
+    return {"median": float(np.median(e)), "max": float(np.max(e))}
+
+
+def _lc_mps_device(n, d, chi, seed, dev):
+    """Left-canonical MPS built on the device (seeded normals, Householder QR,
+    R's diagonal made positive), float64 then rounded to float32 once."""
+    import torch
+    from paper_1905_01330_gb300 import synth
+    bonds = synth.mps_bonds(n, d, chi)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    cores = []
+    for i in range(n):
+        rows, cols = bonds[i] * d, bonds[i + 1]
+        m = torch.randn(rows, cols, dtype=torch.float64, device=dev, generator=g)
+        q, r = torch.linalg.qr(m)
+        sgn = torch.sign(torch.diagonal(r))
+        sgn[sgn == 0] = 1.0
+        cores.append((q * sgn[None, :]).reshape(bonds[i], d, cols).float().contiguous())
+    return cores
+
+
+def _expect_flops(cores, W):
+    f = 0.0
+    d = cores[0].shape[1]
+    for A, w in zip(cores, W):
+        Da, Db = A.shape[0], A.shape[2]
+        wa, wb = w.shape[0], w.shape[1]
+        f += 2.0 * wa * Da * d * Db * Da          # (i)
+        f += 2.0 * wb * d * Da * Db * wa * d      # (ii)
+        f += 2.0 * wb * Db * Db * d * Da          # (iii)
+        f += 2.0 * Da * d * Db * Da + 2.0 * Db * Db * Da * d  # norm sweep
+    return f
+
+
+def run_extras(tn, synth, dev, stream):
+    """Secondary measurements of the other hot-path rows, on their own workloads:
+    classifier forward (784 sites, batch 4096, chi 32/64/128) and training step
+    (chi 64), bf16 tensor-core path vs plain float32; the config-1 norm; the
+    config-5 energy at chi 256. Errors are against the FP64 oracle on a
+    stated subset."""
+    import torch
+    import oracle
+    out = {}
+    B, n, ls, L = 4096, 784, 392, 10
+    px_h = synth.pixels(B, n, seed=3)
+    px = torch.from_numpy(px_h).to(dev)
+    y_h = synth.labels(B, L, seed=4)
+    y = torch.from_numpy(y_h).to(dev)
+    cls = {}
+    for chi in (32, 64, 128):
+        cores_h = synth.classifier_mps(n, chi, ls, L, seed=30 + chi, eps_std=0.1)
+        cores = [torch.from_numpy(c).to(dev) for c in cores_h]
+        flops = sum(4.0 * B * c.shape[0] * c.shape[-1] for i, c in enumerate(cores) if i != ls)
+        entry = {"forward_gflop": flops / 1e9}
+        sub = 32
+        ft_ref, lam_ref = oracle.classify(cores_h, ls, px_h[:sub])
+        for prec in ("bf16", "fp32"):
+            ws = tn.classifier_workspace(cores, ls, L, B, 0)
+            ms = _time(lambda: tn.mps_classify(cores, ls, px, prec=prec, ckpt_every=0, workspace=ws), 3, 1, stream)
+            ft, lam, _ = tn.mps_classify(cores, ls, px, prec=prec, ckpt_every=0, workspace=ws)
+            entry[prec] = {"ms": ms, "samples_per_s": B / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12,
+                           "score_err_vs_oracle_first32": _score_err(ft[:sub], lam[:sub], ft_ref, lam_ref)}
+        entry["bf16_speedup_vs_fp32"] = entry["fp32"]["ms"] / entry["bf16"]["ms"]
+        cls["chi%d" % chi] = entry
+        if chi == 64:
+            # training step: forward with checkpoints every 28 sites, loss head, adjoint backward
+            ck = 28
+            train = {}
+            for prec in ("bf16", "fp32"):
+                ws = tn.classifier_workspace(cores, ls, L, B, ck)
+
+                def step():
+                    ft, lam, _ = tn.mps_classify(cores, ls, px, prec=prec, ckpt_every=ck, workspace=ws)
+                    loss, dft = tn.mps_classify_loss(ft, y)
+                    tn.mps_classify_backward(cores, ls, px, dft, ws, prec=prec, ckpt_every=ck)
+                ms = _time(step, 2, 1, stream)
+                train[prec] = {"ms": ms, "samples_per_s": B / (ms * 1e-3)}
+            # gradient error against the oracle on a 64-sample batch
+            sb = 64
+            _, g_ref = oracle.classify_grad(cores_h, ls, px_h[:sb], y_h[:sb])
+            for prec in ("bf16", "fp32"):
+                ws = tn.classifier_workspace(cores, ls, L, sb, ck)
+                ft, lam, _ = tn.mps_classify(cores, ls, px[:sb].contiguous(), prec=prec, ckpt_every=ck, workspace=ws)
+                _, dft = tn.mps_classify_loss(ft, y[:sb].contiguous())
+                g = tn.mps_classify_backward(cores, ls, px[:sb].contiguous(), dft, ws, prec=prec, ckpt_every=ck)
+                errs = [float(np.linalg.norm(a.double().cpu().numpy() - r) / np.linalg.norm(r)) for a, r in zip(g, g_ref)]
+                train[prec]["grad_err_vs_oracle_batch64"] = {"median": float(np.median(errs)), "max": float(np.max(errs))}
+            train["bf16_speedup_vs_fp32"] = train["fp32"]["ms"] / train["bf16"]["ms"]
+            train["checkpoint_every"] = ck
+            cls["train_chi64"] = train
+        del cores
+    out["classifier"] = cls
+
+    # config 1: <psi|psi>, N=20, chi=32 (one-CTA float32 sweep)
+    m_h = synth.random_mps(20, 2, 32, seed=1)
+    m = [torch.from_numpy(c).to(dev) for c in m_h]
+    res = torch.empty(2, dtype=torch.float64, device=dev)
+    us = 1e3 * _time(lambda: tn.mps_inner(m, m, prec="fp32", out=res), 50, 5, stream)
+    v, lg = oracle.mps_inner(m_h, m_h)
+    r = res.cpu().numpy()
+    out["mps_norm_n20_chi32"] = {"us_per_call": us,
+                                 "rel_err_vs_oracle": abs(r[0] * np.exp(r[1] - lg) - v) / abs(v)}
+
+    # config 5: TFIM energy, N=100, chi=256, left-canonical
+    cores = _lc_mps_device(100, 2, 256, 5, dev)
+    W = [torch.from_numpy(w).to(dev) for w in synth.tfim_mpo(100)]
+    flops = _expect_flops(cores, W)
+    en = {"gflop": flops / 1e9}
+    res = torch.empty(4, dtype=torch.float64, device=dev)
+    for prec in ("bf16x3", "fp32", "bf16"):
+        ms = _time(lambda: tn.mps_expect(cores, W, prec=prec, out=res), 2, 1, stream)
+        r = res.cpu().numpy()
+        e = r[0] * np.exp(r[1]) / (r[2] * np.exp(r[3]))
+        en[prec] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "energy_per_site": e / 100}
+    for prec in ("bf16x3", "bf16"):
+        en[prec]["rel_diff_vs_fp32"] = abs(en[prec]["energy_per_site"] - en["fp32"]["energy_per_site"]) / abs(
+            en["fp32"]["energy_per_site"])
+    out["tfim_energy_n100_chi256"] = en
+    return out
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores (rank 0 only), same metric and unit."""
     rank, world, _ = dist_env()
@@ -173,6 +313,8 @@ def main():
     ap.add_argument("--specs", type=int, default=N_SPECS,
                     help="first N specs only (smaller case for profiling; not a bench line)")
     ap.add_argument("--variants", default="bf16x3,fp32", help="other paths to time, comma separated, or none")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the classifier, MPS-norm and energy measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -293,6 +435,10 @@ def main():
                 "tensor_tflops": flops / (launch_ms * 1e-3) / 1e12,
                 "tensor_frac": flops / (launch_ms * 1e-3) / 1e12 / bf16_peak}
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(tn, synth, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt, fl, cores = cpu_oracle_sample(synth.contraction_specs(N_SPECS, seed=SEED), CPU_SAMPLE_SPECS)
@@ -303,9 +449,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(),
-                "gpu_launches": args.steps, "clocks": clocks, "e2e": e2e, "roofline": roofline,
+                "gpu_launches": args.steps * plan.launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "variants": variants,
-                "tensor_peak_frac": value / world / bf16_peak}
+                "tensor_peak_frac": value / world / bf16_peak, "extras": extras}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

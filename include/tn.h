@@ -151,6 +151,9 @@ int tn_contract_grouped_static(const tn_contract_spec* specs, int nspecs, int pr
  * (|A| + |B| + |C| float32 elements summed over specs) of a plan. */
 double tn_group_plan_flops(const tn_group_plan* plan);
 double tn_group_plan_bytes(const tn_group_plan* plan);
+/* Kernel launches one tn_group_plan_run makes (the contraction kernel, plus
+ * one zeroing kernel when some results are accumulated over split k ranges). */
+int tn_group_plan_launches(const tn_group_plan* plan);
 
 /* ------------------------------------------------------------------------ */
 /* Matrix product states and operators (Sec. II, Fig. 3a)                    */
@@ -289,6 +292,17 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
  */
 int tn_mps_classify_loss(const float* ftilde, const int64_t* labels, int batch, int n_labels,
                          double* loss, float* dftilde, void* stream);
+
+/*
+ * Failure-path check (the paper has no counterpart): launches one small
+ * kernel whose threads wait, with the bounded wait every kernel of the
+ * library uses, on an mbarrier that nothing completes, giving up after
+ * limit_ns nanoseconds of wall time (clamped to 10 ms .. 2 s). The kernel
+ * then records TN_ERR_TIMEOUT in the device status word and returns
+ * normally, so tn_sync_status() reports it and the context stays usable.
+ * Errors: TN_ERR_CUDA (launch failed).
+ */
+int tn_check_wait_timeout(uint64_t limit_ns, void* stream);
 
 /* Device status word: returns the first kernel-side error since the last
  * call (TN_OK if none) after synchronising `stream`, and clears it. */

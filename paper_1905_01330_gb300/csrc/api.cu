@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "ptx.cuh"
 #include "tn_internal.h"
 
 namespace tn {
@@ -80,6 +81,32 @@ const char* tn_status_string(int status) {
     case TN_ERR_WORKSPACE: return "workspace missing or too small";
     default: return "unknown status";
   }
+}
+
+}  // extern "C"
+
+namespace tn {
+namespace {
+// Waits on a freshly initialised mbarrier whose phase nobody completes.
+__global__ void wait_timeout_kernel(uint64_t limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(ptx::smem_addr(&bar), 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  ptx::mbar_wait_for(ptx::smem_addr(&bar), 0u, status, limit_ns);
+}
+}  // namespace
+}  // namespace tn
+
+extern "C" {
+
+int tn_check_wait_timeout(uint64_t limit_ns, void* stream) {
+  const uint64_t lo = 10000000ull, hi = 2000000000ull;
+  const uint64_t lim = limit_ns < lo ? lo : (limit_ns > hi ? hi : limit_ns);
+  tn::wait_timeout_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(lim, status_word());
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
 int tn_sync_status(void* stream) {
@@ -186,6 +213,10 @@ size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
 }
 
 double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
+int tn_group_plan_launches(const tn_group_plan* plan) {
+  if (!plan) return 0;
+  return (plan->total_tiles > 0 ? 1 : 0) + (plan->zero_ranges.empty() ? 0 : 1);
+}
 double tn_group_plan_bytes(const tn_group_plan* plan) { return plan ? plan->bytes : 0.0; }
 
 static int check_ws(const tn_group_plan* plan, void* ws, size_t bytes) {

@@ -156,7 +156,7 @@ cls_sweep_simt(const __grid_constant__ SweepParams p) {
         for (int j = 0; j < 4; ++j) out[i][j] = out[i][j] / sc;
         const int b = bq * 4 + i;
         if (jq == 0) {
-          lam[b] += log((double)sc);
+          lam[b] += (double)logf(sc);  // float32 log, float64 running sum
           if (b0 + b < B) p.sc[(int64_t)t * B + b0 + b] = sc;
         }
       }

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(NT, 1) cls_sweep_tc(const __grid_constant__ Cl
       const float sc = m > 0.0f ? m : 1.0f;
 #pragma unroll
       for (int k = 0; k < CHI; ++k) v[k] = v[k] / sc;
-      lam += log((double)sc);
+      lam += (double)logf(sc);  // float32 log (the FP64 pipe is narrow), float64 running sum
       if (live) p.sc[(int64_t)ts * B + b] = sc;
     } else {
 #pragma unroll

@@ -80,7 +80,7 @@ mps_inner_small_kernel(const __grid_constant__ SmallChain c, double* result) {
     const float m = block_max(mx, red);
     const float sc = m > 0.0f ? m : 1.0f;
     for (int idx = tid; idx < ne; idx += SMALL_THREADS) E[idx] = E2[idx] / sc;
-    lg += log((double)sc);
+    lg += (double)logf(sc);
     __syncthreads();
   }
   if (tid == 0) {

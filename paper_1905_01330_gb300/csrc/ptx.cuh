@@ -58,16 +58,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // TN_ERR_TIMEOUT) when the limit expires.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s; a healthy wait takes microseconds
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, int* status, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 0u && globaltimer() - t0 > kWaitLimitNs) {
+    if ((i & 255u) == 0u && globaltimer() - t0 > limit_ns) {
       set_status(status, TN_ERR_TIMEOUT);
       return false;
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+  return mbar_wait_for(bar, parity, status, kWaitLimitNs);
 }
 
 // Arrives on the mbarrier and adds `bytes` to the transaction count the

@@ -83,6 +83,7 @@ def _signatures():
         "tn_group_plan_destroy": (None, [vp]),
         "tn_group_plan_flops": (ctypes.c_double, [vp]),
         "tn_group_plan_bytes": (ctypes.c_double, [vp]),
+        "tn_group_plan_launches": (i32, [vp]),
         "tn_mps_inner_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
         "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
@@ -93,6 +94,7 @@ def _signatures():
         "tn_mps_classify_backward": (i32, [ctypes.POINTER(TnChain), i32, i32, vp, i32, i32, i32, vp,
                                            ctypes.POINTER(ctypes.c_void_p), vp, ctypes.c_size_t, vp]),
         "tn_mps_classify_loss": (i32, [vp, vp, i32, i32, vp, vp, vp]),
+        "tn_check_wait_timeout": (i32, [ctypes.c_uint64, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
     }
@@ -174,6 +176,11 @@ def sync_status(stream=None) -> int:
     return load().tn_sync_status(_stream(stream))
 
 
+def check_wait_timeout(limit_ns: int = 20_000_000, stream=None) -> None:
+    """Launches the failure-path check kernel (tn_check_wait_timeout)."""
+    _check(load().tn_check_wait_timeout(limit_ns, _stream(stream)), "tn_check_wait_timeout")
+
+
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
@@ -233,6 +240,7 @@ class GroupPlan:
         self.ws_bytes = self.workspace.numel()
         self.flops = lib.tn_group_plan_flops(h)
         self.bytes = lib.tn_group_plan_bytes(h)
+        self.launches = lib.tn_group_plan_launches(h)
         _check(lib.tn_group_plan_upload(h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
                                         _stream(stream)), "tn_group_plan_upload")
 
