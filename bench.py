@@ -148,6 +148,51 @@ def _time(fn, reps, warm, stream):
     return a.elapsed_time(b) / reps
 
 
+def _time_graph(fn, calls, replays, stream):
+    """Per-call time of `fn` captured `calls` times into one CUDA graph, the
+    graph replayed `replays` times (after one eager warm-up call)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fn()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(calls):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(replays):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / (replays * calls)
+
+
+def contract_traffic(nbytes):
+    """DRAM bytes per launch of the contraction kernel, from the committed ncu
+    capture, when that capture was taken of the kernel source as it is now
+    (same SHA-256); else None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "contract_tc_traffic.json")
+    src = os.path.join(ROOT, "paper_1905_01330_gb300", "csrc", "contract_tc.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if d.get("source_sha256") != sha:
+        return None
+    return d["traffic_over_algorithmic"] * nbytes
+
+
 def _score_err(ft, lam, ft_ref, lam_ref):
     ft = ft.double().cpu().numpy()
     got = ft * np.exp(lam.cpu().numpy() - lam_ref)[:, None]
@@ -251,26 +296,49 @@ def run_extras(tn, synth, dev, stream):
     m = [torch.from_numpy(c).to(dev) for c in m_h]
     res = torch.empty(2, dtype=torch.float64, device=dev)
     us = 1e3 * _time(lambda: tn.mps_inner(m, m, prec="fp32", out=res), 50, 5, stream)
+    us_graph = 1e3 * _time_graph(lambda: tn.mps_inner(m, m, prec="fp32", out=res), 20, 10, stream)
     v, lg = oracle.mps_inner(m_h, m_h)
     r = res.cpu().numpy()
-    out["mps_norm_n20_chi32"] = {"us_per_call": us,
+    out["mps_norm_n20_chi32"] = {"us_per_call_graph": us_graph, "us_per_call_eager": us,
                                  "rel_err_vs_oracle": abs(r[0] * np.exp(r[1] - lg) - v) / abs(v)}
 
-    # config 5: TFIM energy, N=100, chi=256, left-canonical
-    cores = _lc_mps_device(100, 2, 256, 5, dev)
+    # config 5: TFIM energy, N=100, chi 256 / 512 / 1024, left-canonical.
+    # |E| is small against the energy scale J(N-1)+hN of a random state, so
+    # the differences are stated per site and relative to that scale.
     W = [torch.from_numpy(w).to(dev) for w in synth.tfim_mpo(100)]
-    flops = _expect_flops(cores, W)
-    en = {"gflop": flops / 1e9}
-    res = torch.empty(4, dtype=torch.float64, device=dev)
+    scale = 1.0 * 99 + 1.0 * 100
+    for chi in (256, 512, 1024):
+        cores = _lc_mps_device(100, 2, chi, 5, dev)
+        flops = _expect_flops(cores, W)
+        en = {"gflop": flops / 1e9}
+        res = torch.empty(4, dtype=torch.float64, device=dev)
+        energy = {}
+        for prec in ("bf16x3", "fp32", "bf16"):
+            ms = _time(lambda: tn.mps_expect(cores, W, prec=prec, out=res), 2, 1, stream)
+            r = res.cpu().numpy()
+            energy[prec] = r[0] * np.exp(r[1]) / (r[2] * np.exp(r[3]))
+            en[prec] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "energy_per_site": energy[prec] / 100}
+        for prec in ("bf16x3", "bf16"):
+            en[prec]["diff_vs_fp32_over_energy_scale"] = abs(energy[prec] - energy["fp32"]) / scale
+        out["tfim_energy_n100_chi%d" % chi] = en
+        del cores
+
+    # config 5 batch: 64 left-canonical MPS, chi ~ U{64, 96, ..., 512} (seed 50), grouped launches
+    chis = synth.uneven_chis(64, seed=50)
+    states = [_lc_mps_device(100, 2, chi, 500 + k, dev) for k, chi in enumerate(chis)]
+    flops = sum(_expect_flops(c, W) for c in states)
+    en = {"gflop": flops / 1e9, "states": len(states), "chi_min": min(chis), "chi_max": max(chis)}
+    res = torch.empty(len(states), 4, dtype=torch.float64, device=dev)
+    energy = {}
     for prec in ("bf16x3", "fp32", "bf16"):
-        ms = _time(lambda: tn.mps_expect(cores, W, prec=prec, out=res), 2, 1, stream)
+        ms = _time(lambda: tn.mps_expect_grouped(states, W, prec=prec, out=res), 2, 1, stream)
         r = res.cpu().numpy()
-        e = r[0] * np.exp(r[1]) / (r[2] * np.exp(r[3]))
-        en[prec] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "energy_per_site": e / 100}
+        energy[prec] = r[:, 0] * np.exp(r[:, 1] - r[:, 3]) / r[:, 2]
+        en[prec] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
     for prec in ("bf16x3", "bf16"):
-        en[prec]["rel_diff_vs_fp32"] = abs(en[prec]["energy_per_site"] - en["fp32"]["energy_per_site"]) / abs(
-            en["fp32"]["energy_per_site"])
-    out["tfim_energy_n100_chi256"] = en
+        en[prec]["max_diff_vs_fp32_over_energy_scale"] = float(np.max(np.abs(energy[prec] - energy["fp32"])) / scale)
+    out["tfim_energy_batch64_n100_chi64_512"] = en
+    del states
     return out
 
 
@@ -429,7 +497,7 @@ def main():
     hbm_peak, bf16_peak, peak_src = measured_peaks()
     achieved_gbs = nbytes / (launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None,
+                "frac": achieved_gbs / hbm_peak, "traffic": contract_traffic(nbytes),
                 "kernel": "tc_contract_kernel<bf16>", "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": nbytes,
                 "tensor_tflops": flops / (launch_ms * 1e-3) / 1e12,

@@ -221,6 +221,28 @@ size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H);
 int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace, size_t ws_bytes,
                   double* result, void* stream);
 
+/*
+ * tn_mps_expect for a batch of `count` MPS sharing one MPO (same n and d for
+ * all; bond dimensions may differ from state to state). Each site step runs
+ * as grouped launches over the whole batch: {norm T, (i)} in one launch,
+ * the norm environment update and (ii) in one each, (iii) in one, then one
+ * grouped rescale of all 2*count environments, so a sweep is a fixed
+ * number of launches per site whatever the batch size.
+ *   psis:   HOST array of `count` chains.
+ *   result: DEVICE pointer to 4*count doubles, {e_value, e_log_scale,
+ *           n_value, n_log_scale} per state, as tn_mps_expect.
+ *   workspace: DEVICE scratch of tn_mps_expect_grouped_workspace_bytes()
+ *           bytes, 256-byte aligned: the environments and intermediates of
+ *           every state plus the uploaded launch tables. The call uploads
+ *           those tables (host -> device copies on `stream`) and then
+ *           launches; it is not meant for stream capture.
+ * Errors: as tn_mps_expect, plus TN_ERR_ARG when count < 1 or the states
+ * differ in length or physical dimension.
+ */
+size_t tn_mps_expect_grouped_workspace_bytes(const tn_mps* psis, int count, const tn_mpo* H, int prec);
+int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
+                          size_t ws_bytes, double* result, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* MPS image classifier (Sec. IV.A)                                          */
 /* ------------------------------------------------------------------------ */

@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "packed.h"
 #include "ptx.cuh"
 #include "tn_internal.h"
 
@@ -48,11 +49,16 @@ static int launch_one(const ContractDesc& d, int prec, cudaStream_t stream) {
 
 using namespace tn;
 
+// A grouped contraction. FP32 plans launch the single-pass float32 kernel
+// over `descs`; BF16 / BF16X3 plans launch pack + GEMM over `pp` (the
+// operands packed once into bf16 blocks inside the workspace).
 struct tn_group_plan {
   std::vector<ContractDesc> descs;  // launched specs, largest first, tile_begin set
   std::vector<ContractDesc> zeros;  // specs with an empty shared index (K = 0): C = 0
   std::vector<ZeroRange> zero_ranges;  // results zeroed on the device before the launch
-  std::vector<int32_t> unit_desc;      // descriptor index of every work unit
+  std::vector<int32_t> unit_desc;      // descriptor (or GEMM) index of every work unit
+  tn::PackedPlan pp;                   // packed path (BF16 / BF16X3)
+  bool packed = false;
   int prec = TN_PREC_FP32;
   int64_t total_tiles = 0;
   double flops = 0.0, bytes = 0.0;
@@ -149,6 +155,13 @@ int tn::contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor*
 extern "C" {
 
 int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn_group_plan** plan) {
+  return tn::group_plan_create_ex(specs, nspecs, prec, true, plan);
+}
+
+}  // extern "C"
+
+int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec, bool allow_packed,
+                             tn_group_plan** plan) {
   if (!plan) return TN_ERR_ARG;
   *plan = nullptr;
   if (nspecs < 0 || (nspecs > 0 && !specs)) return TN_ERR_ARG;
@@ -173,6 +186,37 @@ int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn
     p->descs.push_back(d);
   }
   // largest work units first, so the tail of the launch is made of small ones
+  if (prec != TN_PREC_FP32 && allow_packed) {
+    p->packed = true;
+    for (const auto& d : p->descs) {
+      const int rc = plan_packed(d, prec, &p->pp);
+      if (rc != TN_OK) { delete p; return rc; }
+    }
+    // largest units first: tensor time plus memory time of one unit
+    auto cost = [](const GemmDesc& g) {
+      const double pr = (double)std::min<int64_t>(g.RP, 128), qr = (double)std::min<int64_t>(g.RQ, 128);
+      const double k = 64.0 * std::min<int64_t>(g.slabs, g.slabs_per_split);
+      return 2.0 * pr * qr * k / 1500.0 + (2.0 * (pr + qr) * k + 4.0 * pr * qr) / 5.0;
+    };
+    std::stable_sort(p->pp.gemms.begin(), p->pp.gemms.end(),
+                     [&](const GemmDesc& a, const GemmDesc& b) { return cost(a) > cost(b); });
+    int64_t t = 0;
+    for (auto& g : p->pp.gemms) {
+      g.tile_begin = t;
+      t += (int64_t)g.tiles_p * g.tiles_q * g.splits;
+      if (g.splits > 1) p->zero_ranges.push_back(ZeroRange{g.C, g.RP * g.RQ});
+    }
+    p->total_tiles = t;
+    if (t > 0x7FFFFFFF) { delete p; return TN_ERR_UNSUPPORTED; }
+    p->unit_desc.resize((size_t)t);
+    for (size_t i = 0; i < p->pp.gemms.size(); ++i) {
+      const GemmDesc& g = p->pp.gemms[i];
+      const int64_t n = (int64_t)g.tiles_p * g.tiles_q * g.splits;
+      std::fill(p->unit_desc.begin() + g.tile_begin, p->unit_desc.begin() + g.tile_begin + n, (int32_t)i);
+    }
+    *plan = p;
+    return TN_OK;
+  }
   auto unit_work = [](const ContractDesc& d) {
     return (double)std::min<int64_t>(d.M, TC_BM) * (double)std::min<int64_t>(d.N, TC_BN) *
            (double)std::min<int64_t>(d.K, d.k_per_split);
@@ -198,24 +242,39 @@ int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn
   return TN_OK;
 }
 
-// Workspace layout (each part 256-byte aligned): descriptors, zero ranges,
-// unit -> descriptor map.
+extern "C" {
+
+// Workspace layout (each part 256-byte aligned): descriptors (ContractDesc,
+// or GemmDesc when packed) | zero ranges | unit -> descriptor map |
+// (packed:) pack jobs | pack units | packed blocks.
 static size_t zero_offset(const tn_group_plan* plan) {
-  return align256(sizeof(ContractDesc) * plan->descs.size());
+  return plan->packed ? align256(sizeof(GemmDesc) * plan->pp.gemms.size())
+                      : align256(sizeof(ContractDesc) * plan->descs.size());
 }
 static size_t map_offset(const tn_group_plan* plan) {
   return zero_offset(plan) + align256(sizeof(ZeroRange) * plan->zero_ranges.size());
 }
+static size_t jobs_offset(const tn_group_plan* plan) {
+  return map_offset(plan) + align256(sizeof(int32_t) * plan->unit_desc.size());
+}
+static size_t punits_offset(const tn_group_plan* plan) {
+  return jobs_offset(plan) + align256(sizeof(PackJob) * plan->pp.jobs.size());
+}
+static size_t packed_offset(const tn_group_plan* plan) {
+  return punits_offset(plan) + align256(sizeof(PackUnit) * plan->pp.units.size());
+}
 
 size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
   if (!plan) return 0;
+  if (plan->packed) return packed_offset(plan) + plan->pp.packed_bytes;
   return map_offset(plan) + sizeof(int32_t) * plan->unit_desc.size();
 }
 
 double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
 int tn_group_plan_launches(const tn_group_plan* plan) {
   if (!plan) return 0;
-  return (plan->total_tiles > 0 ? 1 : 0) + (plan->zero_ranges.empty() ? 0 : 1);
+  const int main = plan->total_tiles > 0 ? (plan->packed ? 2 : 1) : 0;
+  return main + (plan->zero_ranges.empty() ? 0 : 1);
 }
 double tn_group_plan_bytes(const tn_group_plan* plan) { return plan ? plan->bytes : 0.0; }
 
@@ -233,10 +292,33 @@ int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t byte
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // pageable sources: each call returns once the bytes are staged, so the
   // plan may be destroyed right after it
-  if (!plan->descs.empty() &&
-      cudaMemcpyAsync(workspace, plan->descs.data(), sizeof(ContractDesc) * plan->descs.size(),
-                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  if (plan->packed) {
+    // device addresses of the packed blocks, patched into copies of the lists
+    uint8_t* packed = base + packed_offset(plan);
+    std::vector<GemmDesc> g = plan->pp.gemms;
+    for (auto& e : g) {
+      e.P = packed + e.P_off;
+      e.Q = packed + e.Q_off;
+    }
+    std::vector<PackJob> j = plan->pp.jobs;
+    for (size_t i = 0; i < j.size(); ++i) {
+      j[i].hi = packed + plan->pp.job_hi_off[i];
+      j[i].lo = plan->pp.job_lo_off[i] == SIZE_MAX ? nullptr : packed + plan->pp.job_lo_off[i];
+    }
+    if ((!g.empty() && cudaMemcpyAsync(base, g.data(), sizeof(GemmDesc) * g.size(), cudaMemcpyHostToDevice, s) !=
+                           cudaSuccess) ||
+        (!j.empty() && cudaMemcpyAsync(base + jobs_offset(plan), j.data(), sizeof(PackJob) * j.size(),
+                                       cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+        (!plan->pp.units.empty() &&
+         cudaMemcpyAsync(base + punits_offset(plan), plan->pp.units.data(), sizeof(PackUnit) * plan->pp.units.size(),
+                         cudaMemcpyHostToDevice, s) != cudaSuccess))
+      return TN_ERR_CUDA;
+  } else if (!plan->descs.empty() &&
+             cudaMemcpyAsync(workspace, plan->descs.data(), sizeof(ContractDesc) * plan->descs.size(),
+                             cudaMemcpyHostToDevice, s) != cudaSuccess) {
     return TN_ERR_CUDA;
+  }
   if (!plan->zero_ranges.empty() &&
       cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + zero_offset(plan), plan->zero_ranges.data(),
                       sizeof(ZeroRange) * plan->zero_ranges.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -261,8 +343,15 @@ int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, 
                      (int)plan->zero_ranges.size(), s);
     if (rc != TN_OK) return rc;
   }
-  const ContractDesc* g = static_cast<const ContractDesc*>(workspace);
   const int32_t* map = reinterpret_cast<const int32_t*>(static_cast<uint8_t*>(workspace) + map_offset(plan));
+  if (plan->packed) {
+    uint8_t* base = static_cast<uint8_t*>(workspace);
+    rc = launch_pack(reinterpret_cast<const PackJob*>(base + jobs_offset(plan)),
+                     reinterpret_cast<const PackUnit*>(base + punits_offset(plan)), (int64_t)plan->pp.units.size(), s);
+    if (rc != TN_OK) return rc;
+    return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->total_tiles, plan->prec, s);
+  }
+  const ContractDesc* g = static_cast<const ContractDesc*>(workspace);
   if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, map, plan->total_tiles, s);
   return launch_contract_tc(plan->descs[0], g, map, plan->total_tiles, plan->prec, s);
 }

@@ -699,7 +699,7 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
         }
       }
       tn_group_plan* plan = nullptr;
-      if ((rc = tn_group_plan_create(specs.data(), (int)specs.size(), dprec, &plan)) != TN_OK) return rc;
+      if ((rc = group_plan_create_ex(specs.data(), (int)specs.size(), dprec, false, &plan)) != TN_OK) return rc;
       rc = tn_group_plan_upload(plan, w.plan_ws, w.plan_bytes, s);
       if (rc == TN_OK) rc = tn_group_plan_run(plan, w.plan_ws, w.plan_bytes, s);
       tn_group_plan_destroy(plan);

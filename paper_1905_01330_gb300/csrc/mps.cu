@@ -30,6 +30,10 @@ struct SmallChain {
   const float* ket[SMALL_MAXN];
 };
 
+__device__ __forceinline__ uint32_t ptx_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
 __device__ float block_max(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -83,6 +87,125 @@ mps_inner_small_kernel(const __grid_constant__ SmallChain c, double* result) {
     lg += (double)logf(sc);
     __syncthreads();
   }
+  if (tid == 0) {
+    result[0] = (double)E[0];
+    result[1] = lg;
+  }
+}
+
+// The same sweep with both cores of every site staged in shared memory: the
+// cores of site i+1 are copied in (cp.async, no registers) while site i is
+// contracted, and each thread computes four consecutive outputs along the
+// ket bond, so every shared-memory operand read feeds four FMAs.
+// Dynamic shared memory: E, E2 (emax floats each), T (tmax), two ket and two
+// bra core buffers (cmax each).
+struct StagedSizes {
+  int32_t emax, tmax, cmax;
+};
+
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(ptx_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ptx_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copies n floats global -> shared by all threads of the block.
+__device__ __forceinline__ void stage_core(float* dst, const float* __restrict__ src, int n) {
+  const bool v16 = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && ((n & 3) == 0);
+  if (v16) {
+    for (int i = threadIdx.x * 4; i < n; i += SMALL_THREADS * 4) cp_async_16(dst + i, src + i);
+  } else {
+    for (int i = threadIdx.x; i < n; i += SMALL_THREADS) cp_async_f32(dst + i, src + i);
+  }
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS)
+mps_inner_staged_kernel(const __grid_constant__ SmallChain c, StagedSizes z, double* result) {
+  extern __shared__ __align__(16) float smf[];
+  float* E = smf;
+  float* E2 = E + z.emax;
+  float* T = E2 + z.emax;
+  float* const kbuf = T + z.tmax;          // ket cores of sites i (i & 1) and i + 1
+  float* const bbuf = kbuf + 2 * z.cmax;   // bra cores, likewise
+  __shared__ float red[SMALL_THREADS / 32];
+  const int tid = threadIdx.x;
+  const int d = c.d;
+  if (tid == 0) E[0] = 1.0f;
+  double lg = 0.0;
+  stage_core(kbuf, c.ket[0], c.bk[0] * d * c.bk[1]);
+  stage_core(bbuf, c.bra[0], c.bb[0] * d * c.bb[1]);
+  cp_async_commit();
+  for (int i = 0; i < c.n; ++i) {
+    const int Da = c.bb[i], Db = c.bb[i + 1], Dak = c.bk[i], Dbk = c.bk[i + 1];
+    cp_async_wait_all();
+    __syncthreads();  // site i's cores (and E) visible to all; buffers of site i-1 free
+    if (i + 1 < c.n) {
+      stage_core(kbuf + ((i + 1) & 1) * z.cmax, c.ket[i + 1], Dbk * d * c.bk[i + 2]);
+      stage_core(bbuf + ((i + 1) & 1) * z.cmax, c.bra[i + 1], Db * d * c.bb[i + 2]);
+    }
+    cp_async_commit();
+    const float* K = kbuf + (i & 1) * z.cmax;
+    const float* Br = bbuf + (i & 1) * z.cmax;
+    // T[a, s, bk] = sum_ak E[a, ak] K[ak, s, bk], four bk per thread when Dbk % 4 == 0
+    const int w = (Dbk & 3) == 0 ? 4 : 1;
+    const int qn = Dbk / w;
+    const int nt = Da * d * qn;
+    for (int idx = tid; idx < nt; idx += SMALL_THREADS) {
+      const int q = idx % qn, rest = idx / qn, sidx = rest % d, a = rest / d;
+      const int bk = q * w;
+      if (w == 4) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int ak = 0; ak < Dak; ++ak) {
+          const float e = E[a * Dak + ak];
+          const float4 k4 = *reinterpret_cast<const float4*>(K + (ak * d + sidx) * Dbk + bk);
+          acc.x = fmaf(e, k4.x, acc.x);
+          acc.y = fmaf(e, k4.y, acc.y);
+          acc.z = fmaf(e, k4.z, acc.z);
+          acc.w = fmaf(e, k4.w, acc.w);
+        }
+        *reinterpret_cast<float4*>(T + (a * d + sidx) * Dbk + bk) = acc;
+      } else {
+        float acc = 0.0f;
+        for (int ak = 0; ak < Dak; ++ak) acc = fmaf(E[a * Dak + ak], K[(ak * d + sidx) * Dbk + bk], acc);
+        T[(a * d + sidx) * Dbk + bk] = acc;
+      }
+    }
+    __syncthreads();
+    // E2[b, bk] = sum_{a, s} Br[a, s, b] T[a, s, bk]
+    const int ne = Db * qn;
+    float mx = 0.0f;
+    for (int idx = tid; idx < ne; idx += SMALL_THREADS) {
+      const int q = idx % qn, b = idx / qn;
+      const int bk = q * w;
+      if (w == 4) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int as = 0; as < Da * d; ++as) {
+          const float br = Br[as * Db + b];
+          const float4 t4 = *reinterpret_cast<const float4*>(T + as * Dbk + bk);
+          acc.x = fmaf(br, t4.x, acc.x);
+          acc.y = fmaf(br, t4.y, acc.y);
+          acc.z = fmaf(br, t4.z, acc.z);
+          acc.w = fmaf(br, t4.w, acc.w);
+        }
+        *reinterpret_cast<float4*>(E2 + b * Dbk + bk) = acc;
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(acc.x), fabsf(acc.y)), fmaxf(fabsf(acc.z), fabsf(acc.w))));
+      } else {
+        float acc = 0.0f;
+        for (int as = 0; as < Da * d; ++as) acc = fmaf(Br[as * Db + b], T[as * Dbk + bk], acc);
+        E2[b * Dbk + bk] = acc;
+        mx = fmaxf(mx, fabsf(acc));
+      }
+    }
+    const float m = block_max(mx, red);
+    const float sc = m > 0.0f ? m : 1.0f;
+    for (int idx = tid; idx < Db * Dbk; idx += SMALL_THREADS) E[idx] = E2[idx] / sc;
+    lg += (double)logf(sc);
+  }
+  cp_async_wait_all();
+  __syncthreads();
   if (tid == 0) {
     result[0] = (double)E[0];
     result[1] = lg;
@@ -283,6 +406,31 @@ int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace
     for (int i = 0; i < bra->n; ++i) {
       c.bra[i] = bra->cores[i];
       c.ket[i] = ket->cores[i];
+    }
+    // staged variant when its buffers fit: E, E2, T and four core buffers
+    StagedSizes z{1, 1, 1};
+    for (int i = 0; i < bra->n; ++i) {
+      z.emax = std::max(z.emax, c.bb[i + 1] * c.bk[i + 1]);
+      z.emax = std::max(z.emax, c.bb[i] * c.bk[i]);
+      z.tmax = std::max(z.tmax, c.bb[i] * c.d * c.bk[i + 1]);
+      z.cmax = std::max(z.cmax, std::max(c.bb[i] * c.d * c.bb[i + 1], c.bk[i] * c.d * c.bk[i + 1]));
+    }
+    // every buffer starts on a 16-byte boundary
+    z.emax = (z.emax + 3) & ~3;
+    z.tmax = (z.tmax + 3) & ~3;
+    z.cmax = (z.cmax + 3) & ~3;
+    const size_t staged = sizeof(float) * (2 * (size_t)z.emax + z.tmax + 4 * (size_t)z.cmax);
+    constexpr size_t STAGED_MAX = 200 * 1024;
+    if (staged <= STAGED_MAX) {
+      static bool attr2 = false;
+      if (!attr2) {
+        if (cudaFuncSetAttribute(mps_inner_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)STAGED_MAX) != cudaSuccess)
+          return TN_ERR_CUDA;
+        attr2 = true;
+      }
+      mps_inner_staged_kernel<<<1, SMALL_THREADS, staged, s>>>(c, z, result);
+      return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
     }
     const size_t smem = sizeof(float) * (2 * SMALL_D * SMALL_D + SMALL_D * SMALL_PHYS * SMALL_D);
     static bool attr = false;

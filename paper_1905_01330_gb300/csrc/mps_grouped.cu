@@ -1,0 +1,326 @@
+// <psi_k|H|psi_k> and <psi_k|psi_k> for a batch of MPS with uneven bond
+// dimensions and one shared MPO (the environment sweep of Sec. II / Fig. 3a
+// applied to many chains at once). Every site step of every chain goes into
+// grouped contraction launches, so the launch count per site does not grow
+// with the batch: stage 1 = {norm: T = E psi, energy (i)}, stage 2 = {norm:
+// E' = psi T} and {energy (ii), float32}, stage 3 = {energy (iii)}, then one
+// grouped rescale of all 2*count new environments.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <vector>
+
+#include "tn_internal.h"
+
+namespace tn {
+namespace {
+
+// One environment to rescale after a site: x[0..n) /= max|x|, log(max) added
+// to *lg; *bits holds the running max (float bits) and starts at 0.
+struct Segment {
+  float* x;
+  int64_t n;
+  unsigned* bits;
+  double* lg;
+};
+
+__device__ float seg_block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float m = 0.0f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+
+// grid (blocks per segment, segments)
+__global__ void seg_absmax_kernel(const Segment* __restrict__ segs) {
+  __shared__ float red[32];
+  const Segment s = segs[blockIdx.y];
+  float m = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(s.x[i]));
+  m = seg_block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(s.bits, __float_as_uint(m));
+}
+
+__global__ void seg_scale_kernel(const Segment* __restrict__ segs) {
+  const Segment s = segs[blockIdx.y];
+  const float m = __uint_as_float(*s.bits);
+  const float sc = m > 0.0f ? m : 1.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x)
+    s.x[i] = s.x[i] / sc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s.lg += log((double)sc);
+}
+
+// Per chain: the two starting environments set to the 1x1 (x1) identity.
+struct ChainInit {
+  float* E;
+  float* L;
+};
+
+__global__ void grouped_init_kernel(const ChainInit* __restrict__ c, int count, double* lg, int nlg,
+                                    unsigned* bits, int64_t nbits) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t; i < nbits; i += stride) bits[i] = 0u;
+  for (int64_t i = t; i < nlg; i += stride) lg[i] = 0.0;
+  for (int64_t i = t; i < count; i += stride) {
+    c[i].E[0] = 1.0f;
+    c[i].L[0] = 1.0f;
+  }
+}
+
+// Per chain: where the final 1x1 environments ended.
+struct ChainFinal {
+  const float* E;
+  const float* L;
+};
+
+__global__ void grouped_finish_kernel(const ChainFinal* __restrict__ f, int count, const double* __restrict__ lg,
+                                      double* result) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    result[4 * k + 0] = (double)f[k].L[0];
+    result[4 * k + 1] = lg[2 * k + 1];
+    result[4 * k + 2] = (double)f[k].E[0];
+    result[4 * k + 3] = lg[2 * k + 0];
+  }
+}
+
+tn_tensor make_tensor(float* p, int rank, const int64_t* sh) {
+  tn_tensor t;
+  tn_tensor_init(&t, p, rank, sh);
+  return t;
+}
+
+tn_contract_spec make_spec(const tn_tensor& A, std::initializer_list<int> la, const tn_tensor& B,
+                           std::initializer_list<int> lb, const tn_tensor& C) {
+  tn_contract_spec s;
+  memset(&s, 0, sizeof(s));
+  s.A = A;
+  s.B = B;
+  s.C = C;
+  s.nshared = (int32_t)la.size();
+  int j = 0;
+  for (int v : la) s.legsA[j++] = v;
+  j = 0;
+  for (int v : lb) s.legsB[j++] = v;
+  return s;
+}
+
+int64_t chain_max_bond(const tn_mps& m) {
+  int64_t x = 1;
+  for (int i = 0; i <= m.n; ++i) x = std::max(x, m.bond[i]);
+  return x;
+}
+
+int check_one(const tn_mps& m) {
+  if (m.n < 1 || m.d < 1 || !m.bond || !m.cores) return TN_ERR_ARG;
+  if (m.bond[0] != 1 || m.bond[m.n] != 1) return TN_ERR_ARG;
+  for (int i = 0; i < m.n; ++i)
+    if (m.bond[i + 1] < 1 || !m.cores[i]) return TN_ERR_ARG;
+  return TN_OK;
+}
+
+struct PlanDeleter {
+  void operator()(tn_group_plan* p) const { tn_group_plan_destroy(p); }
+};
+using PlanPtr = std::unique_ptr<tn_group_plan, PlanDeleter>;
+
+// Host-side layout of one grouped sweep: buffers of every chain, the site
+// plans (four per site) and the per-site rescale tables.
+struct GroupedSweep {
+  struct ChainBufs {
+    float *E[2], *T, *L[2], *T1, *T2;
+  };
+  int count = 0, n = 0;
+  int64_t d = 0;
+  std::vector<ChainBufs> bufs;
+  std::vector<PlanPtr> plans;         // site-major: 4 per site
+  std::vector<size_t> plan_off;       // workspace offset of each plan's work list
+  std::vector<size_t> plan_bytes;
+  std::vector<Segment> segs;          // n * 2 * count
+  std::vector<ChainInit> inits;
+  std::vector<ChainFinal> finals;
+  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_init = 0, off_final = 0, total = 0;
+  int64_t nbits = 0;
+};
+
+// Builds the layout of a workspace at `base` (the plans' work lists decide
+// its size, so they are built even when only the size is wanted; nothing is
+// dereferenced on the host).
+int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_t* base, GroupedSweep* g) {
+  if (!psis || count < 1 || count > 16384 || !H || !H->bond || !H->cores) return TN_ERR_ARG;
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  const int n = psis[0].n;
+  const int64_t d = psis[0].d;
+  for (int k = 0; k < count; ++k) {
+    int rc = check_one(psis[k]);
+    if (rc != TN_OK) return rc;
+    if (psis[k].n != n || psis[k].d != d) return TN_ERR_ARG;
+  }
+  if (H->n != n || H->d != d || H->bond[0] != 1 || H->bond[n] != 1) return TN_ERR_ARG;
+  int64_t Wm = 1;
+  for (int i = 0; i < n; ++i) {
+    if (H->bond[i + 1] < 1 || !H->cores[i]) return TN_ERR_ARG;
+    Wm = std::max(Wm, H->bond[i + 1]);
+  }
+  g->count = count;
+  g->n = n;
+  g->d = d;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    uint8_t* p = base + off;
+    off += align256(b);
+    return reinterpret_cast<float*>(p);
+  };
+  g->bufs.resize((size_t)count);
+  for (int k = 0; k < count; ++k) {
+    const int64_t D = chain_max_bond(psis[k]);
+    auto& b = g->bufs[(size_t)k];
+    b.E[0] = take(sizeof(float) * D * D);
+    b.E[1] = take(sizeof(float) * D * D);
+    b.T = take(sizeof(float) * D * d * D);
+    b.L[0] = take(sizeof(float) * Wm * D * D);
+    b.L[1] = take(sizeof(float) * Wm * D * D);
+    b.T1 = take(sizeof(float) * Wm * D * d * D);
+    b.T2 = take(sizeof(float) * Wm * D * d * D);
+  }
+  g->off_lg = off;
+  off += align256(sizeof(double) * 2 * (size_t)count);
+  g->off_bits = off;
+  g->nbits = (int64_t)n * 2 * count;
+  off += align256(sizeof(unsigned) * (size_t)g->nbits);
+  double* lg = reinterpret_cast<double*>(base + g->off_lg);
+  unsigned* bits = reinterpret_cast<unsigned*>(base + g->off_bits);
+
+  // site plans
+  std::vector<tn_contract_spec> s1, s2a, s2b, s3;
+  for (int i = 0; i < n; ++i) {
+    s1.clear();
+    s2a.clear();
+    s2b.clear();
+    s3.clear();
+    const int64_t wa = H->bond[i], wb = H->bond[i + 1];
+    for (int k = 0; k < count; ++k) {
+      const tn_mps& m = psis[k];
+      auto& b = g->bufs[(size_t)k];
+      const int64_t Da = m.bond[i], Db = m.bond[i + 1];
+      float* core = m.cores[i];
+      const int64_t shE[2] = {Da, Da}, shA[3] = {Da, d, Db}, shT[3] = {Da, d, Db}, shE2[2] = {Db, Db};
+      const tn_tensor tE = make_tensor(b.E[i & 1], 2, shE), tA = make_tensor(core, 3, shA);
+      const tn_tensor tT = make_tensor(b.T, 3, shT), tE2 = make_tensor(b.E[(i + 1) & 1], 2, shE2);
+      const int64_t shL[3] = {wa, Da, Da}, shT1[4] = {wa, Da, d, Db}, shW[4] = {wa, wb, d, d};
+      const int64_t shT2[4] = {wb, d, Da, Db}, shL2[3] = {wb, Db, Db};
+      const tn_tensor tL = make_tensor(b.L[i & 1], 3, shL), tT1 = make_tensor(b.T1, 4, shT1);
+      const tn_tensor tW = make_tensor(H->cores[i], 4, shW), tT2 = make_tensor(b.T2, 4, shT2);
+      const tn_tensor tL2 = make_tensor(b.L[(i + 1) & 1], 3, shL2);
+      // norm:  T[a, s, b'] = sum_a' E[a, a'] psi[a', s, b']
+      s1.push_back(make_spec(tE, {1}, tA, {0}, tT));
+      // (i)   T1[w, a', s, b] = sum_a L[w, a, a'] psi[a, s, b]
+      s1.push_back(make_spec(tL, {1}, tA, {0}, tT1));
+      // norm:  E'[b, b'] = sum_{a, s} psi[a, s, b] T[a, s, b']
+      s2a.push_back(make_spec(tA, {0, 1}, tT, {0, 1}, tE2));
+      // (ii)  T2[w', s', a', b] = sum_{w, s} W[w, w', s, s'] T1[w, a', s, b]
+      s2b.push_back(make_spec(tW, {0, 2}, tT1, {0, 2}, tT2));
+      // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] psi[a', s', b']
+      s3.push_back(make_spec(tT2, {1, 2}, tA, {1, 0}, tL2));
+      g->segs.push_back(Segment{b.E[(i + 1) & 1], Db * Db, bits + (size_t)(2 * count) * i + 2 * k, lg + 2 * k});
+      g->segs.push_back(
+          Segment{b.L[(i + 1) & 1], wb * Db * Db, bits + (size_t)(2 * count) * i + 2 * k + 1, lg + 2 * k + 1});
+    }
+    const std::vector<tn_contract_spec>* stages[4] = {&s1, &s2a, &s2b, &s3};
+    const int precs[4] = {prec, prec, TN_PREC_FP32, prec};
+    for (int j = 0; j < 4; ++j) {
+      tn_group_plan* p = nullptr;
+      int rc = tn_group_plan_create(stages[j]->data(), (int)stages[j]->size(), precs[j], &p);
+      if (rc != TN_OK) return rc;
+      g->plans.emplace_back(p);
+      const size_t bytes = tn_group_plan_workspace_bytes(p);
+      g->plan_off.push_back(off);
+      g->plan_bytes.push_back(bytes);
+      off += align256(bytes);
+    }
+  }
+  g->off_segs = off;
+  off += align256(sizeof(Segment) * g->segs.size());
+  g->inits.resize((size_t)count);
+  g->finals.resize((size_t)count);
+  for (int k = 0; k < count; ++k) {
+    g->inits[(size_t)k] = ChainInit{g->bufs[(size_t)k].E[0], g->bufs[(size_t)k].L[0]};
+    g->finals[(size_t)k] = ChainFinal{g->bufs[(size_t)k].E[n & 1], g->bufs[(size_t)k].L[n & 1]};
+  }
+  g->off_init = off;
+  off += align256(sizeof(ChainInit) * (size_t)count);
+  g->off_final = off;
+  off += align256(sizeof(ChainFinal) * (size_t)count);
+  g->total = off;
+  return TN_OK;
+}
+
+}  // namespace
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+size_t tn_mps_expect_grouped_workspace_bytes(const tn_mps* psis, int count, const tn_mpo* H, int prec) {
+  // sizes only: any 256-byte aligned base gives the same layout
+  GroupedSweep g;
+  if (build_sweep(psis, count, H, prec, reinterpret_cast<uint8_t*>(uintptr_t(1) << 20), &g) != TN_OK) return 0;
+  return g.total;
+}
+
+int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
+                          size_t ws_bytes, double* result, void* stream) {
+  if (!result) return TN_ERR_ARG;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  GroupedSweep g;
+  int rc = build_sweep(psis, count, H, prec, base, &g);
+  if (rc != TN_OK) return rc;
+  if (ws_bytes < g.total) return TN_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // uploads: plan work lists, rescale segments, init and final tables
+  for (size_t j = 0; j < g.plans.size(); ++j) {
+    if (g.plan_bytes[j] == 0) continue;
+    rc = tn_group_plan_upload(g.plans[j].get(), base + g.plan_off[j], g.plan_bytes[j], s);
+    if (rc != TN_OK) return rc;
+  }
+  if (cudaMemcpyAsync(base + g.off_segs, g.segs.data(), sizeof(Segment) * g.segs.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(base + g.off_init, g.inits.data(), sizeof(ChainInit) * g.inits.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + g.off_final, g.finals.data(), sizeof(ChainFinal) * g.finals.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  double* lg = reinterpret_cast<double*>(base + g.off_lg);
+  unsigned* bits = reinterpret_cast<unsigned*>(base + g.off_bits);
+  grouped_init_kernel<<<64, 256, 0, s>>>(reinterpret_cast<const ChainInit*>(base + g.off_init), count, lg,
+                                         2 * count, bits, g.nbits);
+  if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  const Segment* segs = reinterpret_cast<const Segment*>(base + g.off_segs);
+  for (int i = 0; i < g.n; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      const size_t p = (size_t)i * 4 + j;
+      rc = tn_group_plan_run(g.plans[p].get(), base + g.plan_off[p], g.plan_bytes[p], s);
+      if (rc != TN_OK) return rc;
+    }
+    int64_t longest = 1;
+    for (int k = 0; k < 2 * count; ++k) longest = std::max(longest, g.segs[(size_t)(2 * count) * i + k].n);
+    const dim3 grid((unsigned)std::min<int64_t>((longest + 2047) / 2048, 64), (unsigned)(2 * count));
+    seg_absmax_kernel<<<grid, 256, 0, s>>>(segs + (size_t)(2 * count) * i);
+    seg_scale_kernel<<<grid, 256, 0, s>>>(segs + (size_t)(2 * count) * i);
+    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  }
+  grouped_finish_kernel<<<(count + 127) / 128, 128, 0, s>>>(reinterpret_cast<const ChainFinal*>(base + g.off_final),
+                                                           count, lg, result);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+}  // extern "C"

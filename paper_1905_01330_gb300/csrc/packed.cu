@@ -1,0 +1,663 @@
+// Grouped pairwise tensordot in two launches (bf16 operands, tcgen05):
+//
+//   1. pack: every operand of every contraction is gathered once through its
+//      leg strides (the leg permutation and edge flattening of Sec. III.B.2
+//      are folded into this gather), rounded to bf16 (and, for BF16X3, split
+//      into hi + lo), and written as 128-row x 64-k blocks already in the
+//      128-byte-swizzled K-major layout the MMA reads. HBM-bound: 4 bytes
+//      read and 2 (hi) or 4 (hi + lo) written per element.
+//   2. gemm: a persistent, warp-specialised tcgen05 kernel. Warp 0 moves
+//      blocks into a ring of shared-memory stages with 1-D bulk async copies
+//      (one copy per block: the layout needs no gather), warp 1 issues the
+//      MMAs into a double-buffered TMEM accumulator, warps 2-5 drain TMEM and
+//      write C while the next tile is multiplied.
+//
+// The per-tile float32 -> bf16 conversion of the single-launch kernel
+// (contract_tc.cu) repeats for every output tile that reads an operand tile;
+// here it happens once per element, and the MMA loop only moves bytes.
+//
+// The operand with more rows feeds the MMA's M side (128 TMEM lanes); the
+// other one its N side, whose width per tile is cut to the rows present
+// (multiple of 16), so a contraction with one thin side streams its wide
+// operand at memory speed instead of filling a 128x128 tile with padding.
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "gather.cuh"
+#include "packed.h"
+#include "ptx.cuh"
+
+namespace tn {
+namespace {
+
+constexpr int PR = 128;                // rows per block
+constexpr int PK = 64;                 // shared indices per block
+constexpr int PBLOCK = PR * PK * 2;    // bytes of a full bf16 block (16 KB)
+constexpr int PACK_THREADS = 256;
+
+__device__ __forceinline__ uint32_t sw128_chunk(int r, int g) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t bf16x2_rn(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ------------------------------------------------------------------- pack
+// Staging of one block in shared memory. When the source's unit stride runs
+// along k the values are staged row by row (T[row][k]); otherwise column by
+// column (Tt[k][row]). Either way the global reads are coalesced along the
+// unit-stride direction and the 16-byte output chunks are read back without
+// bank conflicts.
+constexpr int TROW = PK + 4;    // row-staged: floats per row
+constexpr int TCOL = PR + 4;    // column-staged: floats per k
+struct PackSmem {
+  union {
+    float T[PR][TROW];
+    float Tt[PK][TCOL];
+  };
+  int64_t roff[PR];      // source offset of each row (valid rows only)
+  int64_t koff[PK];      // source offset of each shared index (valid only)
+};
+
+__device__ __forceinline__ void store_chunk(uint8_t* hi, uint8_t* lo, uint32_t off, const float (&v)[8]) {
+  uint4 h;
+  h.x = bf16x2_rn(v[0], v[1]);
+  h.y = bf16x2_rn(v[2], v[3]);
+  h.z = bf16x2_rn(v[4], v[5]);
+  h.w = bf16x2_rn(v[6], v[7]);
+  *reinterpret_cast<uint4*>(hi + off) = h;
+  if (lo) {
+    const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
+    uint4 l;
+    l.x = bf16x2_rn(v[0] - __low2float(hb[0]), v[1] - __high2float(hb[0]));
+    l.y = bf16x2_rn(v[2] - __low2float(hb[1]), v[3] - __high2float(hb[1]));
+    l.z = bf16x2_rn(v[4] - __low2float(hb[2]), v[5] - __high2float(hb[2]));
+    l.w = bf16x2_rn(v[6] - __low2float(hb[3]), v[7] - __high2float(hb[3]));
+    *reinterpret_cast<uint4*>(lo + off) = l;
+  }
+}
+
+// Packs blocks first .. first+count-1 of job J (all threads of the CTA).
+__device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm) {
+  const int t = threadIdx.x;
+  const float* __restrict__ src = J.src;
+  const int64_t R = J.R, K = J.K;
+  const int slabs = J.slabs;
+  const bool kfast = J.kfast != 0, rfast = J.rfast != 0;
+  for (int b = first; b < first + count; ++b) {
+    const int tile = b / slabs, slab = b - tile * slabs;
+    const int64_t r0 = (int64_t)tile * PR, k0 = (int64_t)slab * PK;
+    const int rv = (int)(R - r0 < PR ? R - r0 : PR);
+    const int kv = (int)(K - k0 < PK ? K - k0 : PK);
+    if (t < PR) sm.roff[t] = t < rv ? leg_offset((uint32_t)(r0 + t), J.nr, J.rdim, J.rstr) : 0;
+    else if (t < PR + PK) sm.koff[t - PR] = (t - PR) < kv ? leg_offset((uint32_t)(k0 + t - PR), J.nk, J.kdim, J.kstr) : 0;
+    __syncthreads();
+    const int rs = (rv + 7) & ~7;  // rows stored: whole 8-row atoms
+    uint8_t* hi = J.hi + (size_t)b * (size_t)J.block_bytes;
+    uint8_t* lo = J.lo ? J.lo + (size_t)b * (size_t)J.block_bytes : nullptr;
+    if (kfast) {
+      // phase A: thread -> (row, 4 consecutive k); consecutive threads walk k
+#pragma unroll 4
+      for (int e = t; e < PR * (PK / 4); e += PACK_THREADS) {
+        const int r = e >> 4, q = (e & 15) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rv && q < kv) {
+          const float* rowp = src + sm.roff[r];
+          const float* p = rowp + sm.koff[q];
+          if (q + 3 < kv && sm.koff[q + 3] == sm.koff[q] + 3 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            v = __ldg(reinterpret_cast<const float4*>(p));
+          } else {
+            v.x = __ldg(p);
+            if (q + 1 < kv) v.y = __ldg(rowp + sm.koff[q + 1]);
+            if (q + 2 < kv) v.z = __ldg(rowp + sm.koff[q + 2]);
+            if (q + 3 < kv) v.w = __ldg(rowp + sm.koff[q + 3]);
+          }
+        }
+        *reinterpret_cast<float4*>(&sm.T[r][q]) = v;
+      }
+      __syncthreads();
+      // phase B: thread -> (row, 8-wide k group)
+      for (int e = t; e < rs * (PK / 8); e += PACK_THREADS) {
+        const int r = e >> 3, g = e & 7;
+        const float4 a = *reinterpret_cast<const float4*>(&sm.T[r][g * 8]);
+        const float4 c = *reinterpret_cast<const float4*>(&sm.T[r][g * 8 + 4]);
+        const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+        store_chunk(hi, lo, sw128_chunk(r, g), v);
+      }
+    } else {
+      // phase A: thread -> (4 consecutive rows, one k); consecutive threads walk rows
+#pragma unroll 4
+      for (int e = t; e < (PR / 4) * PK; e += PACK_THREADS) {
+        const int r = (e & 31) * 4, k = e >> 5;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rv && k < kv) {
+          const float* colp = src + sm.koff[k];
+          const float* p = colp + sm.roff[r];
+          if (rfast && r + 3 < rv && sm.roff[r + 3] == sm.roff[r] + 3 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            v = __ldg(reinterpret_cast<const float4*>(p));
+          } else {
+            v.x = __ldg(p);
+            if (r + 1 < rv) v.y = __ldg(colp + sm.roff[r + 1]);
+            if (r + 2 < rv) v.z = __ldg(colp + sm.roff[r + 2]);
+            if (r + 3 < rv) v.w = __ldg(colp + sm.roff[r + 3]);
+          }
+        }
+        *reinterpret_cast<float4*>(&sm.Tt[k][r]) = v;
+      }
+      __syncthreads();
+      // phase B: thread -> (row, 8-wide k group); consecutive threads walk rows
+      for (int e = t; e < PR * (PK / 8); e += PACK_THREADS) {
+        const int r = e & (PR - 1), g = e >> 7;
+        if (r >= rs) continue;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = sm.Tt[g * 8 + j][r];
+        store_chunk(hi, lo, sw128_chunk(r, g), v);
+      }
+    }
+    __syncthreads();  // staging and offset tables are reused by the next block
+  }
+}
+
+// Grouped form: one CTA per pack unit of the uploaded lists.
+__global__ void __launch_bounds__(PACK_THREADS)
+pack_kernel(const PackJob* __restrict__ jobs, const PackUnit* __restrict__ units) {
+  __shared__ __align__(16) PackSmem sm;
+  const PackUnit un = units[blockIdx.x];
+  pack_blocks(jobs[un.job], un.first, un.count, sm);
+}
+
+// Single-contraction form: both jobs passed by value (nothing to upload, so
+// the launch can be captured in a CUDA graph). CTAs 0 .. units_a-1 pack A,
+// `per_a` blocks each; the rest pack B, `per_b` blocks each.
+struct PackPair {
+  PackJob a, b;
+  int32_t units_a, per_a, per_b, pad;
+};
+
+__global__ void __launch_bounds__(PACK_THREADS)
+pack_pair_kernel(const __grid_constant__ PackPair pp) {
+  __shared__ __align__(16) PackSmem sm;
+  const bool is_a = (int)blockIdx.x < pp.units_a;
+  const PackJob& J = is_a ? pp.a : pp.b;
+  const int per = is_a ? pp.per_a : pp.per_b;
+  const int first = (is_a ? (int)blockIdx.x : (int)blockIdx.x - pp.units_a) * per;
+  const int nb = J.tiles * J.slabs;
+  pack_blocks(J, first, min(per, nb - first), sm);
+}
+
+// ------------------------------------------------------------------- gemm
+constexpr int GEMM_THREADS = 192;   // warp 0 copies, warp 1 MMAs, warps 2-5 epilogue
+constexpr int EPI_WARPS = 4;
+// BF16X3 promotes the TMEM accumulator into float32 registers every KC slabs
+// (256 shared indices): the tensor core's float32 accumulation truncates, and
+// over long k that error would exceed the split's own rounding error.
+constexpr int KC = 4;
+
+template <int SPLIT>
+struct GCfg {
+  static constexpr int OPS = SPLIT ? 4 : 2;            // P hi, Q hi (, P lo, Q lo)
+  static constexpr int STAGES = SPLIT ? 3 : 6;
+  static constexpr int STAGE_BYTES = OPS * PBLOCK;
+  static constexpr uint32_t TMEM_COLS = 256;           // two 128-column accumulators
+};
+
+template <int S>
+struct GemmAux {
+  uint64_t full[S];          // stage s holds its blocks
+  uint64_t empty[S];         // the MMAs reading stage s are complete
+  uint64_t acc_full[2];      // accumulator b holds a finished chunk
+  uint64_t acc_empty[2];     // the epilogue has drained accumulator b
+  uint64_t final_bar;
+  uint32_t tmem_base;
+  volatile int32_t abort;
+};
+
+template <int SPLIT>
+constexpr size_t gemm_smem_bytes() {
+  return 1024 + (size_t)GCfg<SPLIT>::STAGES * GCfg<SPLIT>::STAGE_BYTES + sizeof(GemmAux<GCfg<SPLIT>::STAGES>);
+}
+
+struct GUnit {
+  int64_t p0, q0;        // first row of P and of Q
+  int32_t ks0, nks;      // first slab and slab count
+};
+
+__device__ __forceinline__ GUnit gunit(const GemmDesc& d, int64_t u) {
+  GUnit g;
+  const int64_t tq = u % d.tiles_q;
+  const int64_t rest = u / d.tiles_q;
+  const int64_t tp = rest % d.tiles_p;
+  const int64_t split = rest / d.tiles_p;
+  g.p0 = tp * PR;
+  g.q0 = tq * PR;
+  g.ks0 = (int32_t)(split * d.slabs_per_split);
+  g.nks = (int32_t)(d.slabs - g.ks0 < d.slabs_per_split ? d.slabs - g.ks0 : d.slabs_per_split);
+  return g;
+}
+
+__device__ __forceinline__ uint32_t rows_bytes(int64_t rows_left) {
+  const int64_t r = rows_left < PR ? rows_left : PR;
+  return (uint32_t)(((r + 7) & ~int64_t(7)) * 128);
+}
+
+// The descriptor of global unit u: from the uploaded list, or the by-value
+// single descriptor when there is no list.
+__device__ __forceinline__ GemmDesc load_desc(const GemmDesc& single, const GemmDesc* descs, const int32_t* map,
+                                              int64_t u) {
+  return descs ? descs[__ldg(map + u)] : single;
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __restrict__ descs,
+                   const int32_t* __restrict__ map, int64_t total_units, int* status) {
+  using Cf = GCfg<SPLIT>;
+  constexpr int S = Cf::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(smem + (size_t)S * Cf::STAGE_BYTES);
+  const uint32_t stage0 = ptx::smem_addr(smem);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      ptx::mbar_init(ptx::smem_addr(&x.full[s]), 1);
+      ptx::mbar_init(ptx::smem_addr(&x.empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(ptx::smem_addr(&x.acc_full[b]), 1);
+      ptx::mbar_init(ptx::smem_addr(&x.acc_empty[b]), EPI_WARPS);
+    }
+    ptx::mbar_init(ptx::smem_addr(&x.final_bar), 1);
+    x.abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_addr(&x.tmem_base), Cf::TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = x.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t gs = 0;
+      for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
+        const GemmDesc d = load_desc(single, descs, map, u);
+        const GUnit g = gunit(d, u - d.tile_begin);
+        const uint32_t pb = rows_bytes(d.RP - g.p0), qb = rows_bytes(d.RQ - g.q0);
+        const uint32_t tx = (pb + qb) * (SPLIT ? 2u : 1u);
+        const uint8_t* pbase = d.P + ((g.p0 / PR) * d.slabs + g.ks0) * d.P_block;
+        const uint8_t* qbase = d.Q + ((g.q0 / PR) * d.slabs + g.ks0) * d.Q_block;
+        bool ok = true;
+        for (int ks = 0; ks < g.nks; ++ks, ++gs) {
+          const int s = (int)(gs % S);
+          if (!ptx::mbar_wait(ptx::smem_addr(&x.empty[s]), ((gs / S) & 1u) ^ 1u, status)) { ok = false; break; }
+          const uint32_t full = ptx::smem_addr(&x.full[s]);
+          const uint32_t st = stage0 + (uint32_t)s * Cf::STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(full, tx);
+          ptx::bulk_copy_g2s(st, pbase + ks * d.P_block, pb, full);
+          ptx::bulk_copy_g2s(st + PBLOCK, qbase + ks * d.Q_block, qb, full);
+          if (SPLIT) {
+            ptx::bulk_copy_g2s(st + 2 * PBLOCK, pbase + d.P_lo + ks * d.P_block, pb, full);
+            ptx::bulk_copy_g2s(st + 3 * PBLOCK, qbase + d.Q_lo + ks * d.Q_block, qb, full);
+          }
+        }
+        if (!ok) { x.abort = 1; break; }
+      }
+      // copies still in flight land before the CTA can exit
+      const uint32_t first = gs > (uint32_t)S ? gs - (uint32_t)S : 0u;
+      for (uint32_t q = first; q < gs; ++q)
+        ptx::mbar_wait(ptx::smem_addr(&x.full[q % S]), (q / S) & 1u, status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t gs = 0, gc = 0;
+      for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
+        const GemmDesc d = load_desc(single, descs, map, u);
+        const GUnit g = gunit(d, u - d.tile_begin);
+        const int64_t qrows = d.RQ - g.q0 < PR ? d.RQ - g.q0 : PR;
+        const int nmma = (int)((qrows + 15) & ~int64_t(15));
+        const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, 0, 0);
+        const int chunk = SPLIT ? KC : g.nks;
+        bool ok = true;
+        for (int c0 = 0; c0 < g.nks && ok; c0 += chunk, ++gc) {
+          const int b = (int)(gc & 1);
+          if (!ptx::mbar_wait(ptx::smem_addr(&x.acc_empty[b]), ((gc >> 1) & 1u) ^ 1u, status)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)(b * PR);
+          const int c1 = min(g.nks, c0 + chunk);
+          for (int ks = c0; ks < c1; ++ks, ++gs) {
+            const int s = (int)(gs % S);
+            if (!ptx::mbar_wait(ptx::smem_addr(&x.full[s]), (gs / S) & 1u, status)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t st = stage0 + (uint32_t)s * Cf::STAGE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < PK / 16; ++kk) {
+              const uint64_t pd = ptx::sw128_kmajor_desc(st + kk * 32);
+              const uint64_t qd = ptx::sw128_kmajor_desc(st + PBLOCK + kk * 32);
+              ptx::mma_bf16(dt, pd, qd, idesc, (ks == c0 && kk == 0) ? 0u : 1u);
+              if (SPLIT) {
+                const uint64_t pl = ptx::sw128_kmajor_desc(st + 2 * PBLOCK + kk * 32);
+                const uint64_t ql = ptx::sw128_kmajor_desc(st + 3 * PBLOCK + kk * 32);
+                ptx::mma_bf16(dt, pd, ql, idesc, 1u);
+                ptx::mma_bf16(dt, pl, qd, idesc, 1u);
+              }
+            }
+            ptx::mma_commit(ptx::smem_addr(&x.empty[s]));
+          }
+          if (!ok) break;
+          ptx::mma_commit(ptx::smem_addr(&x.acc_full[b]));
+        }
+        if (!ok) { x.abort = 1; break; }
+      }
+      // every MMA of this thread completes before TMEM is released
+      ptx::mma_commit(ptx::smem_addr(&x.final_bar));
+      ptx::mbar_wait(ptx::smem_addr(&x.final_bar), 0u, status);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;            // TMEM lanes quad*32 .. quad*32+31
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    uint32_t gc = 0;
+    for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
+      const GemmDesc d = load_desc(single, descs, map, u);
+      const GUnit g = gunit(d, u - d.tile_begin);
+      const int64_t i = g.p0 + quad * 32 + lane;            // row of P this thread owns
+      const int64_t qcols = d.RQ - g.q0 < PR ? d.RQ - g.q0 : PR;
+      const int chunk = SPLIT ? KC : g.nks;
+      const int nchunks = (g.nks + chunk - 1) / chunk;
+      const bool accumulate = d.splits > 1;
+      float* __restrict__ C = d.C;
+      float acc[SPLIT ? PR : 1];
+#pragma unroll
+      for (int j = 0; j < (SPLIT ? PR : 1); ++j) acc[j] = 0.0f;
+      // writes columns col .. col+31 of row i (values in r)
+      auto emit = [&](int col, const float* r) {
+        if (i >= d.RP) return;
+        if (d.cj == 1) {
+          float* dst = C + i * d.ci + g.q0 + col;
+          const int64_t nrem = qcols - col;
+          const bool vec = ((d.ci & 3) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 3) == 0;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            if (j < nrem) emit4(dst + j, vec, nrem - j, accumulate, r[j], r[j + 1], r[j + 2], r[j + 3]);
+        } else {
+          float* dst = C + i * d.ci + (g.q0 + col) * d.cj;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (col + j < qcols) {
+              if (accumulate) atomicAdd(dst + j * d.cj, r[j]);
+              else dst[j * d.cj] = r[j];
+            }
+          }
+        }
+      };
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        const int b = (int)(gc & 1);
+        const bool w = ptx::mbar_wait(ptx::smem_addr(&x.acc_full[b]), (gc >> 1) & 1u, status);
+        if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR);
+#pragma unroll
+        for (int cb = 0; cb < PR / 32; ++cb) {
+          if (cb * 32 < qcols) {  // uniform across the warp
+            uint32_t r[32];
+            ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
+            ptx::tmem_ld_wait();
+            if (SPLIT) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) acc[cb * 32 + j] += __uint_as_float(r[j]);
+            } else {
+              float v[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+              emit(cb * 32, v);
+            }
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(ptx::smem_addr(&x.acc_empty[b]));
+      }
+      if (!ok) { x.abort = 1; break; }
+      if (SPLIT) {
+#pragma unroll
+        for (int cb = 0; cb < PR / 32; ++cb)
+          if (cb * 32 < qcols) emit(cb * 32, &acc[cb * 32]);
+      }
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, Cf::TMEM_COLS);
+  }
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return sms;
+}
+
+template <int SPLIT>
+int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* map, int64_t units, cudaStream_t s) {
+  const size_t smem = gemm_smem_bytes<SPLIT>();
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(packed_gemm_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return TN_ERR_CUDA;
+    attr = true;
+  }
+  const int64_t sms = sm_count();
+  const unsigned grid = (unsigned)(units < sms ? units : sms);
+  packed_gemm_kernel<SPLIT><<<grid, GEMM_THREADS, smem, s>>>(single, descs, map, units, status_word());
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_pack(const PackJob* jobs, const PackUnit* units, int64_t nunits, cudaStream_t s) {
+  if (nunits <= 0) return TN_OK;
+  if (nunits > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  pack_kernel<<<(unsigned)nunits, PACK_THREADS, 0, s>>>(jobs, units);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, int prec, cudaStream_t s) {
+  if (units <= 0) return TN_OK;
+  if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  GemmDesc none;
+  memset(&none, 0, sizeof(none));
+  if (prec == TN_PREC_BF16) return launch_gemm<0>(none, descs, map, units, s);
+  if (prec == TN_PREC_BF16X3) return launch_gemm<1>(none, descs, map, units, s);
+  return TN_ERR_ARG;
+}
+
+namespace {
+
+// Pack job of one operand of d (rows: its free legs; k: the shared legs).
+PackJob make_job(const ContractDesc& d, const float* src, int64_t R, int nr, const int32_t* rdim,
+                 const int64_t* rstr, const int64_t* kstr) {
+  PackJob j;
+  memset(&j, 0, sizeof(j));
+  j.src = src;
+  j.R = R;
+  j.K = d.K;
+  j.tiles = (int32_t)((R + PR - 1) / PR);
+  j.slabs = (int32_t)((d.K + PK - 1) / PK);
+  j.block_bytes = R >= PR ? PBLOCK : ((R + 7) & ~int64_t(7)) * 128;
+  j.nr = nr;
+  j.nk = d.nk;
+  for (int q = 0; q < nr; ++q) {
+    j.rdim[q] = rdim[q];
+    j.rstr[q] = rstr[q];
+  }
+  for (int q = 0; q < d.nk; ++q) {
+    j.kdim[q] = d.kdim[q];
+    j.kstr[q] = kstr[q];
+  }
+  j.kfast = (d.nk > 0 && kstr[d.nk - 1] == 1) ? 1 : 0;
+  j.rfast = (nr > 0 && rstr[nr - 1] == 1) ? 1 : 0;
+  return j;
+}
+
+// Pack blocks per CTA: about 64 KB of float32 reads (a block reads twice its
+// bf16 bytes).
+int32_t blocks_per_unit(const PackJob& j) {
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, 65536 / (2 * j.block_bytes)));
+}
+
+size_t job_bytes(const PackJob& j) { return (size_t)j.tiles * j.slabs * j.block_bytes; }
+
+// GEMM descriptor of contraction d over packed A (ja) and B (jb): the side
+// with more rows is P (the MMA's 128 rows). Offsets are left to the caller.
+GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, bool* swapped) {
+  const bool swap = d.N > d.M && d.M < PR;
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.C = d.C;
+  g.RP = swap ? d.N : d.M;
+  g.RQ = swap ? d.M : d.N;
+  g.ci = swap ? 1 : d.N;
+  g.cj = swap ? d.N : 1;
+  const PackJob& jp = swap ? jb : ja;
+  const PackJob& jq = swap ? ja : jb;
+  g.P_block = jp.block_bytes;
+  g.Q_block = jq.block_bytes;
+  g.tiles_p = jp.tiles;
+  g.tiles_q = jq.tiles;
+  g.slabs = ja.slabs;
+  g.splits = d.splits;
+  g.slabs_per_split = (int32_t)(d.k_per_split / PK);
+  *swapped = swap;
+  return g;
+}
+
+}  // namespace
+
+// Host side: pack jobs (two per contraction), their block units, and the GEMM
+// descriptors, with block storage as offsets in the plan's packed region.
+int plan_packed(const ContractDesc& d, int prec, PackedPlan* pp) {
+  const PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
+  const PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
+  if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
+    return TN_ERR_UNSUPPORTED;
+  const size_t bytes_a = (size_t)ja.tiles * ja.slabs * ja.block_bytes;
+  const size_t bytes_b = (size_t)jb.tiles * jb.slabs * jb.block_bytes;
+  const bool split = prec == TN_PREC_BF16X3;
+  // storage offsets (relative to the packed region): A hi, B hi, A lo, B lo
+  const size_t off_a = pp->packed_bytes;
+  size_t off = off_a + align256(bytes_a);
+  const size_t off_b = off;
+  off += align256(bytes_b);
+  size_t off_alo = 0, off_blo = 0;
+  if (split) {
+    off_alo = off;
+    off += align256(bytes_a);
+    off_blo = off;
+    off += align256(bytes_b);
+  }
+  pp->packed_bytes = off;
+
+  const int ja_idx = (int)pp->jobs.size();
+  pp->jobs.push_back(ja);
+  pp->jobs.push_back(jb);
+  pp->job_hi_off.push_back(off_a);
+  pp->job_hi_off.push_back(off_b);
+  pp->job_lo_off.push_back(split ? off_alo : SIZE_MAX);
+  pp->job_lo_off.push_back(split ? off_blo : SIZE_MAX);
+  for (int w = 0; w < 2; ++w) {
+    const PackJob& j = pp->jobs[(size_t)ja_idx + w];
+    const int32_t nb = j.tiles * j.slabs;
+    const int32_t per = blocks_per_unit(j);
+    for (int32_t f = 0; f < nb; f += per) pp->units.push_back(PackUnit{ja_idx + w, f, std::min(per, nb - f), 0});
+  }
+
+  bool swap = false;
+  GemmDesc g = make_gemm(d, ja, jb, &swap);
+  g.P_off = swap ? off_b : off_a;
+  g.Q_off = swap ? off_a : off_b;
+  g.P_lo = split ? (int64_t)(swap ? off_blo : off_alo) - (int64_t)g.P_off : 0;
+  g.Q_lo = split ? (int64_t)(swap ? off_alo : off_blo) - (int64_t)g.Q_off : 0;
+  pp->gemms.push_back(g);
+  return TN_OK;
+}
+
+size_t packed_single_bytes(const ContractDesc& d, int prec) {
+  const PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
+  const PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
+  const size_t planes = prec == TN_PREC_BF16X3 ? 2 : 1;
+  return planes * (align256(job_bytes(ja)) + align256(job_bytes(jb)));
+}
+
+size_t packed_scratch_bound(int64_t M, int64_t N, int64_t K, int prec) {
+  const size_t planes = prec == TN_PREC_BF16X3 ? 2 : 1;
+  const size_t slabs = (size_t)((K + PK - 1) / PK);
+  const size_t ra = (size_t)((M + PR - 1) / PR) * PR, rb = (size_t)((N + PR - 1) / PR) * PR;
+  return planes * (align256(ra * slabs * PK * 2) + align256(rb * slabs * PK * 2));
+}
+
+int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s) {
+  if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
+  PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
+  if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
+    return TN_ERR_UNSUPPORTED;
+  const bool split = prec == TN_PREC_BF16X3;
+  const size_t ba = align256(job_bytes(ja)), bb = align256(job_bytes(jb));
+  if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255) || bytes < (split ? 2 : 1) * (ba + bb))
+    return TN_ERR_WORKSPACE;
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  ja.hi = base;
+  jb.hi = base + ba;
+  ja.lo = split ? base + ba + bb : nullptr;
+  jb.lo = split ? base + 2 * ba + bb : nullptr;
+  PackPair pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.a = ja;
+  pp.b = jb;
+  pp.per_a = blocks_per_unit(ja);
+  pp.per_b = blocks_per_unit(jb);
+  const int64_t na = (ja.tiles * (int64_t)ja.slabs + pp.per_a - 1) / pp.per_a;
+  const int64_t nb = (jb.tiles * (int64_t)jb.slabs + pp.per_b - 1) / pp.per_b;
+  if (na + nb > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  pp.units_a = (int32_t)na;
+  bool swap = false;
+  GemmDesc g = make_gemm(d, ja, jb, &swap);
+  g.P = swap ? jb.hi : ja.hi;
+  g.Q = swap ? ja.hi : jb.hi;
+  g.P_lo = split ? (swap ? jb.lo - jb.hi : ja.lo - ja.hi) : 0;
+  g.Q_lo = split ? (swap ? ja.lo - ja.hi : jb.lo - jb.hi) : 0;
+  g.tile_begin = 0;
+  if (d.splits > 1 && cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  pack_pair_kernel<<<(unsigned)(na + nb), PACK_THREADS, 0, s>>>(pp);
+  if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  const int64_t units = (int64_t)g.tiles_p * g.tiles_q * g.splits;
+  if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (prec == TN_PREC_BF16) return launch_gemm<0>(g, nullptr, nullptr, units, s);
+  return launch_gemm<1>(g, nullptr, nullptr, units, s);
+}
+
+}  // namespace tn

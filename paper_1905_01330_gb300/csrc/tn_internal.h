@@ -75,6 +75,11 @@ int launch_zero(const ZeroRange* ranges, int n, cudaStream_t stream);
 int contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
                       int nshared, const tn_tensor* C, int prec, cudaStream_t stream);
 
+// tn_group_plan_create; allow_packed = false keeps BF16 / BF16X3 plans on
+// the single-launch kernel, whose workspace holds only the work list.
+int group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec, bool allow_packed,
+                         tn_group_plan** plan);
+
 // Device status word (first error wins); defined in api.cu.
 int* status_word();
 

@@ -87,6 +87,10 @@ def _signatures():
         "tn_mps_inner_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
         "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
+        "tn_mps_expect_grouped_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), i32,
+                                                                    ctypes.POINTER(TnChain), i32]),
+        "tn_mps_expect_grouped": (i32, [ctypes.POINTER(TnChain), i32, ctypes.POINTER(TnChain), i32, vp,
+                                        ctypes.c_size_t, vp, vp]),
         "tn_mps_expect": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_classify_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), i32, i32, i32, i32]),
         "tn_mps_classify": (i32, [ctypes.POINTER(TnChain), i32, i32, vp, i32, i32, i32, vp, vp, vp,
@@ -212,6 +216,33 @@ def mps_expect(psi, mpo, prec: str = "fp32", stream=None, out: torch.Tensor | No
     _check(lib.tn_mps_expect(ctypes.byref(cp), ctypes.byref(ch), PREC[prec], ctypes.c_void_p(ws.data_ptr()),
                              ws.numel(), ctypes.c_void_p(res.data_ptr()), _stream(stream)), "tn_mps_expect")
     res._tn_keep = (ws, kp, kh)
+    return res
+
+
+def mps_expect_grouped(psis, mpo, prec: str = "fp32", stream=None, out: torch.Tensor | None = None):
+    """tn_mps_expect for a batch of MPS (a list of core lists, bond dims may
+    differ) sharing one MPO, as grouped launches (tn_mps_expect_grouped).
+    Returns a float64 CUDA tensor [count, 4] of {e_value, e_log_scale,
+    n_value, n_log_scale} per state."""
+    lib = load()
+    count = len(psis)
+    arr = (TnChain * count)()
+    keep = []
+    for k, cores in enumerate(psis):
+        c, kc = chain_desc(cores)
+        arr[k] = c
+        keep.append(kc)
+    ch, kh = chain_desc(mpo, phys_axis=2)
+    dev = psis[0][0].device
+    nbytes = lib.tn_mps_expect_grouped_workspace_bytes(arr, count, ctypes.byref(ch), PREC[prec])
+    if nbytes == 0:
+        raise TnError(1, "tn_mps_expect_grouped_workspace_bytes (invalid chains or MPO)")
+    ws = _workspace(nbytes, dev)
+    res = out if out is not None else torch.empty(count, 4, dtype=torch.float64, device=dev)
+    _check(lib.tn_mps_expect_grouped(arr, count, ctypes.byref(ch), PREC[prec], ctypes.c_void_p(ws.data_ptr()),
+                                     ws.numel(), ctypes.c_void_p(res.data_ptr()), _stream(stream)),
+           "tn_mps_expect_grouped")
+    res._tn_keep = (ws, keep, kh)
     return res
 
 

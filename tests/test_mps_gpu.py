@@ -128,3 +128,49 @@ def test_left_canonical_energy_large_bond(tn, prec):
     assert tn.sync_status() == 0
     assert rel(val(r, 0), e * math.exp(le)) <= tol(prec, 2 * n)
     assert abs(val(r, 1) - 1.0) <= tol(prec, 2 * n) + n * 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_grouped_energy_uneven_bonds(tn, prec):
+    # config-5 batch shape at reduced size: uneven chi (one smallest, one
+    # largest forced), left-canonical states, one shared TFIM MPO
+    n = 12
+    chis = synth.uneven_chis(6, seed=50, lo=8, hi=48, step=8)
+    assert min(chis) == 8 and max(chis) == 48
+    states = [synth.left_canonical_mps(n, 2, chi, seed=60 + k) for k, chi in enumerate(chis)]
+    W = synth.tfim_mpo(n)
+    r = tn.mps_expect_grouped([to_dev(c) for c in states], to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    r = r.cpu().numpy()
+    assert r.shape == (len(chis), 4)
+    # <psi|H|psi> is a sum of terms of both signs: its forward error is bounded
+    # relative to the sum of their magnitudes, at most ||H|| <psi|psi> with
+    # ||H|| <= J (n - 1) + h n, not relative to the (possibly small) sum itself
+    h_norm = 1.0 * (n - 1) + 1.0 * n
+    for k, cores in enumerate(states):
+        e, le = oracle.mpo_expect(cores, W)
+        nv, ln = oracle.mps_inner(cores, cores)
+        norm = nv * math.exp(ln)
+        err = abs(r[k, 0] * math.exp(r[k, 1]) - e * math.exp(le))
+        assert err <= tol(prec, 2 * n) * h_norm * norm, (k, chis[k])
+        assert rel(r[k, 2] * math.exp(r[k, 3]), norm) <= tol(prec, 2 * n), (k, chis[k])
+
+
+def test_grouped_energy_matches_single_sweeps(tn):
+    # the grouped sweep and one tn_mps_expect per state agree (float32)
+    n = 10
+    states = [synth.random_mps(n, 2, chi, seed=70 + chi) for chi in (4, 16, 8)]
+    W = synth.tfim_mpo(n)
+    g = tn.mps_expect_grouped([to_dev(c) for c in states], to_dev(W), prec="fp32").cpu().numpy()
+    for k, cores in enumerate(states):
+        s = tn.mps_expect(to_dev(cores), to_dev(W), prec="fp32").cpu().numpy()
+        for j in (0, 2):
+            assert rel(g[k, j] * math.exp(g[k, j + 1]), s[j] * math.exp(s[j + 1])) <= 1e-5
+
+
+def test_grouped_energy_rejects_mismatched_lengths(tn):
+    W = synth.tfim_mpo(8)
+    a = to_dev(synth.random_mps(8, 2, 4, seed=1))
+    b = to_dev(synth.random_mps(9, 2, 4, seed=2))
+    with pytest.raises(tn.TnError):
+        tn.mps_expect_grouped([a, b], to_dev(W))

@@ -1,0 +1,92 @@
+"""GPU parity of the grouped two-launch path (pack + tcgen05 GEMM on packed
+bf16 blocks) against the FP64 oracle, with the error model and bounds of
+test_contract_gpu.check. Grouped BF16 / BF16X3 plans take this path; the
+shapes below exercise what is particular to it: the operand with fewer rows
+on the MMA's column side (swapped roles, column stores), narrow column tiles
+(16..112), single-row operands, shared-index tails that are not a multiple of
+64, split k ranges with atomically accumulated results, the outer product
+(K = 1), gathers from permuted and strided views, and long k with the
+BF16X3 accumulator promotion."""
+import numpy as np
+import pytest
+
+from paper_1905_01330_gb300 import synth
+from test_contract_gpu import check, rand
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    from paper_1905_01330_gb300 import build, tn as tnmod
+    build.build()
+    tnmod.load()
+    return tnmod
+
+
+def run_group(tn, cases, prec, seed0):
+    """cases: (A, la, B, lb) as host arrays, or (At, la, Bt, lb, A_host, B_host)
+    for device views; one plan over all, every result checked."""
+    specs, host = [], []
+    for i, c in enumerate(cases):
+        if len(c) == 4:
+            A, la, B, lb = c
+            At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        else:
+            At, la, Bt, lb, A, B = c
+        C = torch.full(tn.result_shape(At, la, Bt, lb), float("nan"), device="cuda")
+        specs.append((At, list(la), Bt, list(lb), C))
+        host.append((A, la, B, lb))
+    plan = tn.GroupPlan(specs, prec=prec)
+    assert plan.launches >= 2
+    plan.run()
+    torch.cuda.synchronize()
+    assert tn.sync_status() == 0
+    for (A, la, B, lb), sp in zip(host, specs):
+        check(sp[4], A, la, B, lb, prec)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_packed_shapes(tn, prec):
+    cases = [
+        (rand(1, (4096,)), [0], rand(2, (4096, 200)), [0]),      # M = 1, swapped, split k
+        (rand(3, (300, 4096)), [1], rand(4, (4096,)), [0]),      # N = 1
+        (rand(5, (100, 72)), [1], rand(6, (72, 300)), [0]),      # swapped, K tail 8, 112-wide columns
+        (rand(7, (300, 5000)), [1], rand(8, (20, 5000)), [1]),   # 32-wide columns, 3 k ranges
+        (rand(9, (50, 3)), [], rand(10, (7, 130)), []),          # outer product (K = 1)
+        (rand(11, (130, 20000)), [1], rand(12, (20000, 130)), [0]),  # long k: promotion, 10 k ranges
+        (rand(13, (256, 256)), [1], rand(14, (256, 384)), [0]),  # whole tiles only
+        (rand(15, (8, 9, 10)), [1], rand(16, (9, 11)), [0]),     # ragged everything
+    ]
+    run_group(tn, cases, prec, 0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_packed_permuted_and_strided(tn, prec):
+    A = rand(21, (16, 24, 8, 5))
+    B = rand(22, (8, 7, 24, 16))
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Ap = At.permute(3, 1, 0, 2)                     # non-contiguous view, unit stride on a free leg
+    Anp = np.ascontiguousarray(A.transpose(3, 1, 0, 2))
+    Bs = Bt[:, ::2]                                 # strided slice: no unit-stride leg run of 4
+    Bsnp = np.ascontiguousarray(B[:, ::2])
+    cases = [
+        (A, [2, 0, 1], B, [0, 3, 2]),
+        (Ap, [1, 2], Bt, [2, 3], Anp, B),
+        (At, [2], Bs, [0], A, Bsnp),
+        (rand(23, (48, 64, 32)), [0, 2], rand(24, (32, 9, 48)), [2, 0]),  # k legs in reverse order
+        (rand(25, (64, 40)), [0], rand(26, (64, 40)), [0]),               # both operands m/n-fast
+    ]
+    run_group(tn, cases, prec, 0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("seed", range(6))
+def test_packed_random_specs(tn, prec, seed):
+    st = synth.Stream(4000 + seed)
+    cases = []
+    for i in range(12):
+        sha, la, shb, lb = synth.contraction_spec(st, dims=(3, 8, 13, 24, 48, 64), cap=1 << 17)
+        cases.append((rand(7000 + 100 * seed + 2 * i, sha), la, rand(7001 + 100 * seed + 2 * i, shb), lb))
+    run_group(tn, cases, prec, seed)
