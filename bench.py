@@ -8,7 +8,8 @@ drawn on the device (torch Philox, seeded). 2.01 TFLOP and 31.9 GB of
 float32 operands and results per step, far larger than L2 (129 MB), so no
 L2 flush is needed between steps.
 
-One step = one tn_group_plan_run (a single kernel launch). The line also
+One step = one tn_group_plan_run (pack + GEMM, plus a zeroing launch for
+the results accumulated over split k ranges). The line also
 reports the split-bf16x3 and plain-fp32 paths on the same workload, the
 end-to-end rate through the C ABI with pinned host buffers, the roofline of
 the dominant kernel, SM clocks sampled during the timed region, and the FP64
@@ -175,22 +176,24 @@ def _time_graph(fn, calls, replays, stream):
     return a.elapsed_time(b) / (replays * calls)
 
 
-def contract_traffic(nbytes):
-    """DRAM bytes per launch of the contraction kernel, from the committed ncu
-    capture, when that capture was taken of the kernel source as it is now
-    (same SHA-256); else None."""
+def kernel_traffic(kernel, nbytes):
+    """DRAM bytes per launch of `kernel` ("pack" or "gemm"), from the committed
+    ncu capture, when that capture was taken of the kernel source as it is now
+    (same SHA-256); else None. The capture ran a smaller case; its measured
+    traffic over its algorithmic bytes scales to this launch's algorithmic
+    bytes (both kernels move bytes in proportion to the operands)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "contract_tc_traffic.json")
-    src = os.path.join(ROOT, "paper_1905_01330_gb300", "csrc", "contract_tc.cu")
+    p = os.path.join(ROOT, "profiles", "packed_traffic.json")
+    src = os.path.join(ROOT, "paper_1905_01330_gb300", "csrc", "packed.cu")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    if d.get("source_sha256") != sha:
+    if d.get("source_sha256") != sha or kernel not in d.get("kernels", {}):
         return None
-    return d["traffic_over_algorithmic"] * nbytes
+    return d["kernels"][kernel]["traffic_over_algorithmic"] * nbytes
 
 
 def _score_err(ft, lam, ft_ref, lam_ref):
@@ -444,6 +447,20 @@ def main():
         per = [a.elapsed_time(b) for a, b in ev]
         return total_ms, per, clocks
 
+    def timed_launches(pl, steps):
+        """Average device time of each launch of a run, timed one at a time."""
+        names = pl.launch_names()
+        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
+              for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for row in ev:
+            for i, (a, b) in enumerate(row):
+                a.record(stream)
+                pl.run_launch(i)
+                b.record(stream)
+        torch.cuda.synchronize(dev)
+        return {n: float(np.mean([row[i][0].elapsed_time(row[i][1]) for row in ev])) for i, n in enumerate(names)}
+
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     total_ms, per, clocks = timed(plan, args.steps, args.warmup, sampler)
     status = tn.sync_status()
@@ -494,12 +511,31 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         del host_in, host_out
 
+    # ---- roofline of each launch of the step, timed one at a time
     hbm_peak, bf16_peak, peak_src = measured_peaks()
-    achieved_gbs = nbytes / (launch_ms * 1e-3) / 1e9
+    n_ops = sum(A.numel() + B.numel() for A, _, B, _, _ in specs)   # operand elements
+    n_out = sum(C.numel() for *_, C in specs)                        # result elements
+    algo = {"pack": 4.0 * n_ops + 2.0 * n_ops,     # read float32 operands, write bf16
+            "gemm": 2.0 * n_ops + 4.0 * n_out}     # read bf16 operands, write float32 results
+    lt = timed_launches(plan, max(2, args.steps // 2))
+    launches = {}
+    for name, ms in lt.items():
+        if name not in algo:   # the zeroing of split results: time only
+            launches[name] = {"ms": ms}
+            continue
+        b = algo[name]
+        launches[name] = {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9,
+                          "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm_peak}
+    lt = {k: v for k, v in lt.items() if k in algo}
+    dom = max(lt, key=lt.get)
+    achieved_gbs = launches[dom]["gbs"]
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": contract_traffic(nbytes),
-                "kernel": "tc_contract_kernel<bf16>", "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": nbytes,
+                "frac": achieved_gbs / hbm_peak, "traffic": kernel_traffic(dom, launches[dom]["algorithmic_bytes"]),
+                "kernel": dom, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": launches[dom]["algorithmic_bytes"],
+                "launches": launches,
+                "step_gbs": nbytes / (launch_ms * 1e-3) / 1e9,
+                "step_frac": nbytes / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                 "tensor_tflops": flops / (launch_ms * 1e-3) / 1e12,
                 "tensor_frac": flops / (launch_ms * 1e-3) / 1e12 / bf16_peak}
 

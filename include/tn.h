@@ -151,9 +151,17 @@ int tn_contract_grouped_static(const tn_contract_spec* specs, int nspecs, int pr
  * (|A| + |B| + |C| float32 elements summed over specs) of a plan. */
 double tn_group_plan_flops(const tn_group_plan* plan);
 double tn_group_plan_bytes(const tn_group_plan* plan);
-/* Kernel launches one tn_group_plan_run makes (the contraction kernel, plus
- * one zeroing kernel when some results are accumulated over split k ranges). */
+/* Kernel launches one tn_group_plan_run makes: [a zeroing kernel, when some
+ * results are accumulated over split k ranges] [the pack kernel, for BF16 /
+ * BF16X3 plans] and the contraction kernel. */
 int tn_group_plan_launches(const tn_group_plan* plan);
+/* Runs launch `index` (0 .. launches-1) of that sequence alone, so each can
+ * be timed by itself; running them all in order is one tn_group_plan_run.
+ * Errors: TN_ERR_ARG (index out of range), as tn_group_plan_run. */
+int tn_group_plan_run_launch(const tn_group_plan* plan, void* workspace, size_t bytes, int index, void* stream);
+/* "zero", "pack", "gemm" (packed bf16 blocks) or "contract" (single-pass
+ * kernel) for launch `index`; NULL when out of range. */
+const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index);
 
 /* ------------------------------------------------------------------------ */
 /* Matrix product states and operators (Sec. II, Fig. 3a)                    */

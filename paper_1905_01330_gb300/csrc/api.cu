@@ -136,7 +136,8 @@ int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const 
 }  // extern "C"
 
 int tn::contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
-                          int nshared, const tn_tensor* C, int prec, cudaStream_t s) {
+                          int nshared, const tn_tensor* C, int prec, cudaStream_t s, void* scratch,
+                          size_t scratch_bytes) {
   if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
   ContractDesc d;
   int rc = plan_contract(A, legsA, B, legsB, nshared, C, &d);
@@ -146,6 +147,8 @@ int tn::contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor*
     return cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) == cudaSuccess ? TN_OK
                                                                                           : TN_ERR_CUDA;
   plan_units(&d, min_units_single());
+  if (prec != TN_PREC_FP32 && scratch && packed_single_bytes(d, prec) <= scratch_bytes)
+    return contract_packed_single(d, prec, scratch, scratch_bytes, s);
   if (d.splits > 1 &&
       cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) != cudaSuccess)
     return TN_ERR_CUDA;
@@ -188,7 +191,8 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
   // largest work units first, so the tail of the launch is made of small ones
   if (prec != TN_PREC_FP32 && allow_packed) {
     p->packed = true;
-    for (const auto& d : p->descs) {
+    for (auto& d : p->descs) {
+      plan_units_packed(&d);
       const int rc = plan_packed(d, prec, &p->pp);
       if (rc != TN_OK) { delete p; return rc; }
     }
@@ -272,11 +276,21 @@ size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
 
 double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
 int tn_group_plan_launches(const tn_group_plan* plan) {
-  if (!plan) return 0;
-  const int main = plan->total_tiles > 0 ? (plan->packed ? 2 : 1) : 0;
-  return main + (plan->zero_ranges.empty() ? 0 : 1);
+  if (!plan || plan->total_tiles == 0) return 0;
+  return (plan->packed ? 2 : 1) + (plan->zero_ranges.empty() ? 0 : 1);
 }
 double tn_group_plan_bytes(const tn_group_plan* plan) { return plan ? plan->bytes : 0.0; }
+
+// Bytes of the work lists alone (without the packed blocks).
+static size_t list_bytes(const tn_group_plan* plan) {
+  return plan->packed ? packed_offset(plan) : tn_group_plan_workspace_bytes(plan);
+}
+
+static int check_ws_need(size_t need, void* ws, size_t bytes) {
+  if (need == 0) return TN_OK;
+  if (!ws || bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return TN_ERR_WORKSPACE;
+  return TN_OK;
+}
 
 static int check_ws(const tn_group_plan* plan, void* ws, size_t bytes) {
   const size_t need = tn_group_plan_workspace_bytes(plan);
@@ -285,17 +299,16 @@ static int check_ws(const tn_group_plan* plan, void* ws, size_t bytes) {
   return TN_OK;
 }
 
-int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
-  if (!plan) return TN_ERR_ARG;
-  int rc = check_ws(plan, workspace, bytes);
-  if (rc != TN_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+// Upload with the packed blocks at `packed` (inside the workspace, or a
+// separate region shared by plans that run one after another).
+static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* packed, cudaStream_t s) {
   // pageable sources: each call returns once the bytes are staged, so the
   // plan may be destroyed right after it
   uint8_t* base = static_cast<uint8_t*>(workspace);
   if (plan->packed) {
     // device addresses of the packed blocks, patched into copies of the lists
-    uint8_t* packed = base + packed_offset(plan);
     std::vector<GemmDesc> g = plan->pp.gemms;
     for (auto& e : g) {
       e.P = packed + e.P_off;
@@ -330,31 +343,129 @@ int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t byte
   return TN_OK;
 }
 
+size_t tn::group_plan_list_bytes(const tn_group_plan* plan) { return plan ? list_bytes(plan) : 0; }
+size_t tn::group_plan_packed_bytes(const tn_group_plan* plan) {
+  return plan && plan->packed ? plan->pp.packed_bytes : 0;
+}
+
+int tn::group_plan_upload_shared(const tn_group_plan* plan, void* lists, size_t bytes, void* packed,
+                                 cudaStream_t s) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws_need(list_bytes(plan), lists, bytes);
+  if (rc != TN_OK) return rc;
+  if (plan->packed && plan->pp.packed_bytes > 0 && (!packed || (reinterpret_cast<uintptr_t>(packed) & 255)))
+    return TN_ERR_WORKSPACE;
+  return upload_impl(plan, lists, static_cast<uint8_t*>(packed), s);
+}
+
+extern "C" {
+
+int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws(plan, workspace, bytes);
+  if (rc != TN_OK) return rc;
+  return upload_impl(plan, workspace, static_cast<uint8_t*>(workspace) + packed_offset(plan),
+                     static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+static int run_impl(const tn_group_plan* plan, void* workspace, cudaStream_t s);
+
+int tn::group_plan_run_shared(const tn_group_plan* plan, void* lists, size_t bytes, cudaStream_t s) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws_need(list_bytes(plan), lists, bytes);
+  if (rc != TN_OK) return rc;
+  return run_impl(plan, lists, s);
+}
+
+extern "C" {
+
 int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
   if (!plan) return TN_ERR_ARG;
   int rc = check_ws(plan, workspace, bytes);
   if (rc != TN_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (const auto& z : plan->zeros)
-    if (cudaMemsetAsync(z.C, 0, sizeof(float) * (size_t)(z.M * z.N), s) != cudaSuccess) return TN_ERR_CUDA;
-  if (plan->total_tiles == 0) return TN_OK;
-  if (!plan->zero_ranges.empty()) {
-    rc = launch_zero(reinterpret_cast<const ZeroRange*>(static_cast<uint8_t*>(workspace) + zero_offset(plan)),
-                     (int)plan->zero_ranges.size(), s);
-    if (rc != TN_OK) return rc;
+  return run_impl(plan, workspace, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+// The launch sequence of a run: [zeroing of split results] [pack] contract.
+enum LaunchKind { L_ZERO, L_PACK, L_CONTRACT };
+
+static int launch_list(const tn_group_plan* plan, LaunchKind* kinds) {
+  int n = 0;
+  if (plan->total_tiles == 0) return 0;
+  if (!plan->zero_ranges.empty()) kinds[n++] = L_ZERO;
+  if (plan->packed) kinds[n++] = L_PACK;
+  kinds[n++] = L_CONTRACT;
+  return n;
+}
+
+static int run_one(const tn_group_plan* plan, void* workspace, LaunchKind k, cudaStream_t s) {
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  const int32_t* map = reinterpret_cast<const int32_t*>(base + map_offset(plan));
+  switch (k) {
+    case L_ZERO:
+      return launch_zero(reinterpret_cast<const ZeroRange*>(base + zero_offset(plan)), (int)plan->zero_ranges.size(),
+                         s);
+    case L_PACK:
+      return launch_pack(reinterpret_cast<const PackJob*>(base + jobs_offset(plan)),
+                         reinterpret_cast<const PackUnit*>(base + punits_offset(plan)),
+                         (int64_t)plan->pp.units.size(), s);
+    default:
+      break;
   }
-  const int32_t* map = reinterpret_cast<const int32_t*>(static_cast<uint8_t*>(workspace) + map_offset(plan));
-  if (plan->packed) {
-    uint8_t* base = static_cast<uint8_t*>(workspace);
-    rc = launch_pack(reinterpret_cast<const PackJob*>(base + jobs_offset(plan)),
-                     reinterpret_cast<const PackUnit*>(base + punits_offset(plan)), (int64_t)plan->pp.units.size(), s);
-    if (rc != TN_OK) return rc;
+  if (plan->packed)
     return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->total_tiles, plan->prec, s);
-  }
-  const ContractDesc* g = static_cast<const ContractDesc*>(workspace);
+  const ContractDesc* g = reinterpret_cast<const ContractDesc*>(base);
   if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, map, plan->total_tiles, s);
   return launch_contract_tc(plan->descs[0], g, map, plan->total_tiles, plan->prec, s);
 }
+
+static int run_impl(const tn_group_plan* plan, void* workspace, cudaStream_t s) {
+  for (const auto& z : plan->zeros)
+    if (cudaMemsetAsync(z.C, 0, sizeof(float) * (size_t)(z.M * z.N), s) != cudaSuccess) return TN_ERR_CUDA;
+  LaunchKind kinds[3];
+  const int n = launch_list(plan, kinds);
+  for (int i = 0; i < n; ++i) {
+    const int rc = run_one(plan, workspace, kinds[i], s);
+    if (rc != TN_OK) return rc;
+  }
+  return TN_OK;
+}
+
+extern "C" {
+
+int tn_group_plan_run_launch(const tn_group_plan* plan, void* workspace, size_t bytes, int index, void* stream) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws(plan, workspace, bytes);
+  if (rc != TN_OK) return rc;
+  LaunchKind kinds[3];
+  const int n = launch_list(plan, kinds);
+  if (index < 0 || index >= n) return TN_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (index == 0)
+    for (const auto& z : plan->zeros)
+      if (cudaMemsetAsync(z.C, 0, sizeof(float) * (size_t)(z.M * z.N), s) != cudaSuccess) return TN_ERR_CUDA;
+  return run_one(plan, workspace, kinds[index], s);
+}
+
+const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index) {
+  if (!plan) return nullptr;
+  LaunchKind kinds[3];
+  const int n = launch_list(plan, kinds);
+  if (index < 0 || index >= n) return nullptr;
+  switch (kinds[index]) {
+    case L_ZERO: return "zero";
+    case L_PACK: return "pack";
+    default: return plan->packed ? "gemm" : "contract";
+  }
+}
+
+}  // extern "C"
+
+extern "C" {
 
 void tn_group_plan_destroy(tn_group_plan* plan) { delete plan; }
 

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "packed.h"
 #include "tn_internal.h"
 
 namespace tn {
@@ -300,11 +301,14 @@ bool small_ok(const tn_mps* bra, const tn_mps* ket) {
 }
 
 // Workspace of the contraction-kernel inner sweep: E0, E1 (Dmax^2 each),
-// T (Dmax d Dmax), n max slots, one log-scale.
+// T (Dmax d Dmax), n max slots, one log-scale, and scratch for the packed
+// bf16 operands of the largest contraction (sized for BF16X3, the larger).
 struct InnerWs {
   float *E0, *E1, *T;
   unsigned* bits;
   double* lg;
+  uint8_t* scratch;
+  size_t scratch_bytes;
   size_t bytes;
 };
 
@@ -317,6 +321,10 @@ InnerWs inner_layout(uint8_t* base, int64_t D, int64_t d, int n) {
   w.T = reinterpret_cast<float*>(take(sizeof(float) * D * d * D));
   w.bits = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)n));
   w.lg = reinterpret_cast<double*>(take(sizeof(double) * 2));
+  // T = E psi (D x D by D x dD) and E' = psi T (D x dD by dD x D)
+  w.scratch_bytes = std::max(packed_scratch_bound(D, d * D, D, TN_PREC_BF16X3),
+                             packed_scratch_bound(D, D, d * D, TN_PREC_BF16X3));
+  w.scratch = take(w.scratch_bytes);
   w.bytes = off;
   return w;
 }
@@ -336,12 +344,12 @@ int inner_sweep(const tn_mps* bra, const tn_mps* ket, int prec, const InnerWs& w
     tn_tensor tK = tensor3(ket->cores[i], Dak, d, Dbk);
     tn_tensor tT = tensor3(w.T, Da, d, Dbk);
     const int l1a[1] = {1}, l1b[1] = {0};
-    int rc = contract_internal(&tE, l1a, &tK, l1b, 1, &tT, prec, s);
+    int rc = contract_internal(&tE, l1a, &tK, l1b, 1, &tT, prec, s, w.scratch, w.scratch_bytes);
     if (rc != TN_OK) return rc;
     tn_tensor tB = tensor3(bra->cores[i], Da, d, Db);
     tn_tensor tE2 = tensor2(E2, Db, Dbk);
     const int l2a[2] = {0, 1}, l2b[2] = {0, 1};
-    rc = contract_internal(&tB, l2a, &tT, l2b, 2, &tE2, prec, s);
+    rc = contract_internal(&tB, l2a, &tT, l2b, 2, &tE2, prec, s, w.scratch, w.scratch_bytes);
     if (rc != TN_OK) return rc;
     rc = rescale(E2, Db * Dbk, w.bits + i, w.lg, s);
     if (rc != TN_OK) return rc;
@@ -357,6 +365,8 @@ struct ExpectWs {
   float *L0, *L1, *T1, *T2;
   unsigned* bits;
   double* lg;
+  uint8_t* scratch;
+  size_t scratch_bytes;
   size_t bytes;
 };
 
@@ -370,6 +380,10 @@ ExpectWs expect_layout(uint8_t* base, int64_t D, int64_t W, int64_t d, int n) {
   w.T2 = reinterpret_cast<float*>(take(sizeof(float) * W * D * d * D));
   w.bits = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)n));
   w.lg = reinterpret_cast<double*>(take(sizeof(double) * 2));
+  // (i) W D x D by D x dD and (iii) W D x dD by dD x D, packed
+  w.scratch_bytes = std::max(packed_scratch_bound(W * D, d * D, D, TN_PREC_BF16X3),
+                             packed_scratch_bound(W * D, D, d * D, TN_PREC_BF16X3));
+  w.scratch = take(w.scratch_bytes);
   w.bytes = off;
   return w;
 }
@@ -499,7 +513,8 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
     tn_tensor tA = tensor3(psi->cores[i], Da, d, Db);
     tn_tensor tT1 = tensor4(w.T1, wa, Da, d, Db);
     const int la1[1] = {1}, lb1[1] = {0};
-    if ((rc = contract_internal(&tL, la1, &tA, lb1, 1, &tT1, prec, s)) != TN_OK) return rc;
+    if ((rc = contract_internal(&tL, la1, &tA, lb1, 1, &tT1, prec, s, w.scratch, w.scratch_bytes)) != TN_OK)
+      return rc;
     // (ii) T2[w', s', a', b] = sum_{w,s} W[w, w', s, s'] T1[w, a', s, b]
     tn_tensor tW = tensor4(H->cores[i], wa, wb, d, d);
     tn_tensor tT2 = tensor4(w.T2, wb, d, Da, Db);
@@ -508,7 +523,8 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
     // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] A[a', s', b']
     tn_tensor tL2 = tensor3(L2, wb, Db, Db);
     const int la3[2] = {1, 2}, lb3[2] = {1, 0};
-    if ((rc = contract_internal(&tT2, la3, &tA, lb3, 2, &tL2, prec, s)) != TN_OK) return rc;
+    if ((rc = contract_internal(&tT2, la3, &tA, lb3, 2, &tL2, prec, s, w.scratch, w.scratch_bytes)) != TN_OK)
+      return rc;
     if ((rc = rescale(L2, wb * Db * Db, w.bits + i, w.lg, s)) != TN_OK) return rc;
     std::swap(L, L2);
   }

@@ -132,7 +132,8 @@ struct PlanDeleter {
 using PlanPtr = std::unique_ptr<tn_group_plan, PlanDeleter>;
 
 // Host-side layout of one grouped sweep: buffers of every chain, the site
-// plans (four per site) and the per-site rescale tables.
+// plans (four per site, their work lists only), one packed-operand region
+// they share, and the per-site rescale tables.
 struct GroupedSweep {
   struct ChainBufs {
     float *E[2], *T, *L[2], *T1, *T2;
@@ -146,7 +147,8 @@ struct GroupedSweep {
   std::vector<Segment> segs;          // n * 2 * count
   std::vector<ChainInit> inits;
   std::vector<ChainFinal> finals;
-  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_init = 0, off_final = 0, total = 0;
+  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_init = 0, off_final = 0, off_packed = 0, total = 0;
+  size_t packed_bytes = 0;  // largest packed-operand region of one plan
   int64_t nbits = 0;
 };
 
@@ -240,12 +242,17 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
       int rc = tn_group_plan_create(stages[j]->data(), (int)stages[j]->size(), precs[j], &p);
       if (rc != TN_OK) return rc;
       g->plans.emplace_back(p);
-      const size_t bytes = tn_group_plan_workspace_bytes(p);
+      const size_t bytes = group_plan_list_bytes(p);
       g->plan_off.push_back(off);
       g->plan_bytes.push_back(bytes);
       off += align256(bytes);
+      g->packed_bytes = std::max(g->packed_bytes, group_plan_packed_bytes(p));
     }
   }
+  // one region for the packed operands of whichever plan is running (the
+  // plans run one after another on the stream)
+  g->off_packed = off;
+  off += align256(g->packed_bytes);
   g->off_segs = off;
   off += align256(sizeof(Segment) * g->segs.size());
   g->inits.resize((size_t)count);
@@ -289,7 +296,7 @@ int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int pr
   // uploads: plan work lists, rescale segments, init and final tables
   for (size_t j = 0; j < g.plans.size(); ++j) {
     if (g.plan_bytes[j] == 0) continue;
-    rc = tn_group_plan_upload(g.plans[j].get(), base + g.plan_off[j], g.plan_bytes[j], s);
+    rc = group_plan_upload_shared(g.plans[j].get(), base + g.plan_off[j], g.plan_bytes[j], base + g.off_packed, s);
     if (rc != TN_OK) return rc;
   }
   if (cudaMemcpyAsync(base + g.off_segs, g.segs.data(), sizeof(Segment) * g.segs.size(), cudaMemcpyHostToDevice,
@@ -308,7 +315,7 @@ int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int pr
   for (int i = 0; i < g.n; ++i) {
     for (int j = 0; j < 4; ++j) {
       const size_t p = (size_t)i * 4 + j;
-      rc = tn_group_plan_run(g.plans[p].get(), base + g.plan_off[p], g.plan_bytes[p], s);
+      rc = group_plan_run_shared(g.plans[p].get(), base + g.plan_off[p], g.plan_bytes[p], s);
       if (rc != TN_OK) return rc;
     }
     int64_t longest = 1;

@@ -48,21 +48,25 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float a, float b) {
 }
 
 // ------------------------------------------------------------------- pack
-// Staging of one block in shared memory. When the source's unit stride runs
-// along k the values are staged row by row (T[row][k]); otherwise column by
-// column (Tt[k][row]). Either way the global reads are coalesced along the
-// unit-stride direction and the 16-byte output chunks are read back without
-// bank conflicts.
-constexpr int TROW = PK + 4;    // row-staged: floats per row
-constexpr int TCOL = PR + 4;    // column-staged: floats per k
+// Each output chunk (one row, 8 consecutive shared indices: 16 bytes of
+// bf16) is made by one thread from 8 float32 values it loads itself, so the
+// blocks need no shared-memory staging and no barrier besides the one that
+// publishes a block's offset tables. A thread takes PACK_CPT chunks per
+// block and issues all their loads before converting any.
+//  - Source with unit stride along k: a thread's 8 values are consecutive in
+//    memory (two 16-byte loads when aligned); eight consecutive threads cover
+//    a row's 64 shared indices, so a warp reads 4 x 256 contiguous bytes and
+//    writes 4 whole 128-byte rows.
+//  - Otherwise: consecutive threads take consecutive rows at the same 8
+//    shared indices, so each of the 8 loads of a warp reads 32 consecutive
+//    rows (128 contiguous bytes when the unit stride is along the rows).
+constexpr int PACK_CPT = 4;  // chunks per thread and block (1024 chunks / 256 threads)
+
 struct PackSmem {
-  union {
-    float T[PR][TROW];
-    float Tt[PK][TCOL];
-  };
-  int64_t roff[PR];      // source offset of each row (valid rows only)
-  int64_t koff[PK];      // source offset of each shared index (valid only)
+  int64_t roff[2][PR];   // source offset of each row (valid rows only)
+  int64_t koff[2][PK];   // source offset of each shared index (valid only)
 };
+constexpr size_t PACK_SMEM = sizeof(PackSmem);
 
 __device__ __forceinline__ void store_chunk(uint8_t* hi, uint8_t* lo, uint32_t off, const float (&v)[8]) {
   uint4 h;
@@ -82,92 +86,95 @@ __device__ __forceinline__ void store_chunk(uint8_t* hi, uint8_t* lo, uint32_t o
   }
 }
 
-// Packs blocks first .. first+count-1 of job J (all threads of the CTA).
-__device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm) {
+struct BlockGeom {
+  int rv, kv;  // valid rows and shared indices of the block
+};
+
+__device__ __forceinline__ BlockGeom block_geom(const PackJob& J, int b) {
+  const int tile = b / J.slabs, slab = b - tile * J.slabs;
+  const int64_t r0 = (int64_t)tile * PR, k0 = (int64_t)slab * PK;
+  BlockGeom g;
+  g.rv = (int)(J.R - r0 < PR ? J.R - r0 : PR);
+  g.kv = (int)(J.K - k0 < PK ? J.K - k0 : PK);
+  return g;
+}
+
+// Offset tables of block b into slot `sl` (threads 0 .. PR+PK-1).
+__device__ __forceinline__ void block_tables(const PackJob& J, int b, int sl, PackSmem& sm) {
+  const int t = threadIdx.x;
+  const int tile = b / J.slabs, slab = b - tile * J.slabs;
+  const int64_t r0 = (int64_t)tile * PR, k0 = (int64_t)slab * PK;
+  const BlockGeom g = block_geom(J, b);
+  if (t < PR) sm.roff[sl][t] = t < g.rv ? leg_offset((uint32_t)(r0 + t), J.nr, J.rdim, J.rstr) : 0;
+  else if (t < PR + PK)
+    sm.koff[sl][t - PR] = (t - PR) < g.kv ? leg_offset((uint32_t)(k0 + t - PR), J.nk, J.kdim, J.kstr) : 0;
+}
+
+// Block b with its tables in slot sl: rows 0 .. ceil8(rv)-1 of the output
+// (zeros outside the valid rows and shared indices).
+__device__ __forceinline__ void block_pack(const PackJob& J, int b, int sl, const PackSmem& sm) {
   const int t = threadIdx.x;
   const float* __restrict__ src = J.src;
-  const int64_t R = J.R, K = J.K;
-  const int slabs = J.slabs;
-  const bool kfast = J.kfast != 0, rfast = J.rfast != 0;
-  for (int b = first; b < first + count; ++b) {
-    const int tile = b / slabs, slab = b - tile * slabs;
-    const int64_t r0 = (int64_t)tile * PR, k0 = (int64_t)slab * PK;
-    const int rv = (int)(R - r0 < PR ? R - r0 : PR);
-    const int kv = (int)(K - k0 < PK ? K - k0 : PK);
-    if (t < PR) sm.roff[t] = t < rv ? leg_offset((uint32_t)(r0 + t), J.nr, J.rdim, J.rstr) : 0;
-    else if (t < PR + PK) sm.koff[t - PR] = (t - PR) < kv ? leg_offset((uint32_t)(k0 + t - PR), J.nk, J.kdim, J.kstr) : 0;
-    __syncthreads();
-    const int rs = (rv + 7) & ~7;  // rows stored: whole 8-row atoms
-    uint8_t* hi = J.hi + (size_t)b * (size_t)J.block_bytes;
-    uint8_t* lo = J.lo ? J.lo + (size_t)b * (size_t)J.block_bytes : nullptr;
-    if (kfast) {
-      // phase A: thread -> (row, 4 consecutive k); consecutive threads walk k
-#pragma unroll 4
-      for (int e = t; e < PR * (PK / 4); e += PACK_THREADS) {
-        const int r = e >> 4, q = (e & 15) * 4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < rv && q < kv) {
-          const float* rowp = src + sm.roff[r];
-          const float* p = rowp + sm.koff[q];
-          if (q + 3 < kv && sm.koff[q + 3] == sm.koff[q] + 3 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-            v = __ldg(reinterpret_cast<const float4*>(p));
-          } else {
-            v.x = __ldg(p);
-            if (q + 1 < kv) v.y = __ldg(rowp + sm.koff[q + 1]);
-            if (q + 2 < kv) v.z = __ldg(rowp + sm.koff[q + 2]);
-            if (q + 3 < kv) v.w = __ldg(rowp + sm.koff[q + 3]);
-          }
-        }
-        *reinterpret_cast<float4*>(&sm.T[r][q]) = v;
-      }
-      __syncthreads();
-      // phase B: thread -> (row, 8-wide k group)
-      for (int e = t; e < rs * (PK / 8); e += PACK_THREADS) {
-        const int r = e >> 3, g = e & 7;
-        const float4 a = *reinterpret_cast<const float4*>(&sm.T[r][g * 8]);
-        const float4 c = *reinterpret_cast<const float4*>(&sm.T[r][g * 8 + 4]);
-        const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
-        store_chunk(hi, lo, sw128_chunk(r, g), v);
-      }
-    } else {
-      // phase A: thread -> (4 consecutive rows, one k); consecutive threads walk rows
-#pragma unroll 4
-      for (int e = t; e < (PR / 4) * PK; e += PACK_THREADS) {
-        const int r = (e & 31) * 4, k = e >> 5;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < rv && k < kv) {
-          const float* colp = src + sm.koff[k];
-          const float* p = colp + sm.roff[r];
-          if (rfast && r + 3 < rv && sm.roff[r + 3] == sm.roff[r] + 3 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-            v = __ldg(reinterpret_cast<const float4*>(p));
-          } else {
-            v.x = __ldg(p);
-            if (r + 1 < rv) v.y = __ldg(colp + sm.roff[r + 1]);
-            if (r + 2 < rv) v.z = __ldg(colp + sm.roff[r + 2]);
-            if (r + 3 < rv) v.w = __ldg(colp + sm.roff[r + 3]);
-          }
-        }
-        *reinterpret_cast<float4*>(&sm.Tt[k][r]) = v;
-      }
-      __syncthreads();
-      // phase B: thread -> (row, 8-wide k group); consecutive threads walk rows
-      for (int e = t; e < PR * (PK / 8); e += PACK_THREADS) {
-        const int r = e & (PR - 1), g = e >> 7;
-        if (r >= rs) continue;
-        float v[8];
+  const BlockGeom g = block_geom(J, b);
+  const int rs = (g.rv + 7) & ~7;
+  const int64_t* roff = sm.roff[sl];
+  const int64_t* koff = sm.koff[sl];
+  uint8_t* hi = J.hi + (size_t)b * (size_t)J.block_bytes;
+  uint8_t* lo = J.lo ? J.lo + (size_t)b * (size_t)J.block_bytes : nullptr;
+  float v[PACK_CPT][8];
+  int rr[PACK_CPT], gg[PACK_CPT];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = sm.Tt[g * 8 + j][r];
-        store_chunk(hi, lo, sw128_chunk(r, g), v);
-      }
+  for (int c = 0; c < PACK_CPT; ++c) {
+    const int e = t + c * PACK_THREADS;
+    int r, grp;
+    if (J.kfast) {
+      r = e >> 3;
+      grp = e & 7;
+    } else {
+      r = e & (PR - 1);
+      grp = e >> 7;
     }
-    __syncthreads();  // staging and offset tables are reused by the next block
+    rr[c] = r;
+    gg[c] = grp;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[c][j] = 0.0f;
+    if (r >= g.rv) continue;
+    const int k0 = grp * 8;
+    const float* rowp = src + roff[r];
+    if (J.kfast && k0 + 7 < g.kv && koff[k0 + 7] == koff[k0] + 7 &&
+        (reinterpret_cast<uintptr_t>(rowp + koff[k0]) & 15) == 0) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(rowp + koff[k0]));
+      const float4 d = __ldg(reinterpret_cast<const float4*>(rowp + koff[k0]) + 1);
+      v[c][0] = a.x; v[c][1] = a.y; v[c][2] = a.z; v[c][3] = a.w;
+      v[c][4] = d.x; v[c][5] = d.y; v[c][6] = d.z; v[c][7] = d.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (k0 + j < g.kv) v[c][j] = __ldg(rowp + koff[k0 + j]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < PACK_CPT; ++c)
+    if (rr[c] < rs) store_chunk(hi, lo, sw128_chunk(rr[c], gg[c]), v[c]);
+}
+
+// Packs blocks first .. first+count-1 of job J (all threads of the CTA). The
+// tables of block j+1 go to the other slot, so one barrier per block orders
+// both their publication and the reuse of the slot two blocks later.
+__device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm) {
+  for (int j = 0; j < count; ++j) {
+    const int sl = j & 1;
+    block_tables(J, first + j, sl, sm);
+    __syncthreads();
+    block_pack(J, first + j, sl, sm);
   }
 }
 
 // Grouped form: one CTA per pack unit of the uploaded lists.
 __global__ void __launch_bounds__(PACK_THREADS)
 pack_kernel(const PackJob* __restrict__ jobs, const PackUnit* __restrict__ units) {
-  __shared__ __align__(16) PackSmem sm;
+  extern __shared__ __align__(16) uint8_t pack_smem_raw[];
+  PackSmem& sm = *reinterpret_cast<PackSmem*>(pack_smem_raw);
   const PackUnit un = units[blockIdx.x];
   pack_blocks(jobs[un.job], un.first, un.count, sm);
 }
@@ -182,7 +189,8 @@ struct PackPair {
 
 __global__ void __launch_bounds__(PACK_THREADS)
 pack_pair_kernel(const __grid_constant__ PackPair pp) {
-  __shared__ __align__(16) PackSmem sm;
+  extern __shared__ __align__(16) uint8_t pack_smem_raw[];
+  PackSmem& sm = *reinterpret_cast<PackSmem*>(pack_smem_raw);
   const bool is_a = (int)blockIdx.x < pp.units_a;
   const PackJob& J = is_a ? pp.a : pp.b;
   const int per = is_a ? pp.per_a : pp.per_b;
@@ -291,8 +299,12 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t gs = 0;
+      // each role loads the descriptor of its next unit while the current
+      // one runs, so unit boundaries do not wait on global-memory latency
+      GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
       for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
-        const GemmDesc d = load_desc(single, descs, map, u);
+        const GemmDesc d = dn;
+        if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
         const GUnit g = gunit(d, u - d.tile_begin);
         const uint32_t pb = rows_bytes(d.RP - g.p0), qb = rows_bytes(d.RQ - g.q0);
         const uint32_t tx = (pb + qb) * (SPLIT ? 2u : 1u);
@@ -323,8 +335,10 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t gs = 0, gc = 0;
+      GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
       for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
-        const GemmDesc d = load_desc(single, descs, map, u);
+        const GemmDesc d = dn;
+        if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qrows = d.RQ - g.q0 < PR ? d.RQ - g.q0 : PR;
         const int nmma = (int)((qrows + 15) & ~int64_t(15));
@@ -370,8 +384,10 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
     const int quad = warp & 3;            // TMEM lanes quad*32 .. quad*32+31
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     uint32_t gc = 0;
+    GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
     for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
-      const GemmDesc d = load_desc(single, descs, map, u);
+      const GemmDesc d = dn;
+      if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
       const GUnit g = gunit(d, u - d.tile_begin);
       const int64_t i = g.p0 + quad * 32 + lane;            // row of P this thread owns
       const int64_t qcols = d.RQ - g.q0 < PR ? d.RQ - g.q0 : PR;
@@ -383,9 +399,12 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
 #pragma unroll
       for (int j = 0; j < (SPLIT ? PR : 1); ++j) acc[j] = 0.0f;
       // writes columns col .. col+31 of row i (values in r)
+      // Writes columns col .. col+31 of row i (this thread's values r):
+      // 16-byte stores along a row of C, or, with the roles swapped, one
+      // store per column with the warp's lanes on consecutive addresses.
       auto emit = [&](int col, const float* r) {
-        if (i >= d.RP) return;
         if (d.cj == 1) {
+          if (i >= d.RP) return;
           float* dst = C + i * d.ci + g.q0 + col;
           const int64_t nrem = qcols - col;
           const bool vec = ((d.ci & 3) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 3) == 0;
@@ -393,6 +412,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           for (int j = 0; j < 32; j += 4)
             if (j < nrem) emit4(dst + j, vec, nrem - j, accumulate, r[j], r[j + 1], r[j + 2], r[j + 3]);
         } else {
+          if (i >= d.RP) return;
           float* dst = C + i * d.ci + (g.q0 + col) * d.cj;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -448,6 +468,21 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
   }
 }
 
+// Both pack kernels take PACK_SMEM of dynamic shared memory (above the 48 KB
+// default); set once per process.
+bool pack_attr() {
+  static bool done = false;
+  if (!done) {
+    if (cudaFuncSetAttribute(pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PACK_SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(pack_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PACK_SMEM) !=
+            cudaSuccess)
+      return false;
+    done = true;
+  }
+  return true;
+}
+
 int sm_count() {
   static int sms = 0;
   if (!sms) {
@@ -480,7 +515,8 @@ int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* ma
 int launch_pack(const PackJob* jobs, const PackUnit* units, int64_t nunits, cudaStream_t s) {
   if (nunits <= 0) return TN_OK;
   if (nunits > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
-  pack_kernel<<<(unsigned)nunits, PACK_THREADS, 0, s>>>(jobs, units);
+  if (!pack_attr()) return TN_ERR_CUDA;
+  pack_kernel<<<(unsigned)nunits, PACK_THREADS, PACK_SMEM, s>>>(jobs, units);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
@@ -652,7 +688,8 @@ int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_
   g.tile_begin = 0;
   if (d.splits > 1 && cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) != cudaSuccess)
     return TN_ERR_CUDA;
-  pack_pair_kernel<<<(unsigned)(na + nb), PACK_THREADS, 0, s>>>(pp);
+  if (!pack_attr()) return TN_ERR_CUDA;
+  pack_pair_kernel<<<(unsigned)(na + nb), PACK_THREADS, PACK_SMEM, s>>>(pp);
   if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   const int64_t units = (int64_t)g.tiles_p * g.tiles_q * g.splits;
   if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;

@@ -63,6 +63,8 @@ constexpr int MAX_SLABS_PER_UNIT = 32;
 // Sets tiles_m/n, splits and k_per_split; `min_units` asks for at least that
 // many work units when K is long enough to split (keeping >= 4 slabs per unit).
 void plan_units(ContractDesc* d, int64_t min_units);
+// The same for the packed GEMM (longer k ranges when a spec has many tiles).
+void plan_units_packed(ContractDesc* d);
 
 // Zeroes the results of split specs: list of (pointer, element count).
 struct ZeroRange {
@@ -71,14 +73,25 @@ struct ZeroRange {
 };
 int launch_zero(const ZeroRange* ranges, int n, cudaStream_t stream);
 
-// tn_contract without the C-ABI wrapper (used by the chain sweeps).
+// tn_contract without the C-ABI wrapper (used by the chain sweeps). With a
+// scratch buffer large enough for the packed operands (BF16 / BF16X3), the
+// contraction runs as pack + GEMM; otherwise on the single-pass kernels.
 int contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
-                      int nshared, const tn_tensor* C, int prec, cudaStream_t stream);
+                      int nshared, const tn_tensor* C, int prec, cudaStream_t stream, void* scratch = nullptr,
+                      size_t scratch_bytes = 0);
 
 // tn_group_plan_create; allow_packed = false keeps BF16 / BF16X3 plans on
 // the single-launch kernel, whose workspace holds only the work list.
 int group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec, bool allow_packed,
                          tn_group_plan** plan);
+
+// Plans that run one after another on a stream can share one region for
+// their packed bf16 blocks: the lists go to `lists` (group_plan_list_bytes),
+// the blocks to `packed` (group_plan_packed_bytes, 256-byte aligned).
+size_t group_plan_list_bytes(const tn_group_plan* plan);
+size_t group_plan_packed_bytes(const tn_group_plan* plan);
+int group_plan_upload_shared(const tn_group_plan* plan, void* lists, size_t bytes, void* packed, cudaStream_t s);
+int group_plan_run_shared(const tn_group_plan* plan, void* lists, size_t bytes, cudaStream_t s);
 
 // Device status word (first error wins); defined in api.cu.
 int* status_word();

@@ -84,6 +84,8 @@ def _signatures():
         "tn_group_plan_flops": (ctypes.c_double, [vp]),
         "tn_group_plan_bytes": (ctypes.c_double, [vp]),
         "tn_group_plan_launches": (i32, [vp]),
+        "tn_group_plan_run_launch": (i32, [vp, vp, ctypes.c_size_t, i32, vp]),
+        "tn_group_plan_launch_name": (ctypes.c_char_p, [vp, i32]),
         "tn_mps_inner_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
         "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
@@ -278,6 +280,15 @@ class GroupPlan:
     def run(self, stream=None):
         _check(load().tn_group_plan_run(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
                                         _stream(stream)), "tn_group_plan_run")
+
+    def launch_names(self):
+        lib = load()
+        return [lib.tn_group_plan_launch_name(self._h, i).decode() for i in range(self.launches)]
+
+    def run_launch(self, index: int, stream=None):
+        """Launch `index` of the run's sequence alone (tn_group_plan_run_launch)."""
+        _check(load().tn_group_plan_run_launch(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                               index, _stream(stream)), "tn_group_plan_run_launch")
 
     def __del__(self):
         h = getattr(self, "_h", None)
