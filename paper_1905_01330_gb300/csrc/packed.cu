@@ -9,7 +9,7 @@
 //   2. gemm: a persistent, warp-specialised tcgen05 kernel. Warp 0 moves
 //      blocks into a ring of shared-memory stages with 1-D bulk async copies
 //      (one copy per block: the layout needs no gather), warp 1 issues the
-//      MMAs into a double-buffered TMEM accumulator, warps 2-5 drain TMEM and
+//      MMAs into a double-buffered TMEM accumulator, warps 2-9 drain TMEM and
 //      write C while the next tile is multiplied.
 //
 // The per-tile float32 -> bf16 conversion of the single-launch kernel
@@ -110,19 +110,20 @@ __device__ __forceinline__ void block_tables(const PackJob& J, int b, int sl, Pa
     sm.koff[sl][t - PR] = (t - PR) < g.kv ? leg_offset((uint32_t)(k0 + t - PR), J.nk, J.kdim, J.kstr) : 0;
 }
 
-// Block b with its tables in slot sl: rows 0 .. ceil8(rv)-1 of the output
-// (zeros outside the valid rows and shared indices).
-__device__ __forceinline__ void block_pack(const PackJob& J, int b, int sl, const PackSmem& sm) {
+// The chunks a thread makes for one block: values and output coordinates.
+struct ChunkRegs {
+  float v[PACK_CPT][8];
+  int rr[PACK_CPT], gg[PACK_CPT];
+};
+
+// Loads this thread's chunks of block b (tables in slot sl); zeros outside
+// the valid rows and shared indices.
+__device__ __forceinline__ void block_load(const PackJob& J, int b, int sl, const PackSmem& sm, ChunkRegs& cr) {
   const int t = threadIdx.x;
   const float* __restrict__ src = J.src;
   const BlockGeom g = block_geom(J, b);
-  const int rs = (g.rv + 7) & ~7;
   const int64_t* roff = sm.roff[sl];
   const int64_t* koff = sm.koff[sl];
-  uint8_t* hi = J.hi + (size_t)b * (size_t)J.block_bytes;
-  uint8_t* lo = J.lo ? J.lo + (size_t)b * (size_t)J.block_bytes : nullptr;
-  float v[PACK_CPT][8];
-  int rr[PACK_CPT], gg[PACK_CPT];
 #pragma unroll
   for (int c = 0; c < PACK_CPT; ++c) {
     const int e = t + c * PACK_THREADS;
@@ -134,39 +135,55 @@ __device__ __forceinline__ void block_pack(const PackJob& J, int b, int sl, cons
       r = e & (PR - 1);
       grp = e >> 7;
     }
-    rr[c] = r;
-    gg[c] = grp;
+    cr.rr[c] = r;
+    cr.gg[c] = grp;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[c][j] = 0.0f;
+    for (int j = 0; j < 8; ++j) cr.v[c][j] = 0.0f;
     if (r >= g.rv) continue;
     const int k0 = grp * 8;
     const float* rowp = src + roff[r];
-    if (J.kfast && k0 + 7 < g.kv && koff[k0 + 7] == koff[k0] + 7 &&
-        (reinterpret_cast<uintptr_t>(rowp + koff[k0]) & 15) == 0) {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(rowp + koff[k0]));
-      const float4 d = __ldg(reinterpret_cast<const float4*>(rowp + koff[k0]) + 1);
-      v[c][0] = a.x; v[c][1] = a.y; v[c][2] = a.z; v[c][3] = a.w;
-      v[c][4] = d.x; v[c][5] = d.y; v[c][6] = d.z; v[c][7] = d.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (k0 + j < g.kv) v[c][j] = __ldg(rowp + koff[k0 + j]);
+    if (J.kfast && k0 + 7 < g.kv) {
+      const int64_t ka = koff[k0];
+      if (koff[k0 + 7] == ka + 7 && (reinterpret_cast<uintptr_t>(rowp + ka) & 15) == 0) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(rowp + ka));
+        const float4 d = __ldg(reinterpret_cast<const float4*>(rowp + ka) + 1);
+        cr.v[c][0] = a.x; cr.v[c][1] = a.y; cr.v[c][2] = a.z; cr.v[c][3] = a.w;
+        cr.v[c][4] = d.x; cr.v[c][5] = d.y; cr.v[c][6] = d.z; cr.v[c][7] = d.w;
+        continue;
+      }
     }
-  }
 #pragma unroll
-  for (int c = 0; c < PACK_CPT; ++c)
-    if (rr[c] < rs) store_chunk(hi, lo, sw128_chunk(rr[c], gg[c]), v[c]);
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < g.kv) cr.v[c][j] = __ldg(rowp + koff[k0 + j]);
+  }
 }
 
-// Packs blocks first .. first+count-1 of job J (all threads of the CTA). The
-// tables of block j+1 go to the other slot, so one barrier per block orders
-// both their publication and the reuse of the slot two blocks later.
+// Converts and writes this thread's chunks of block b (rows < ceil8(rv)).
+__device__ __forceinline__ void block_write(const PackJob& J, int b, const ChunkRegs& cr) {
+  const BlockGeom g = block_geom(J, b);
+  const int rs = (g.rv + 7) & ~7;
+  uint8_t* hi = J.hi + (size_t)b * (size_t)J.block_bytes;
+  uint8_t* lo = J.lo ? J.lo + (size_t)b * (size_t)J.block_bytes : nullptr;
+#pragma unroll
+  for (int c = 0; c < PACK_CPT; ++c)
+    if (cr.rr[c] < rs) store_chunk(hi, lo, sw128_chunk(cr.rr[c], cr.gg[c]), cr.v[c]);
+}
+
+// Packs blocks first .. first+count-1 of job J (all threads of the CTA).
+// The offset tables of block j+1 are decoded into the other slot while the
+// loads of block j are in flight; one barrier per block publishes them (and
+// orders the reuse of a slot two blocks later).
 __device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm) {
+  if (count <= 0) return;
+  block_tables(J, first, 0, sm);
+  __syncthreads();
+  ChunkRegs cr;
   for (int j = 0; j < count; ++j) {
     const int sl = j & 1;
-    block_tables(J, first + j, sl, sm);
+    block_load(J, first + j, sl, sm, cr);
+    if (j + 1 < count) block_tables(J, first + j + 1, sl ^ 1, sm);
+    block_write(J, first + j, cr);
     __syncthreads();
-    block_pack(J, first + j, sl, sm);
   }
 }
 
@@ -200,8 +217,11 @@ pack_pair_kernel(const __grid_constant__ PackPair pp) {
 }
 
 // ------------------------------------------------------------------- gemm
-constexpr int GEMM_THREADS = 192;   // warp 0 copies, warp 1 MMAs, warps 2-5 epilogue
-constexpr int EPI_WARPS = 4;
+// warp 0 copies, warp 1 issues the MMAs, warps 2-9 drain TMEM: two per lane
+// quadrant, each taking 64 of the tile's 128 columns
+constexpr int EPI_WARPS = 8;
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int EPI_COLS = PR * 4 / EPI_WARPS;  // columns drained per epilogue warp
 // BF16X3 promotes the TMEM accumulator into float32 registers every KC slabs
 // (256 shared indices): the tensor core's float32 accumulation truncates, and
 // over long k that error would exceed the split's own rounding error.
@@ -382,6 +402,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
   } else {
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;            // TMEM lanes quad*32 .. quad*32+31
+    const int col0 = ((warp - 2) >> 2) * EPI_COLS;  // first accumulator column of this warp
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     uint32_t gc = 0;
     GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
@@ -395,28 +416,33 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       const int nchunks = (g.nks + chunk - 1) / chunk;
       const bool accumulate = d.splits > 1;
       float* __restrict__ C = d.C;
-      float acc[SPLIT ? PR : 1];
+      // 16-byte stores along a row of C: C row-major along j, rows 16-byte aligned
+      const bool vec = d.cj == 1 && ((d.ci & 3) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 3) == 0;
+      float acc[SPLIT ? EPI_COLS : 1];
 #pragma unroll
-      for (int j = 0; j < (SPLIT ? PR : 1); ++j) acc[j] = 0.0f;
-      // writes columns col .. col+31 of row i (values in r)
+      for (int j = 0; j < (SPLIT ? EPI_COLS : 1); ++j) acc[j] = 0.0f;
       // Writes columns col .. col+31 of row i (this thread's values r):
       // 16-byte stores along a row of C, or, with the roles swapped, one
       // store per column with the warp's lanes on consecutive addresses.
       auto emit = [&](int col, const float* r) {
+        if (i >= d.RP) return;
+        const int64_t nrem = qcols - col;
         if (d.cj == 1) {
-          if (i >= d.RP) return;
           float* dst = C + i * d.ci + g.q0 + col;
-          const int64_t nrem = qcols - col;
-          const bool vec = ((d.ci & 3) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 3) == 0;
+          if (vec && !accumulate && nrem >= 32) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(dst + j) = make_float4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+            return;
+          }
 #pragma unroll
           for (int j = 0; j < 32; j += 4)
             if (j < nrem) emit4(dst + j, vec, nrem - j, accumulate, r[j], r[j + 1], r[j + 2], r[j + 3]);
         } else {
-          if (i >= d.RP) return;
           float* dst = C + i * d.ci + (g.q0 + col) * d.cj;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            if (col + j < qcols) {
+            if (j < nrem) {
               if (accumulate) atomicAdd(dst + j * d.cj, r[j]);
               else dst[j * d.cj] = r[j];
             }
@@ -429,10 +455,10 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         const bool w = ptx::mbar_wait(ptx::smem_addr(&x.acc_full[b]), (gc >> 1) & 1u, status);
         if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR);
+        const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR + col0);
 #pragma unroll
-        for (int cb = 0; cb < PR / 32; ++cb) {
-          if (cb * 32 < qcols) {  // uniform across the warp
+        for (int cb = 0; cb < EPI_COLS / 32; ++cb) {
+          if (col0 + cb * 32 < qcols) {  // uniform across the warp
             uint32_t r[32];
             ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
             ptx::tmem_ld_wait();
@@ -443,7 +469,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
               float v[32];
 #pragma unroll
               for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-              emit(cb * 32, v);
+              emit(col0 + cb * 32, v);
             }
           }
         }
@@ -454,8 +480,8 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       if (!ok) { x.abort = 1; break; }
       if (SPLIT) {
 #pragma unroll
-        for (int cb = 0; cb < PR / 32; ++cb)
-          if (cb * 32 < qcols) emit(cb * 32, &acc[cb * 32]);
+        for (int cb = 0; cb < EPI_COLS / 32; ++cb)
+          if (col0 + cb * 32 < qcols) emit(col0 + cb * 32, &acc[cb * 32]);
       }
     }
   }
