@@ -294,6 +294,32 @@ def run_extras(tn, synth, dev, stream):
         del cores
     out["classifier"] = cls
 
+    # large contractions: C[m, n] = sum_k A[m, k] B[k, n] at 8192^3 and
+    # 16384^3, one-spec plans (pack + GEMM), each launch timed alone
+    _, bf16_peak, _ = measured_peaks()
+    big = {}
+    for n in (8192, 16384):
+        A = torch.randn(n, n, device=dev)
+        B = torch.randn(n, n, device=dev)
+        C = torch.empty(n, n, device=dev)
+        f = 2.0 * n ** 3
+        for prec in ("bf16", "bf16x3"):
+            pl = tn.GroupPlan([(A, [1], B, [0], C)], prec=prec)
+            pl.autotune()
+            times = {}
+            for i, name in enumerate(pl.launch_names()):
+                times[name] = _time(lambda: pl.run_launch(i), 3, 1, stream)
+            step = sum(times.values())
+            big["n%d_%s" % (n, prec)] = {
+                "ms": {k: round(v, 4) for k, v in times.items()},
+                "gemm_tflops": f / (times["gemm"] * 1e-3) / 1e12,
+                "gemm_frac_of_bf16_peak": f / (times["gemm"] * 1e-3) / 1e12 / bf16_peak,
+                "step_tflops": f / (step * 1e-3) / 1e12,
+                "step_frac_of_bf16_peak": f / (step * 1e-3) / 1e12 / bf16_peak}
+            del pl
+        del A, B, C
+    out["large_contractions"] = big
+
     # config 1: <psi|psi>, N=20, chi=32 (one-CTA float32 sweep)
     m_h = synth.random_mps(20, 2, 32, seed=1)
     m = [torch.from_numpy(c).to(dev) for c in m_h]
@@ -424,6 +450,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     var_list = [] if args.variants == "none" else [v for v in args.variants.split(",") if v]
     plans = {p: tn.GroupPlan(specs, prec=p) for p in ["bf16"] + var_list}
+    # setup, outside the timed region: the autotuner times the candidate GEMM
+    # schedules on this workload and keeps the fastest
+    schedules = {p: pl.autotune() for p, pl in plans.items() if p != "fp32"}
     plan = plans["bf16"]
     flops, nbytes = plan.flops, plan.bytes
 
@@ -557,7 +586,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(),
                 "gpu_launches": args.steps * plan.launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
-                "cpu_baseline": cpu, "variants": variants,
+                "cpu_baseline": cpu, "variants": variants, "schedules": schedules,
                 "tensor_peak_frac": value / world / bf16_peak, "extras": extras}
         print(json.dumps(line), flush=True)
     if world > 1:

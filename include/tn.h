@@ -94,6 +94,23 @@ int tn_tensor_init(tn_tensor* t, void* data, int rank, const int64_t* shape);
 int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
                 int nshared, const tn_tensor* C, int prec, void* stream);
 
+/*
+ * tn_contract with scratch space: BF16 / BF16X3 contractions then run as two
+ * launches, a pack of both operands into bf16 blocks (in `workspace`) and the
+ * warp-specialised tcgen05 GEMM that reads them (the path of the grouped
+ * launch; much faster on large contractions than tn_contract's single-pass
+ * kernel, which converts every operand tile once per output tile). Both
+ * launches take their lists by value, so the call can be captured in a graph.
+ *   workspace: DEVICE scratch, 256-byte aligned, at least
+ *     tn_contract_workspace_bytes() bytes (0 for FP32 and empty contractions),
+ *     or NULL to run tn_contract's kernels.
+ * Errors: as tn_contract, plus TN_ERR_WORKSPACE (misaligned or too small).
+ */
+size_t tn_contract_workspace_bytes(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                                   int nshared, const tn_tensor* C, int prec);
+int tn_contract_ws(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB, int nshared,
+                   const tn_tensor* C, int prec, void* workspace, size_t bytes, void* stream);
+
 /* One pairwise contraction of a grouped launch. */
 typedef struct tn_contract_spec {
   tn_tensor A, B, C;
@@ -162,6 +179,37 @@ int tn_group_plan_run_launch(const tn_group_plan* plan, void* workspace, size_t 
 /* "zero", "pack", "gemm" (packed bf16 blocks) or "contract" (single-pass
  * kernel) for launch `index`; NULL when out of range. */
 const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index);
+/*
+ * Autotuner of a BF16 / BF16X3 plan's GEMM schedule (the paper has no
+ * counterpart; its contractions run through TensorFlow). The contractions
+ * fall in three classes, tuned one after the other: 0 thin (fewer than 128
+ * rows on one side), 1 short shared index (K <= 512), 2 the rest. For each
+ * class the candidates are the output tile width (128 or 64 rows of the
+ * narrower operand per tile), the epilogue's tensor-memory read shape (one
+ * row per thread, or 16-lane x 256-bit blocks whose stores cover whole
+ * 32-byte sectors), and, for class 2, whether a contraction with at least 16
+ * output tiles keeps each tile's whole k range in one work unit or cuts it
+ * into 2048-long ranges accumulated with atomics. Each candidate runs on the
+ * device with the plan's own operands (one warm-up run, two timed with CUDA
+ * events) and the fastest is kept; the choice is also stored in a host-side
+ * cache inside the library, keyed by precision and the contractions' shapes,
+ * from which later plans of the same shapes start.
+ *   workspace: the plan's workspace (any schedule fits it); on return the
+ *     plan is uploaded there with the chosen schedule.
+ *   The call runs the contractions (results are written, correctly, several
+ *   times) and synchronises `stream`; it cannot be captured in a graph.
+ *   FP32 plans have nothing to tune: TN_OK, nothing launched.
+ * Errors: as tn_group_plan_run.
+ */
+int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
+/* The schedule a plan runs for class `cls` (0, 1, 2 as above): the output
+ * tile width (128 or 64), whether long k ranges are kept whole, and whether
+ * the epilogue reads 16-lane x 256-bit blocks. Errors: TN_ERR_ARG. */
+int tn_group_plan_schedule(const tn_group_plan* plan, int cls, int* tile_width, int* long_k, int* store16);
+/* Sets that schedule by hand (tile_width 128 or 64); the plan must be
+ * uploaded again before its next run. FP32 plans ignore it.
+ * Errors: TN_ERR_ARG, TN_ERR_UNSUPPORTED. */
+int tn_group_plan_set_schedule(tn_group_plan* plan, int cls, int tile_width, int long_k, int store16);
 
 /* ------------------------------------------------------------------------ */
 /* Matrix product states and operators (Sec. II, Fig. 3a)                    */

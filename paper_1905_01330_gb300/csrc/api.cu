@@ -3,6 +3,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -58,6 +60,9 @@ struct tn_group_plan {
   std::vector<ZeroRange> zero_ranges;  // results zeroed on the device before the launch
   std::vector<int32_t> unit_desc;      // descriptor (or GEMM) index of every work unit
   tn::PackedPlan pp;                   // packed path (BF16 / BF16X3)
+  tn::PackedSchedule sched[3];         // packed schedules: thin (min(M, N) < 128), short k (<= 512), long k
+  size_t reserve_zero = 0, reserve_units = 0;  // list sizes of the largest schedule (workspace layout)
+  uint64_t signature = 0;              // shapes of the specs (tuning cache key)
   bool packed = false;
   int prec = TN_PREC_FP32;
   int64_t total_tiles = 0;
@@ -133,6 +138,28 @@ int tn_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, const 
   return tn::contract_internal(A, legsA, B, legsB, nshared, C, prec, static_cast<cudaStream_t>(stream));
 }
 
+size_t tn_contract_workspace_bytes(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
+                                   int nshared, const tn_tensor* C, int prec) {
+  if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return 0;
+  ContractDesc d;
+  if (plan_contract(A, legsA, B, legsB, nshared, C, &d) != TN_OK) return 0;
+  if (d.M == 0 || d.N == 0 || d.K == 0) return 0;
+  plan_units(&d, min_units_single());
+  return packed_single_bytes(d, prec);
+}
+
+int tn_contract_ws(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB, int nshared,
+                   const tn_tensor* C, int prec, void* workspace, size_t bytes, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!workspace) return tn::contract_internal(A, legsA, B, legsB, nshared, C, prec, s);
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return TN_ERR_WORKSPACE;
+  if (prec == TN_PREC_BF16 || prec == TN_PREC_BF16X3) {
+    const size_t need = tn_contract_workspace_bytes(A, legsA, B, legsB, nshared, C, prec);
+    if (bytes < need) return TN_ERR_WORKSPACE;
+  }
+  return tn::contract_internal(A, legsA, B, legsB, nshared, C, prec, s, workspace, bytes);
+}
+
 }  // extern "C"
 
 int tn::contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, const int* legsB,
@@ -163,6 +190,80 @@ int tn_group_plan_create(const tn_contract_spec* specs, int nspecs, int prec, tn
 
 }  // extern "C"
 
+namespace {
+
+// Schedule class of a contraction: 0 thin (fewer than 128 rows on one side),
+// 1 short shared index (K <= 512: bound by writing C), 2 the rest.
+int spec_class(const ContractDesc& d) {
+  if (std::min(d.M, d.N) < 128) return 0;
+  return d.K <= 512 ? 1 : 2;
+}
+
+tn::PackedSchedule default_schedule(int cls) {
+  tn::PackedSchedule sc;
+  sc.store16 = cls == 2 ? 1 : 0;  // measured: whole-sector stores help long-k specs only
+  return sc;
+}
+
+// (Re)builds a packed plan's GEMM list, zero ranges and unit map from its
+// contractions under its schedules.
+int build_packed(tn_group_plan* p) {
+  p->pp = tn::PackedPlan();
+  p->zero_ranges.clear();
+  for (const auto& d0 : p->descs) {
+    ContractDesc d = d0;
+    const tn::PackedSchedule& sc = p->sched[spec_class(d)];
+    plan_units_packed(&d, sc.long_k != 0);
+    const int rc = plan_packed(d, p->prec, sc, &p->pp);
+    if (rc != TN_OK) return rc;
+  }
+  // largest units first: tensor time plus memory time of one unit
+  auto cost = [](const GemmDesc& g) {
+    const double pr = (double)std::min<int64_t>(g.RP, 128), qr = (double)std::min<int64_t>(g.RQ, g.q_tile);
+    const double k = 64.0 * std::min<int64_t>(g.slabs, g.slabs_per_split);
+    return 2.0 * pr * qr * k / 1500.0 + (2.0 * (pr + qr) * k + 4.0 * pr * qr) / 5.0;
+  };
+  std::stable_sort(p->pp.gemms.begin(), p->pp.gemms.end(),
+                   [&](const GemmDesc& a, const GemmDesc& b) { return cost(a) > cost(b); });
+  int64_t t = 0;
+  for (auto& g : p->pp.gemms) {
+    g.tile_begin = t;
+    t += (int64_t)g.tiles_p * g.tiles_q * g.splits;
+    if (g.splits > 1) p->zero_ranges.push_back(ZeroRange{g.C, g.RP * g.RQ});
+  }
+  p->total_tiles = t;
+  if (t > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  p->unit_desc.assign((size_t)t, 0);
+  for (size_t i = 0; i < p->pp.gemms.size(); ++i) {
+    const GemmDesc& g = p->pp.gemms[i];
+    const int64_t n = (int64_t)g.tiles_p * g.tiles_q * g.splits;
+    std::fill(p->unit_desc.begin() + g.tile_begin, p->unit_desc.begin() + g.tile_begin + n, (int32_t)i);
+  }
+  return TN_OK;
+}
+
+// Host-side tuning cache: schedules picked by tn_group_plan_autotune, keyed
+// by precision and the specs' shapes; a later plan of the same shapes starts
+// from them.
+std::mutex g_tune_lock;
+struct TunedSchedules {
+  tn::PackedSchedule sc[3];
+};
+std::map<uint64_t, TunedSchedules> g_tune_cache;
+
+uint64_t plan_signature(const tn_group_plan* p) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)p->prec;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  for (const auto& d : p->descs) {
+    mix((uint64_t)d.M);
+    mix((uint64_t)d.N);
+    mix((uint64_t)d.K);
+  }
+  return h;
+}
+
+}  // namespace
+
 int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec, bool allow_packed,
                              tn_group_plan** plan) {
   if (!plan) return TN_ERR_ARG;
@@ -191,33 +292,23 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
   // largest work units first, so the tail of the launch is made of small ones
   if (prec != TN_PREC_FP32 && allow_packed) {
     p->packed = true;
-    for (auto& d : p->descs) {
-      plan_units_packed(&d);
-      const int rc = plan_packed(d, prec, &p->pp);
-      if (rc != TN_OK) { delete p; return rc; }
+    p->signature = plan_signature(p);
+    // the workspace is laid out for the schedule with the longest lists
+    // (64-wide tiles, 32-slab k ranges), so any schedule fits it
+    for (auto& sc : p->sched) sc = tn::PackedSchedule{64, 0, 0};
+    int rc = build_packed(p);
+    if (rc != TN_OK) { delete p; return rc; }
+    p->reserve_zero = p->zero_ranges.size();
+    p->reserve_units = p->unit_desc.size();
+    for (int c = 0; c < 3; ++c) p->sched[c] = default_schedule(c);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_lock);
+      auto it = g_tune_cache.find(p->signature);
+      if (it != g_tune_cache.end())
+        for (int c = 0; c < 3; ++c) p->sched[c] = it->second.sc[c];
     }
-    // largest units first: tensor time plus memory time of one unit
-    auto cost = [](const GemmDesc& g) {
-      const double pr = (double)std::min<int64_t>(g.RP, 128), qr = (double)std::min<int64_t>(g.RQ, 128);
-      const double k = 64.0 * std::min<int64_t>(g.slabs, g.slabs_per_split);
-      return 2.0 * pr * qr * k / 1500.0 + (2.0 * (pr + qr) * k + 4.0 * pr * qr) / 5.0;
-    };
-    std::stable_sort(p->pp.gemms.begin(), p->pp.gemms.end(),
-                     [&](const GemmDesc& a, const GemmDesc& b) { return cost(a) > cost(b); });
-    int64_t t = 0;
-    for (auto& g : p->pp.gemms) {
-      g.tile_begin = t;
-      t += (int64_t)g.tiles_p * g.tiles_q * g.splits;
-      if (g.splits > 1) p->zero_ranges.push_back(ZeroRange{g.C, g.RP * g.RQ});
-    }
-    p->total_tiles = t;
-    if (t > 0x7FFFFFFF) { delete p; return TN_ERR_UNSUPPORTED; }
-    p->unit_desc.resize((size_t)t);
-    for (size_t i = 0; i < p->pp.gemms.size(); ++i) {
-      const GemmDesc& g = p->pp.gemms[i];
-      const int64_t n = (int64_t)g.tiles_p * g.tiles_q * g.splits;
-      std::fill(p->unit_desc.begin() + g.tile_begin, p->unit_desc.begin() + g.tile_begin + n, (int32_t)i);
-    }
+    rc = build_packed(p);
+    if (rc != TN_OK) { delete p; return rc; }
     *plan = p;
     return TN_OK;
   }
@@ -256,10 +347,12 @@ static size_t zero_offset(const tn_group_plan* plan) {
                       : align256(sizeof(ContractDesc) * plan->descs.size());
 }
 static size_t map_offset(const tn_group_plan* plan) {
-  return zero_offset(plan) + align256(sizeof(ZeroRange) * plan->zero_ranges.size());
+  const size_t nz = plan->packed ? plan->reserve_zero : plan->zero_ranges.size();
+  return zero_offset(plan) + align256(sizeof(ZeroRange) * nz);
 }
 static size_t jobs_offset(const tn_group_plan* plan) {
-  return map_offset(plan) + align256(sizeof(int32_t) * plan->unit_desc.size());
+  const size_t nu = plan->packed ? plan->reserve_units : plan->unit_desc.size();
+  return map_offset(plan) + align256(sizeof(int32_t) * nu);
 }
 static size_t punits_offset(const tn_group_plan* plan) {
   return jobs_offset(plan) + align256(sizeof(PackJob) * plan->pp.jobs.size());
@@ -466,6 +559,83 @@ const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index) {
 }  // extern "C"
 
 extern "C" {
+
+int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, void* stream) {
+  if (!plan) return TN_ERR_ARG;
+  int rc = check_ws(plan, workspace, bytes);
+  if (rc != TN_OK) return rc;
+  if (!plan->packed || plan->total_tiles == 0) return TN_OK;  // nothing to choose
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return TN_ERR_CUDA;
+  }
+  // one candidate: rebuild, upload, one warm run, the mean of two timed runs
+  auto trial = [&](float* ms) -> int {
+    int r = build_packed(plan);
+    if (r == TN_OK) r = upload_impl(plan, workspace, base + packed_offset(plan), s);
+    if (r == TN_OK) r = run_impl(plan, workspace, s);
+    if (r == TN_OK && cudaEventRecord(e0, s) != cudaSuccess) r = TN_ERR_CUDA;
+    for (int k = 0; k < 2 && r == TN_OK; ++k) r = run_impl(plan, workspace, s);
+    if (r == TN_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                       cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+      r = TN_ERR_CUDA;
+    return r;
+  };
+  bool has[3] = {false, false, false};
+  for (const auto& d : plan->descs) has[spec_class(d)] = true;
+  // candidates: tile width 128 / 64, epilogue shape, and (long-k class only)
+  // whole or cut k ranges; coordinate descent over the three classes
+  std::vector<tn::PackedSchedule> cand;
+  for (int cls = 0; cls < 3 && rc == TN_OK; ++cls) {
+    if (!has[cls]) continue;
+    cand.clear();
+    for (int w : {128, 64})
+      for (int s16 : {0, 1})
+        for (int lk : {1, 0})
+          if (cls == 2 || lk == 1) cand.push_back(tn::PackedSchedule{w, lk, s16});
+    float best = 0.0f;
+    tn::PackedSchedule pick = plan->sched[cls];
+    for (size_t c = 0; c < cand.size() && rc == TN_OK; ++c) {
+      plan->sched[cls] = cand[c];
+      float ms = 0.0f;
+      rc = trial(&ms);
+      if (rc == TN_OK && (c == 0 || ms < best)) {
+        best = ms;
+        pick = cand[c];
+      }
+    }
+    plan->sched[cls] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TN_OK) return rc;
+  rc = build_packed(plan);
+  if (rc == TN_OK) rc = upload_impl(plan, workspace, base + packed_offset(plan), s);
+  if (rc != TN_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_tune_lock);
+  TunedSchedules& t = g_tune_cache[plan->signature];
+  for (int c = 0; c < 3; ++c) t.sc[c] = plan->sched[c];
+  return TN_OK;
+}
+
+int tn_group_plan_set_schedule(tn_group_plan* plan, int cls, int tile_width, int long_k, int store16) {
+  if (!plan || cls < 0 || cls > 2 || (tile_width != 64 && tile_width != 128)) return TN_ERR_ARG;
+  if (!plan->packed) return TN_OK;
+  plan->sched[cls] = tn::PackedSchedule{tile_width, long_k ? 1 : 0, store16 ? 1 : 0};
+  return build_packed(plan);
+}
+
+int tn_group_plan_schedule(const tn_group_plan* plan, int cls, int* tile_width, int* long_k, int* store16) {
+  if (!plan || cls < 0 || cls > 2 || !tile_width || !long_k || !store16) return TN_ERR_ARG;
+  const tn::PackedSchedule& sc = plan->sched[cls];
+  *tile_width = plan->packed ? sc.q_tile : TC_BN;
+  *long_k = plan->packed ? sc.long_k : 0;
+  *store16 = plan->packed ? sc.store16 : 0;
+  return TN_OK;
+}
 
 void tn_group_plan_destroy(tn_group_plan* plan) { delete plan; }
 

@@ -198,7 +198,7 @@ pack_kernel(const PackJob* __restrict__ jobs, const PackUnit* __restrict__ units
 
 // Single-contraction form: both jobs passed by value (nothing to upload, so
 // the launch can be captured in a CUDA graph). CTAs 0 .. units_a-1 pack A,
-// `per_a` blocks each; the rest pack B, `per_b` blocks each.
+// `per_a` slabs of one row tile each; the rest pack B, `per_b` each.
 struct PackPair {
   PackJob a, b;
   int32_t units_a, per_a, per_b, pad;
@@ -263,7 +263,7 @@ __device__ __forceinline__ GUnit gunit(const GemmDesc& d, int64_t u) {
   const int64_t tp = rest % d.tiles_p;
   const int64_t split = rest / d.tiles_p;
   g.p0 = tp * PR;
-  g.q0 = tq * PR;
+  g.q0 = tq * d.q_tile;
   g.ks0 = (int32_t)(split * d.slabs_per_split);
   g.nks = (int32_t)(d.slabs - g.ks0 < d.slabs_per_split ? d.slabs - g.ks0 : d.slabs_per_split);
   return g;
@@ -326,10 +326,12 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         const GemmDesc d = dn;
         if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
         const GUnit g = gunit(d, u - d.tile_begin);
-        const uint32_t pb = rows_bytes(d.RP - g.p0), qb = rows_bytes(d.RQ - g.q0);
+        const int64_t qleft = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
+        const uint32_t pb = rows_bytes(d.RP - g.p0), qb = rows_bytes(qleft);
         const uint32_t tx = (pb + qb) * (SPLIT ? 2u : 1u);
         const uint8_t* pbase = d.P + ((g.p0 / PR) * d.slabs + g.ks0) * d.P_block;
-        const uint8_t* qbase = d.Q + ((g.q0 / PR) * d.slabs + g.ks0) * d.Q_block;
+        // a 64-row tile starts 64 rows (8 atoms, 8 KB) into its 128-row block
+        const uint8_t* qbase = d.Q + ((g.q0 / PR) * d.slabs + g.ks0) * d.Q_block + (g.q0 % PR) * 128;
         bool ok = true;
         for (int ks = 0; ks < g.nks; ++ks, ++gs) {
           const int s = (int)(gs % S);
@@ -360,7 +362,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         const GemmDesc d = dn;
         if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
         const GUnit g = gunit(d, u - d.tile_begin);
-        const int64_t qrows = d.RQ - g.q0 < PR ? d.RQ - g.q0 : PR;
+        const int64_t qrows = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
         const int nmma = (int)((qrows + 15) & ~int64_t(15));
         const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, 0, 0);
         const int chunk = SPLIT ? KC : g.nks;
@@ -411,7 +413,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
       const GUnit g = gunit(d, u - d.tile_begin);
       const int64_t i = g.p0 + quad * 32 + lane;            // row of P this thread owns
-      const int64_t qcols = d.RQ - g.q0 < PR ? d.RQ - g.q0 : PR;
+      const int64_t qcols = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
       const int chunk = SPLIT ? KC : g.nks;
       const int nchunks = (g.nks + chunk - 1) / chunk;
       const bool accumulate = d.splits > 1;
@@ -449,27 +451,78 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           }
         }
       };
+      // C row-major along j: the accumulator is read as 16-lane x 256-bit
+      // blocks, so each thread holds two consecutive columns of two rows and
+      // a warp's store covers 8 rows x 32 contiguous bytes (whole sectors).
+      const bool rows16 = d.cj == 1 && d.store16 != 0;
+      const bool vec2 = rows16 && ((d.ci & 1) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 1) == 0 &&
+                        ((reinterpret_cast<uintptr_t>(C) & 7) == 0);
+      // values r[4j..4j+3] of lane half h (rows +0 and +8), columns col0 + 8j + 2(lane % 4) + {0, 1}
+      auto emit16 = [&](int h, const float* r) {
+        const int64_t row = g.p0 + quad * 32 + h * 16 + (lane >> 2);
+        const int cq = col0 + 2 * (lane & 3);
+#pragma unroll
+        for (int j = 0; j < EPI_COLS / 8; ++j) {
+          const int c = cq + 8 * j;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int64_t rr = row + 8 * e;
+            if (rr >= d.RP || c >= qcols) continue;
+            float* dst = C + rr * d.ci + g.q0 + c;
+            const float a = r[4 * j + 2 * e], bq = r[4 * j + 2 * e + 1];
+            if (accumulate) {
+              atomicAdd(dst, a);
+              if (c + 1 < qcols) atomicAdd(dst + 1, bq);
+            } else if (vec2 && c + 1 < qcols) {
+              *reinterpret_cast<float2*>(dst) = make_float2(a, bq);
+            } else {
+              dst[0] = a;
+              if (c + 1 < qcols) dst[1] = bq;
+            }
+          }
+        }
+      };
       bool ok = true;
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int b = (int)(gc & 1);
         const bool w = ptx::mbar_wait(ptx::smem_addr(&x.acc_full[b]), (gc >> 1) & 1u, status);
         if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR + col0);
+        if (rows16) {
 #pragma unroll
-        for (int cb = 0; cb < EPI_COLS / 32; ++cb) {
-          if (col0 + cb * 32 < qcols) {  // uniform across the warp
-            uint32_t r[32];
-            ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
-            ptx::tmem_ld_wait();
-            if (SPLIT) {
+          for (int h = 0; h < 2; ++h) {
+            if (col0 < qcols) {  // uniform across the warp
+              uint32_t r[32];
+              ptx::tmem_ld_16x256b_x8(tmem + ((uint32_t)(quad * 32 + h * 16) << 16) + (uint32_t)(b * PR + col0), r);
+              ptx::tmem_ld_wait();
+              if (SPLIT) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) acc[cb * 32 + j] += __uint_as_float(r[j]);
-            } else {
-              float v[32];
+                for (int j = 0; j < 32; ++j) acc[h * 32 + j] += __uint_as_float(r[j]);
+              } else {
+                float v[32];
 #pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-              emit(col0 + cb * 32, v);
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                emit16(h, v);
+              }
+            }
+          }
+        } else {
+          const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR + col0);
+#pragma unroll
+          for (int cb = 0; cb < EPI_COLS / 32; ++cb) {
+            if (col0 + cb * 32 < qcols) {  // uniform across the warp
+              uint32_t r[32];
+              ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
+              ptx::tmem_ld_wait();
+              if (SPLIT) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[cb * 32 + j] += __uint_as_float(r[j]);
+              } else {
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                emit(col0 + cb * 32, v);
+              }
             }
           }
         }
@@ -479,9 +532,15 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       }
       if (!ok) { x.abort = 1; break; }
       if (SPLIT) {
+        if (rows16) {
 #pragma unroll
-        for (int cb = 0; cb < EPI_COLS / 32; ++cb)
-          if (col0 + cb * 32 < qcols) emit(col0 + cb * 32, &acc[cb * 32]);
+          for (int h = 0; h < 2; ++h)
+            if (col0 < qcols) emit16(h, &acc[h * 32]);
+        } else {
+#pragma unroll
+          for (int cb = 0; cb < EPI_COLS / 32; ++cb)
+            if (col0 + cb * 32 < qcols) emit(col0 + cb * 32, &acc[cb * 32]);
+        }
       }
     }
   }
@@ -584,17 +643,17 @@ PackJob make_job(const ContractDesc& d, const float* src, int64_t R, int nr, con
   return j;
 }
 
-// Pack blocks per CTA: about 64 KB of float32 reads (a block reads twice its
-// bf16 bytes).
+// Pack blocks per CTA: about 256 KB of float32 reads (a block reads twice
+// its bf16 bytes); measured best among 64, 128, 256 and 512 KB.
 int32_t blocks_per_unit(const PackJob& j) {
-  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, 65536 / (2 * j.block_bytes)));
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, 262144 / (2 * j.block_bytes)));
 }
 
 size_t job_bytes(const PackJob& j) { return (size_t)j.tiles * j.slabs * j.block_bytes; }
 
 // GEMM descriptor of contraction d over packed A (ja) and B (jb): the side
 // with more rows is P (the MMA's 128 rows). Offsets are left to the caller.
-GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, bool* swapped) {
+GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, int q_tile, bool* swapped) {
   const bool swap = d.N > d.M && d.M < PR;
   GemmDesc g;
   memset(&g, 0, sizeof(g));
@@ -607,8 +666,9 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
   const PackJob& jq = swap ? ja : jb;
   g.P_block = jp.block_bytes;
   g.Q_block = jq.block_bytes;
+  g.q_tile = q_tile == 64 ? 64 : PR;
   g.tiles_p = jp.tiles;
-  g.tiles_q = jq.tiles;
+  g.tiles_q = (int32_t)((g.RQ + g.q_tile - 1) / g.q_tile);
   g.slabs = ja.slabs;
   g.splits = d.splits;
   g.slabs_per_split = (int32_t)(d.k_per_split / PK);
@@ -620,7 +680,7 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
 
 // Host side: pack jobs (two per contraction), their block units, and the GEMM
 // descriptors, with block storage as offsets in the plan's packed region.
-int plan_packed(const ContractDesc& d, int prec, PackedPlan* pp) {
+int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, PackedPlan* pp) {
   const PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
   const PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
   if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
@@ -657,7 +717,8 @@ int plan_packed(const ContractDesc& d, int prec, PackedPlan* pp) {
   }
 
   bool swap = false;
-  GemmDesc g = make_gemm(d, ja, jb, &swap);
+  GemmDesc g = make_gemm(d, ja, jb, sc.q_tile, &swap);
+  g.store16 = sc.store16;
   g.P_off = swap ? off_b : off_a;
   g.Q_off = swap ? off_a : off_b;
   g.P_lo = split ? (int64_t)(swap ? off_blo : off_alo) - (int64_t)g.P_off : 0;
@@ -706,7 +767,7 @@ int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_
   if (na + nb > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
   pp.units_a = (int32_t)na;
   bool swap = false;
-  GemmDesc g = make_gemm(d, ja, jb, &swap);
+  GemmDesc g = make_gemm(d, ja, jb, PR, &swap);
   g.P = swap ? jb.hi : ja.hi;
   g.Q = swap ? ja.hi : jb.hi;
   g.P_lo = split ? (swap ? jb.lo - jb.hi : ja.lo - ja.hi) : 0;

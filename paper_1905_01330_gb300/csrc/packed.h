@@ -49,7 +49,21 @@ struct GemmDesc {
   int64_t P_block, Q_block;
   int64_t tile_begin;     // first global work unit
   uint64_t P_off, Q_off;  // host: offsets of the hi blocks in the packed region
-  int32_t tiles_p, tiles_q, slabs, splits, slabs_per_split, pad;
+  int32_t tiles_p, tiles_q, slabs, splits, slabs_per_split;
+  int32_t q_tile;         // rows of Q per unit (the output tile's width): 128 or 64
+  int32_t store16;        // C row-major along j: drain TMEM as 16-lane x 256-bit blocks
+                          // (whole-sector stores) instead of one row per thread
+  int32_t pad;
+};
+
+// Schedule of the packed GEMM for one class of contractions: the output
+// tile width (rows of Q per unit), whether a spec with many tiles keeps each
+// tile's whole k range in one unit, and the epilogue's TMEM read shape.
+// Picked by tn_group_plan_autotune.
+struct PackedSchedule {
+  int32_t q_tile = 128;
+  int32_t long_k = 1;
+  int32_t store16 = 0;
 };
 
 struct PackedPlan {
@@ -61,8 +75,9 @@ struct PackedPlan {
   size_t packed_bytes = 0;
 };
 
-// Appends contraction d (units already planned by plan_units) to the plan.
-int plan_packed(const ContractDesc& d, int prec, PackedPlan* pp);
+// Appends contraction d (units already planned by plan_units) to the plan
+// under schedule sc (tile width and epilogue shape).
+int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, PackedPlan* pp);
 
 int launch_pack(const PackJob* jobs, const PackUnit* units, int64_t nunits, cudaStream_t s);
 

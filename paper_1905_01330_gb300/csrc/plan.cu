@@ -165,11 +165,12 @@ void plan_units(ContractDesc* d, int64_t min_units) {
 // Units of the packed GEMM: no shared-memory table bounds its k range, so a
 // spec with many output tiles keeps each tile's whole k range in one unit (up
 // to 512 slabs: no zeroing pass, no atomics); a spec with few tiles is still
-// cut into 32-slab ranges so its work spreads over the SMs.
-void plan_units_packed(ContractDesc* d) {
+// cut into 32-slab ranges so its work spreads over the SMs. long_k = false
+// keeps the 32-slab ranges everywhere (a schedule the autotuner may pick).
+void plan_units_packed(ContractDesc* d, bool long_k) {
   plan_units(d, 1);
   const int64_t tiles = (int64_t)d->tiles_m * d->tiles_n;
-  if (tiles < 16) return;
+  if (!long_k || tiles < 16) return;
   const int64_t slabs = (d->K + 63) / 64;
   const int64_t per = slabs < 512 ? slabs : 512;
   d->splits = (int32_t)((slabs + per - 1) / per);

@@ -64,7 +64,7 @@ constexpr int MAX_SLABS_PER_UNIT = 32;
 // many work units when K is long enough to split (keeping >= 4 slabs per unit).
 void plan_units(ContractDesc* d, int64_t min_units);
 // The same for the packed GEMM (longer k ranges when a spec has many tiles).
-void plan_units_packed(ContractDesc* d);
+void plan_units_packed(ContractDesc* d, bool long_k);
 
 // Zeroes the results of split specs: list of (pointer, element count).
 struct ZeroRange {

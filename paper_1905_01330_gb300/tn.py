@@ -76,6 +76,8 @@ def _signatures():
     return {
         "tn_tensor_init": (i32, [tp, vp, i32, ctypes.POINTER(i64)]),
         "tn_contract": (i32, [tp, ip, tp, ip, i32, tp, i32, vp]),
+        "tn_contract_workspace_bytes": (ctypes.c_size_t, [tp, ip, tp, ip, i32, tp, i32]),
+        "tn_contract_ws": (i32, [tp, ip, tp, ip, i32, tp, i32, vp, ctypes.c_size_t, vp]),
         "tn_group_plan_create": (i32, [ctypes.POINTER(TnContractSpec), i32, i32, ctypes.POINTER(vp)]),
         "tn_group_plan_workspace_bytes": (ctypes.c_size_t, [vp]),
         "tn_group_plan_upload": (i32, [vp, vp, ctypes.c_size_t, vp]),
@@ -86,6 +88,9 @@ def _signatures():
         "tn_group_plan_launches": (i32, [vp]),
         "tn_group_plan_run_launch": (i32, [vp, vp, ctypes.c_size_t, i32, vp]),
         "tn_group_plan_launch_name": (ctypes.c_char_p, [vp, i32]),
+        "tn_group_plan_autotune": (i32, [vp, vp, ctypes.c_size_t, vp]),
+        "tn_group_plan_schedule": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "tn_group_plan_set_schedule": (i32, [vp, i32, i32, i32, i32]),
         "tn_mps_inner_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
         "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
@@ -160,8 +165,10 @@ def result_shape(A: torch.Tensor, legsA, B: torch.Tensor, legsB):
 
 
 def contract(A: torch.Tensor, legsA, B: torch.Tensor, legsB, prec: str = "bf16",
-             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """tensordot of A and B over legsA[j] <-> legsB[j] (tn_contract)."""
+             out: torch.Tensor | None = None, stream=None, packed: bool = True) -> torch.Tensor:
+    """tensordot of A and B over legsA[j] <-> legsB[j]. BF16 / BF16X3 run as
+    pack + tcgen05 GEMM on a scratch workspace (tn_contract_ws); packed=False
+    (or FP32) runs tn_contract's single-pass kernels."""
     lib = load()
     legsA, legsB = list(legsA), list(legsB)
     if len(legsA) != len(legsB):
@@ -173,6 +180,15 @@ def contract(A: torch.Tensor, legsA, B: torch.Tensor, legsB, prec: str = "bf16",
     k = len(legsA)
     la = (ctypes.c_int * max(k, 1))(*legsA)
     lb = (ctypes.c_int * max(k, 1))(*legsB)
+    if packed and prec != "fp32":
+        nbytes = lib.tn_contract_workspace_bytes(ctypes.byref(da), la, ctypes.byref(db), lb, k, ctypes.byref(dc),
+                                                 PREC[prec])
+        ws = _workspace(nbytes, A.device) if nbytes > 0 else None
+        _check(lib.tn_contract_ws(ctypes.byref(da), la, ctypes.byref(db), lb, k, ctypes.byref(dc), PREC[prec],
+                                  ctypes.c_void_p(ws.data_ptr() if ws is not None else None),
+                                  ws.numel() if ws is not None else 0, _stream(stream)), "tn_contract_ws")
+        out._tn_keep = ws
+        return out
     _check(lib.tn_contract(ctypes.byref(da), la, ctypes.byref(db), lb, k, ctypes.byref(dc),
                            PREC[prec], _stream(stream)), "tn_contract")
     return out
@@ -280,6 +296,37 @@ class GroupPlan:
     def run(self, stream=None):
         _check(load().tn_group_plan_run(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
                                         _stream(stream)), "tn_group_plan_run")
+
+    def autotune(self, stream=None):
+        """Times the candidate GEMM schedules on the device and keeps the
+        fastest (tn_group_plan_autotune); returns self.schedule()."""
+        _check(load().tn_group_plan_autotune(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                             _stream(stream)), "tn_group_plan_autotune")
+        self.launches = load().tn_group_plan_launches(self._h)
+        return self.schedule()
+
+    SCHEDULE_CLASSES = ("thin", "short_k", "long_k")
+
+    def set_schedule(self, cls: str, tile_width: int, long_k: bool, store16: bool, stream=None):
+        """Sets the GEMM schedule of one class by hand and uploads the plan again."""
+        lib = load()
+        _check(lib.tn_group_plan_set_schedule(self._h, self.SCHEDULE_CLASSES.index(cls), tile_width,
+                                              1 if long_k else 0, 1 if store16 else 0),
+               "tn_group_plan_set_schedule")
+        _check(lib.tn_group_plan_upload(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                        _stream(stream)), "tn_group_plan_upload")
+        self.launches = lib.tn_group_plan_launches(self._h)
+
+    def schedule(self):
+        """{class: (tile_width, long_k, store16)} for the classes thin, short_k, long_k."""
+        lib = load()
+        out = {}
+        for c, name in enumerate(self.SCHEDULE_CLASSES):
+            w, lk, s16 = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+            _check(lib.tn_group_plan_schedule(self._h, c, ctypes.byref(w), ctypes.byref(lk), ctypes.byref(s16)),
+                   "tn_group_plan_schedule")
+            out[name] = (w.value, lk.value, s16.value)
+        return out
 
     def launch_names(self):
         lib = load()

@@ -81,6 +81,21 @@ def test_random_specs_parity(tn, prec, seed):
     check(C, A, la, B, lb, prec)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("seed", range(4))
+def test_random_specs_single_pass_kernel(tn, prec, seed):
+    # tn_contract without scratch: the single-pass kernel that gathers and
+    # converts operand tiles inside the GEMM CTA
+    st = synth.Stream(1500 + seed)
+    sha, la, shb, lb = synth.contraction_spec(st, dims=(3, 8, 13, 24, 48), cap=1 << 17)
+    A = rand(2500 + seed, sha)
+    B = rand(3500 + seed, shb)
+    C = tn.contract(torch.from_numpy(A).cuda(), la, torch.from_numpy(B).cuda(), lb, prec=prec, packed=False)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == 0
+    check(C, A, la, B, lb, prec)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
 def test_multi_tile_matmul_with_ragged_tail(tn, prec):
     A = rand(11, (300, 200))

@@ -90,3 +90,58 @@ def test_packed_random_specs(tn, prec, seed):
         sha, la, shb, lb = synth.contraction_spec(st, dims=(3, 8, 13, 24, 48, 64), cap=1 << 17)
         cases.append((rand(7000 + 100 * seed + 2 * i, sha), la, rand(7001 + 100 * seed + 2 * i, shb), lb))
     run_group(tn, cases, prec, seed)
+
+
+def mixed_cases():
+    return [
+        (rand(31, (4096,)), [0], rand(32, (4096, 200)), [0]),      # thin
+        (rand(33, (300, 5000)), [1], rand(34, (20, 5000)), [1]),   # thin, split k
+        (rand(35, (100, 72)), [1], rand(36, (72, 300)), [0]),      # thin, swapped
+        (rand(37, (640, 4608)), [1], rand(38, (4608, 520)), [0]),  # 20 tiles, 72 slabs
+        (rand(39, (256, 96)), [1], rand(40, (96, 384)), [0]),      # short k
+        (rand(43, (130, 2, 64)), [1, 2], rand(44, (2, 64, 264)), [0, 1]),  # short k, ragged columns
+        (rand(41, (8, 9, 10)), [1], rand(42, (9, 11)), [0]),       # ragged
+    ]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_every_schedule_keeps_parity(tn, prec):
+    cases = mixed_cases()
+    specs = []
+    for A, la, B, lb in cases:
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        specs.append((At, la, Bt, lb, torch.empty(tn.result_shape(At, la, Bt, lb), device="cuda")))
+    plan = tn.GroupPlan(specs, prec=prec)
+    for width, long_k, store16 in ((128, 1, 0), (64, 1, 1), (128, 0, 1), (64, 0, 0)):
+        for cls in plan.SCHEDULE_CLASSES:
+            plan.set_schedule(cls, width, long_k, store16)
+        assert plan.schedule() == {c: (width, long_k, store16) for c in plan.SCHEDULE_CLASSES}
+        for sp in specs:
+            sp[4].fill_(float("nan"))
+        plan.run()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == 0
+        for (A, la, B, lb), sp in zip(cases, specs):
+            check(sp[4], A, la, B, lb, prec)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_autotune_picks_a_schedule_and_caches_it(tn, prec):
+    cases = mixed_cases()
+    specs = []
+    for A, la, B, lb in cases:
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        specs.append((At, la, Bt, lb, torch.empty(tn.result_shape(At, la, Bt, lb), device="cuda")))
+    plan = tn.GroupPlan(specs, prec=prec)
+    sched = plan.autotune()
+    assert tn.sync_status() == 0
+    assert all(w in (64, 128) and lk in (0, 1) and s16 in (0, 1) for w, lk, s16 in sched.values())
+    for sp in specs:
+        sp[4].fill_(float("nan"))
+    plan.run()
+    torch.cuda.synchronize()
+    for (A, la, B, lb), sp in zip(cases, specs):
+        check(sp[4], A, la, B, lb, prec)
+    # a new plan over the same shapes starts from the cached choice
+    again = tn.GroupPlan(specs, prec=prec)
+    assert again.schedule() == sched
