@@ -110,10 +110,8 @@ class ClockSampler:
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1905_01330_gb300 import dist as tndist
+    return tndist.env()
 
 
 def cpu_oracle_sample(specs_h, count):
@@ -420,27 +418,26 @@ def main():
         return run_reference(args)
 
     import torch
-    import torch.distributed as dist
 
     from paper_1905_01330_gb300 import build, synth, tn
 
+    from paper_1905_01330_gb300 import dist as tndist
     rank, world, local = dist_env()
     if world > 1:
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        tndist.init("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     build.build()
     tn.load()
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        tndist.barrier()
 
     # ---- inputs: spec shapes from SplitMix64, entries from a seeded device generator
     specs_h = synth.contraction_specs(N_SPECS, seed=SEED)[:args.specs]
     gen = torch.Generator(device=dev)
-    gen.manual_seed(SEED * 1000 + rank)
+    gen.manual_seed(tndist.data_seed(SEED, rank))
     specs = []
     for sa, la, sb, lb in specs_h:
         At = torch.randn(sa, device=dev, generator=gen)
@@ -498,13 +495,9 @@ def main():
     status = tn.sync_status()
     if status != 0:
         raise RuntimeError("kernel status %d during the timed region" % status)
-    ms_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = tndist.max_over_ranks(total_ms, dev)
     ms_per_step = ms_max / args.steps
-    value = world * flops / (ms_per_step * 1e-3) / 1e12
+    value = tndist.weak_scaling_value(flops, ms_per_step, world) / 1e12
     launch_ms = float(np.mean(per))
 
     # ---- same workload with the other two arithmetic paths (not the headline)
@@ -535,11 +528,8 @@ def main():
         s1.record(stream)
         torch.cuda.synchronize(dev)
         e_ms = s0.elapsed_time(s1) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+        e_ms = tndist.max_over_ranks(e_ms, dev)
+        e2e = {"value": tndist.weak_scaling_value(flops, e_ms, world) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         del host_in, host_out
 
@@ -589,8 +579,7 @@ def main():
                 "cpu_baseline": cpu, "variants": variants, "schedules": schedules,
                 "tensor_peak_frac": value / world / bf16_peak, "extras": extras}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    tndist.finish()
     return 0
 
 
