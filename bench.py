@@ -175,11 +175,12 @@ def _time_graph(fn, calls, replays, stream):
 
 
 def kernel_traffic(kernel, nbytes):
-    """DRAM bytes per launch of `kernel` ("pack" or "gemm"), from the committed
-    ncu capture, when that capture was taken of the kernel source as it is now
-    (same SHA-256); else None. The capture ran a smaller case; its measured
-    traffic over its algorithmic bytes scales to this launch's algorithmic
-    bytes (both kernels move bytes in proportion to the operands)."""
+    """DRAM bytes per launch of `kernel` (a launch name of the plan: "pack",
+    "gemm", "gemm_fused"), from the committed ncu capture, when that capture
+    was taken of the kernel source as it is now (same SHA-256); else None. The
+    capture ran a smaller case; its measured traffic over its algorithmic
+    bytes scales to this launch's algorithmic bytes (the kernels move bytes in
+    proportion to the operands and results)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "packed_traffic.json")
     src = os.path.join(ROOT, "paper_1905_01330_gb300", "csrc", "packed.cu")
@@ -533,12 +534,11 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         del host_in, host_out
 
-    # ---- roofline of each launch of the step, timed one at a time
+    # ---- roofline of each launch of the step, timed one at a time; the
+    # algorithmic bytes of each launch come from the plan (each operand
+    # element read once, each result written once)
     hbm_peak, bf16_peak, peak_src = measured_peaks()
-    n_ops = sum(A.numel() + B.numel() for A, _, B, _, _ in specs)   # operand elements
-    n_out = sum(C.numel() for *_, C in specs)                        # result elements
-    algo = {"pack": 4.0 * n_ops + 2.0 * n_ops,     # read float32 operands, write bf16
-            "gemm": 2.0 * n_ops + 4.0 * n_out}     # read bf16 operands, write float32 results
+    algo = {n: b for n, b in zip(plan.launch_names(), plan.launch_bytes()) if n != "zero"}
     lt = timed_launches(plan, max(2, args.steps // 2))
     launches = {}
     for name, ms in lt.items():

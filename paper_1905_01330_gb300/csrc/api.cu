@@ -61,11 +61,19 @@ struct tn_group_plan {
   std::vector<int32_t> unit_desc;      // descriptor (or GEMM) index of every work unit
   tn::PackedPlan pp;                   // packed path (BF16 / BF16X3)
   tn::PackedSchedule sched[3];         // packed schedules: thin (min(M, N) < 128), short k (<= 512), long k
-  size_t reserve_zero = 0, reserve_units = 0;  // list sizes of the largest schedule (workspace layout)
+  // list sizes and packed bytes of the largest layout (workspace offsets):
+  // the schedule with the longest lists, nothing fused
+  size_t reserve_zero = 0, reserve_units = 0, reserve_punits = 0, reserve_packed = 0;
   uint64_t signature = 0;              // shapes of the specs (tuning cache key)
   bool packed = false;
   int prec = TN_PREC_FP32;
   int64_t total_tiles = 0;
+  int64_t packed_tiles = 0;            // units of the GEMM on packed P; the fused GEMM's follow them
+  // offset tables of the P operand of every contraction that may take the
+  // fused GEMM (BF16, narrower side at most 128 rows): element offsets of
+  // its row and shared-index runs in `ctab`, -1 for the others
+  std::vector<int32_t> ctab;
+  std::vector<int64_t> ctab_r, ctab_k;
   double flops = 0.0, bytes = 0.0;
 };
 
@@ -206,15 +214,18 @@ tn::PackedSchedule default_schedule(int cls) {
 }
 
 // (Re)builds a packed plan's GEMM list, zero ranges and unit map from its
-// contractions under its schedules.
-int build_packed(tn_group_plan* p) {
+// contractions under its schedules. The GEMMs on packed P come first, the
+// fused ones (P rounded inside the GEMM) after them; each launch numbers its
+// units from 0.
+int build_packed(tn_group_plan* p, bool allow_fuse = true) {
   p->pp = tn::PackedPlan();
   p->zero_ranges.clear();
-  for (const auto& d0 : p->descs) {
-    ContractDesc d = d0;
+  for (size_t i = 0; i < p->descs.size(); ++i) {
+    ContractDesc d = p->descs[i];
     const tn::PackedSchedule& sc = p->sched[spec_class(d)];
     plan_units_packed(&d, sc.long_k != 0);
-    const int rc = plan_packed(d, p->prec, sc, &p->pp);
+    const int64_t rt = p->ctab_r.empty() ? -1 : p->ctab_r[i], kt = p->ctab_k.empty() ? -1 : p->ctab_k[i];
+    const int rc = plan_packed(d, p->prec, sc, allow_fuse, rt, kt, &p->pp);
     if (rc != TN_OK) return rc;
   }
   // largest units first: tensor time plus memory time of one unit
@@ -223,21 +234,27 @@ int build_packed(tn_group_plan* p) {
     const double k = 64.0 * std::min<int64_t>(g.slabs, g.slabs_per_split);
     return 2.0 * pr * qr * k / 1500.0 + (2.0 * (pr + qr) * k + 4.0 * pr * qr) / 5.0;
   };
-  std::stable_sort(p->pp.gemms.begin(), p->pp.gemms.end(),
-                   [&](const GemmDesc& a, const GemmDesc& b) { return cost(a) > cost(b); });
-  int64_t t = 0;
+  std::stable_sort(p->pp.gemms.begin(), p->pp.gemms.end(), [&](const GemmDesc& a, const GemmDesc& b) {
+    if ((a.pjob >= 0) != (b.pjob >= 0)) return a.pjob < 0;
+    return cost(a) > cost(b);
+  });
+  int64_t t = 0, base = 0;
+  p->packed_tiles = -1;
   for (auto& g : p->pp.gemms) {
-    g.tile_begin = t;
+    if (g.pjob >= 0 && p->packed_tiles < 0) p->packed_tiles = base = t;
+    g.tile_begin = t - base;
     t += (int64_t)g.tiles_p * g.tiles_q * g.splits;
     if (g.splits > 1) p->zero_ranges.push_back(ZeroRange{g.C, g.RP * g.RQ});
   }
+  if (p->packed_tiles < 0) p->packed_tiles = t;
   p->total_tiles = t;
   if (t > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
   p->unit_desc.assign((size_t)t, 0);
   for (size_t i = 0; i < p->pp.gemms.size(); ++i) {
     const GemmDesc& g = p->pp.gemms[i];
     const int64_t n = (int64_t)g.tiles_p * g.tiles_q * g.splits;
-    std::fill(p->unit_desc.begin() + g.tile_begin, p->unit_desc.begin() + g.tile_begin + n, (int32_t)i);
+    const int64_t b = g.tile_begin + (g.pjob >= 0 ? p->packed_tiles : 0);
+    std::fill(p->unit_desc.begin() + b, p->unit_desc.begin() + b + n, (int32_t)i);
   }
   return TN_OK;
 }
@@ -293,13 +310,22 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
   if (prec != TN_PREC_FP32 && allow_packed) {
     p->packed = true;
     p->signature = plan_signature(p);
+    if (prec == TN_PREC_BF16) {
+      p->ctab_r.assign(p->descs.size(), -1);
+      p->ctab_k.assign(p->descs.size(), -1);
+      for (size_t i = 0; i < p->descs.size(); ++i)
+        if (std::min(p->descs[i].M, p->descs[i].N) <= 128)
+          tn::fused_tables(p->descs[i], &p->ctab, &p->ctab_r[i], &p->ctab_k[i]);
+    }
     // the workspace is laid out for the schedule with the longest lists
     // (64-wide tiles, 32-slab k ranges), so any schedule fits it
     for (auto& sc : p->sched) sc = tn::PackedSchedule{64, 0, 0};
-    int rc = build_packed(p);
+    int rc = build_packed(p, false);
     if (rc != TN_OK) { delete p; return rc; }
     p->reserve_zero = p->zero_ranges.size();
     p->reserve_units = p->unit_desc.size();
+    p->reserve_punits = p->pp.units.size();
+    p->reserve_packed = p->pp.packed_bytes;
     for (int c = 0; c < 3; ++c) p->sched[c] = default_schedule(c);
     {
       std::lock_guard<std::mutex> lk(g_tune_lock);
@@ -357,21 +383,22 @@ static size_t jobs_offset(const tn_group_plan* plan) {
 static size_t punits_offset(const tn_group_plan* plan) {
   return jobs_offset(plan) + align256(sizeof(PackJob) * plan->pp.jobs.size());
 }
+static size_t tables_offset(const tn_group_plan* plan) {
+  return punits_offset(plan) + align256(sizeof(PackUnit) * plan->reserve_punits);
+}
 static size_t packed_offset(const tn_group_plan* plan) {
-  return punits_offset(plan) + align256(sizeof(PackUnit) * plan->pp.units.size());
+  return tables_offset(plan) + align256(sizeof(int32_t) * plan->ctab.size());
 }
 
 size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
   if (!plan) return 0;
-  if (plan->packed) return packed_offset(plan) + plan->pp.packed_bytes;
+  if (plan->packed) return packed_offset(plan) + plan->reserve_packed;
   return map_offset(plan) + sizeof(int32_t) * plan->unit_desc.size();
 }
 
 double tn_group_plan_flops(const tn_group_plan* plan) { return plan ? plan->flops : 0.0; }
-int tn_group_plan_launches(const tn_group_plan* plan) {
-  if (!plan || plan->total_tiles == 0) return 0;
-  return (plan->packed ? 2 : 1) + (plan->zero_ranges.empty() ? 0 : 1);
-}
+static int launch_count(const tn_group_plan* plan);
+int tn_group_plan_launches(const tn_group_plan* plan) { return plan ? launch_count(plan) : 0; }
 double tn_group_plan_bytes(const tn_group_plan* plan) { return plan ? plan->bytes : 0.0; }
 
 // Bytes of the work lists alone (without the packed blocks).
@@ -396,7 +423,8 @@ static int check_ws(const tn_group_plan* plan, void* ws, size_t bytes) {
 
 // Upload with the packed blocks at `packed` (inside the workspace, or a
 // separate region shared by plans that run one after another).
-static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* packed, cudaStream_t s) {
+static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* packed, cudaStream_t s,
+                       bool with_tables = true) {
   // pageable sources: each call returns once the bytes are staged, so the
   // plan may be destroyed right after it
   uint8_t* base = static_cast<uint8_t*>(workspace);
@@ -408,10 +436,17 @@ static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* pack
       e.Q = packed + e.Q_off;
     }
     std::vector<PackJob> j = plan->pp.jobs;
+    const int32_t* tabs = reinterpret_cast<const int32_t*>(base + tables_offset(plan));
     for (size_t i = 0; i < j.size(); ++i) {
-      j[i].hi = packed + plan->pp.job_hi_off[i];
+      j[i].hi = plan->pp.job_hi_off[i] == SIZE_MAX ? nullptr : packed + plan->pp.job_hi_off[i];
       j[i].lo = plan->pp.job_lo_off[i] == SIZE_MAX ? nullptr : packed + plan->pp.job_lo_off[i];
+      j[i].rtab = j[i].rtab_off >= 0 ? tabs + j[i].rtab_off : nullptr;
+      j[i].ktab = j[i].ktab_off >= 0 ? tabs + j[i].ktab_off : nullptr;
     }
+    if (with_tables && !plan->ctab.empty() &&
+        cudaMemcpyAsync(base + tables_offset(plan), plan->ctab.data(), sizeof(int32_t) * plan->ctab.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return TN_ERR_CUDA;
     if ((!g.empty() && cudaMemcpyAsync(base, g.data(), sizeof(GemmDesc) * g.size(), cudaMemcpyHostToDevice, s) !=
                            cudaSuccess) ||
         (!j.empty() && cudaMemcpyAsync(base + jobs_offset(plan), j.data(), sizeof(PackJob) * j.size(),
@@ -438,7 +473,7 @@ static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* pack
 
 size_t tn::group_plan_list_bytes(const tn_group_plan* plan) { return plan ? list_bytes(plan) : 0; }
 size_t tn::group_plan_packed_bytes(const tn_group_plan* plan) {
-  return plan && plan->packed ? plan->pp.packed_bytes : 0;
+  return plan && plan->packed ? plan->reserve_packed : 0;
 }
 
 int tn::group_plan_upload_shared(const tn_group_plan* plan, void* lists, size_t bytes, void* packed,
@@ -483,16 +518,29 @@ int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, 
 
 }  // extern "C"
 
-// The launch sequence of a run: [zeroing of split results] [pack] contract.
-enum LaunchKind { L_ZERO, L_PACK, L_CONTRACT };
+// The launch sequence of a run: [zeroing of split results] [pack] then the
+// contraction kernel (single-pass), or the GEMM on packed P and / or the
+// fused GEMM.
+enum LaunchKind { L_ZERO, L_PACK, L_CONTRACT, L_FUSED };
+constexpr int MAX_LAUNCHES = 4;
 
 static int launch_list(const tn_group_plan* plan, LaunchKind* kinds) {
   int n = 0;
   if (plan->total_tiles == 0) return 0;
   if (!plan->zero_ranges.empty()) kinds[n++] = L_ZERO;
-  if (plan->packed) kinds[n++] = L_PACK;
+  if (plan->packed) {
+    if (!plan->pp.units.empty()) kinds[n++] = L_PACK;
+    if (plan->packed_tiles > 0) kinds[n++] = L_CONTRACT;
+    if (plan->total_tiles > plan->packed_tiles) kinds[n++] = L_FUSED;
+    return n;
+  }
   kinds[n++] = L_CONTRACT;
   return n;
+}
+
+static int launch_count(const tn_group_plan* plan) {
+  LaunchKind kinds[MAX_LAUNCHES];
+  return launch_list(plan, kinds);
 }
 
 static int run_one(const tn_group_plan* plan, void* workspace, LaunchKind k, cudaStream_t s) {
@@ -506,11 +554,15 @@ static int run_one(const tn_group_plan* plan, void* workspace, LaunchKind k, cud
       return launch_pack(reinterpret_cast<const PackJob*>(base + jobs_offset(plan)),
                          reinterpret_cast<const PackUnit*>(base + punits_offset(plan)),
                          (int64_t)plan->pp.units.size(), s);
+    case L_FUSED:
+      return launch_fused_gemm(reinterpret_cast<const GemmDesc*>(base), map + plan->packed_tiles,
+                               reinterpret_cast<const PackJob*>(base + jobs_offset(plan)),
+                               plan->total_tiles - plan->packed_tiles, s);
     default:
       break;
   }
   if (plan->packed)
-    return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->total_tiles, plan->prec, s);
+    return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->packed_tiles, plan->prec, s);
   const ContractDesc* g = reinterpret_cast<const ContractDesc*>(base);
   if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, map, plan->total_tiles, s);
   return launch_contract_tc(plan->descs[0], g, map, plan->total_tiles, plan->prec, s);
@@ -519,7 +571,7 @@ static int run_one(const tn_group_plan* plan, void* workspace, LaunchKind k, cud
 static int run_impl(const tn_group_plan* plan, void* workspace, cudaStream_t s) {
   for (const auto& z : plan->zeros)
     if (cudaMemsetAsync(z.C, 0, sizeof(float) * (size_t)(z.M * z.N), s) != cudaSuccess) return TN_ERR_CUDA;
-  LaunchKind kinds[3];
+  LaunchKind kinds[MAX_LAUNCHES];
   const int n = launch_list(plan, kinds);
   for (int i = 0; i < n; ++i) {
     const int rc = run_one(plan, workspace, kinds[i], s);
@@ -534,7 +586,7 @@ int tn_group_plan_run_launch(const tn_group_plan* plan, void* workspace, size_t 
   if (!plan) return TN_ERR_ARG;
   int rc = check_ws(plan, workspace, bytes);
   if (rc != TN_OK) return rc;
-  LaunchKind kinds[3];
+  LaunchKind kinds[MAX_LAUNCHES];
   const int n = launch_list(plan, kinds);
   if (index < 0 || index >= n) return TN_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -546,14 +598,51 @@ int tn_group_plan_run_launch(const tn_group_plan* plan, void* workspace, size_t 
 
 const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index) {
   if (!plan) return nullptr;
-  LaunchKind kinds[3];
+  LaunchKind kinds[MAX_LAUNCHES];
   const int n = launch_list(plan, kinds);
   if (index < 0 || index >= n) return nullptr;
   switch (kinds[index]) {
     case L_ZERO: return "zero";
     case L_PACK: return "pack";
+    case L_FUSED: return "gemm_fused";
     default: return plan->packed ? "gemm" : "contract";
   }
+}
+
+double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index) {
+  if (!plan) return -1.0;
+  LaunchKind kinds[MAX_LAUNCHES];
+  const int n = launch_list(plan, kinds);
+  if (index < 0 || index >= n) return -1.0;
+  double b = 0.0;
+  switch (kinds[index]) {
+    case L_ZERO:
+      for (const auto& z : plan->zero_ranges) b += 4.0 * (double)z.count;
+      return b;
+    case L_PACK: {
+      const double out = plan->prec == TN_PREC_BF16X3 ? 4.0 : 2.0;  // hi (+ lo) per element
+      for (size_t i = 0; i < plan->pp.jobs.size(); ++i)
+        if (plan->pp.job_hi_off[i] != SIZE_MAX)
+          b += (4.0 + out) * (double)plan->pp.jobs[i].R * (double)plan->pp.jobs[i].K;
+      return b;
+    }
+    case L_FUSED:
+    case L_CONTRACT:
+      break;
+  }
+  if (!plan->packed) {
+    for (const auto& d : plan->descs)
+      b += 4.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
+    return b;
+  }
+  const bool fused = kinds[index] == L_FUSED;
+  const double pe = plan->prec == TN_PREC_BF16X3 ? 4.0 : 2.0;  // packed bytes per element
+  for (const auto& g : plan->pp.gemms) {
+    if ((g.pjob >= 0) != fused) continue;
+    const double K = (double)g.K;
+    b += (fused ? 4.0 : pe) * (double)g.RP * K + pe * (double)g.RQ * K + 4.0 * (double)g.RP * (double)g.RQ;
+  }
+  return b;
 }
 
 }  // extern "C"
@@ -573,9 +662,17 @@ int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, v
     return TN_ERR_CUDA;
   }
   // one candidate: rebuild, upload, one warm run, the mean of two timed runs
+  // the offset tables do not depend on the schedule: uploaded once
+  if (!plan->ctab.empty() &&
+      cudaMemcpyAsync(base + tables_offset(plan), plan->ctab.data(), sizeof(int32_t) * plan->ctab.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return TN_ERR_CUDA;
+  }
   auto trial = [&](float* ms) -> int {
     int r = build_packed(plan);
-    if (r == TN_OK) r = upload_impl(plan, workspace, base + packed_offset(plan), s);
+    if (r == TN_OK) r = upload_impl(plan, workspace, base + packed_offset(plan), s, false);
     if (r == TN_OK) r = run_impl(plan, workspace, s);
     if (r == TN_OK && cudaEventRecord(e0, s) != cudaSuccess) r = TN_ERR_CUDA;
     for (int k = 0; k < 2 && r == TN_OK; ++k) r = run_impl(plan, workspace, s);
@@ -613,7 +710,7 @@ int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, v
   cudaEventDestroy(e1);
   if (rc != TN_OK) return rc;
   rc = build_packed(plan);
-  if (rc == TN_OK) rc = upload_impl(plan, workspace, base + packed_offset(plan), s);
+  if (rc == TN_OK) rc = upload_impl(plan, workspace, base + packed_offset(plan), s, false);
   if (rc != TN_OK) return rc;
   std::lock_guard<std::mutex> lk(g_tune_lock);
   TunedSchedules& t = g_tune_cache[plan->signature];

@@ -217,22 +217,49 @@ pack_pair_kernel(const __grid_constant__ PackPair pp) {
 }
 
 // ------------------------------------------------------------------- gemm
-// warp 0 copies, warp 1 issues the MMAs, warps 2-9 drain TMEM: two per lane
-// quadrant, each taking 64 of the tile's 128 columns
-constexpr int EPI_WARPS = 8;
-constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
-constexpr int EPI_COLS = PR * 4 / EPI_WARPS;  // columns drained per epilogue warp
+// warp 0 copies, warp 1 issues the MMAs, then (fused GEMM only) eight
+// converter warps, then the epilogue warps that drain TMEM: eight (two per
+// lane quadrant, 64 of the tile's 128 columns each), or four in the fused
+// GEMM (one per quadrant, all 128 columns: its tiles are narrow, and 14 warps
+// leave each sub-partition's register file 128 registers per thread)
 // BF16X3 promotes the TMEM accumulator into float32 registers every KC slabs
 // (256 shared indices): the tensor core's float32 accumulation truncates, and
 // over long k that error would exceed the split's own rounding error.
 constexpr int KC = 4;
 
-template <int SPLIT>
+// Fused GEMM: eight converter warps copy each 128-row x 64-k float32 slab of
+// P through its leg strides into a ring of XSLOTS staging slots (cp.async,
+// XSLOTS - 1 slabs ahead of the one they round), then round it to bf16 into
+// the stage the MMA reads. Each warp owns a fixed part of every slab -- its
+// own rows, or its own 8 shared indices -- and runs ahead or behind the other
+// warps at will: no barrier wider than a warp. Source offsets come from the
+// job's precomputed row and shared-index tables, loaded into registers one
+// slab before they are used, so no composite index is divided on the device.
+// Staging layouts: "K" = rows of 64 floats (256 B), a warp owning 16 rows,
+// for sources contiguous along k (16-byte copies of 4 k, a warp's lanes on
+// two 256-byte row runs) and for the 4-byte fallback (lanes on 32 consecutive
+// k); "R" = 64 k-rows of 128 floats (512 B), a warp owning 8 of them, for
+// sources contiguous along the rows (16-byte copies of 4 rows, lanes on one
+// 512-byte run). Rounding reads and writes shared memory without bank
+// conflicts in both.
+constexpr int CONV_WARPS = 8;
+constexpr int XSLOTS = 4;
+constexpr int XDIST = XSLOTS - 1;          // slabs copied ahead of the rounding
+constexpr int XSLOT_BYTES = PR * PK * 4;   // 32 KB
+
+template <int SPLIT, int FUSE>
 struct GCfg {
   static constexpr int OPS = SPLIT ? 4 : 2;            // P hi, Q hi (, P lo, Q lo)
-  static constexpr int STAGES = SPLIT ? 3 : 6;
-  static constexpr int STAGE_BYTES = OPS * PBLOCK;
+  static constexpr int STAGES = FUSE ? 3 : (SPLIT ? 3 : 6);
+  // fused: P 16 KB + Q at most 64 rows (8 KB)
+  static constexpr int STAGE_BYTES = FUSE ? PBLOCK + PBLOCK / 2 : OPS * PBLOCK;
   static constexpr uint32_t TMEM_COLS = 256;           // two 128-column accumulators
+  static constexpr int CONV = FUSE ? CONV_WARPS : 0;
+  static constexpr int EPI0 = 2 + CONV;                // first epilogue warp
+  static constexpr int EPI = FUSE ? 4 : 8;             // epilogue warps
+  static constexpr int ECOLS = PR * 4 / EPI;           // accumulator columns per epilogue warp
+  static constexpr int THREADS = 32 * (2 + CONV + EPI);
+  static_assert(!(SPLIT && FUSE), "the fused GEMM is BF16 only");
 };
 
 template <int S>
@@ -246,9 +273,17 @@ struct GemmAux {
   volatile int32_t abort;
 };
 
-template <int SPLIT>
+// Offsets of the 4-byte fallback copies (each converter warp its own).
+struct ConvTables {
+  int32_t roff[CONV_WARPS][16];  // the warp's 16 rows of the unit
+  int32_t koff[CONV_WARPS][PK];  // the slab's 64 shared indices
+};
+
+template <int SPLIT, int FUSE>
 constexpr size_t gemm_smem_bytes() {
-  return 1024 + (size_t)GCfg<SPLIT>::STAGES * GCfg<SPLIT>::STAGE_BYTES + sizeof(GemmAux<GCfg<SPLIT>::STAGES>);
+  using C = GCfg<SPLIT, FUSE>;
+  return 1024 + (size_t)C::STAGES * C::STAGE_BYTES +
+         (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables) : 0) + sizeof(GemmAux<C::STAGES>);
 }
 
 struct GUnit {
@@ -281,26 +316,199 @@ __device__ __forceinline__ GemmDesc load_desc(const GemmDesc& single, const Gemm
   return descs ? descs[__ldg(map + u)] : single;
 }
 
-template <int SPLIT>
-__global__ void __launch_bounds__(GEMM_THREADS, 1)
+// Walks this CTA's (unit, slab) pairs in the order the copy warp and the MMA
+// issuer consume them: the slab's first row and shared index, its valid rows
+// and shared indices, the source job, its copy mode (PackJob::vec4), and
+// whether it is the first slab of its unit.
+struct ConvIter {
+  int64_t u, total, p0, R, K;
+  const float* src;
+  const int32_t* rtab;
+  const int32_t* ktab;
+  int32_t ks, nks, ks0, mode;
+
+  __device__ __forceinline__ void load(const GemmDesc* descs, const int32_t* map, const PackJob* jobs) {
+    if (u >= total) return;
+    const GemmDesc& d = descs[__ldg(map + u)];
+    const GUnit g = gunit(d, u - d.tile_begin);
+    p0 = g.p0;
+    ks0 = g.ks0;
+    nks = g.nks;
+    ks = 0;
+    const PackJob& J = jobs[d.pjob];
+    src = J.src;
+    rtab = J.rtab;
+    ktab = J.ktab;
+    R = J.R;
+    K = J.K;
+    mode = J.vec4;
+  }
+  __device__ __forceinline__ void next(const GemmDesc* descs, const int32_t* map, const PackJob* jobs) {
+    if (++ks == nks) {
+      u += gridDim.x;
+      load(descs, map, jobs);
+    }
+  }
+  __device__ __forceinline__ bool valid() const { return u < total; }
+  __device__ __forceinline__ int64_t k0() const { return (int64_t)(ks0 + ks) * PK; }
+  __device__ __forceinline__ int rv() const { return (int)(R - p0 < PR ? R - p0 : PR); }
+  __device__ __forceinline__ int kv() const { return (int)(K - k0() < PK ? K - k0() : PK); }
+  // what rounding needs, in one word: valid (bit 0), copy mode (bits 1-2),
+  // valid rows (bits 3-10), valid shared indices (11-17)
+  __device__ __forceinline__ uint32_t info() const {
+    return valid() ? 1u | ((uint32_t)mode << 1) | ((uint32_t)rv() << 3) | ((uint32_t)kv() << 11) : 0u;
+  }
+};
+
+// The table entries converter warp cw (lane l) needs for the slab `it`
+// points at: mode 1 -- row (l / 16) + 2i of its 16 (i = 0..7, on the unit's
+// first slab) and shared index 4(l % 16); mode 2 -- row group l (4 rows, on
+// the first slab) and shared indices 8cw + i. Mode 0 keeps its tables in
+// shared memory (ConvTables).
+struct ConvRegs {
+  int32_t r[8], k[8];
+};
+
+// Entries past the operand's end are read at its last row or shared index
+// (always in bounds) and never used: no select waits on the loads, which
+// land while the current slab is rounded.
+__device__ __forceinline__ void conv_fetch(const ConvIter& it, int cw, int l, ConvRegs& cr) {
+  if (!it.valid() || it.mode == 0) return;
+  const int64_t k0 = it.k0(), rl = it.R - 1, kl = it.K - 1;
+  if (it.mode == 1) {
+    if (it.ks == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cr.r[i] = __ldg(it.rtab + min(it.p0 + 16 * cw + (l >> 4) + 2 * i, rl));
+    }
+    cr.k[0] = __ldg(it.ktab + min(k0 + 4 * (l & 15), kl));
+  } else {
+    if (it.ks == 0) cr.r[0] = __ldg(it.rtab + min(it.p0 + 4 * l, rl));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cr.k[i] = __ldg(it.ktab + min(k0 + 8 * cw + i, kl));
+  }
+}
+
+// Converter warp cw issues its copies of slab `it` into staging slot `xs`
+// (shared address), with the table entries in cr (modes 1 and 2).
+__device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr, int cw, int l, ConvTables& tb,
+                                          uint32_t xs) {
+  const int rv = it.rv(), kv = it.kv();
+  const float* __restrict__ src = it.src;
+  if (it.mode == 1) {
+    // 16 rows x 16 chunks of 4 k; an instruction covers two 256-byte rows
+    const int q = l & 15;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = 16 * cw + (l >> 4) + 2 * i;
+      if (r < rv && 4 * q < kv) ptx::cp_async16(xs + (uint32_t)(r * 256 + q * 16), src + cr.r[i] + cr.k[0]);
+    }
+  } else if (it.mode == 2) {
+    // 8 k-rows x 32 chunks of 4 rows; an instruction covers one 512-byte k-row
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = 8 * cw + i;
+      if (k < kv && 4 * l < rv) ptx::cp_async16(xs + (uint32_t)(k * 512 + l * 16), src + cr.r[0] + cr.k[i]);
+    }
+  } else {
+    // 16 rows x 64 k, one float each; an instruction covers 32 consecutive k
+    int32_t* roff = tb.roff[cw];
+    int32_t* koff = tb.koff[cw];
+    const int64_t k0 = it.k0();
+    __syncwarp();  // the previous slab's copies have read the tables
+    if (it.ks == 0 && l < 16) roff[l] = 16 * cw + l < rv ? __ldg(it.rtab + it.p0 + 16 * cw + l) : 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) koff[l + 32 * h] = l + 32 * h < kv ? __ldg(it.ktab + k0 + l + 32 * h) : 0;
+    __syncwarp();
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+      const int e = l + 32 * i, rl = e >> 6, k = e & 63, r = 16 * cw + rl;
+      if (r < rv && k < kv) ptx::cp_async4(xs + (uint32_t)(r * 256 + 4 * k), src + roff[rl] + koff[k]);
+    }
+  }
+}
+
+// Converter warp cw rounds its part of a staged slab (info word w, slot
+// `xs`) into the bf16 P tile `pt`; zeros outside the valid rows and shared
+// indices (rows past the end could hold anything -- their products are never
+// stored -- but shared indices past the end must be zero). All shared-memory
+// loads are issued before the first store.
+__device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint8_t* xs, uint8_t* pt) {
+  const int mode = (int)((w >> 1) & 3), rv = (int)((w >> 3) & 255), kv = (int)((w >> 11) & 127);
+  const bool full = rv == PR && kv == PK;
+  float v[4][8];
+  if (mode != 2) {
+    // chunk (r, g) = row r, k 8g .. 8g+7; an instruction takes 4 rows x 8
+    // chunks, the two 16-byte halves in the order that spreads its loads
+    // over all eight bank groups
+    const int g = l & 7, hf = (g >> 2) & 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = 16 * cw + (l >> 3) + 4 * i;
+      const uint8_t* row = xs + r * 256 + g * 32;
+      const float4 a = *reinterpret_cast<const float4*>(row + 16 * hf);
+      const float4 b = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
+      const float4 lo = hf ? b : a, hi = hf ? a : b;
+      v[i][0] = lo.x; v[i][1] = lo.y; v[i][2] = lo.z; v[i][3] = lo.w;
+      v[i][4] = hi.x; v[i][5] = hi.y; v[i][6] = hi.z; v[i][7] = hi.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = 16 * cw + (l >> 3) + 4 * i;
+      if (!full) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (!(r < rv && 8 * g + j < kv)) v[i][j] = 0.0f;
+      }
+      store_chunk(pt, nullptr, sw128_chunk(r, g), v[i]);
+    }
+  } else {
+    // chunk column g = cw: rows l, l + 32, l + 64, l + 96 (an instruction
+    // covers 32 consecutive rows), one float per k-row read
+    const int g = cw;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float* krow = reinterpret_cast<const float*>(xs + (8 * g + j) * 512);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i][j] = krow[l + 32 * i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = l + 32 * i;
+      if (!full) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (!(r < rv && 8 * g + j < kv)) v[i][j] = 0.0f;
+      }
+      store_chunk(pt, nullptr, sw128_chunk(r, g), v[i]);
+    }
+  }
+}
+
+template <int SPLIT, int FUSE>
+__global__ void __launch_bounds__(GCfg<SPLIT, FUSE>::THREADS, 1)
 packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __restrict__ descs,
-                   const int32_t* __restrict__ map, int64_t total_units, int* status) {
-  using Cf = GCfg<SPLIT>;
+                   const int32_t* __restrict__ map, const PackJob* __restrict__ jobs, int64_t total_units,
+                   int* status) {
+  using Cf = GCfg<SPLIT, FUSE>;
   constexpr int S = Cf::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(smem + (size_t)S * Cf::STAGE_BYTES);
+  uint8_t* xstage = smem + (size_t)S * Cf::STAGE_BYTES;  // fused: staging slots, then the tables
+  ConvTables& tb = *reinterpret_cast<ConvTables*>(xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES : 0));
+  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables)
+                                                                : 0));
   const uint32_t stage0 = ptx::smem_addr(smem);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
-      ptx::mbar_init(ptx::smem_addr(&x.full[s]), 1);
+      // fused: the copy warp's transaction arrival and one per converter warp
+      ptx::mbar_init(ptx::smem_addr(&x.full[s]), 1 + Cf::CONV);
       ptx::mbar_init(ptx::smem_addr(&x.empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_addr(&x.acc_full[b]), 1);
-      ptx::mbar_init(ptx::smem_addr(&x.acc_empty[b]), EPI_WARPS);
+      ptx::mbar_init(ptx::smem_addr(&x.acc_empty[b]), Cf::EPI);
     }
     ptx::mbar_init(ptx::smem_addr(&x.final_bar), 1);
     x.abort = 0;
@@ -327,7 +535,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qleft = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
-        const uint32_t pb = rows_bytes(d.RP - g.p0), qb = rows_bytes(qleft);
+        const uint32_t pb = FUSE ? 0u : rows_bytes(d.RP - g.p0), qb = rows_bytes(qleft);
         const uint32_t tx = (pb + qb) * (SPLIT ? 2u : 1u);
         const uint8_t* pbase = d.P + ((g.p0 / PR) * d.slabs + g.ks0) * d.P_block;
         // a 64-row tile starts 64 rows (8 atoms, 8 KB) into its 128-row block
@@ -339,7 +547,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           const uint32_t full = ptx::smem_addr(&x.full[s]);
           const uint32_t st = stage0 + (uint32_t)s * Cf::STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(full, tx);
-          ptx::bulk_copy_g2s(st, pbase + ks * d.P_block, pb, full);
+          if (!FUSE) ptx::bulk_copy_g2s(st, pbase + ks * d.P_block, pb, full);
           ptx::bulk_copy_g2s(st + PBLOCK, qbase + ks * d.Q_block, qb, full);
           if (SPLIT) {
             ptx::bulk_copy_g2s(st + 2 * PBLOCK, pbase + d.P_lo + ks * d.P_block, pb, full);
@@ -401,10 +609,65 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       ptx::mma_commit(ptx::smem_addr(&x.final_bar));
       ptx::mbar_wait(ptx::smem_addr(&x.final_bar), 0u, status);
     }
+  } else if (FUSE && warp < Cf::EPI0) {
+    // ------------------------------------------------------------ converters
+    const int cw = warp - 2;
+    const uint32_t xs0 = ptx::smem_addr(xstage);
+    ConvIter itr;  // the next slab to copy
+    itr.u = blockIdx.x;
+    itr.total = total_units;
+    itr.ks = itr.nks = itr.ks0 = itr.mode = 0;
+    itr.p0 = itr.R = itr.K = 0;
+    itr.src = nullptr;
+    itr.rtab = itr.ktab = nullptr;
+    itr.load(descs, map, jobs);
+    ConvRegs cr;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cr.r[i] = cr.k[i] = 0;
+    conv_fetch(itr, cw, lane, cr);
+    // copies of the slab XDIST ahead (one commit group per slab, empty
+    // groups included), then the table entries of the slab after it
+    auto issue = [&](int sl) -> uint32_t {
+      const uint32_t info = itr.info();
+      if (itr.valid()) {
+        conv_copy(itr, cr, cw, lane, tb, xs0 + (uint32_t)(sl * XSLOT_BYTES));
+        itr.next(descs, map, jobs);
+        conv_fetch(itr, cw, lane, cr);
+      }
+      ptx::cp_async_commit();
+      return info;
+    };
+    uint32_t w[XDIST + 1];
+#pragma unroll
+    for (int d = 0; d < XDIST; ++d) w[d] = issue(d);
+    uint32_t gs = 0;
+    int sl = 0;  // slot of slab gs; slab gs + XDIST goes to the slot before it
+    while ((w[0] & 1u) && !x.abort) {
+      w[XDIST] = issue(sl == 0 ? XSLOTS - 1 : sl - 1);
+      ptx::cp_async_wait<XDIST>();  // this thread's copies of slab gs have landed
+      __syncwarp();                 // ... and those of the whole warp
+      const int s = (int)(gs % S);
+      const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(ptx::smem_addr(&x.empty[s]), ((gs / S) & 1u) ^ 1u,
+                                                             status));
+      if (!ok) {
+        x.abort = 1;
+        break;
+      }
+      conv_round(w[0], cw, lane, xstage + (size_t)sl * XSLOT_BYTES, smem + (size_t)s * Cf::STAGE_BYTES);
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ptx::smem_addr(&x.full[s]));
+      ++gs;
+#pragma unroll
+      for (int d = 0; d < XDIST; ++d) w[d] = w[d + 1];
+      sl = sl == XSLOTS - 1 ? 0 : sl + 1;
+    }
+    ptx::cp_async_wait<0>();
   } else {
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;            // TMEM lanes quad*32 .. quad*32+31
-    const int col0 = ((warp - 2) >> 2) * EPI_COLS;  // first accumulator column of this warp
+    constexpr int ECOLS = Cf::ECOLS;
+    const int col0 = ((warp - Cf::EPI0) >> 2) * ECOLS;  // first accumulator column of this warp
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     uint32_t gc = 0;
     GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
@@ -420,9 +683,9 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       float* __restrict__ C = d.C;
       // 16-byte stores along a row of C: C row-major along j, rows 16-byte aligned
       const bool vec = d.cj == 1 && ((d.ci & 3) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 3) == 0;
-      float acc[SPLIT ? EPI_COLS : 1];
+      float acc[SPLIT ? ECOLS : 1];
 #pragma unroll
-      for (int j = 0; j < (SPLIT ? EPI_COLS : 1); ++j) acc[j] = 0.0f;
+      for (int j = 0; j < (SPLIT ? ECOLS : 1); ++j) acc[j] = 0.0f;
       // Writes columns col .. col+31 of row i (this thread's values r):
       // 16-byte stores along a row of C, or, with the roles swapped, one
       // store per column with the warp's lanes on consecutive addresses.
@@ -457,12 +720,13 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       const bool rows16 = d.cj == 1 && d.store16 != 0;
       const bool vec2 = rows16 && ((d.ci & 1) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 1) == 0 &&
                         ((reinterpret_cast<uintptr_t>(C) & 7) == 0);
-      // values r[4j..4j+3] of lane half h (rows +0 and +8), columns col0 + 8j + 2(lane % 4) + {0, 1}
-      auto emit16 = [&](int h, const float* r) {
+      // values r[4j..4j+3] of lane half h (rows +0 and +8), columns
+      // cbase + 8j + 2(lane % 4) + {0, 1} (a block of 64 columns)
+      auto emit16 = [&](int h, const float* r, int cbase) {
         const int64_t row = g.p0 + quad * 32 + h * 16 + (lane >> 2);
-        const int cq = col0 + 2 * (lane & 3);
+        const int cq = cbase + 2 * (lane & 3);
 #pragma unroll
-        for (int j = 0; j < EPI_COLS / 8; ++j) {
+        for (int j = 0; j < 8; ++j) {
           const int c = cq + 8 * j;
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
@@ -490,26 +754,31 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         ptx::tc_fence_after();
         if (rows16) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (col0 < qcols) {  // uniform across the warp
-              uint32_t r[32];
-              ptx::tmem_ld_16x256b_x8(tmem + ((uint32_t)(quad * 32 + h * 16) << 16) + (uint32_t)(b * PR + col0), r);
-              ptx::tmem_ld_wait();
-              if (SPLIT) {
+          for (int blk = 0; blk < ECOLS / 64; ++blk) {
+            const int cbase = col0 + 64 * blk;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[h * 32 + j] += __uint_as_float(r[j]);
-              } else {
-                float v[32];
+            for (int h = 0; h < 2; ++h) {
+              if (cbase < qcols) {  // uniform across the warp
+                uint32_t r[32];
+                ptx::tmem_ld_16x256b_x8(tmem + ((uint32_t)(quad * 32 + h * 16) << 16) + (uint32_t)(b * PR + cbase),
+                                        r);
+                ptx::tmem_ld_wait();
+                if (SPLIT) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                emit16(h, v);
+                  for (int j = 0; j < 32; ++j) acc[blk * 64 + h * 32 + j] += __uint_as_float(r[j]);
+                } else {
+                  float v[32];
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                  emit16(h, v, cbase);
+                }
               }
             }
           }
         } else {
           const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR + col0);
 #pragma unroll
-          for (int cb = 0; cb < EPI_COLS / 32; ++cb) {
+          for (int cb = 0; cb < ECOLS / 32; ++cb) {
             if (col0 + cb * 32 < qcols) {  // uniform across the warp
               uint32_t r[32];
               ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
@@ -534,11 +803,13 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       if (SPLIT) {
         if (rows16) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
-            if (col0 < qcols) emit16(h, &acc[h * 32]);
+          for (int blk = 0; blk < ECOLS / 64; ++blk)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              if (col0 + 64 * blk < qcols) emit16(h, &acc[blk * 64 + h * 32], col0 + 64 * blk);
         } else {
 #pragma unroll
-          for (int cb = 0; cb < EPI_COLS / 32; ++cb)
+          for (int cb = 0; cb < ECOLS / 32; ++cb)
             if (col0 + cb * 32 < qcols) emit(col0 + cb * 32, &acc[cb * 32]);
         }
       }
@@ -579,19 +850,21 @@ int sm_count() {
   return sms;
 }
 
-template <int SPLIT>
-int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* map, int64_t units, cudaStream_t s) {
-  const size_t smem = gemm_smem_bytes<SPLIT>();
+template <int SPLIT, int FUSE>
+int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* map, const PackJob* jobs,
+                int64_t units, cudaStream_t s) {
+  const size_t smem = gemm_smem_bytes<SPLIT, FUSE>();
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(packed_gemm_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(packed_gemm_kernel<SPLIT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
       return TN_ERR_CUDA;
     attr = true;
   }
   const int64_t sms = sm_count();
   const unsigned grid = (unsigned)(units < sms ? units : sms);
-  packed_gemm_kernel<SPLIT><<<grid, GEMM_THREADS, smem, s>>>(single, descs, map, units, status_word());
+  packed_gemm_kernel<SPLIT, FUSE>
+      <<<grid, GCfg<SPLIT, FUSE>::THREADS, smem, s>>>(single, descs, map, jobs, units, status_word());
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
@@ -610,9 +883,19 @@ int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units,
   if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
   GemmDesc none;
   memset(&none, 0, sizeof(none));
-  if (prec == TN_PREC_BF16) return launch_gemm<0>(none, descs, map, units, s);
-  if (prec == TN_PREC_BF16X3) return launch_gemm<1>(none, descs, map, units, s);
+  if (prec == TN_PREC_BF16) return launch_gemm<0, 0>(none, descs, map, nullptr, units, s);
+  if (prec == TN_PREC_BF16X3) return launch_gemm<1, 0>(none, descs, map, nullptr, units, s);
   return TN_ERR_ARG;
+}
+
+int launch_fused_gemm(const GemmDesc* descs, const int32_t* map, const PackJob* jobs, int64_t units,
+                      cudaStream_t s) {
+  if (units <= 0) return TN_OK;
+  if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (!descs || !map || !jobs) return TN_ERR_ARG;
+  GemmDesc none;
+  memset(&none, 0, sizeof(none));
+  return launch_gemm<0, 1>(none, descs, map, jobs, units, s);
 }
 
 namespace {
@@ -640,6 +923,20 @@ PackJob make_job(const ContractDesc& d, const float* src, int64_t R, int nr, con
   }
   j.kfast = (d.nk > 0 && kstr[d.nk - 1] == 1) ? 1 : 0;
   j.rfast = (nr > 0 && rstr[nr - 1] == 1) ? 1 : 0;
+  // 16-byte copies along the unit-stride leg: it is the last shared (or
+  // free) leg with a length divisible by 4, every other stride is a multiple
+  // of 4 elements, and the base is 16-byte aligned
+  int mode = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    if (j.kfast && d.kdim[d.nk - 1] % 4 == 0) mode = 1;
+    else if (j.rfast && rdim[nr - 1] % 4 == 0) mode = 2;
+    for (int q = 0; q < nr && mode; ++q)
+      if (!(mode == 2 && q == nr - 1) && rdim[q] > 1 && rstr[q] % 4 != 0) mode = 0;
+    for (int q = 0; q < d.nk && mode; ++q)
+      if (!(mode == 1 && q == d.nk - 1) && d.kdim[q] > 1 && kstr[q] % 4 != 0) mode = 0;
+  }
+  j.vec4 = mode;
+  j.rtab_off = j.ktab_off = -1;
   return j;
 }
 
@@ -654,7 +951,7 @@ size_t job_bytes(const PackJob& j) { return (size_t)j.tiles * j.slabs * j.block_
 // GEMM descriptor of contraction d over packed A (ja) and B (jb): the side
 // with more rows is P (the MMA's 128 rows). Offsets are left to the caller.
 GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, int q_tile, bool* swapped) {
-  const bool swap = d.N > d.M && d.M < PR;
+  const bool swap = p_is_b(d);
   GemmDesc g;
   memset(&g, 0, sizeof(g));
   g.C = d.C;
@@ -672,6 +969,8 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
   g.slabs = ja.slabs;
   g.splits = d.splits;
   g.slabs_per_split = (int32_t)(d.k_per_split / PK);
+  g.pjob = -1;
+  g.K = d.K;
   *swapped = swap;
   return g;
 }
@@ -680,13 +979,48 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
 
 // Host side: pack jobs (two per contraction), their block units, and the GEMM
 // descriptors, with block storage as offsets in the plan's packed region.
-int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, PackedPlan* pp) {
+void fused_tables(const ContractDesc& d, std::vector<int32_t>* tab, int64_t* rtab_off, int64_t* ktab_off) {
+  const bool b = p_is_b(d);
+  const int nr = b ? d.nn : d.nm;
+  const int32_t* rdim = b ? d.ndim : d.mdim;
+  const int64_t* rstr = b ? d.nstr : d.mstr;
+  const int64_t* kstr = b ? d.kstrB : d.kstrA;
+  const int64_t R = b ? d.N : d.M;
+  // odometer over the legs, last leg fastest (offsets fit 32 bits: the
+  // planner rejects operands spanning 2^31 elements or more)
+  auto run = [&](int64_t n, int nl, const int32_t* dims, const int64_t* str) {
+    int32_t idx[TN_MAX_RANK] = {0};
+    int64_t off = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      tab->push_back((int32_t)off);
+      for (int q = nl - 1; q >= 0; --q) {
+        off += str[q];
+        if (++idx[q] < dims[q]) break;
+        off -= (int64_t)dims[q] * str[q];
+        idx[q] = 0;
+      }
+    }
+  };
+  *rtab_off = (int64_t)tab->size();
+  run(R, nr, rdim, rstr);
+  *ktab_off = (int64_t)tab->size();
+  run(d.K, d.nk, d.kdim, kstr);
+}
+
+int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,
+                int64_t ktab_off, PackedPlan* pp) {
   const PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
   const PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
   if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
     return TN_ERR_UNSUPPORTED;
-  const size_t bytes_a = (size_t)ja.tiles * ja.slabs * ja.block_bytes;
-  const size_t bytes_b = (size_t)jb.tiles * jb.slabs * jb.block_bytes;
+  bool swap = false;
+  GemmDesc g = make_gemm(d, ja, jb, sc.q_tile, &swap);
+  fuse = fuse && prec == TN_PREC_BF16 && g.RQ <= PR / 2 && rtab_off >= 0 && ktab_off >= 0;
+  // a fused contraction packs Q only: P (A, or B when swapped) is read by
+  // the fused GEMM's converters
+  const bool pack_a = !(fuse && !swap), pack_b = !(fuse && swap);
+  const size_t bytes_a = pack_a ? (size_t)ja.tiles * ja.slabs * ja.block_bytes : 0;
+  const size_t bytes_b = pack_b ? (size_t)jb.tiles * jb.slabs * jb.block_bytes : 0;
   const bool split = prec == TN_PREC_BF16X3;
   // storage offsets (relative to the packed region): A hi, B hi, A lo, B lo
   const size_t off_a = pp->packed_bytes;
@@ -705,24 +1039,29 @@ int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, Packe
   const int ja_idx = (int)pp->jobs.size();
   pp->jobs.push_back(ja);
   pp->jobs.push_back(jb);
-  pp->job_hi_off.push_back(off_a);
-  pp->job_hi_off.push_back(off_b);
+  if (fuse) {
+    PackJob& jp = pp->jobs[(size_t)ja_idx + (swap ? 1 : 0)];
+    jp.rtab_off = rtab_off;
+    jp.ktab_off = ktab_off;
+  }
+  pp->job_hi_off.push_back(pack_a ? off_a : SIZE_MAX);
+  pp->job_hi_off.push_back(pack_b ? off_b : SIZE_MAX);
   pp->job_lo_off.push_back(split ? off_alo : SIZE_MAX);
   pp->job_lo_off.push_back(split ? off_blo : SIZE_MAX);
   for (int w = 0; w < 2; ++w) {
+    if (!(w == 0 ? pack_a : pack_b)) continue;
     const PackJob& j = pp->jobs[(size_t)ja_idx + w];
     const int32_t nb = j.tiles * j.slabs;
     const int32_t per = blocks_per_unit(j);
     for (int32_t f = 0; f < nb; f += per) pp->units.push_back(PackUnit{ja_idx + w, f, std::min(per, nb - f), 0});
   }
 
-  bool swap = false;
-  GemmDesc g = make_gemm(d, ja, jb, sc.q_tile, &swap);
   g.store16 = sc.store16;
   g.P_off = swap ? off_b : off_a;
   g.Q_off = swap ? off_a : off_b;
   g.P_lo = split ? (int64_t)(swap ? off_blo : off_alo) - (int64_t)g.P_off : 0;
   g.Q_lo = split ? (int64_t)(swap ? off_alo : off_blo) - (int64_t)g.Q_off : 0;
+  g.pjob = fuse ? ja_idx + (swap ? 1 : 0) : -1;
   pp->gemms.push_back(g);
   return TN_OK;
 }
@@ -780,8 +1119,8 @@ int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_
   if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   const int64_t units = (int64_t)g.tiles_p * g.tiles_q * g.splits;
   if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
-  if (prec == TN_PREC_BF16) return launch_gemm<0>(g, nullptr, nullptr, units, s);
-  return launch_gemm<1>(g, nullptr, nullptr, units, s);
+  if (prec == TN_PREC_BF16) return launch_gemm<0, 0>(g, nullptr, nullptr, nullptr, units, s);
+  return launch_gemm<1, 0>(g, nullptr, nullptr, nullptr, units, s);
 }
 
 }  // namespace tn

@@ -26,6 +26,13 @@ struct PackJob {
   int32_t tiles, slabs;
   int32_t nr, nk;         // free legs and shared legs
   int32_t rfast, kfast;   // the source's unit stride is the last free / shared leg
+  int32_t vec4;           // 16-byte copies: 1 along k, 2 along rows (every 4 consecutive
+                          // elements from a 4-aligned index are contiguous and 16-byte
+                          // aligned), 0 none
+  int32_t pad;
+  const int32_t* rtab;    // device (fused P only): source offset of every row, R entries
+  const int32_t* ktab;    // and of every shared index, K entries
+  int64_t rtab_off, ktab_off;  // host: their element offsets in the plan's table region, -1 none
   int32_t rdim[TN_MAX_RANK];
   int32_t kdim[TN_MAX_RANK];
   int64_t rstr[TN_MAX_RANK];
@@ -47,13 +54,15 @@ struct GemmDesc {
   int64_t ci, cj;         // element strides of C along i and j
   int64_t RP, RQ;         // rows of P and of Q
   int64_t P_block, Q_block;
-  int64_t tile_begin;     // first global work unit
+  int64_t tile_begin;     // first work unit (numbered per launch)
+  int64_t K;              // shared extent (host: algorithmic bytes)
   uint64_t P_off, Q_off;  // host: offsets of the hi blocks in the packed region
   int32_t tiles_p, tiles_q, slabs, splits, slabs_per_split;
   int32_t q_tile;         // rows of Q per unit (the output tile's width): 128 or 64
   int32_t store16;        // C row-major along j: drain TMEM as 16-lane x 256-bit blocks
                           // (whole-sector stores) instead of one row per thread
-  int32_t pad;
+  int32_t pjob;           // fused: index of P's job in the job list (P is read as float32
+                          // and rounded inside the GEMM, never packed); -1: P is packed
 };
 
 // Schedule of the packed GEMM for one class of contractions: the output
@@ -76,8 +85,25 @@ struct PackedPlan {
 };
 
 // Appends contraction d (units already planned by plan_units) to the plan
-// under schedule sc (tile width and epilogue shape).
-int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, PackedPlan* pp);
+// under schedule sc (tile width and epilogue shape). fuse (allowed): a BF16
+// contraction whose narrower operand has at most 64 rows takes the fused
+// GEMM -- every element of its wider operand P is read by exactly one work
+// unit, so rounding P inside the GEMM repeats no conversion, where packing it
+// would cost 4 more bytes per element than reading it once; P is then not
+// packed, and its job (with the offset tables at rtab_off / ktab_off) is kept
+// for the fused GEMM's converters (pjob).
+int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,
+                int64_t ktab_off, PackedPlan* pp);
+
+// The operand on the MMA's 128-row side of contraction d: B when it has more
+// rows and A fewer than 128, else A.
+inline bool p_is_b(const ContractDesc& d) { return d.N > d.M && d.M < 128; }
+
+// Appends to `tab` the source offsets of every row (R entries) and every
+// shared index (K entries) of d's P operand, for the fused GEMM's converters
+// (they then read offsets instead of dividing composite indices by leg
+// lengths); returns the element offsets of the two runs.
+void fused_tables(const ContractDesc& d, std::vector<int32_t>* tab, int64_t* rtab_off, int64_t* ktab_off);
 
 int launch_pack(const PackJob* jobs, const PackUnit* units, int64_t nunits, cudaStream_t s);
 
@@ -89,5 +115,9 @@ size_t packed_single_bytes(const ContractDesc& d, int prec);
 size_t packed_scratch_bound(int64_t M, int64_t N, int64_t K, int prec);
 int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s);
 int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, int prec, cudaStream_t s);
+// The fused GEMM (BF16): units whose P is read as float32 through jobs[pjob]
+// and rounded to bf16 in shared memory, Q packed.
+int launch_fused_gemm(const GemmDesc* descs, const int32_t* map, const PackJob* jobs, int64_t units,
+                      cudaStream_t s);
 
 }  // namespace tn

@@ -89,22 +89,24 @@ int plan_contract(const tn_tensor* A, const int* legsA, const tn_tensor* B, cons
     }
   }
 
-  // shared legs: keep the caller's pairing; put the pair holding the
-  // smallest-stride leg of A (else of B) innermost so k runs are unit-stride
+  // shared legs: keep the caller's pairing; put innermost the pair holding
+  // the unit-stride leg of the larger operand (B when N > M, else A), else
+  // that of the other one, so k runs of the operand with more bytes are
+  // contiguous
   int order[TN_MAX_RANK];
   for (int j = 0; j < nshared; ++j) order[j] = j;
   if (nshared > 1) {
-    int best = -1;
-    int64_t bs = INT64_MAX;
-    for (int j = 0; j < nshared; ++j)
-      if (A->shape[legsA[j]] > 1 && sa[legsA[j]] < bs) { bs = sa[legsA[j]]; best = j; }
-    if (bs != 1) {
-      int64_t bb = INT64_MAX;
-      int bestb = -1;
-      for (int j = 0; j < nshared; ++j)
-        if (B->shape[legsB[j]] > 1 && sb[legsB[j]] < bb) { bb = sb[legsB[j]]; bestb = j; }
-      if (bb == 1 || best < 0) best = bestb;
+    int best_a = -1, best_b = -1;
+    int64_t bs_a = INT64_MAX, bs_b = INT64_MAX;
+    for (int j = 0; j < nshared; ++j) {
+      if (A->shape[legsA[j]] > 1 && sa[legsA[j]] < bs_a) { bs_a = sa[legsA[j]]; best_a = j; }
+      if (B->shape[legsB[j]] > 1 && sb[legsB[j]] < bs_b) { bs_b = sb[legsB[j]]; best_b = j; }
     }
+    const bool prefer_b = N > M;
+    int best;
+    if (prefer_b) best = (bs_b == 1 || bs_a != 1) ? best_b : best_a;
+    else best = (bs_a == 1 || bs_b != 1) ? best_a : best_b;
+    if (best < 0) best = best_a >= 0 ? best_a : best_b;
     if (best >= 0) {
       int w = 0;
       for (int j = 0; j < nshared; ++j)

@@ -88,6 +88,7 @@ def _signatures():
         "tn_group_plan_launches": (i32, [vp]),
         "tn_group_plan_run_launch": (i32, [vp, vp, ctypes.c_size_t, i32, vp]),
         "tn_group_plan_launch_name": (ctypes.c_char_p, [vp, i32]),
+        "tn_group_plan_launch_bytes": (ctypes.c_double, [vp, i32]),
         "tn_group_plan_autotune": (i32, [vp, vp, ctypes.c_size_t, vp]),
         "tn_group_plan_schedule": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "tn_group_plan_set_schedule": (i32, [vp, i32, i32, i32, i32]),
@@ -331,6 +332,11 @@ class GroupPlan:
     def launch_names(self):
         lib = load()
         return [lib.tn_group_plan_launch_name(self._h, i).decode() for i in range(self.launches)]
+
+    def launch_bytes(self):
+        """Algorithmic bytes of each launch (tn_group_plan_launch_bytes)."""
+        lib = load()
+        return [lib.tn_group_plan_launch_bytes(self._h, i) for i in range(self.launches)]
 
     def run_launch(self, index: int, stream=None):
         """Launch `index` of the run's sequence alone (tn_group_plan_run_launch)."""

@@ -72,3 +72,51 @@ def test_validation_errors_without_gpu(libpath):
     assert lib.tn_contract(ctypes.byref(a), la2, ctypes.byref(b), lb, 1, ctypes.byref(c), 0, None) == 1
     assert lib.tn_contract(None, la, ctypes.byref(b), lb, 1, ctypes.byref(c), 0, None) == 1
     assert lib.tn_contract(ctypes.byref(a), la, ctypes.byref(b), lb, 1, ctypes.byref(c), 9, None) == 1
+
+
+def test_group_plan_launches_without_gpu(libpath):
+    """Planning runs on the host: a BF16 plan sends a contraction whose
+    narrower operand has at most 64 rows to the fused GEMM (its wider
+    operand is never packed) and the rest to pack + GEMM; a BF16X3 plan packs
+    everything. Algorithmic bytes per launch follow from the shapes."""
+    from paper_1905_01330_gb300 import tn
+    lib = ctypes.CDLL(libpath)
+    for n, (res, args) in tn._signatures().items():
+        getattr(lib, n).restype = res
+        getattr(lib, n).argtypes = args
+
+    def desc(shape, addr):
+        t = tn.TnTensor()
+        t.data, t.rank = addr, len(shape)
+        for i, n in enumerate(shape):
+            t.shape[i] = n
+        return t
+
+    specs = [((4096, 64), [1], (64, 32), [0], (4096, 32)),      # thin: P = A
+             ((16, 96), [1], (96, 3000), [0], (16, 3000)),      # thin, swapped: P = B
+             ((512, 256), [1], (256, 384), [0], (512, 384))]    # packed
+    arr = (tn.TnContractSpec * len(specs))()
+    for i, (sa, la, sb, lb, sc) in enumerate(specs):
+        arr[i].A, arr[i].B, arr[i].C = desc(sa, 0x10000 * (3 * i + 1)), desc(sb, 0x10000 * (3 * i + 2)), \
+            desc(sc, 0x10000 * (3 * i + 3))
+        arr[i].nshared = 1
+        arr[i].legsA[0], arr[i].legsB[0] = la[0], lb[0]
+
+    def launches(prec):
+        h = ctypes.c_void_p()
+        assert lib.tn_group_plan_create(arr, len(specs), tn.PREC[prec], ctypes.byref(h)) == 0
+        out = {lib.tn_group_plan_launch_name(h, i).decode(): lib.tn_group_plan_launch_bytes(h, i)
+               for i in range(lib.tn_group_plan_launches(h))}
+        assert lib.tn_group_plan_launch_bytes(h, lib.tn_group_plan_launches(h)) == -1.0
+        lib.tn_group_plan_destroy(h)
+        return out
+
+    got = launches("bf16")
+    assert got == {
+        "pack": 6.0 * (64 * 32 + 16 * 96 + 512 * 256 + 256 * 384),           # only Q of the fused two
+        "gemm": 2.0 * (512 * 256 + 256 * 384) + 4.0 * 512 * 384,
+        "gemm_fused": 4.0 * (4096 * 64 + 3000 * 96) + 2.0 * (32 * 64 + 16 * 96) + 4.0 * (4096 * 32 + 16 * 3000),
+    }
+    got = launches("bf16x3")
+    ops = 4096 * 64 + 64 * 32 + 16 * 96 + 96 * 3000 + 512 * 256 + 256 * 384
+    assert got == {"pack": 8.0 * ops, "gemm": 4.0 * ops + 4.0 * (4096 * 32 + 16 * 3000 + 512 * 384)}

@@ -145,3 +145,47 @@ def test_autotune_picks_a_schedule_and_caches_it(tn, prec):
     # a new plan over the same shapes starts from the cached choice
     again = tn.GroupPlan(specs, prec=prec)
     assert again.schedule() == sched
+
+
+def test_fused_gemm_access_patterns(tn):
+    """BF16 contractions whose narrower operand has at most 64 rows take the
+    fused GEMM (the wider operand rounded to bf16 inside it, never packed). Cases
+    cover its converters' paths: the wider operand unit-stride along k
+    (16-byte copies), along its rows (4-byte copies with lanes on rows), with
+    no unit stride, at an address that is not 16-byte aligned (4-byte
+    fallback), on either side (A, or B with the roles swapped), row and k
+    tails, K < 8, many units per CTA, and split k ranges."""
+    base = torch.from_numpy(rand(60, (1 + 700 * 96,))).cuda()
+    Au = base[1:].view(700, 96)                          # 4-byte aligned only
+    Aunp = Au.cpu().numpy()
+    Bfull = torch.from_numpy(rand(61, (40, 600))).cuda()
+    Bx = Bfull[:, ::2]                                   # (40, 300), strides (600, 2): no unit stride
+    cases = [
+        (rand(50, (1000, 192)), [1], rand(51, (192, 40)), [0]),         # k unit stride, P = A
+        (rand(52, (72, 900)), [0], rand(53, (72, 24)), [0]),            # rows unit stride (k outer)
+        (Au, [1], rand(54, (96, 33)), [0], Aunp, None),                  # misaligned rows: 4-byte copies
+        (rand(55, (24, 77)), [1], rand(56, (3000, 77)), [1]),           # swapped: P = B, k tail 13
+        (rand(57, (5, 4000)), [0], rand(58, (5, 16)), [0]),             # K = 5
+        (rand(59, (20000, 64)), [1], rand(62, (64, 60)), [0]),          # 157 units: CTAs run several
+        (rand(63, (300, 6000)), [1], rand(64, (6000, 50)), [0]),        # 3 tiles: split k ranges
+        (rand(65, (40, 8)), [0], Bx, [0], None, None),                  # swapped, P without unit stride
+    ]
+    specs, host = [], []
+    for c in cases:
+        A, la, B, lb = c[:4]
+        At = A if torch.is_tensor(A) else torch.from_numpy(A).cuda()
+        Btt = B if torch.is_tensor(B) else torch.from_numpy(B).cuda()
+        Ah = c[4] if len(c) > 4 and c[4] is not None else (At.cpu().numpy() if torch.is_tensor(A) else A)
+        Bh = c[5] if len(c) > 5 and c[5] is not None else (Btt.cpu().numpy() if torch.is_tensor(B) else B)
+        specs.append((At, list(la), Btt, list(lb), torch.empty(tn.result_shape(At, la, Btt, lb), device="cuda")))
+        host.append((np.ascontiguousarray(Ah), la, np.ascontiguousarray(Bh), lb))
+    plan = tn.GroupPlan(specs, prec="bf16")
+    assert "gemm_fused" in plan.launch_names()
+    for rep in range(2):   # twice: the second run reuses stale shared memory and staging
+        for sp in specs:
+            sp[4].fill_(float("nan"))
+        plan.run()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == 0
+        for (A, la, B, lb), sp in zip(host, specs):
+            check(sp[4], A, la, B, lb, "bf16")
