@@ -62,9 +62,14 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float a, float b) {
 //    rows (128 contiguous bytes when the unit stride is along the rows).
 constexpr int PACK_CPT = 4;  // chunks per thread and block (1024 chunks / 256 threads)
 
+// A CTA packs "virtual blocks": J.nbv consecutive blocks of one tile at a
+// time, J.rg rows each (nbv * rg <= 128). Operands with 128 rows or more (or
+// more than 64) take one block at a time (rg = 128 or their row count); a
+// narrow operand (at most 64 rows, e.g. the thin side of a contraction)
+// takes 128 / rg of its slabs at once, so all threads have rows to pack.
 struct PackSmem {
-  int64_t roff[2][PR];   // source offset of each row (valid rows only)
-  int64_t koff[2][PK];   // source offset of each shared index (valid only)
+  int32_t roff[2][PR];           // source offset of each row of the tile (valid rows only)
+  int32_t koff[2][PR * PK / 8];  // source offset of each shared index of the nbv slabs
 };
 constexpr size_t PACK_SMEM = sizeof(PackSmem);
 
@@ -86,64 +91,75 @@ __device__ __forceinline__ void store_chunk(uint8_t* hi, uint8_t* lo, uint32_t o
   }
 }
 
-struct BlockGeom {
-  int rv, kv;  // valid rows and shared indices of the block
+// Virtual block: blocks b0 .. b0+nb-1 (nb <= J.nbv, one tile).
+struct VBlock {
+  int b0, nb, slab0, rv;  // first block, blocks, first slab, valid rows of the tile
 };
 
-__device__ __forceinline__ BlockGeom block_geom(const PackJob& J, int b) {
-  const int tile = b / J.slabs, slab = b - tile * J.slabs;
-  const int64_t r0 = (int64_t)tile * PR, k0 = (int64_t)slab * PK;
-  BlockGeom g;
-  g.rv = (int)(J.R - r0 < PR ? J.R - r0 : PR);
-  g.kv = (int)(J.K - k0 < PK ? J.K - k0 : PK);
-  return g;
+__device__ __forceinline__ VBlock vblock(const PackJob& J, int b0, int nb) {
+  VBlock v;
+  const int tile = b0 / J.slabs;
+  v.b0 = b0;
+  v.nb = nb;
+  v.slab0 = b0 - tile * J.slabs;
+  const int64_t r0 = (int64_t)tile * PR;
+  v.rv = (int)(J.R - r0 < PR ? J.R - r0 : PR);
+  return v;
 }
 
-// Offset tables of block b into slot `sl` (threads 0 .. PR+PK-1).
-__device__ __forceinline__ void block_tables(const PackJob& J, int b, int sl, PackSmem& sm) {
+// Offset tables of virtual block v into slot `sl` (all threads).
+__device__ __forceinline__ void block_tables(const PackJob& J, const VBlock& v, int sl, PackSmem& sm) {
   const int t = threadIdx.x;
-  const int tile = b / J.slabs, slab = b - tile * J.slabs;
-  const int64_t r0 = (int64_t)tile * PR, k0 = (int64_t)slab * PK;
-  const BlockGeom g = block_geom(J, b);
-  if (t < PR) sm.roff[sl][t] = t < g.rv ? leg_offset((uint32_t)(r0 + t), J.nr, J.rdim, J.rstr) : 0;
-  else if (t < PR + PK)
-    sm.koff[sl][t - PR] = (t - PR) < g.kv ? leg_offset((uint32_t)(k0 + t - PR), J.nk, J.kdim, J.kstr) : 0;
+  const int64_t r0 = (int64_t)(v.b0 / J.slabs) * PR;
+  if (t < PR) sm.roff[sl][t] = t < v.rv ? (int32_t)leg_offset((uint32_t)(r0 + t), J.nr, J.rdim, J.rstr) : 0;
+  // shared indices from thread 128 on, so one block's rows and shared
+  // indices are decoded by different threads at once
+  for (int e = t ^ PR; e < v.nb * PK; e += PACK_THREADS) {
+    const int64_t k = (int64_t)(v.slab0 + (e >> 6)) * PK + (e & (PK - 1));
+    sm.koff[sl][e] = k < J.K ? (int32_t)leg_offset((uint32_t)k, J.nk, J.kdim, J.kstr) : 0;
+  }
 }
 
-// The chunks a thread makes for one block: values and output coordinates.
+// The chunks a thread makes for one virtual block: values and output
+// coordinates (block -1: none).
 struct ChunkRegs {
   float v[PACK_CPT][8];
-  int rr[PACK_CPT], gg[PACK_CPT];
+  int rr[PACK_CPT], gg[PACK_CPT], bb[PACK_CPT];
 };
 
-// Loads this thread's chunks of block b (tables in slot sl); zeros outside
-// the valid rows and shared indices.
-__device__ __forceinline__ void block_load(const PackJob& J, int b, int sl, const PackSmem& sm, ChunkRegs& cr) {
+// Loads this thread's chunks of virtual block v (tables in slot sl); zeros
+// outside the valid rows and shared indices.
+__device__ __forceinline__ void block_load(const PackJob& J, const VBlock& v, int sl, const PackSmem& sm,
+                                           ChunkRegs& cr) {
   const int t = threadIdx.x;
   const float* __restrict__ src = J.src;
-  const BlockGeom g = block_geom(J, b);
-  const int64_t* roff = sm.roff[sl];
-  const int64_t* koff = sm.koff[sl];
+  const int32_t* roff = sm.roff[sl];
 #pragma unroll
   for (int c = 0; c < PACK_CPT; ++c) {
     const int e = t + c * PACK_THREADS;
-    int r, grp;
+    int vr, grp;
     if (J.kfast) {
-      r = e >> 3;
+      vr = e >> 3;
       grp = e & 7;
     } else {
-      r = e & (PR - 1);
+      vr = e & (PR - 1);
       grp = e >> 7;
     }
+    const int bl = J.nbv == 1 ? 0 : vr / J.rg;
+    const int r = vr - bl * J.rg;
     cr.rr[c] = r;
     cr.gg[c] = grp;
+    cr.bb[c] = bl < v.nb ? bl : -1;
 #pragma unroll
     for (int j = 0; j < 8; ++j) cr.v[c][j] = 0.0f;
-    if (r >= g.rv) continue;
+    if (bl >= v.nb || r >= v.rv) continue;
+    const int64_t kb = (int64_t)(v.slab0 + bl) * PK;
+    const int kv = (int)(J.K - kb < PK ? J.K - kb : PK);
+    const int32_t* koff = sm.koff[sl] + bl * PK;
     const int k0 = grp * 8;
     const float* rowp = src + roff[r];
-    if (J.kfast && k0 + 7 < g.kv) {
-      const int64_t ka = koff[k0];
+    if (J.kfast && k0 + 7 < kv) {
+      const int32_t ka = koff[k0];
       if (koff[k0 + 7] == ka + 7 && (reinterpret_cast<uintptr_t>(rowp + ka) & 15) == 0) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(rowp + ka));
         const float4 d = __ldg(reinterpret_cast<const float4*>(rowp + ka) + 1);
@@ -154,36 +170,45 @@ __device__ __forceinline__ void block_load(const PackJob& J, int b, int sl, cons
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      if (k0 + j < g.kv) cr.v[c][j] = __ldg(rowp + koff[k0 + j]);
+      if (k0 + j < kv) cr.v[c][j] = __ldg(rowp + koff[k0 + j]);
   }
 }
 
-// Converts and writes this thread's chunks of block b (rows < ceil8(rv)).
-__device__ __forceinline__ void block_write(const PackJob& J, int b, const ChunkRegs& cr) {
-  const BlockGeom g = block_geom(J, b);
-  const int rs = (g.rv + 7) & ~7;
-  uint8_t* hi = J.hi + (size_t)b * (size_t)J.block_bytes;
-  uint8_t* lo = J.lo ? J.lo + (size_t)b * (size_t)J.block_bytes : nullptr;
+// Converts and writes this thread's chunks of virtual block v (rows < ceil8(rv)).
+__device__ __forceinline__ void block_write(const PackJob& J, const VBlock& v, const ChunkRegs& cr) {
+  const int rs = (v.rv + 7) & ~7;
 #pragma unroll
-  for (int c = 0; c < PACK_CPT; ++c)
-    if (cr.rr[c] < rs) store_chunk(hi, lo, sw128_chunk(cr.rr[c], cr.gg[c]), cr.v[c]);
+  for (int c = 0; c < PACK_CPT; ++c) {
+    if (cr.bb[c] < 0 || cr.rr[c] >= rs) continue;
+    const size_t b = (size_t)(v.b0 + cr.bb[c]);
+    uint8_t* hi = J.hi + b * (size_t)J.block_bytes;
+    uint8_t* lo = J.lo ? J.lo + b * (size_t)J.block_bytes : nullptr;
+    store_chunk(hi, lo, sw128_chunk(cr.rr[c], cr.gg[c]), cr.v[c]);
+  }
 }
 
-// Packs blocks first .. first+count-1 of job J (all threads of the CTA).
-// The offset tables of block j+1 are decoded into the other slot while the
-// loads of block j are in flight; one barrier per block publishes them (and
-// orders the reuse of a slot two blocks later).
+// Packs blocks first .. first+count-1 of job J (all threads of the CTA), one
+// virtual block at a time. The offset tables of the next virtual block are
+// decoded into the other slot while the loads of this one are in flight; one
+// barrier per virtual block publishes them (and orders the reuse of a slot
+// two virtual blocks later).
 __device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm) {
   if (count <= 0) return;
-  block_tables(J, first, 0, sm);
+  const int nbv = J.nbv;
+  VBlock v = vblock(J, first, min(nbv, count));
+  block_tables(J, v, 0, sm);
   __syncthreads();
   ChunkRegs cr;
-  for (int j = 0; j < count; ++j) {
-    const int sl = j & 1;
-    block_load(J, first + j, sl, sm, cr);
-    if (j + 1 < count) block_tables(J, first + j + 1, sl ^ 1, sm);
-    block_write(J, first + j, cr);
+  for (int j = 0, sl = 0; j < count; j += nbv, sl ^= 1) {
+    block_load(J, v, sl, sm, cr);
+    VBlock vn = v;
+    if (j + nbv < count) {
+      vn = vblock(J, first + j + nbv, min(nbv, count - j - nbv));
+      block_tables(J, vn, sl ^ 1, sm);
+    }
+    block_write(J, v, cr);
     __syncthreads();
+    v = vn;
   }
 }
 
@@ -259,6 +284,12 @@ struct GCfg {
   static constexpr int EPI = FUSE ? 4 : 8;             // epilogue warps
   static constexpr int ECOLS = PR * 4 / EPI;           // accumulator columns per epilogue warp
   static constexpr int THREADS = 32 * (2 + CONV + EPI);
+  // BF16 on packed operands: each epilogue warp transposes its 32 x 32 blocks
+  // through shared memory (rows padded to 33 words: conflict-free both
+  // ways), so a store instruction writes four whole 128-byte row segments
+  // of C instead of 16 bytes in each of 32 rows
+  static constexpr bool TR = !SPLIT && !FUSE;
+  static constexpr int TR_BYTES = TR ? EPI * 32 * 33 * 4 : 0;
   static_assert(!(SPLIT && FUSE), "the fused GEMM is BF16 only");
 };
 
@@ -283,7 +314,8 @@ template <int SPLIT, int FUSE>
 constexpr size_t gemm_smem_bytes() {
   using C = GCfg<SPLIT, FUSE>;
   return 1024 + (size_t)C::STAGES * C::STAGE_BYTES +
-         (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables) : 0) + sizeof(GemmAux<C::STAGES>);
+         (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables) : 0) + (size_t)C::TR_BYTES +
+         sizeof(GemmAux<C::STAGES>);
 }
 
 struct GUnit {
@@ -361,13 +393,18 @@ struct ConvIter {
 };
 
 // The table entries converter warp cw (lane l) needs for the slab `it`
-// points at: mode 1 -- row (l / 16) + 2i of its 16 (i = 0..7, on the unit's
-// first slab) and shared index 4(l % 16); mode 2 -- row group l (4 rows, on
-// the first slab) and shared indices 8cw + i. Mode 0 keeps its tables in
-// shared memory (ConvTables).
+// points at: mode 1 -- row (l / 16) + 2i of its rows (i < rpw / 2, on the
+// unit's first slab) and shared index 4(l % 16); mode 2 -- row group l (4
+// rows, on the first slab) and shared indices 8cw + i. Mode 0 keeps its
+// tables in shared memory (ConvTables).
 struct ConvRegs {
   int32_t r[8], k[8];
 };
+
+// Rows per converter warp in layout K: a tile's valid rows spread evenly over
+// the eight warps (an even count, at most 16), so a tile with few rows takes
+// proportionally less time.
+__device__ __forceinline__ int conv_rpw(int rv) { return rv >= PR ? 16 : ((((rv + 7) >> 3) + 1) & ~1); }
 
 // Entries past the operand's end are read at its last row or shared index
 // (always in bounds) and never used: no select waits on the loads, which
@@ -377,8 +414,9 @@ __device__ __forceinline__ void conv_fetch(const ConvIter& it, int cw, int l, Co
   const int64_t k0 = it.k0(), rl = it.R - 1, kl = it.K - 1;
   if (it.mode == 1) {
     if (it.ks == 0) {
+      const int rpw = conv_rpw(it.rv());
 #pragma unroll
-      for (int i = 0; i < 8; ++i) cr.r[i] = __ldg(it.rtab + min(it.p0 + 16 * cw + (l >> 4) + 2 * i, rl));
+      for (int i = 0; i < 8; ++i) cr.r[i] = __ldg(it.rtab + min(it.p0 + rpw * cw + (l >> 4) + 2 * i, rl));
     }
     cr.k[0] = __ldg(it.ktab + min(k0 + 4 * (l & 15), kl));
   } else {
@@ -394,13 +432,15 @@ __device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr
                                           uint32_t xs) {
   const int rv = it.rv(), kv = it.kv();
   const float* __restrict__ src = it.src;
+  const int rpw = conv_rpw(rv);
   if (it.mode == 1) {
-    // 16 rows x 16 chunks of 4 k; an instruction covers two 256-byte rows
+    // rpw rows x 16 chunks of 4 k; an instruction covers two 256-byte rows
     const int q = l & 15;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int r = 16 * cw + (l >> 4) + 2 * i;
-      if (r < rv && 4 * q < kv) ptx::cp_async16(xs + (uint32_t)(r * 256 + q * 16), src + cr.r[i] + cr.k[0]);
+      const int r = rpw * cw + (l >> 4) + 2 * i;
+      if (2 * i < rpw && r < rv && 4 * q < kv)
+        ptx::cp_async16(xs + (uint32_t)(r * 256 + q * 16), src + cr.r[i] + cr.k[0]);
     }
   } else if (it.mode == 2) {
     // 8 k-rows x 32 chunks of 4 rows; an instruction covers one 512-byte k-row
@@ -410,18 +450,17 @@ __device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr
       if (k < kv && 4 * l < rv) ptx::cp_async16(xs + (uint32_t)(k * 512 + l * 16), src + cr.r[0] + cr.k[i]);
     }
   } else {
-    // 16 rows x 64 k, one float each; an instruction covers 32 consecutive k
+    // rpw rows x 64 k, one float each; an instruction covers 32 consecutive k
     int32_t* roff = tb.roff[cw];
     int32_t* koff = tb.koff[cw];
     const int64_t k0 = it.k0();
     __syncwarp();  // the previous slab's copies have read the tables
-    if (it.ks == 0 && l < 16) roff[l] = 16 * cw + l < rv ? __ldg(it.rtab + it.p0 + 16 * cw + l) : 0;
+    if (it.ks == 0 && l < rpw) roff[l] = rpw * cw + l < rv ? __ldg(it.rtab + it.p0 + rpw * cw + l) : 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) koff[l + 32 * h] = l + 32 * h < kv ? __ldg(it.ktab + k0 + l + 32 * h) : 0;
     __syncwarp();
-#pragma unroll 8
-    for (int i = 0; i < 32; ++i) {
-      const int e = l + 32 * i, rl = e >> 6, k = e & 63, r = 16 * cw + rl;
+    for (int i = 0; i < 2 * rpw; ++i) {
+      const int e = l + 32 * i, rl = e >> 6, k = e & 63, r = rpw * cw + rl;
       if (r < rv && k < kv) ptx::cp_async4(xs + (uint32_t)(r * 256 + 4 * k), src + roff[rl] + koff[k]);
     }
   }
@@ -437,10 +476,23 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
   const bool full = rv == PR && kv == PK;
   float v[4][8];
   if (mode != 2) {
-    // chunk (r, g) = row r, k 8g .. 8g+7; an instruction takes 4 rows x 8
-    // chunks, the two 16-byte halves in the order that spreads its loads
-    // over all eight bank groups
-    const int g = l & 7, hf = (g >> 2) & 1;
+    // chunk (r, g) = row r, k 8g .. 8g+7 of the warp's rpw rows; an
+    // instruction takes 4 rows x 8 chunks, the two 16-byte halves in the
+    // order that spreads its loads over all eight bank groups
+    const int g = l & 7, hf = (g >> 2) & 1, rpw = conv_rpw(rv);
+    if (rpw < 16) {
+      // few rows: chunks (l / 8) + 4i of the warp's rows, i < rpw / 4
+      for (int i = 0; 4 * i < rpw; ++i) {
+        const int rl = (l >> 3) + 4 * i, r = rpw * cw + rl;
+        if (rl >= rpw) continue;
+        const float* row = reinterpret_cast<const float*>(xs + r * 256 + g * 32);
+        float u[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = (r < rv && 8 * g + j < kv) ? row[j] : 0.0f;
+        store_chunk(pt, nullptr, sw128_chunk(r, g), u);
+      }
+      return;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = 16 * cw + (l >> 3) + 4 * i;
@@ -463,16 +515,18 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
     }
   } else {
     // chunk column g = cw: rows l, l + 32, l + 64, l + 96 (an instruction
-    // covers 32 consecutive rows), one float per k-row read
-    const int g = cw;
+    // covers 32 consecutive rows; only the row blocks holding valid rows),
+    // one float per k-row read
+    const int g = cw, ni = (rv + 31) >> 5;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float* krow = reinterpret_cast<const float*>(xs + (8 * g + j) * 512);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i][j] = krow[l + 32 * i];
+      for (int i = 0; i < 4; ++i) v[i][j] = i < ni ? krow[l + 32 * i] : 0.0f;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      if (i >= ni) break;
       const int r = l + 32 * i;
       if (!full) {
 #pragma unroll
@@ -493,10 +547,13 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
   constexpr int S = Cf::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* xstage = smem + (size_t)S * Cf::STAGE_BYTES;  // fused: staging slots, then the tables
+  // after the stages: fused -- staging slots, then the tables; BF16 on
+  // packed operands -- the epilogue's transpose buffers; then the barriers
+  uint8_t* xstage = smem + (size_t)S * Cf::STAGE_BYTES;
   ConvTables& tb = *reinterpret_cast<ConvTables*>(xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES : 0));
-  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables)
-                                                                : 0));
+  float* trbuf = reinterpret_cast<float*>(xstage);
+  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(
+      xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables) : 0) + Cf::TR_BYTES);
   const uint32_t stage0 = ptx::smem_addr(smem);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
@@ -714,6 +771,26 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           }
         }
       };
+      // C row-major along j, transposed through shared memory: this warp's 32
+      // rows x 32 columns written row per lane, read back 4 rows x 8 lanes x
+      // 16 bytes per store instruction
+      float* tr = trbuf + (warp - Cf::EPI0) * (32 * 33);
+      auto emit_tr = [&](int col, const float* r) {
+        __syncwarp();  // the previous block has been read back
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tr[lane * 33 + j] = r[j];
+        __syncwarp();
+        const int64_t nrem = qcols - col;
+        const int q = lane & 7;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int rr = it * 4 + (lane >> 3);
+          const int64_t row = g.p0 + quad * 32 + rr;
+          if (row >= d.RP || 4 * q >= nrem) continue;
+          const float* sp = tr + rr * 33 + 4 * q;
+          emit4(C + row * d.ci + g.q0 + col + 4 * q, vec, nrem - 4 * q, accumulate, sp[0], sp[1], sp[2], sp[3]);
+        }
+      };
       // C row-major along j: the accumulator is read as 16-lane x 256-bit
       // blocks, so each thread holds two consecutive columns of two rows and
       // a warp's store covers 8 rows x 32 contiguous bytes (whole sectors).
@@ -790,7 +867,8 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
                 float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                emit(col0 + cb * 32, v);
+                if (Cf::TR && d.cj == 1) emit_tr(col0 + cb * 32, v);
+                else emit(col0 + cb * 32, v);
               }
             }
           }
@@ -911,6 +989,8 @@ PackJob make_job(const ContractDesc& d, const float* src, int64_t R, int nr, con
   j.tiles = (int32_t)((R + PR - 1) / PR);
   j.slabs = (int32_t)((d.K + PK - 1) / PK);
   j.block_bytes = R >= PR ? PBLOCK : ((R + 7) & ~int64_t(7)) * 128;
+  j.rg = R >= PR ? PR : (int32_t)((R + 7) & ~int64_t(7));
+  j.nbv = (R >= PR || j.rg > PR / 2) ? 1 : PR / j.rg;
   j.nr = nr;
   j.nk = d.nk;
   for (int q = 0; q < nr; ++q) {
@@ -941,9 +1021,10 @@ PackJob make_job(const ContractDesc& d, const float* src, int64_t R, int nr, con
 }
 
 // Pack blocks per CTA: about 256 KB of float32 reads (a block reads twice
-// its bf16 bytes); measured best among 64, 128, 256 and 512 KB.
+// its bf16 bytes); measured best among 64, 128, 256 and 512 KB. At most 16
+// virtual blocks.
 int32_t blocks_per_unit(const PackJob& j) {
-  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, 262144 / (2 * j.block_bytes)));
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>(16 * j.nbv, 262144 / (2 * j.block_bytes)));
 }
 
 size_t job_bytes(const PackJob& j) { return (size_t)j.tiles * j.slabs * j.block_bytes; }

@@ -29,7 +29,7 @@ struct PackJob {
   int32_t vec4;           // 16-byte copies: 1 along k, 2 along rows (every 4 consecutive
                           // elements from a 4-aligned index are contiguous and 16-byte
                           // aligned), 0 none
-  int32_t pad;
+  int32_t rg, nbv;        // pack: rows per block, and blocks packed at once (nbv * rg <= 128)
   const int32_t* rtab;    // device (fused P only): source offset of every row, R entries
   const int32_t* ktab;    // and of every shared index, K entries
   int64_t rtab_off, ktab_off;  // host: their element offsets in the plan's table region, -1 none
