@@ -260,17 +260,21 @@ constexpr int KC = 4;
 // warps at will: no barrier wider than a warp. Source offsets come from the
 // job's precomputed row and shared-index tables, loaded into registers one
 // slab before they are used, so no composite index is divided on the device.
-// Staging layouts: "K" = rows of 64 floats (256 B), a warp owning 16 rows,
-// for sources contiguous along k (16-byte copies of 4 k, a warp's lanes on
-// two 256-byte row runs) and for the 4-byte fallback (lanes on 32 consecutive
-// k); "R" = 64 k-rows of 128 floats (512 B), a warp owning 8 of them, for
-// sources contiguous along the rows (16-byte copies of 4 rows, lanes on one
-// 512-byte run). Rounding reads and writes shared memory without bank
-// conflicts in both.
+// Each warp stages its part in its own fixed 4 KB of every slot, whatever the
+// slab's layout or rows per warp, so a warp copying a later slab into a slot
+// never overwrites what another warp has yet to round from it. Staging
+// layouts of that 4 KB: "K" = up to 16 rows of 64 floats (256 B), the warp's
+// rows, for sources contiguous along k (16-byte copies of 4 k, a warp's lanes
+// on two 256-byte row runs) and for the 4-byte fallback (lanes on 32
+// consecutive k); "R" = 8 k-rows of 128 floats (512 B), the warp's 8 shared
+// indices, for sources contiguous along the rows (16-byte copies of 4 rows,
+// lanes on one 512-byte run). Rounding reads and writes shared memory without
+// bank conflicts in both.
 constexpr int CONV_WARPS = 8;
 constexpr int XSLOTS = 4;
 constexpr int XDIST = XSLOTS - 1;          // slabs copied ahead of the rounding
 constexpr int XSLOT_BYTES = PR * PK * 4;   // 32 KB
+constexpr int XPART = XSLOT_BYTES / CONV_WARPS;  // one converter warp's part of a slot (4 KB)
 
 template <int SPLIT, int FUSE>
 struct GCfg {
@@ -438,16 +442,17 @@ __device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr
     const int q = l & 15;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int r = rpw * cw + (l >> 4) + 2 * i;
+      const int rl = (l >> 4) + 2 * i, r = rpw * cw + rl;
       if (2 * i < rpw && r < rv && 4 * q < kv)
-        ptx::cp_async16(xs + (uint32_t)(r * 256 + q * 16), src + cr.r[i] + cr.k[0]);
+        ptx::cp_async16(xs + (uint32_t)(cw * XPART + rl * 256 + q * 16), src + cr.r[i] + cr.k[0]);
     }
   } else if (it.mode == 2) {
     // 8 k-rows x 32 chunks of 4 rows; an instruction covers one 512-byte k-row
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = 8 * cw + i;
-      if (k < kv && 4 * l < rv) ptx::cp_async16(xs + (uint32_t)(k * 512 + l * 16), src + cr.r[0] + cr.k[i]);
+      if (k < kv && 4 * l < rv)
+        ptx::cp_async16(xs + (uint32_t)(cw * XPART + i * 512 + l * 16), src + cr.r[0] + cr.k[i]);
     }
   } else {
     // rpw rows x 64 k, one float each; an instruction covers 32 consecutive k
@@ -461,7 +466,7 @@ __device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr
     __syncwarp();
     for (int i = 0; i < 2 * rpw; ++i) {
       const int e = l + 32 * i, rl = e >> 6, k = e & 63, r = rpw * cw + rl;
-      if (r < rv && k < kv) ptx::cp_async4(xs + (uint32_t)(r * 256 + 4 * k), src + roff[rl] + koff[k]);
+      if (r < rv && k < kv) ptx::cp_async4(xs + (uint32_t)(cw * XPART + rl * 256 + 4 * k), src + roff[rl] + koff[k]);
     }
   }
 }
@@ -485,7 +490,7 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
       for (int i = 0; 4 * i < rpw; ++i) {
         const int rl = (l >> 3) + 4 * i, r = rpw * cw + rl;
         if (rl >= rpw) continue;
-        const float* row = reinterpret_cast<const float*>(xs + r * 256 + g * 32);
+        const float* row = reinterpret_cast<const float*>(xs + cw * XPART + rl * 256 + g * 32);
         float u[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) u[j] = (r < rv && 8 * g + j < kv) ? row[j] : 0.0f;
@@ -495,8 +500,7 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int r = 16 * cw + (l >> 3) + 4 * i;
-      const uint8_t* row = xs + r * 256 + g * 32;
+      const uint8_t* row = xs + cw * XPART + ((l >> 3) + 4 * i) * 256 + g * 32;
       const float4 a = *reinterpret_cast<const float4*>(row + 16 * hf);
       const float4 b = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
       const float4 lo = hf ? b : a, hi = hf ? a : b;
@@ -520,7 +524,7 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
     const int g = cw, ni = (rv + 31) >> 5;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float* krow = reinterpret_cast<const float*>(xs + (8 * g + j) * 512);
+      const float* krow = reinterpret_cast<const float*>(xs + cw * XPART + j * 512);
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i][j] = i < ni ? krow[l + 32 * i] : 0.0f;
     }
