@@ -198,7 +198,9 @@ double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index);
  * fall in three classes, tuned one after the other: 0 thin (fewer than 128
  * rows on one side), 1 short shared index (K <= 512), 2 the rest. For each
  * class the candidates are the output tile width (128 or 64 rows of the
- * narrower operand per tile), the epilogue's tensor-memory read shape (one
+ * narrower operand per tile, and for BF16 classes 1 and 2 also 256: each
+ * block of the wider operand then feeds 256 result columns), the
+ * epilogue's tensor-memory read shape (one
  * row per thread, or 16-lane x 256-bit blocks whose stores cover whole
  * 32-byte sectors), and, for class 2, whether a contraction with at least 16
  * output tiles keeps each tile's whole k range in one work unit or cuts it
@@ -216,12 +218,12 @@ double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index);
  */
 int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
 /* The schedule a plan runs for class `cls` (0, 1, 2 as above): the output
- * tile width (128 or 64), whether long k ranges are kept whole, and whether
+ * tile width (64, 128 or 256), whether long k ranges are kept whole, and whether
  * the epilogue reads 16-lane x 256-bit blocks. Errors: TN_ERR_ARG. */
 int tn_group_plan_schedule(const tn_group_plan* plan, int cls, int* tile_width, int* long_k, int* store16);
-/* Sets that schedule by hand (tile_width 128 or 64); the plan must be
- * uploaded again before its next run. FP32 plans ignore it.
- * Errors: TN_ERR_ARG, TN_ERR_UNSUPPORTED. */
+/* Sets that schedule by hand (tile_width 64, 128, or 256 for BF16 plans);
+ * the plan must be uploaded again before its next run. FP32 plans ignore it.
+ * Errors: TN_ERR_ARG, TN_ERR_UNSUPPORTED (256 on a BF16X3 plan). */
 int tn_group_plan_set_schedule(tn_group_plan* plan, int cls, int tile_width, int long_k, int store16);
 
 /* ------------------------------------------------------------------------ */

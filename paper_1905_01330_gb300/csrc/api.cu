@@ -689,10 +689,12 @@ int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, v
   for (int cls = 0; cls < 3 && rc == TN_OK; ++cls) {
     if (!has[cls]) continue;
     cand.clear();
-    for (int w : {128, 64})
+    // 256-wide tiles (BF16): P is loaded once per 256 result columns
+    for (int w : {128, 64, 256})
       for (int s16 : {0, 1})
         for (int lk : {1, 0})
-          if (cls == 2 || lk == 1) cand.push_back(tn::PackedSchedule{w, lk, s16});
+          if ((cls == 2 || lk == 1) && (w != 256 || (plan->prec == TN_PREC_BF16 && cls != 0)))
+            cand.push_back(tn::PackedSchedule{w, lk, s16});
     float best = 0.0f;
     tn::PackedSchedule pick = plan->sched[cls];
     for (size_t c = 0; c < cand.size() && rc == TN_OK; ++c) {
@@ -719,7 +721,8 @@ int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, v
 }
 
 int tn_group_plan_set_schedule(tn_group_plan* plan, int cls, int tile_width, int long_k, int store16) {
-  if (!plan || cls < 0 || cls > 2 || (tile_width != 64 && tile_width != 128)) return TN_ERR_ARG;
+  if (!plan || cls < 0 || cls > 2 || (tile_width != 64 && tile_width != 128 && tile_width != 256)) return TN_ERR_ARG;
+  if (tile_width == 256 && plan->prec != TN_PREC_BF16) return TN_ERR_UNSUPPORTED;
   if (!plan->packed) return TN_OK;
   plan->sched[cls] = tn::PackedSchedule{tile_width, long_k ? 1 : 0, store16 ? 1 : 0};
   return build_packed(plan);

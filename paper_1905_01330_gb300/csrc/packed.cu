@@ -279,14 +279,17 @@ constexpr int XPART = XSLOT_BYTES / CONV_WARPS;  // one converter warp's part of
 template <int SPLIT, int FUSE>
 struct GCfg {
   static constexpr int OPS = SPLIT ? 4 : 2;            // P hi, Q hi (, P lo, Q lo)
-  static constexpr int STAGES = FUSE ? 3 : (SPLIT ? 3 : 6);
-  // fused: P 16 KB + Q at most 64 rows (8 KB)
-  static constexpr int STAGE_BYTES = FUSE ? PBLOCK + PBLOCK / 2 : OPS * PBLOCK;
-  static constexpr uint32_t TMEM_COLS = 256;           // two 128-column accumulators
+  // BF16 on packed operands: tiles up to 256 wide (Q up to two 128-row blocks)
+  static constexpr bool WIDE = !SPLIT && !FUSE;
+  static constexpr int STAGES = FUSE ? 3 : (SPLIT ? 3 : 4);
+  // fused: P 16 KB + Q at most 64 rows (8 KB); wide: P 16 KB + Q 32 KB
+  static constexpr int STAGE_BYTES = FUSE ? PBLOCK + PBLOCK / 2 : (WIDE ? 3 * PBLOCK : OPS * PBLOCK);
+  static constexpr int ACC_COLS = WIDE ? 256 : 128;   // columns of one accumulator
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS; // two accumulators
   static constexpr int CONV = FUSE ? CONV_WARPS : 0;
   static constexpr int EPI0 = 2 + CONV;                // first epilogue warp
   static constexpr int EPI = FUSE ? 4 : 8;             // epilogue warps
-  static constexpr int ECOLS = PR * 4 / EPI;           // accumulator columns per epilogue warp
+  static constexpr int ECOLS = ACC_COLS * 4 / EPI;     // at most this many accumulator columns per warp
   static constexpr int THREADS = 32 * (2 + CONV + EPI);
   // BF16 on packed operands: each epilogue warp transposes its 32 x 32 blocks
   // through shared memory (rows padded to 33 words: conflict-free both
@@ -596,8 +599,10 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qleft = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
+        // a 256-wide tile takes its Q rows from two consecutive 128-row blocks
         const uint32_t pb = FUSE ? 0u : rows_bytes(d.RP - g.p0), qb = rows_bytes(qleft);
-        const uint32_t tx = (pb + qb) * (SPLIT ? 2u : 1u);
+        const uint32_t qb2 = qleft > PR ? rows_bytes(qleft - PR) : 0u;
+        const uint32_t tx = (pb + qb + qb2) * (SPLIT ? 2u : 1u);
         const uint8_t* pbase = d.P + ((g.p0 / PR) * d.slabs + g.ks0) * d.P_block;
         // a 64-row tile starts 64 rows (8 atoms, 8 KB) into its 128-row block
         const uint8_t* qbase = d.Q + ((g.q0 / PR) * d.slabs + g.ks0) * d.Q_block + (g.q0 % PR) * 128;
@@ -610,6 +615,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           ptx::mbar_arrive_expect_tx(full, tx);
           if (!FUSE) ptx::bulk_copy_g2s(st, pbase + ks * d.P_block, pb, full);
           ptx::bulk_copy_g2s(st + PBLOCK, qbase + ks * d.Q_block, qb, full);
+          if (qb2) ptx::bulk_copy_g2s(st + 2 * PBLOCK, qbase + (d.slabs + ks) * d.Q_block, qb2, full);
           if (SPLIT) {
             ptx::bulk_copy_g2s(st + 2 * PBLOCK, pbase + d.P_lo + ks * d.P_block, pb, full);
             ptx::bulk_copy_g2s(st + 3 * PBLOCK, qbase + d.Q_lo + ks * d.Q_block, qb, full);
@@ -640,7 +646,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           const int b = (int)(gc & 1);
           if (!ptx::mbar_wait(ptx::smem_addr(&x.acc_empty[b]), ((gc >> 1) & 1u) ^ 1u, status)) { ok = false; break; }
           ptx::tc_fence_after();
-          const uint32_t dt = tmem + (uint32_t)(b * PR);
+          const uint32_t dt = tmem + (uint32_t)(b * Cf::ACC_COLS);
           const int c1 = min(g.nks, c0 + chunk);
           for (int ks = c0; ks < c1; ++ks, ++gs) {
             const int s = (int)(gs % S);
@@ -728,7 +734,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;            // TMEM lanes quad*32 .. quad*32+31
     constexpr int ECOLS = Cf::ECOLS;
-    const int col0 = ((warp - Cf::EPI0) >> 2) * ECOLS;  // first accumulator column of this warp
+    const int grp = (warp - Cf::EPI0) >> 2;  // column group of this warp (eight warps: two groups)
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     uint32_t gc = 0;
     GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
@@ -738,6 +744,12 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       const GUnit g = gunit(d, u - d.tile_begin);
       const int64_t i = g.p0 + quad * 32 + lane;            // row of P this thread owns
       const int64_t qcols = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
+      // columns of the tile this warp drains: eight warps split the tile
+      // width in two (the 64-column reads of the 16x256b shape: in 64s)
+      const bool rows16 = d.cj == 1 && d.store16 != 0;
+      const int span = Cf::EPI == 8 ? d.q_tile / 2 : d.q_tile;
+      const int gspan = rows16 && span < 64 ? 64 : span;
+      const int col0 = grp * gspan;
       const int chunk = SPLIT ? KC : g.nks;
       const int nchunks = (g.nks + chunk - 1) / chunk;
       const bool accumulate = d.splits > 1;
@@ -798,7 +810,6 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       // C row-major along j: the accumulator is read as 16-lane x 256-bit
       // blocks, so each thread holds two consecutive columns of two rows and
       // a warp's store covers 8 rows x 32 contiguous bytes (whole sectors).
-      const bool rows16 = d.cj == 1 && d.store16 != 0;
       const bool vec2 = rows16 && ((d.ci & 1) == 0) && (((reinterpret_cast<uintptr_t>(C) >> 2) + g.q0) & 1) == 0 &&
                         ((reinterpret_cast<uintptr_t>(C) & 7) == 0);
       // values r[4j..4j+3] of lane half h (rows +0 and +8), columns
@@ -839,9 +850,9 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
             const int cbase = col0 + 64 * blk;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              if (cbase < qcols) {  // uniform across the warp
+              if (64 * blk < gspan && cbase < qcols) {  // uniform across the warp
                 uint32_t r[32];
-                ptx::tmem_ld_16x256b_x8(tmem + ((uint32_t)(quad * 32 + h * 16) << 16) + (uint32_t)(b * PR + cbase),
+                ptx::tmem_ld_16x256b_x8(tmem + ((uint32_t)(quad * 32 + h * 16) << 16) + (uint32_t)(b * Cf::ACC_COLS + cbase),
                                         r);
                 ptx::tmem_ld_wait();
                 if (SPLIT) {
@@ -857,17 +868,27 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
             }
           }
         } else {
-          const uint32_t ta = tmem + lane_base + (uint32_t)(b * PR + col0);
+          const uint32_t ta = tmem + lane_base + (uint32_t)(b * Cf::ACC_COLS + col0);
+          if constexpr (SPLIT) {
 #pragma unroll
-          for (int cb = 0; cb < ECOLS / 32; ++cb) {
-            if (col0 + cb * 32 < qcols) {  // uniform across the warp
-              uint32_t r[32];
-              ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
-              ptx::tmem_ld_wait();
-              if (SPLIT) {
+            for (int cb = 0; cb < ECOLS / 32; ++cb) {
+              if (32 * cb < gspan && col0 + cb * 32 < qcols) {  // uniform across the warp
+                uint32_t r[32];
+                ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
+                ptx::tmem_ld_wait();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) acc[cb * 32 + j] += __uint_as_float(r[j]);
-              } else {
+              }
+            }
+          } else {
+            // one 32-column block at a time (a loop, not unrolled: one
+            // block's registers live at once)
+#pragma unroll 1
+            for (int cb = 0; cb < ECOLS / 32; ++cb) {
+              if (32 * cb < gspan && col0 + cb * 32 < qcols) {  // uniform across the warp
+                uint32_t r[32];
+                ptx::tmem_ld_32x32b_x32(ta + (uint32_t)(cb * 32), r);
+                ptx::tmem_ld_wait();
                 float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
@@ -888,11 +909,11 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           for (int blk = 0; blk < ECOLS / 64; ++blk)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-              if (col0 + 64 * blk < qcols) emit16(h, &acc[blk * 64 + h * 32], col0 + 64 * blk);
+              if (64 * blk < gspan && col0 + 64 * blk < qcols) emit16(h, &acc[blk * 64 + h * 32], col0 + 64 * blk);
         } else {
 #pragma unroll
           for (int cb = 0; cb < ECOLS / 32; ++cb)
-            if (col0 + cb * 32 < qcols) emit(col0 + cb * 32, &acc[cb * 32]);
+            if (32 * cb < gspan && col0 + cb * 32 < qcols) emit(col0 + cb * 32, &acc[cb * 32]);
         }
       }
     }
@@ -1048,7 +1069,7 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
   const PackJob& jq = swap ? ja : jb;
   g.P_block = jp.block_bytes;
   g.Q_block = jq.block_bytes;
-  g.q_tile = q_tile == 64 ? 64 : PR;
+  g.q_tile = q_tile == 64 ? 64 : (q_tile == 256 ? 256 : PR);
   g.tiles_p = jp.tiles;
   g.tiles_q = (int32_t)((g.RQ + g.q_tile - 1) / g.q_tile);
   g.slabs = ja.slabs;

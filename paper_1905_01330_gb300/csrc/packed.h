@@ -58,7 +58,7 @@ struct GemmDesc {
   int64_t K;              // shared extent (host: algorithmic bytes)
   uint64_t P_off, Q_off;  // host: offsets of the hi blocks in the packed region
   int32_t tiles_p, tiles_q, slabs, splits, slabs_per_split;
-  int32_t q_tile;         // rows of Q per unit (the output tile's width): 128 or 64
+  int32_t q_tile;         // rows of Q per unit (the output tile's width): 64, 128, or 256 (BF16)
   int32_t store16;        // C row-major along j: drain TMEM as 16-lane x 256-bit blocks
                           // (whole-sector stores) instead of one row per thread
   int32_t pjob;           // fused: index of P's job in the job list (P is read as float32
