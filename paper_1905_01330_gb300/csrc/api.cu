@@ -693,7 +693,10 @@ int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, v
     for (int w : {128, 64, 256})
       for (int s16 : {0, 1})
         for (int lk : {1, 0})
-          if ((cls == 2 || lk == 1) && (w != 256 || (plan->prec == TN_PREC_BF16 && cls != 0)))
+          // (BF16 stores through the epilogue's shared-memory transpose in
+          // both read shapes: one candidate each)
+          if ((cls == 2 || lk == 1) && (w != 256 || (plan->prec == TN_PREC_BF16 && cls != 0)) &&
+              !(s16 && plan->prec == TN_PREC_BF16 && cls != 0))
             cand.push_back(tn::PackedSchedule{w, lk, s16});
     float best = 0.0f;
     tn::PackedSchedule pick = plan->sched[cls];

@@ -330,15 +330,16 @@ struct GUnit {
   int32_t ks0, nks;      // first slab and slab count
 };
 
+// Unit u of descriptor d (u < 2^31: the host rejects larger launches); 32-bit
+// division, far cheaper on the device than 64-bit.
 __device__ __forceinline__ GUnit gunit(const GemmDesc& d, int64_t u) {
   GUnit g;
-  const int64_t tq = u % d.tiles_q;
-  const int64_t rest = u / d.tiles_q;
-  const int64_t tp = rest % d.tiles_p;
-  const int64_t split = rest / d.tiles_p;
-  g.p0 = tp * PR;
-  g.q0 = tq * d.q_tile;
-  g.ks0 = (int32_t)(split * d.slabs_per_split);
+  const uint32_t uu = (uint32_t)u, nq = (uint32_t)d.tiles_q, np = (uint32_t)d.tiles_p;
+  const uint32_t rest = uu / nq, tq = uu - rest * nq;
+  const uint32_t split = rest / np, tp = rest - split * np;
+  g.p0 = (int64_t)tp * PR;
+  g.q0 = (int64_t)tq * d.q_tile;
+  g.ks0 = (int32_t)(split * (uint32_t)d.slabs_per_split);
   g.nks = (int32_t)(d.slabs - g.ks0 < d.slabs_per_split ? d.slabs - g.ks0 : d.slabs_per_split);
   return g;
 }
@@ -353,6 +354,46 @@ __device__ __forceinline__ uint32_t rows_bytes(int64_t rows_left) {
 __device__ __forceinline__ GemmDesc load_desc(const GemmDesc& single, const GemmDesc* descs, const int32_t* map,
                                               int64_t u) {
   return descs ? descs[__ldg(map + u)] : single;
+}
+
+// The fields of a unit's descriptor the epilogue uses, loaded one by one (a
+// copy of the whole descriptor, current and next, would hold ~80 registers).
+struct EpiDesc {
+  float* C;
+  int64_t ci, cj, RP, RQ, tile_begin;
+  int32_t tiles_q, tiles_p, slabs, slabs_per_split, q_tile, splits, store16;
+};
+
+__device__ __forceinline__ EpiDesc load_epi(const GemmDesc& single, const GemmDesc* descs, const int32_t* map,
+                                           int64_t u) {
+  const GemmDesc* d = descs ? descs + __ldg(map + u) : &single;
+  EpiDesc e;
+  e.C = d->C;
+  e.ci = d->ci;
+  e.cj = d->cj;
+  e.RP = d->RP;
+  e.RQ = d->RQ;
+  e.tile_begin = d->tile_begin;
+  e.tiles_q = d->tiles_q;
+  e.tiles_p = d->tiles_p;
+  e.slabs = d->slabs;
+  e.slabs_per_split = d->slabs_per_split;
+  e.q_tile = d->q_tile;
+  e.splits = d->splits;
+  e.store16 = d->store16;
+  return e;
+}
+
+__device__ __forceinline__ GUnit gunit(const EpiDesc& d, int64_t u) {
+  GUnit g;
+  const uint32_t uu = (uint32_t)u, nq = (uint32_t)d.tiles_q, np = (uint32_t)d.tiles_p;
+  const uint32_t rest = uu / nq, tq = uu - rest * nq;
+  const uint32_t split = rest / np, tp = rest - split * np;
+  g.p0 = (int64_t)tp * PR;
+  g.q0 = (int64_t)tq * d.q_tile;
+  g.ks0 = (int32_t)(split * (uint32_t)d.slabs_per_split);
+  g.nks = (int32_t)(d.slabs - g.ks0 < d.slabs_per_split ? d.slabs - g.ks0 : d.slabs_per_split);
+  return g;
 }
 
 // Walks this CTA's (unit, slab) pairs in the order the copy warp and the MMA
@@ -489,14 +530,19 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
     // order that spreads its loads over all eight bank groups
     const int g = l & 7, hf = (g >> 2) & 1, rpw = conv_rpw(rv);
     if (rpw < 16) {
-      // few rows: chunks (l / 8) + 4i of the warp's rows, i < rpw / 4
+      // few rows: chunks (l / 8) + 4i of the warp's rows, i < rpw / 4 (the
+      // same bank-group order of the two 16-byte halves as below)
       for (int i = 0; 4 * i < rpw; ++i) {
         const int rl = (l >> 3) + 4 * i, r = rpw * cw + rl;
         if (rl >= rpw) continue;
-        const float* row = reinterpret_cast<const float*>(xs + cw * XPART + rl * 256 + g * 32);
-        float u[8];
+        const uint8_t* row = xs + cw * XPART + rl * 256 + g * 32;
+        const float4 a = *reinterpret_cast<const float4*>(row + 16 * hf);
+        const float4 b = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
+        const float4 lo = hf ? b : a, hi = hf ? a : b;
+        float u[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int j = 0; j < 8; ++j) u[j] = (r < rv && 8 * g + j < kv) ? row[j] : 0.0f;
+        for (int j = 0; j < 8; ++j)
+          if (!(r < rv && 8 * g + j < kv)) u[j] = 0.0f;
         store_chunk(pt, nullptr, sw128_chunk(r, g), u);
       }
       return;
@@ -737,16 +783,18 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
     const int grp = (warp - Cf::EPI0) >> 2;  // column group of this warp (eight warps: two groups)
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     uint32_t gc = 0;
-    GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
+    EpiDesc dn = load_epi(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
     for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
-      const GemmDesc d = dn;
-      if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
+      const EpiDesc d = dn;
+      if (u + gridDim.x < total_units) dn = load_epi(single, descs, map, u + gridDim.x);
       const GUnit g = gunit(d, u - d.tile_begin);
       const int64_t i = g.p0 + quad * 32 + lane;            // row of P this thread owns
       const int64_t qcols = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
       // columns of the tile this warp drains: eight warps split the tile
       // width in two (the 64-column reads of the 16x256b shape: in 64s)
-      const bool rows16 = d.cj == 1 && d.store16 != 0;
+      // (BF16 on packed operands stores through the shared-memory
+      // transpose instead: whole 128-byte row segments)
+      const bool rows16 = !Cf::TR && d.cj == 1 && d.store16 != 0;
       const int span = Cf::EPI == 8 ? d.q_tile / 2 : d.q_tile;
       const int gspan = rows16 && span < 64 ? 64 : span;
       const int col0 = grp * gspan;

@@ -112,7 +112,15 @@ def test_every_schedule_keeps_parity(tn, prec):
         At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
         specs.append((At, la, Bt, lb, torch.empty(tn.result_shape(At, la, Bt, lb), device="cuda")))
     plan = tn.GroupPlan(specs, prec=prec)
-    for width, long_k, store16 in ((128, 1, 0), (64, 1, 1), (128, 0, 1), (64, 0, 0)):
+    schedules = [(128, 1, 0), (64, 1, 1), (128, 0, 1), (64, 0, 0)]
+    if prec == "bf16":
+        # 256-wide tiles: Q from two 128-row blocks, a partial second block
+        # (520 = 2 x 256 + 8, 264 = 256 + 8 rows), a single block (384 = 256 + 128)
+        schedules += [(256, 1, 0), (256, 0, 1)]
+    else:
+        with pytest.raises(tn.TnError):
+            plan.set_schedule("long_k", 256, True, False)
+    for width, long_k, store16 in schedules:
         for cls in plan.SCHEDULE_CLASSES:
             plan.set_schedule(cls, width, long_k, store16)
         assert plan.schedule() == {c: (width, long_k, store16) for c in plan.SCHEDULE_CLASSES}
