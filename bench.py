@@ -8,10 +8,13 @@ drawn on the device (torch Philox, seeded). 2.01 TFLOP and 31.9 GB of
 float32 operands and results per step, far larger than L2 (129 MB), so no
 L2 flush is needed between steps.
 
-One step = one tn_group_plan_run (pack + GEMM, plus a zeroing launch for
-the results accumulated over split k ranges). The line also
-reports the split-bf16x3 and plain-fp32 paths on the same workload, the
-end-to-end rate through the C ABI with pinned host buffers, the roofline of
+One step = one tn_group_plan_run (pack, the GEMM on packed operands and the
+fused GEMM of the thin contractions, plus a zeroing launch for the results
+accumulated over split k ranges). The operands live in one device buffer
+and the results in another (each tensor a view). The line also reports the
+split-bf16x3 and plain-fp32 paths on the same workload, the end-to-end rate
+through the C ABI (each step: one host-to-device copy of all operands from a
+pinned buffer, the run, one device-to-host copy of all results), the roofline of
 the dominant kernel, SM clocks sampled during the timed region, and the FP64
 CPU oracle timed on a bounded sample (first 16 specs) on the host cores.
 
@@ -439,11 +442,30 @@ def main():
     specs_h = synth.contraction_specs(N_SPECS, seed=SEED)[:args.specs]
     gen = torch.Generator(device=dev)
     gen.manual_seed(tndist.data_seed(SEED, rank))
+    # all operands in one device buffer and all results in another (each
+    # tensor a view starting on a 256-byte boundary), so a step's inputs and
+    # results move between host and device as one copy each
+    def layout(shapes):
+        offs, n = [], 0
+        for sh in shapes:
+            offs.append(n)
+            n += (int(np.prod(sh)) + 63) // 64 * 64
+        return offs, n
+    in_shapes = [sh for sa, _, sb, _ in specs_h for sh in (sa, sb)]
+    out_shapes = [tuple(sa[p] for p in range(len(sa)) if p not in la) + tuple(sb[p] for p in range(len(sb)) if p not in lb)
+                  for sa, la, sb, lb in specs_h]
+    in_offs, n_in = layout(in_shapes)
+    out_offs, n_out_all = layout(out_shapes)
+    big_in = torch.empty(n_in, device=dev)
+    big_out = torch.empty(n_out_all, device=dev)
     specs = []
-    for sa, la, sb, lb in specs_h:
-        At = torch.randn(sa, device=dev, generator=gen)
-        Bt = torch.randn(sb, device=dev, generator=gen)
-        Ct = torch.empty(tn.result_shape(At, la, Bt, lb), device=dev)
+    for i, (sa, la, sb, lb) in enumerate(specs_h):
+        At = big_in[in_offs[2 * i]:in_offs[2 * i] + int(np.prod(sa))].view(sa)
+        Bt = big_in[in_offs[2 * i + 1]:in_offs[2 * i + 1] + int(np.prod(sb))].view(sb)
+        At.normal_(generator=gen)
+        Bt.normal_(generator=gen)
+        Ct = big_out[out_offs[i]:out_offs[i] + int(np.prod(out_shapes[i]))].view(out_shapes[i])
+        assert tuple(Ct.shape) == tuple(tn.result_shape(At, la, Bt, lb))
         specs.append((At, list(la), Bt, list(lb), Ct))
     stream = torch.cuda.current_stream(dev)
     var_list = [] if args.variants == "none" else [v for v in args.variants.split(",") if v]
@@ -511,21 +533,20 @@ def main():
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
-        host_in = [(A.cpu().pin_memory(), B.cpu().pin_memory()) for A, _, B, _, _ in specs]
-        host_out = [torch.empty(C.shape, dtype=torch.float32, pin_memory=True) for *_, C in specs]
-        h2d = sum(a.numel() * 4 + b.numel() * 4 for a, b in host_in)
-        d2h = sum(c.numel() * 4 for c in host_out)
+        # one pinned host buffer for the operands, one for the results, laid
+        # out like the device buffers
+        host_in = big_in.cpu().pin_memory()
+        host_out = torch.empty(big_out.shape, dtype=torch.float32, pin_memory=True)
+        h2d = sum(A.numel() * 4 + B.numel() * 4 for A, _, B, _, _ in specs)
+        d2h = sum(C.numel() * 4 for *_, C in specs)
         torch.cuda.synchronize(dev)
         barrier()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         for _ in range(args.e2e_steps):
-            for (ha, hb), (A, _, B, _, _) in zip(host_in, specs):
-                A.copy_(ha, non_blocking=True)
-                B.copy_(hb, non_blocking=True)
+            big_in.copy_(host_in, non_blocking=True)
             plan.run()
-            for hc, (*_, C) in zip(host_out, specs):
-                hc.copy_(C, non_blocking=True)
+            host_out.copy_(big_out, non_blocking=True)
         s1.record(stream)
         torch.cuda.synchronize(dev)
         e_ms = s0.elapsed_time(s1) / args.e2e_steps
