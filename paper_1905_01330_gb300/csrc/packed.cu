@@ -292,11 +292,12 @@ struct GCfg {
   static constexpr int ECOLS = ACC_COLS * 4 / EPI;     // at most this many accumulator columns per warp
   static constexpr int THREADS = 32 * (2 + CONV + EPI);
   // BF16 on packed operands: each epilogue warp transposes its 32 x 32 blocks
-  // through shared memory (rows padded to 33 words: conflict-free both
-  // ways), so a store instruction writes four whole 128-byte row segments
-  // of C instead of 16 bytes in each of 32 rows
+  // through shared memory (16-byte chunks of a row XOR-permuted by row % 8:
+  // 16-byte accesses conflict-free both ways), so a store instruction writes
+  // four whole 128-byte row segments of C instead of 16 bytes in each of 32
+  // rows
   static constexpr bool TR = !SPLIT && !FUSE;
-  static constexpr int TR_BYTES = TR ? EPI * 32 * 33 * 4 : 0;
+  static constexpr int TR_BYTES = TR ? EPI * 32 * 32 * 4 : 0;
   static_assert(!(SPLIT && FUSE), "the fused GEMM is BF16 only");
 };
 
@@ -836,13 +837,16 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         }
       };
       // C row-major along j, transposed through shared memory: this warp's 32
-      // rows x 32 columns written row per lane, read back 4 rows x 8 lanes x
-      // 16 bytes per store instruction
-      float* tr = trbuf + (warp - Cf::EPI0) * (32 * 33);
+      // rows x 32 columns written row per lane (chunk c of row r at slot
+      // c ^ (r % 8)), read back 4 rows x 8 lanes x 16 bytes per store
+      // instruction
+      float* tr = trbuf + (warp - Cf::EPI0) * (32 * 32);
       auto emit_tr = [&](int col, const float* r) {
         __syncwarp();  // the previous block has been read back
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tr[lane * 33 + j] = r[j];
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<float4*>(tr + lane * 32 + ((c ^ (lane & 7)) << 2)) =
+              make_float4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
         __syncwarp();
         const int64_t nrem = qcols - col;
         const int q = lane & 7;
@@ -851,8 +855,8 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           const int rr = it * 4 + (lane >> 3);
           const int64_t row = g.p0 + quad * 32 + rr;
           if (row >= d.RP || 4 * q >= nrem) continue;
-          const float* sp = tr + rr * 33 + 4 * q;
-          emit4(C + row * d.ci + g.q0 + col + 4 * q, vec, nrem - 4 * q, accumulate, sp[0], sp[1], sp[2], sp[3]);
+          const float4 v4 = *reinterpret_cast<const float4*>(tr + rr * 32 + ((q ^ (rr & 7)) << 2));
+          emit4(C + row * d.ci + g.q0 + col + 4 * q, vec, nrem - 4 * q, accumulate, v4.x, v4.y, v4.z, v4.w);
         }
       };
       // C row-major along j: the accumulator is read as 16-lane x 256-bit
