@@ -433,7 +433,12 @@ struct ConvIter {
   __device__ __forceinline__ bool valid() const { return u < total; }
   __device__ __forceinline__ int64_t k0() const { return (int64_t)(ks0 + ks) * PK; }
   __device__ __forceinline__ int rv() const { return (int)(R - p0 < PR ? R - p0 : PR); }
-  __device__ __forceinline__ int kv() const { return (int)(K - k0() < PK ? K - k0() : PK); }
+  // shared indices left from this slab on: K - k0 < 2^31 (operands span
+  // fewer than 2^31 elements), so 32-bit arithmetic suffices
+  __device__ __forceinline__ int kv() const {
+    const int left = (int)K - (ks0 + ks) * PK;
+    return left < PK ? left : PK;
+  }
   // what rounding needs, in one word: valid (bit 0), copy mode (bits 1-2),
   // valid rows (bits 3-10), valid shared indices (11-17)
   __device__ __forceinline__ uint32_t info() const {
@@ -483,21 +488,32 @@ __device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr
   const float* __restrict__ src = it.src;
   const int rpw = conv_rpw(rv);
   if (it.mode == 1) {
-    // rpw rows x 16 chunks of 4 k; an instruction covers two 256-byte rows
+    // rpw rows x 16 chunks of 4 k; an instruction covers two 256-byte rows.
+    // Chunk q lands at position q ^ ((q >> 3) & 1) of its row (see conv_round).
     const int q = l & 15;
+    const uint32_t dst = xs + (uint32_t)(cw * XPART + (l >> 4) * 256 + ((q ^ ((q >> 3) & 1)) << 4));
+    const float* base = src + cr.k[0];
+    if (rv == PR && kv == PK) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int rl = (l >> 4) + 2 * i, r = rpw * cw + rl;
-      if (2 * i < rpw && r < rv && 4 * q < kv)
-        ptx::cp_async16(xs + (uint32_t)(cw * XPART + rl * 256 + q * 16), src + cr.r[i] + cr.k[0]);
+      for (int i = 0; i < 8; ++i) ptx::cp_async16(dst + i * 512, base + cr.r[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rpw * cw + (l >> 4) + 2 * i;
+        if (2 * i < rpw && r < rv && 4 * q < kv) ptx::cp_async16(dst + i * 512, base + cr.r[i]);
+      }
     }
   } else if (it.mode == 2) {
     // 8 k-rows x 32 chunks of 4 rows; an instruction covers one 512-byte k-row
+    const uint32_t dst = xs + (uint32_t)(cw * XPART + l * 16);
+    const float* base = src + cr.r[0];
+    if (rv == PR && kv == PK) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int k = 8 * cw + i;
-      if (k < kv && 4 * l < rv)
-        ptx::cp_async16(xs + (uint32_t)(cw * XPART + i * 512 + l * 16), src + cr.r[0] + cr.k[i]);
+      for (int i = 0; i < 8; ++i) ptx::cp_async16(dst + i * 512, base + cr.k[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (8 * cw + i < kv && 4 * l < rv) ptx::cp_async16(dst + i * 512, base + cr.k[i]);
     }
   } else {
     // rpw rows x 64 k, one float each; an instruction covers 32 consecutive k
@@ -511,7 +527,9 @@ __device__ __forceinline__ void conv_copy(const ConvIter& it, const ConvRegs& cr
     __syncwarp();
     for (int i = 0; i < 2 * rpw; ++i) {
       const int e = l + 32 * i, rl = e >> 6, k = e & 63, r = rpw * cw + rl;
-      if (r < rv && k < kv) ptx::cp_async4(xs + (uint32_t)(cw * XPART + rl * 256 + 4 * k), src + roff[rl] + koff[k]);
+      const int qk = k >> 2, pos = qk ^ ((qk >> 3) & 1);  // chunk position, as in mode 1
+      if (r < rv && k < kv)
+        ptx::cp_async4(xs + (uint32_t)(cw * XPART + rl * 256 + pos * 16 + 4 * (k & 3)), src + roff[rl] + koff[k]);
     }
   }
 }
@@ -527,8 +545,10 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
   float v[4][8];
   if (mode != 2) {
     // chunk (r, g) = row r, k 8g .. 8g+7 of the warp's rpw rows; an
-    // instruction takes 4 rows x 8 chunks, the two 16-byte halves in the
-    // order that spreads its loads over all eight bank groups
+    // instruction takes 4 rows x 8 chunks. The copies stored the two 16-byte
+    // halves of chunk g swapped when g >= 4 (hf = 1), so reading the half at
+    // position 2g + hf first takes k 8g .. 8g+3 and spreads the
+    // instruction's loads over all eight bank groups
     const int g = l & 7, hf = (g >> 2) & 1, rpw = conv_rpw(rv);
     if (rpw < 16) {
       // few rows: chunks (l / 8) + 4i of the warp's rows, i < rpw / 4 (the
@@ -537,9 +557,8 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
         const int rl = (l >> 3) + 4 * i, r = rpw * cw + rl;
         if (rl >= rpw) continue;
         const uint8_t* row = xs + cw * XPART + rl * 256 + g * 32;
-        const float4 a = *reinterpret_cast<const float4*>(row + 16 * hf);
-        const float4 b = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
-        const float4 lo = hf ? b : a, hi = hf ? a : b;
+        const float4 lo = *reinterpret_cast<const float4*>(row + 16 * hf);
+        const float4 hi = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
         float u[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -551,9 +570,8 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const uint8_t* row = xs + cw * XPART + ((l >> 3) + 4 * i) * 256 + g * 32;
-      const float4 a = *reinterpret_cast<const float4*>(row + 16 * hf);
-      const float4 b = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
-      const float4 lo = hf ? b : a, hi = hf ? a : b;
+      const float4 lo = *reinterpret_cast<const float4*>(row + 16 * hf);
+      const float4 hi = *reinterpret_cast<const float4*>(row + 16 * (1 - hf));
       v[i][0] = lo.x; v[i][1] = lo.y; v[i][2] = lo.z; v[i][3] = lo.w;
       v[i][4] = hi.x; v[i][5] = hi.y; v[i][6] = hi.z; v[i][7] = hi.w;
     }
