@@ -70,6 +70,9 @@ constexpr int PACK_CPT = 4;  // chunks per thread and block (1024 chunks / 256 t
 struct PackSmem {
   int32_t roff[2][PR];           // source offset of each row of the tile (valid rows only)
   int32_t koff[2][PR * PK / 8];  // source offset of each shared index of the nbv slabs
+  PackJob job;                   // the CTA's job, copied in once (its fields are read
+                                 // throughout; from global memory each read would be a
+                                 // long-latency load)
 };
 constexpr size_t PACK_SMEM = sizeof(PackSmem);
 
@@ -213,12 +216,22 @@ __device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int cou
 }
 
 // Grouped form: one CTA per pack unit of the uploaded lists.
+// Copies job J into shared memory (all threads, then a barrier).
+__device__ __forceinline__ void stage_job(const PackJob& J, PackSmem& sm) {
+  static_assert(sizeof(PackJob) % 4 == 0, "PackJob is copied as 32-bit words");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&J);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.job);
+  for (int i = threadIdx.x; i < (int)(sizeof(PackJob) / 4); i += PACK_THREADS) dst[i] = src[i];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(PACK_THREADS)
 pack_kernel(const PackJob* __restrict__ jobs, const PackUnit* __restrict__ units) {
   extern __shared__ __align__(16) uint8_t pack_smem_raw[];
   PackSmem& sm = *reinterpret_cast<PackSmem*>(pack_smem_raw);
   const PackUnit un = units[blockIdx.x];
-  pack_blocks(jobs[un.job], un.first, un.count, sm);
+  stage_job(jobs[un.job], sm);
+  pack_blocks(sm.job, un.first, un.count, sm);
 }
 
 // Single-contraction form: both jobs passed by value (nothing to upload, so
@@ -234,7 +247,8 @@ pack_pair_kernel(const __grid_constant__ PackPair pp) {
   extern __shared__ __align__(16) uint8_t pack_smem_raw[];
   PackSmem& sm = *reinterpret_cast<PackSmem*>(pack_smem_raw);
   const bool is_a = (int)blockIdx.x < pp.units_a;
-  const PackJob& J = is_a ? pp.a : pp.b;
+  stage_job(is_a ? pp.a : pp.b, sm);
+  const PackJob& J = sm.job;
   const int per = is_a ? pp.per_a : pp.per_b;
   const int first = (is_a ? (int)blockIdx.x : (int)blockIdx.x - pp.units_a) * per;
   const int nb = J.tiles * J.slabs;
