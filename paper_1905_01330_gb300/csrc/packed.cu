@@ -285,6 +285,11 @@ constexpr int KC = 4;
 // lanes on one 512-byte run). Rounding reads and writes shared memory without
 // bank conflicts in both.
 constexpr int CONV_WARPS = 8;
+// MN-major bf16 P tile (P contiguous along its rows): atoms of 8 k-rows x 64
+// rows (128 B per k-row, 128-byte swizzle), the two 64-row halves MN_HALF
+// bytes apart, 8-row k groups MN_KGROUP bytes apart
+constexpr uint32_t MN_HALF = 8192;
+constexpr uint32_t MN_KGROUP = 1024;
 constexpr int XSLOTS = 4;
 constexpr int XDIST = XSLOTS - 1;          // slabs copied ahead of the rounding
 constexpr int XSLOT_BYTES = PR * PK * 4;   // 32 KB
@@ -600,26 +605,23 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
       store_chunk(pt, nullptr, sw128_chunk(r, g), v[i]);
     }
   } else {
-    // chunk column g = cw: rows l, l + 32, l + 64, l + 96 (an instruction
-    // covers 32 consecutive rows; only the row blocks holding valid rows),
-    // one float per k-row read
-    const int g = cw, ni = (rv + 31) >> 5;
+    // MN-major tile: the warp's k group g = cw (8 k-rows), rows 4l .. 4l+3
+    // of each: one 16-byte load of 4 rows per k-row, rounded to 4 bf16 and
+    // stored as 8 bytes at row group l / 2 (k-row chunks XOR-swizzled by k %
+    // 8, as the MN-major descriptor reads them). Shared indices past kv are
+    // zeros; rows past rv are never stored, so they may hold anything.
+    const int g = cw, mg = l >> 1;
+    const uint32_t base = (uint32_t)((mg >> 3) * MN_HALF + g * MN_KGROUP + (l & 1) * 8);
+    float4 f[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = *reinterpret_cast<const float4*>(xs + cw * XPART + j * 512 + l * 16);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float* krow = reinterpret_cast<const float*>(xs + cw * XPART + j * 512);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) v[i][j] = i < ni ? krow[l + 32 * i] : 0.0f;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (i >= ni) break;
-      const int r = l + 32 * i;
-      if (!full) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (!(r < rv && 8 * g + j < kv)) v[i][j] = 0.0f;
-      }
-      store_chunk(pt, nullptr, sw128_chunk(r, g), v[i]);
+      const bool ok = full || 8 * g + j < kv;
+      uint2 h;
+      h.x = ok ? bf16x2_rn(f[j].x, f[j].y) : 0u;
+      h.y = ok ? bf16x2_rn(f[j].z, f[j].w) : 0u;
+      *reinterpret_cast<uint2*>(pt + base + j * 128 + (((mg & 7) ^ j) << 4)) = h;
     }
   }
 }
@@ -718,7 +720,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qrows = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
         const int nmma = (int)((qrows + 15) & ~int64_t(15));
-        const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, 0, 0);
+        const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, FUSE ? d.p_mn : 0, 0);
         const int chunk = SPLIT ? KC : g.nks;
         bool ok = true;
         for (int c0 = 0; c0 < g.nks && ok; c0 += chunk, ++gc) {
@@ -734,7 +736,8 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
             const uint32_t st = stage0 + (uint32_t)s * Cf::STAGE_BYTES;
 #pragma unroll
             for (int kk = 0; kk < PK / 16; ++kk) {
-              const uint64_t pd = ptx::sw128_kmajor_desc(st + kk * 32);
+              const uint64_t pd = (FUSE && d.p_mn) ? ptx::sw128_mnmajor_desc(st + kk * 2 * MN_KGROUP, MN_HALF, MN_KGROUP)
+                                                   : ptx::sw128_kmajor_desc(st + kk * 32);
               const uint64_t qd = ptx::sw128_kmajor_desc(st + PBLOCK + kk * 32);
               ptx::mma_bf16(dt, pd, qd, idesc, (ks == c0 && kk == 0) ? 0u : 1u);
               if (SPLIT) {
@@ -1160,6 +1163,7 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
   g.splits = d.splits;
   g.slabs_per_split = (int32_t)(d.k_per_split / PK);
   g.pjob = -1;
+  g.p_mn = 0;
   g.K = d.K;
   *swapped = swap;
   return g;
@@ -1252,6 +1256,7 @@ int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool 
   g.P_lo = split ? (int64_t)(swap ? off_blo : off_alo) - (int64_t)g.P_off : 0;
   g.Q_lo = split ? (int64_t)(swap ? off_alo : off_blo) - (int64_t)g.Q_off : 0;
   g.pjob = fuse ? ja_idx + (swap ? 1 : 0) : -1;
+  g.p_mn = fuse && pp->jobs[(size_t)ja_idx + (swap ? 1 : 0)].vec4 == 2 ? 1 : 0;
   pp->gemms.push_back(g);
   return TN_OK;
 }

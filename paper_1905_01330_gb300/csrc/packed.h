@@ -63,6 +63,9 @@ struct GemmDesc {
                           // (whole-sector stores) instead of one row per thread
   int32_t pjob;           // fused: index of P's job in the job list (P is read as float32
                           // and rounded inside the GEMM, never packed); -1: P is packed
+  int32_t p_mn;           // fused, P contiguous along its rows: the P tile is staged
+                          // MN-major (rows fastest), else K-major
+  int32_t pad2;
 };
 
 // Schedule of the packed GEMM for one class of contractions: the output
