@@ -181,6 +181,10 @@ int tn::contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor*
   if (d.K == 0)
     return cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) == cudaSuccess ? TN_OK
                                                                                           : TN_ERR_CUDA;
+  // FP32 with a small first operand and a long second one (an MPO core
+  // against an environment): one thread per result column
+  if (prec == TN_PREC_FP32 && d.M <= SKINNY_MAX && d.K <= SKINNY_MAX && d.N >= 4096)
+    return launch_contract_skinny(d, s);
   plan_units(&d, min_units_single());
   if (prec != TN_PREC_FP32 && scratch && packed_single_bytes(d, prec) <= scratch_bytes)
     return contract_packed_single(d, prec, scratch, scratch_bytes, s);

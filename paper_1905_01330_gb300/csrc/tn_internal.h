@@ -52,6 +52,10 @@ int launch_contract_simt(const ContractDesc& single, const ContractDesc* group, 
                          int64_t total_tiles, cudaStream_t stream);
 int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc,
                        int64_t total_tiles, int prec, cudaStream_t stream);
+// FP32 contraction with a small first operand (M, K <= SKINNY_MAX; any N):
+// one thread per result column, the first operand in shared memory.
+constexpr int SKINNY_MAX = 16;
+int launch_contract_skinny(const ContractDesc& d, cudaStream_t stream);
 
 // Tile shapes of the kernels (used by the planner to count tiles).
 constexpr int SIMT_BM = 128, SIMT_BN = 128;

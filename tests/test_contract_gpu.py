@@ -118,6 +118,30 @@ def test_permuted_legs_and_strided_views(tn, prec):
     check(tn.contract(Ap, [1, 2], Bt, [2, 3], prec=prec), Anp, [1, 2], B, [2, 3], prec)
 
 
+def test_small_first_operand_fp32(tn):
+    """FP32 contractions with a first operand of at most 16 rows and 16 shared
+    indices against a long second one take the one-thread-per-column kernel:
+    the MPO step of an energy sweep (W[w, w', s, s'] with T1[w, a', s, b] over
+    w and s), a permuted view, K = 1 and the 16 x 16 limit."""
+    cases = [
+        (rand(81, (3, 3, 2, 2)), [0, 2], rand(82, (3, 96, 2, 80)), [0, 2]),   # MPO step
+        (rand(83, (16, 16)), [1], rand(84, (16, 5000)), [0]),                  # at the limit
+        (rand(85, (4, 1)), [1], rand(86, (1, 9000)), [0]),                     # K = 1
+        (rand(87, (2, 7, 2)), [1, 2], rand(88, (40, 7, 2, 130)), [1, 2]),      # N over two legs
+    ]
+    for A, la, B, lb in cases:
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        C = tn.contract(At, la, Bt, lb, prec="fp32")
+        torch.cuda.synchronize()
+        check(C, A, la, B, lb, "fp32")
+    # a permuted (non-contiguous) second operand
+    B = rand(89, (64, 6, 128))
+    Bt = torch.from_numpy(B).cuda().permute(2, 1, 0)
+    A = rand(90, (5, 6))
+    C = tn.contract(torch.from_numpy(A).cuda(), [1], Bt, [1], prec="fp32")
+    check(C, A, [1], np.ascontiguousarray(B.transpose(2, 1, 0)), [1], "fp32")
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
 def test_degenerate_shapes(tn, prec):
     # inner product (rank-0 result), mat-vec (N = 1), vec-mat (M = 1), outer product (K = 1)
