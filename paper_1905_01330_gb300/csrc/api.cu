@@ -69,6 +69,8 @@ struct tn_group_plan {
   int prec = TN_PREC_FP32;
   int64_t total_tiles = 0;
   int64_t packed_tiles = 0;            // units of the GEMM on packed P; the fused GEMM's follow them
+  bool skinny = false;                 // FP32, every contraction with M, K <= SKINNY_MAX
+  int64_t max_n = 0;
   // offset tables of the P operand of every contraction that may take the
   // fused GEMM (BF16, narrower side at most 128 rows): element offsets of
   // its row and shared-index runs in `ctab`, -1 for the others
@@ -363,6 +365,15 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
     const int64_t n = (int64_t)d.tiles_m * d.tiles_n * d.splits;
     std::fill(p->unit_desc.begin() + d.tile_begin, p->unit_desc.begin() + d.tile_begin + n, (int32_t)i);
   }
+  // FP32 plans whose contractions all have a small first operand (the MPO
+  // step of a batch of environment sweeps) run one thread per result column
+  if (prec == TN_PREC_FP32 && !p->descs.empty()) {
+    p->skinny = true;
+    for (const auto& d : p->descs) {
+      if (d.M > SKINNY_MAX || d.K > SKINNY_MAX) p->skinny = false;
+      p->max_n = std::max(p->max_n, d.N);
+    }
+  }
   *plan = p;
   return TN_OK;
 }
@@ -568,6 +579,8 @@ static int run_one(const tn_group_plan* plan, void* workspace, LaunchKind k, cud
   if (plan->packed)
     return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->packed_tiles, plan->prec, s);
   const ContractDesc* g = reinterpret_cast<const ContractDesc*>(base);
+  if (plan->prec == TN_PREC_FP32 && plan->skinny)
+    return launch_contract_skinny_grouped(g, (int)plan->descs.size(), plan->max_n, s);
   if (plan->prec == TN_PREC_FP32) return launch_contract_simt(plan->descs[0], g, map, plan->total_tiles, s);
   return launch_contract_tc(plan->descs[0], g, map, plan->total_tiles, plan->prec, s);
 }

@@ -56,6 +56,9 @@ int launch_contract_tc(const ContractDesc& single, const ContractDesc* group, co
 // one thread per result column, the first operand in shared memory.
 constexpr int SKINNY_MAX = 16;
 int launch_contract_skinny(const ContractDesc& d, cudaStream_t stream);
+// The same over an uploaded list of `count` such contractions (max_n: the
+// largest N among them).
+int launch_contract_skinny_grouped(const ContractDesc* descs, int count, int64_t max_n, cudaStream_t stream);
 
 // Tile shapes of the kernels (used by the planner to count tiles).
 constexpr int SIMT_BM = 128, SIMT_BN = 128;

@@ -142,6 +142,24 @@ def test_small_first_operand_fp32(tn):
     check(C, A, [1], np.ascontiguousarray(B.transpose(2, 1, 0)), [1], "fp32")
 
 
+def test_small_first_operand_fp32_grouped(tn):
+    """An FP32 grouped plan whose contractions all have a small first operand
+    (the MPO steps of a batch of environment sweeps, uneven environments)
+    runs the grouped one-thread-per-column kernel."""
+    cases = [(rand(91 + i, (3, 3, 2, 2)), [0, 2], rand(101 + i, (3, 16 * (i + 1), 2, 24 * (i + 2))), [0, 2])
+             for i in range(5)]
+    specs = []
+    for A, la, B, lb in cases:
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        specs.append((At, la, Bt, lb, torch.full(tn.result_shape(At, la, Bt, lb), float("nan"), device="cuda")))
+    plan = tn.GroupPlan(specs, prec="fp32")
+    plan.run()
+    torch.cuda.synchronize()
+    assert tn.sync_status() == 0
+    for (A, la, B, lb), sp in zip(cases, specs):
+        check(sp[4], A, la, B, lb, "fp32")
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
 def test_degenerate_shapes(tn, prec):
     # inner product (rank-0 result), mat-vec (N = 1), vec-mat (M = 1), outer product (K = 1)
