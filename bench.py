@@ -42,11 +42,15 @@ CPU_SAMPLE_SPECS = 16     # cpu_baseline: first 16 specs (6.2 GFLOP)
 REF_STEP_SPECS = 4        # --impl reference: first 4 specs per step
 
 
-def workload_config():
-    return {"workload": "grouped tensordot: 2048 random specs (rank 3-5, dims {8,16,24,32,48,64}, "
+def workload_config(n=N_SPECS):
+    """The workload's description; n < 2048 (--specs) is a smaller case of it
+    for profiling, not the bench workload, and says so."""
+    spec = ("2048 random specs" if n >= N_SPECS else "the first %d of the 2048 random specs" % n)
+    return {"workload": "grouped tensordot: " + spec + " (rank 3-5, dims {8,16,24,32,48,64}, "
                         "1-3 shared legs in random order, 2^24-element cap), fp32 in/out, one launch",
-            "specs": N_SPECS, "seed": SEED, "precision": "bf16 operands, fp32 accumulate (tcgen05)",
-            "l2": "inputs and results (31.9 GB) larger than L2; no flush needed"}
+            "specs": min(n, N_SPECS), "seed": SEED, "precision": "bf16 operands, fp32 accumulate (tcgen05)",
+            "l2": ("inputs and results (31.9 GB) larger than L2; no flush needed" if n >= N_SPECS else
+                   "a subset of the bench workload (profiling case)")}
 
 
 def measured_peaks():
@@ -595,7 +599,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(),
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(args.specs),
                 "gpu_launches": args.steps * plan.launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "variants": variants, "schedules": schedules,
                 "tensor_peak_frac": value / world / bf16_peak, "extras": extras}
