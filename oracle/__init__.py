@@ -205,3 +205,6 @@ def classify_grad(cores, label_site: int, pixels, labels):
     if rc != 0:
         raise ValueError("invalid classifier")
     return out.value, d
+
+
+from .split import matrix_view, split_node, svd, truncation_count  # noqa: E402  (node splitting, numpy)
