@@ -397,6 +397,50 @@ int tn_mps_classify_loss(const float* ftilde, const int64_t* labels, int batch, 
  */
 int tn_check_wait_timeout(uint64_t limit_ns, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Node splitting (Sec. III.B "Node Splitting", Appendix A "Saving Memory")  */
+/* ------------------------------------------------------------------------ */
+/*
+ * Splits node A by the singular value decomposition of its matrix view: rows
+ * run over the legs `left` (in that order, last fastest), columns over the
+ * legs `right`; left and right together name every leg of A exactly once.
+ * With M = prod of the left dims, N = prod of the right dims and
+ * r = min(M, N), A = U S V^T with S descending. The new bond keeps k <= r
+ * singular values:
+ *  - max_truncation_err >= 0: the smallest values are dropped while the sum
+ *    of the dropped ones stays <= max_truncation_err (Appendix A); < 0: none;
+ *  - max_singular_values > 0: at most that many are kept; <= 0: no cap;
+ *  - with both, the smaller count; at least one value is always kept.
+ * Outputs (device, row-major, written for the k kept values; size them for
+ * r): U_out holds M x k -- the left node, shape (left dims..., k); Vt_out
+ * holds k x N -- the right node, shape (k, right dims...). absorb = 1
+ * (split_node): U sqrt(S) and sqrt(S) V^T. absorb = 0 (split_node_full_svd):
+ * U and V^T, and S_out (k values) the diagonal of the singular-value node.
+ * S_out (optional when absorb = 1) gets the k kept values, dropped_out
+ * (optional) the r - k dropped ones, both descending. *kept (host) = k;
+ * *sweeps (host, optional) = Jacobi sweeps used, negative if the sweep limit
+ * (40) was reached before every column pair was orthogonal.
+ *
+ * Arithmetic: float32 one-sided Jacobi (Hestenes) on the r columns of
+ * length max(M, N), the rotation angles computed in float64; singular values
+ * are column norms. Columns of U (or of V when M < N) that belong to a zero
+ * singular value are zeros. Workspace: tn_split_node_workspace_bytes (256-B
+ * aligned). Unlike the other entry points this call synchronises `stream`
+ * (once per sweep and before the outputs, whose shapes depend on k).
+ * Errors: TN_ERR_ARG (legs not a partition of A's, null outputs or kept),
+ * TN_ERR_UNSUPPORTED (dtype, negative strides, r >= 2^30), TN_ERR_WORKSPACE,
+ * TN_ERR_CUDA. An empty node (r = 0) returns TN_OK with k = 0.
+ */
+size_t tn_split_node_workspace_bytes(const tn_tensor* A, const int* left, int nleft, const int* right, int nright);
+int tn_split_node(const tn_tensor* A, const int* left, int nleft, const int* right, int nright,
+                  int64_t max_singular_values, double max_truncation_err, int absorb, float* U_out, float* S_out,
+                  float* Vt_out, float* dropped_out, int64_t* kept, int32_t* sweeps, void* workspace,
+                  size_t ws_bytes, void* stream);
+/* The truncation rule alone (host): how many of the r singular values
+ * sigma_desc (descending, host array) tn_split_node keeps. */
+int64_t tn_split_truncation(const float* sigma_desc, int64_t r, int64_t max_singular_values,
+                            double max_truncation_err);
+
 /* Device status word: returns the first kernel-side error since the last
  * call (TN_OK if none) after synchronising `stream`, and clears it. */
 int tn_sync_status(void* stream);

@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -106,6 +107,10 @@ def _signatures():
         "tn_mps_classify_backward": (i32, [ctypes.POINTER(TnChain), i32, i32, vp, i32, i32, i32, vp,
                                            ctypes.POINTER(ctypes.c_void_p), vp, ctypes.c_size_t, vp]),
         "tn_mps_classify_loss": (i32, [vp, vp, i32, i32, vp, vp, vp]),
+        "tn_split_node_workspace_bytes": (ctypes.c_size_t, [tp, ip, i32, ip, i32]),
+        "tn_split_node": (i32, [tp, ip, i32, ip, i32, i64, ctypes.c_double, i32, vp, vp, vp, vp,
+                                ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32), vp, ctypes.c_size_t, vp]),
+        "tn_split_truncation": (i64, [ctypes.POINTER(ctypes.c_float), i64, i64, ctypes.c_double]),
         "tn_check_wait_timeout": (i32, [ctypes.c_uint64, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
@@ -206,6 +211,54 @@ def check_wait_timeout(limit_ns: int = 20_000_000, stream=None) -> None:
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def split_node(A: torch.Tensor, left_legs, right_legs, max_singular_values: int | None = None,
+               max_truncation_err: float | None = None, full_svd: bool = False, stream=None,
+               info: dict | None = None):
+    """Splits node A by the SVD of its matrix view (tn_split_node): rows over
+    left_legs, columns over right_legs. Returns (u_s, s_vh, dropped) -- U sqrt(S)
+    of shape left dims + (k,), sqrt(S) V^T of shape (k,) + right dims, and the
+    dropped singular values -- or, with full_svd, (u, s, vh, dropped) with s
+    the k kept singular values (the diagonal of the singular-value node).
+    Synchronises the stream (k decides the output shapes). info, if given,
+    receives the Jacobi sweep count."""
+    lib = load()
+    left, right = [int(p) for p in left_legs], [int(p) for p in right_legs]
+    ad = tensor_desc(A)
+    la = (ctypes.c_int * max(len(left), 1))(*left)
+    ra = (ctypes.c_int * max(len(right), 1))(*right)
+    ws_bytes = lib.tn_split_node_workspace_bytes(ctypes.byref(ad), la, len(left), ra, len(right))
+    if ws_bytes == 0:
+        raise TnError(1, "tn_split_node: legs must partition the node's legs")
+    ldims = [A.shape[p] for p in left]
+    rdims = [A.shape[p] for p in right]
+    M = int(np.prod(ldims)) if ldims else 1
+    N = int(np.prod(rdims)) if rdims else 1
+    r = min(M, N)
+    dev = A.device
+    U = torch.empty(max(M * r, 1), dtype=torch.float32, device=dev)
+    Vt = torch.empty(max(r * N, 1), dtype=torch.float32, device=dev)
+    S = torch.empty(max(r, 1), dtype=torch.float32, device=dev)
+    D = torch.empty(max(r, 1), dtype=torch.float32, device=dev)
+    ws = _workspace(ws_bytes, dev)
+    kept = ctypes.c_int64(0)
+    sweeps = ctypes.c_int32(0)
+    _check(lib.tn_split_node(ctypes.byref(ad), la, len(left), ra, len(right),
+                             int(max_singular_values) if max_singular_values is not None else 0,
+                             float(max_truncation_err) if max_truncation_err is not None else -1.0,
+                             0 if full_svd else 1, U.data_ptr(), S.data_ptr(), Vt.data_ptr(), D.data_ptr(),
+                             ctypes.byref(kept), ctypes.byref(sweeps), ws.data_ptr(), ws.numel(),
+                             _stream(stream)), "tn_split_node")
+    k = kept.value
+    if info is not None:
+        info["sweeps"] = sweeps.value
+    u = U[:M * k].view(ldims + [k])
+    vh = Vt[:k * N].view([k] + rdims)
+    dropped = D[:r - k]
+    if full_svd:
+        return u, S[:k], vh, dropped
+    return u, vh, dropped
 
 
 def mps_inner(bra, ket, prec: str = "fp32", stream=None, out: torch.Tensor | None = None):

@@ -120,3 +120,62 @@ def test_group_plan_launches_without_gpu(libpath):
     got = launches("bf16x3")
     ops = 4096 * 64 + 64 * 32 + 16 * 96 + 96 * 3000 + 512 * 256 + 256 * 384
     assert got == {"pack": 8.0 * ops, "gemm": 4.0 * ops + 4.0 * (4096 * 32 + 16 * 3000 + 512 * 384)}
+
+
+def _bound(libpath):
+    from paper_1905_01330_gb300 import tn
+    lib = ctypes.CDLL(libpath)
+    for n, (res, args) in tn._signatures().items():
+        getattr(lib, n).restype = res
+        getattr(lib, n).argtypes = args
+    return lib, tn
+
+
+def test_split_truncation_rule_matches_the_oracle(libpath):
+    """The host truncation rule of tn_split_node (Appendix A: drop the smallest
+    singular values while their sum stays within max_truncation_err, keep at
+    most max_singular_values, at least one) agrees with the oracle's on
+    hand-made spectra and on random ones, limits placed between partial sums."""
+    import numpy as np
+    import oracle
+    lib, _ = _bound(libpath)
+
+    def k_lib(s, max_sv, max_err):
+        arr = (ctypes.c_float * max(len(s), 1))(*[float(v) for v in s])
+        return lib.tn_split_truncation(arr, len(s), max_sv or 0, -1.0 if max_err is None else max_err)
+
+    cases = [([5, 3, 0.06, 0.03, 0.02], None, 0.1), ([5, 3, 0.06, 0.03, 0.02], 2, None),
+             ([5, 3, 0.06, 0.03, 0.02], 4, 0.1), ([2, 1, 0, 0], None, 0.0), ([0.05, 0.01], None, 1.0),
+             ([1.0], 1, 0.5), ([], None, 1.0)]
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        s = np.sort(rng.exponential(size=int(rng.integers(1, 40))).astype(np.float32))[::-1]
+        tail = np.cumsum(s[::-1].astype(np.float64))
+        err = float(tail[int(rng.integers(0, len(s)))] * rng.uniform(0.5, 1.5))
+        cases.append((list(s), int(rng.integers(0, len(s) + 2)) or None, err))
+    for s, max_sv, max_err in cases:
+        s32 = [float(np.float32(v)) for v in s]
+        assert k_lib(s32, max_sv, max_err) == oracle.truncation_count(s32, max_sv, max_err), (s, max_sv, max_err)
+
+
+def test_split_node_validation_without_gpu(libpath):
+    lib, tn = _bound(libpath)
+    a = tn.TnTensor()
+    a.data, a.rank = 0x1000, 3
+    for i, n in enumerate((2, 3, 4)):
+        a.shape[i] = n
+    ip = lambda *v: (ctypes.c_int * max(len(v), 1))(*v)  # noqa: E731
+    assert lib.tn_split_node_workspace_bytes(ctypes.byref(a), ip(0, 1), 2, ip(2), 1) > 0
+    for left, right in (((0,), (1,)), ((0, 1), (1, 2)), ((0, 3), (1, 2)), ((0, 0), (1, 2))):
+        assert lib.tn_split_node_workspace_bytes(ctypes.byref(a), ip(*left), len(left), ip(*right), len(right)) == 0
+    kept = ctypes.c_int64(-1)
+    rc = lib.tn_split_node(ctypes.byref(a), ip(0, 1), 2, ip(1, 2), 2, 0, -1.0, 1, None, None, None, None,
+                           ctypes.byref(kept), None, None, 0, None)
+    assert rc == 1
+    # valid legs but no outputs / no workspace: refused before any CUDA call
+    rc = lib.tn_split_node(ctypes.byref(a), ip(0, 1), 2, ip(2), 1, 0, -1.0, 1, None, None, None, None,
+                           ctypes.byref(kept), None, None, 0, None)
+    assert rc == 1
+    rc = lib.tn_split_node(ctypes.byref(a), ip(0, 1), 2, ip(2), 1, 0, -1.0, 1, 0x2000, None, 0x3000, None,
+                           ctypes.byref(kept), None, None, 0, None)
+    assert rc == 6
