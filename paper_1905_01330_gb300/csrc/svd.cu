@@ -9,8 +9,8 @@
 // view itself when M >= N, else its transpose) by plane rotations of column
 // pairs, accumulating the rotations in V (r x r, starting from I). A sweep
 // visits every pair once, in r - 1 rounds of r / 2 disjoint pairs (the circle
-// method of round-robin scheduling), one launch per round and one CTA per
-// pair. At convergence W = U S and the matrix (or its transpose) is W V^T:
+// method of round-robin scheduling), one kernel per round (a CUDA graph per
+// sweep) and one CTA per pair. At convergence W = U S and the matrix (or its transpose) is W V^T:
 // the singular values are the column norms of W.
 #include <math.h>
 #include <string.h>
@@ -24,6 +24,7 @@ namespace {
 
 constexpr int SVD_THREADS = 256;
 constexpr int SVD_MAX_SWEEPS = 40;
+constexpr int SVD_CACHE = 8;  // register-held entries per thread and column
 
 // The node's matrix view: element (i, j) at A + loff(i) + roff(j).
 struct SplitView {
@@ -108,12 +109,28 @@ svd_round(float* __restrict__ W, float* __restrict__ V, int64_t L, int r, int rp
   if (p >= r || q >= r) return;  // the dummy slot of an odd r
   float* wp = W + (int64_t)p * L;
   float* wq = W + (int64_t)q * L;
+  // columns of up to SVD_CACHE * SVD_THREADS entries stay in registers
+  // between the dot products and the rotation
+  const bool cached = L <= (int64_t)SVD_CACHE * SVD_THREADS;
+  float xs[SVD_CACHE], ys[SVD_CACHE];
   float a = 0.0f, b = 0.0f, g = 0.0f;
-  for (int64_t i = threadIdx.x; i < L; i += SVD_THREADS) {
-    const float x = wp[i], y = wq[i];
-    a = fmaf(x, x, a);
-    b = fmaf(y, y, b);
-    g = fmaf(x, y, g);
+  if (cached) {
+#pragma unroll
+    for (int u = 0; u < SVD_CACHE; ++u) {
+      const int64_t i = threadIdx.x + (int64_t)u * SVD_THREADS;
+      xs[u] = i < L ? wp[i] : 0.0f;
+      ys[u] = i < L ? wq[i] : 0.0f;
+      a = fmaf(xs[u], xs[u], a);
+      b = fmaf(ys[u], ys[u], b);
+      g = fmaf(xs[u], ys[u], g);
+    }
+  } else {
+    for (int64_t i = threadIdx.x; i < L; i += SVD_THREADS) {
+      const float x = wp[i], y = wq[i];
+      a = fmaf(x, x, a);
+      b = fmaf(y, y, b);
+      g = fmaf(x, y, g);
+    }
   }
   __shared__ double sums[3];
   __shared__ float rot[2];
@@ -135,10 +152,21 @@ svd_round(float* __restrict__ W, float* __restrict__ V, int64_t L, int r, int rp
   __syncthreads();
   if (skip) return;
   const float c = rot[0], s = rot[1];
-  for (int64_t i = threadIdx.x; i < L; i += SVD_THREADS) {
-    const float x = wp[i], y = wq[i];
-    wp[i] = c * x - s * y;
-    wq[i] = s * x + c * y;
+  if (cached) {
+#pragma unroll
+    for (int u = 0; u < SVD_CACHE; ++u) {
+      const int64_t i = threadIdx.x + (int64_t)u * SVD_THREADS;
+      if (i < L) {
+        wp[i] = c * xs[u] - s * ys[u];
+        wq[i] = s * xs[u] + c * ys[u];
+      }
+    }
+  } else {
+    for (int64_t i = threadIdx.x; i < L; i += SVD_THREADS) {
+      const float x = wp[i], y = wq[i];
+      wp[i] = c * x - s * y;
+      wq[i] = s * x + c * y;
+    }
   }
   float* vp = V + (int64_t)p * r;
   float* vq = V + (int64_t)q * r;
@@ -341,18 +369,67 @@ int tn_split_node(const tn_tensor* A, const int* left, int nleft, const int* rig
   if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   // off-diagonal threshold: a few times the float32 rounding of a length-L dot product
   const float tol = 4.0f * sqrtf((float)L) * 5.9604645e-8f;
+  // one sweep = a CUDA graph: the counter reset, then the r - 1 rounds in
+  // order (built once per call, launched once per sweep)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  };
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return TN_ERR_CUDA;
+  {
+    cudaGraphNode_t prev = nullptr, node = nullptr;
+    cudaMemsetParams mp;
+    memset(&mp, 0, sizeof(mp));
+    mp.dst = counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    if (cudaGraphAddMemsetNode(&prev, graph, nullptr, 0, &mp) != cudaSuccess) {
+      cleanup();
+      return TN_ERR_CUDA;
+    }
+    float* w_arg = W;
+    float* v_arg = V;
+    int64_t l_arg = L;
+    int r_arg = r, rp_arg = rp;
+    float tol_arg = tol;
+    int* c_arg = counter;
+    for (int t = 0; t < rp - 1; ++t) {
+      int t_arg = t;
+      void* args[] = {&w_arg, &v_arg, &l_arg, &r_arg, &rp_arg, &t_arg, &tol_arg, &c_arg};
+      cudaKernelNodeParams kp;
+      memset(&kp, 0, sizeof(kp));
+      kp.func = reinterpret_cast<void*>(svd_round);
+      kp.gridDim = dim3((unsigned)(rp / 2));
+      kp.blockDim = dim3(SVD_THREADS);
+      kp.kernelParams = args;
+      if (cudaGraphAddKernelNode(&node, graph, &prev, 1, &kp) != cudaSuccess) {
+        cleanup();
+        return TN_ERR_CUDA;
+      }
+      prev = node;
+    }
+  }
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cleanup();
+    return TN_ERR_CUDA;
+  }
   int done = 0, used = 0;
   for (int sw = 0; sw < SVD_MAX_SWEEPS && !done; ++sw) {
-    if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return TN_ERR_CUDA;
-    for (int t = 0; t < rp - 1; ++t) svd_round<<<rp / 2, SVD_THREADS, 0, s>>>(W, V, L, r, rp, t, tol, counter);
-    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
     int host_count = -1;
-    if (cudaMemcpyAsync(&host_count, counter, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (cudaGraphLaunch(exec, s) != cudaSuccess ||
+        cudaMemcpyAsync(&host_count, counter, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cleanup();
       return TN_ERR_CUDA;
+    }
     ++used;
     done = host_count == 0;
   }
+  cleanup();
   if (sweeps) *sweeps = done ? used : -used;
   svd_norms<<<r, SVD_THREADS, 0, s>>>(W, L, sigma);
   svd_sort<<<(r + 255) / 256, 256, 0, s>>>(sigma, r, order, sorted);
