@@ -441,6 +441,43 @@ int tn_split_node(const tn_tensor* A, const int* left, int nleft, const int* rig
 int64_t tn_split_truncation(const float* sigma_desc, int64_t r, int64_t max_singular_values,
                             double max_truncation_err);
 
+/* ------------------------------------------------------------------------ */
+/* ncon (Appendix B): planning a labelled network into pairwise steps        */
+/* ------------------------------------------------------------------------ */
+/*
+ * n tensors; tensor t has ranks[t] legs with dims and labels given in
+ * tensor order (concatenated). A label >= 0 is an edge: exactly two legs,
+ * of equal dimension (on two tensors, or twice on one -- a trace). A label
+ * < 0 is a dangling leg of the result; -1, -2, ... each appear once. Edges
+ * are taken in con_order (n_order labels, each edge once; n_order = 0:
+ * ascending). An edge between two tensors contracts every edge the two share
+ * in one step (contract_between, Sec. III.B.2); its result holds the first
+ * tensor's free legs, then the second's (tensordot order), and joins the end
+ * of the operand list (inputs first, in order; a step consumes its operands).
+ * An edge on one tensor is a trace step (b = -1, legs_a[0] and legs_b[0] both
+ * legs of a). Tensors still unconnected at the end are joined by outer
+ * products (nshared = 0) in list order. out_perm[i] is the leg of the last
+ * result (or of the single input when there are no steps) that becomes
+ * output leg i, the output legs ordered as out_order (n_out labels; 0:
+ * -1, -2, ...); *out_rank = number of dangling legs.
+ * steps may be NULL to count them (*n_steps); otherwise max_steps bounds
+ * the array (at most the number of edges plus n - 1 are needed).
+ * Host only: no device memory is touched. Errors: TN_ERR_ARG (labels,
+ * orders, counts), TN_ERR_SHAPE (an edge's two legs differ in dimension),
+ * TN_ERR_UNSUPPORTED (an intermediate or the result above rank 8).
+ */
+typedef struct tn_ncon_step {
+  int32_t a, b;                 /* operands: input t is t, step s's result is n + s; b = -1: a trace of a */
+  int32_t nshared;              /* leg pairs legs_a[j] (of a) <-> legs_b[j] (of b; of a for a trace) */
+  int32_t rank;                 /* rank of the step's result */
+  int32_t legs_a[TN_MAX_RANK];
+  int32_t legs_b[TN_MAX_RANK];
+  int64_t shape[TN_MAX_RANK];   /* the result's shape */
+} tn_ncon_step;
+int tn_ncon_plan(int n, const int* ranks, const int64_t* dims, const int* labels, const int* con_order, int n_order,
+                 const int* out_order, int n_out, tn_ncon_step* steps, int max_steps, int* n_steps, int* out_perm,
+                 int* out_rank);
+
 /* Device status word: returns the first kernel-side error since the last
  * call (TN_OK if none) after synchronising `stream`, and clears it. */
 int tn_sync_status(void* stream);

@@ -208,3 +208,4 @@ def classify_grad(cores, label_site: int, pixels, labels):
 
 
 from .split import matrix_view, split_node, svd, truncation_count  # noqa: E402  (node splitting, numpy)
+from .ncon import ncon  # noqa: E402  (ncon over tensordot / trace)

@@ -42,6 +42,12 @@ class TnChain(ctypes.Structure):
                 ("cores", ctypes.POINTER(ctypes.c_void_p))]
 
 
+class TnNconStep(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("nshared", ctypes.c_int32),
+                ("rank", ctypes.c_int32), ("legs_a", ctypes.c_int32 * TN_MAX_RANK),
+                ("legs_b", ctypes.c_int32 * TN_MAX_RANK), ("shape", ctypes.c_int64 * TN_MAX_RANK)]
+
+
 def chain_desc(cores, phys_axis: int = 1):
     """(TnChain, keepalive) for a list of contiguous float32 CUDA tensors; bonds
     are the first axis of each core plus the last core's second bond axis."""
@@ -111,6 +117,8 @@ def _signatures():
         "tn_split_node": (i32, [tp, ip, i32, ip, i32, i64, ctypes.c_double, i32, vp, vp, vp, vp,
                                 ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32), vp, ctypes.c_size_t, vp]),
         "tn_split_truncation": (i64, [ctypes.POINTER(ctypes.c_float), i64, i64, ctypes.c_double]),
+        "tn_ncon_plan": (i32, [i32, ip, ctypes.POINTER(i64), ip, ip, i32, ip, i32, ctypes.POINTER(TnNconStep), i32,
+                               ip, ip, ip]),
         "tn_check_wait_timeout": (i32, [ctypes.c_uint64, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
@@ -211,6 +219,58 @@ def check_wait_timeout(limit_ns: int = 20_000_000, stream=None) -> None:
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def ncon_plan(shapes, network, con_order=None, out_order=None, lib=None):
+    """tn_ncon_plan on host shapes and labels: (steps, out_perm) -- steps as
+    (a, b, legs_a, legs_b, result shape), b = -1 for a trace."""
+    lib = lib or load()
+    n = len(shapes)
+    if len(network) != n:
+        raise TnError(1, "ncon: one label list per tensor")
+    ranks = (ctypes.c_int * n)(*[len(sh) for sh in shapes])
+    flat_dims = [int(d) for sh in shapes for d in sh]
+    flat_labels = [int(x) for labels in network for x in labels]
+    if any(len(labels) != len(sh) for labels, sh in zip(network, shapes)):
+        raise TnError(1, "ncon: one label per leg")
+    dims = (ctypes.c_int64 * max(len(flat_dims), 1))(*flat_dims)
+    labs = (ctypes.c_int * max(len(flat_labels), 1))(*flat_labels)
+    co = list(con_order) if con_order is not None else []
+    oo = list(out_order) if out_order is not None else []
+    coa = (ctypes.c_int * max(len(co), 1))(*co)
+    ooa = (ctypes.c_int * max(len(oo), 1))(*oo)
+    cnt, perm, orank = ctypes.c_int(0), (ctypes.c_int * TN_MAX_RANK)(), ctypes.c_int(0)
+    _check(lib.tn_ncon_plan(n, ranks, dims, labs, coa, len(co), ooa, len(oo), None, 0, ctypes.byref(cnt), perm,
+                            ctypes.byref(orank)), "tn_ncon_plan")
+    steps = (TnNconStep * max(cnt.value, 1))()
+    _check(lib.tn_ncon_plan(n, ranks, dims, labs, coa, len(co), ooa, len(oo), steps, cnt.value, ctypes.byref(cnt),
+                            perm, ctypes.byref(orank)), "tn_ncon_plan")
+    out = []
+    for st in steps[:cnt.value]:
+        k = st.nshared
+        out.append((st.a, st.b, list(st.legs_a[:k]), list(st.legs_b[:k]), list(st.shape[:st.rank])))
+    return out, list(perm[:orank.value])
+
+
+def ncon(tensors, network, con_order=None, out_order=None, prec: str = "fp32", stream=None):
+    """ncon (Appendix B): evaluates a labelled network by the steps tn_ncon_plan
+    gives, each a tn_contract call (a trace contracts the traced legs with the
+    identity matrix); returns the result with its legs in out order (a
+    permuted view of the last step's result)."""
+    lib = load()
+    steps, perm = ncon_plan([list(t.shape) for t in tensors], network, con_order, out_order, lib)
+    ops = list(tensors)
+    for a, b, la, lb, shape in steps:
+        A = ops[a]
+        if b < 0:
+            d = A.shape[la[0]]
+            eye = torch.from_numpy(np.eye(d, dtype=np.float32)).to(A.device)
+            R = contract(A, [la[0], lb[0]], eye, [0, 1], prec=prec, stream=stream)
+        else:
+            R = contract(A, la, ops[b], lb, prec=prec, stream=stream)
+        assert list(R.shape) == shape
+        ops.append(R)
+    return ops[-1].permute(perm) if perm else ops[-1]
 
 
 def split_node(A: torch.Tensor, left_legs, right_legs, max_singular_values: int | None = None,

@@ -179,3 +179,31 @@ def test_split_node_validation_without_gpu(libpath):
     rc = lib.tn_split_node(ctypes.byref(a), ip(0, 1), 2, ip(2), 1, 0, -1.0, 1, 0x2000, None, 0x3000, None,
                            ctypes.byref(kept), None, None, 0, None)
     assert rc == 6
+
+
+def test_ncon_planner_without_gpu(libpath):
+    """tn_ncon_plan (host): the paper's example is one contraction of a's leg 1
+    with b's leg 0; a trace step; unconnected pieces joined by outer products;
+    contract_between semantics (all shared edges in one step); a custom
+    contraction and output order; invalid labels refused."""
+    lib, tn = _bound(libpath)
+    steps, perm = tn.ncon_plan([(2, 2), (2, 2)], [(-1, 0), (0, -2)], lib=lib)
+    assert steps == [(0, 1, [1], [0], [2, 2])] and perm == [0, 1]
+    steps, perm = tn.ncon_plan([(3, 4, 3)], [(0, -1, 0)], lib=lib)
+    assert steps == [(0, -1, [0], [2], [4])] and perm == [0]
+    steps, perm = tn.ncon_plan([(2, 3), (4, 5), (6,)], [(-2, -1), (-3, -4), (-5,)], lib=lib)
+    assert steps == [(0, 1, [], [], [2, 3, 4, 5]), (3, 2, [], [], [2, 3, 4, 5, 6])] and perm == [1, 0, 2, 3, 4]
+    steps, perm = tn.ncon_plan([(2, 3, 4), (4, 3, 5)], [(-1, 0, 1), (1, 0, -2)], lib=lib)
+    assert steps == [(0, 1, [1, 2], [1, 0], [2, 5])] and perm == [0, 1]
+    steps, perm = tn.ncon_plan([(2, 3, 4), (4, 3, 5), (5, 6)], [(-1, 0, 1), (1, 0, 2), (2, -2)],
+                               con_order=[2, 0, 1], out_order=[-2, -1], lib=lib)
+    assert steps == [(1, 2, [2], [0], [4, 3, 6]), (0, 3, [1, 2], [1, 0], [2, 6])] and perm == [1, 0]
+    bad = [([(2, 2), (2, 2)], [(0, -1), (1, -2)], None, None, 1),      # edges seen once
+           ([(2, 2), (3, 2)], [(0, -1), (0, -2)], None, None, 2),      # edge dims differ
+           ([(2, 2), (2, 2)], [(0, -1), (0, -3)], None, None, 1),      # dangling -1, -3
+           ([(2, 2), (2, 2)], [(-1, 0), (0, -2)], [0, 0], None, 1),    # con_order repeats
+           ([(2, 2), (2, 2)], [(-1, 0), (0, -2)], None, [-1], 1)]      # out_order short
+    for shapes, net, co, oo, code in bad:
+        with pytest.raises(tn.TnError) as e:
+            tn.ncon_plan(shapes, net, co, oo, lib=lib)
+        assert e.value.code == code
