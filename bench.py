@@ -357,6 +357,21 @@ def run_extras(tn, synth, dev, stream):
     out["mps_norm_n20_chi32"] = {"us_per_call_graph": us_graph, "us_per_call_eager": us,
                                  "log_norm": float(np.log(abs(r[0])) + r[1])}
 
+    # ncon (Appendix B): the same <psi|psi> network written as ncon labels
+    # (bra and ket cores, physical legs joined, boundary legs joined), 40 steps
+    # of tn_contract in float32; no rescaling, so it is compared in value
+    net = []
+    for base in (1000, 2000):
+        for i in range(20):
+            net.append((base + i if i > 0 else 0, 100 + i, base + i + 1 if i < 19 else 1))
+    ts = m + m
+    val = float(tn.ncon(ts, net, prec="fp32"))
+    ms_ncon = _time(lambda: tn.ncon(ts, net, prec="fp32"), 5, 2, stream)
+    out["ncon_mps_norm_n20_chi32"] = {"ms_per_call": ms_ncon, "steps": len(tn.ncon_plan([t.shape for t in ts], net)[0]),
+                                      "log_norm": float(np.log(abs(val))),
+                                      "log_norm_diff_vs_tn_mps_inner": float(abs(np.log(abs(val)) -
+                                                                               (np.log(abs(r[0])) + r[1])))}
+
     # config 5: TFIM energy, N=100, chi 256 / 512 / 1024, left-canonical.
     # |E| is small against the energy scale J(N-1)+hN of a random state, so
     # the differences are stated per site and relative to that scale.
