@@ -304,6 +304,28 @@ def run_extras(tn, synth, dev, stream):
         del cores
     out["classifier"] = cls
 
+    # one MPS per label (Sec. IV.A): 10 MPS of 784 sites, batch 4096
+    sep = {}
+    for chi in (32, 64):
+        mps = [[torch.from_numpy(c).to(dev) for c in m]
+               for m in synth.classifier_separate_mps(n, chi, L, seed=90 + chi, eps_std=0.1)]
+        flops = L * sum(4.0 * B * c.shape[0] * c.shape[-1] for c in mps[0])
+        entry = {"forward_gflop": flops / 1e9}
+        ref = None
+        for prec in ("fp32", "bf16"):
+            ws = tn.classifier_separate_workspace(mps, B, 0)
+            ms = _time(lambda: tn.mps_classify_separate(mps, px, prec=prec, ckpt_every=0, workspace=ws), 2, 1, stream)
+            ft, lam, _ = tn.mps_classify_separate(mps, px, prec=prec, ckpt_every=0, workspace=ws)
+            entry[prec] = {"ms": ms, "samples_per_s": B / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12}
+            if ref is None:
+                ref = (ft[:32].double().cpu().numpy(), lam[:32].cpu().numpy())
+            else:
+                entry[prec]["score_diff_vs_fp32_first32"] = _score_err(ft[:32], lam[:32], *ref)
+            del ws
+        sep["chi%d_L%d" % (chi, L)] = entry
+        del mps
+    out["classifier_separate"] = sep
+
     # large contractions: C[m, n] = sum_k A[m, k] B[k, n] at 8192^3 and
     # 16384^3, one-spec plans (pack + GEMM), each launch timed alone
     _, bf16_peak, _ = measured_peaks()

@@ -398,6 +398,34 @@ int tn_mps_classify_loss(const float* ftilde, const int64_t* labels, int batch, 
 int tn_check_wait_timeout(uint64_t limit_ns, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Classifier with one MPS per label (Sec. IV.A)                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * n_mps MPS of n sites each (cores (D_{i-1}, 2, D_i), D_0 = D_n = 1, D <= 128,
+ * bonds may differ between the MPS): the score of label l for image b is the
+ * overlap of the image's product state phi(x_b) = (x) (cos pi x/2, sin pi x/2)
+ * with MPS l. Output as for tn_mps_classify: f[b, l] = ftilde[b, l] *
+ * exp(log_scale[b]) (ftilde [batch, n_mps] float32, log_scale [batch]
+ * float64, one log-scale per sample shared by its labels), so
+ * tn_mps_classify_loss applies unchanged. Each MPS is swept as a one-label
+ * classifier (its middle core n/2 read as the label core (D, 2, 1, D')) in
+ * its own part of the workspace; prec TN_PREC_FP32 or TN_PREC_BF16 as for
+ * tn_mps_classify. The backward takes dLoss/dftilde [batch, n_mps] and the
+ * forward's workspace (same ckpt_every >= 1) and writes the gradients of
+ * every core: dcores[l * n + i] is core i of MPS l (device, the core's
+ * shape). Workspace: tn_mps_classify_separate_workspace_bytes (256-B
+ * aligned). Errors: TN_ERR_ARG (counts, null pointers, n_mps > 64),
+ * TN_ERR_SHAPE (the MPS differ in length, or bonds as in tn_mps_classify),
+ * TN_ERR_UNSUPPORTED, TN_ERR_WORKSPACE, TN_ERR_CUDA.
+ */
+size_t tn_mps_classify_separate_workspace_bytes(const tn_mps* Ws, int n_mps, int batch, int ckpt_every);
+int tn_mps_classify_separate(const tn_mps* Ws, int n_mps, const float* pixels, int batch, int prec, int ckpt_every,
+                             float* ftilde, double* log_scale, void* workspace, size_t ws_bytes, void* stream);
+int tn_mps_classify_separate_backward(const tn_mps* Ws, int n_mps, const float* pixels, int batch, int prec,
+                                      int ckpt_every, const float* dftilde, float* const* dcores, void* workspace,
+                                      size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Node splitting (Sec. III.B "Node Splitting", Appendix A "Saving Memory")  */
 /* ------------------------------------------------------------------------ */
 /*

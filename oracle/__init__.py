@@ -209,3 +209,4 @@ def classify_grad(cores, label_site: int, pixels, labels):
 
 from .split import matrix_view, split_node, svd, truncation_count  # noqa: E402  (node splitting, numpy)
 from .ncon import ncon  # noqa: E402  (ncon over tensordot / trace)
+from .classifier_separate import classify_separate, classify_separate_loss  # noqa: E402

@@ -262,3 +262,11 @@ def classifier_mps(n_sites: int, chi: int, label_site: int, n_labels: int, seed:
             core = eye[:, None, :] + eps
         cores.append(core.astype(np.float32))
     return cores
+
+
+def classifier_separate_mps(n_sites: int, chi: int, n_labels: int, seed: int, eps_std: float = 0.1,
+                            d: int = 2):
+    """One MPS per label (the paper's L separate MPS), each near the identity
+    like classifier_mps without a label core: n_labels lists of n_sites cores
+    (D, d, D'), MPS l drawn from substream (seed, l)."""
+    return [classifier_mps(n_sites, chi, -1, 1, substream(seed, 1000 + l), eps_std, d) for l in range(n_labels)]

@@ -119,6 +119,11 @@ def _signatures():
         "tn_split_truncation": (i64, [ctypes.POINTER(ctypes.c_float), i64, i64, ctypes.c_double]),
         "tn_ncon_plan": (i32, [i32, ip, ctypes.POINTER(i64), ip, ip, i32, ip, i32, ctypes.POINTER(TnNconStep), i32,
                                ip, ip, ip]),
+        "tn_mps_classify_separate_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), i32, i32, i32]),
+        "tn_mps_classify_separate": (i32, [ctypes.POINTER(TnChain), i32, vp, i32, i32, i32, vp, vp, vp,
+                                           ctypes.c_size_t, vp]),
+        "tn_mps_classify_separate_backward": (i32, [ctypes.POINTER(TnChain), i32, vp, i32, i32, i32, vp,
+                                                    ctypes.POINTER(ctypes.c_void_p), vp, ctypes.c_size_t, vp]),
         "tn_check_wait_timeout": (i32, [ctypes.c_uint64, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
@@ -525,6 +530,63 @@ def mps_classify_backward(cores, label_site: int, pixels: torch.Tensor, dftilde:
                                         PREC[prec], ckpt_every, ctypes.c_void_p(dft.data_ptr()), table,
                                         ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream)),
            "tn_mps_classify_backward")
+    return grads
+
+
+def _separate_chains(mps_list):
+    arr = (TnChain * len(mps_list))()
+    keep = []
+    for l, cores in enumerate(mps_list):
+        ch, k = chain_desc_classifier(cores, len(cores) // 2)
+        arr[l] = ch
+        keep.append(k)
+    return arr, keep
+
+
+def classifier_separate_workspace(mps_list, batch: int, ckpt_every: int) -> torch.Tensor:
+    lib = load()
+    arr, keep = _separate_chains(mps_list)
+    nbytes = lib.tn_mps_classify_separate_workspace_bytes(arr, len(mps_list), batch, ckpt_every)
+    if nbytes == 0:
+        raise TnError(1, "tn_mps_classify_separate_workspace_bytes")
+    return _workspace(nbytes, mps_list[0][0].device)
+
+
+def mps_classify_separate(mps_list, pixels: torch.Tensor, prec: str = "fp32", ckpt_every: int = 1,
+                          workspace: torch.Tensor | None = None, stream=None):
+    """One MPS per label (tn_mps_classify_separate): (ftilde [B, L] float32,
+    log_scale [B] float64, workspace), scores = ftilde * exp(log_scale)."""
+    lib = load()
+    B, L = pixels.shape[0], len(mps_list)
+    if pixels.dtype != torch.float32 or not pixels.is_contiguous():
+        raise TypeError("pixels must be a contiguous float32 CUDA tensor [batch, n]")
+    arr, keep = _separate_chains(mps_list)
+    if workspace is None:
+        workspace = classifier_separate_workspace(mps_list, B, ckpt_every)
+    ft = torch.empty((B, L), dtype=torch.float32, device=pixels.device)
+    lam = torch.empty((B,), dtype=torch.float64, device=pixels.device)
+    _check(lib.tn_mps_classify_separate(arr, L, ctypes.c_void_p(pixels.data_ptr()), B, PREC[prec], ckpt_every,
+                                        ctypes.c_void_p(ft.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream)),
+           "tn_mps_classify_separate")
+    return ft, lam, workspace
+
+
+def mps_classify_separate_backward(mps_list, pixels: torch.Tensor, dftilde: torch.Tensor, workspace: torch.Tensor,
+                                   prec: str = "fp32", ckpt_every: int = 1, stream=None):
+    """Core gradients of every MPS (a list per MPS, shaped like its cores) from
+    dLoss/dftilde [B, L]; needs the forward's workspace and ckpt_every."""
+    lib = load()
+    B, L = pixels.shape[0], len(mps_list)
+    arr, keep = _separate_chains(mps_list)
+    dft = dftilde.contiguous().float()
+    grads = [[torch.empty_like(c) for c in cores] for cores in mps_list]
+    flat = [g for gl in grads for g in gl]
+    table = (ctypes.c_void_p * len(flat))(*[g.data_ptr() for g in flat])
+    _check(lib.tn_mps_classify_separate_backward(arr, L, ctypes.c_void_p(pixels.data_ptr()), B, PREC[prec],
+                                                 ckpt_every, ctypes.c_void_p(dft.data_ptr()), table,
+                                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                                 _stream(stream)), "tn_mps_classify_separate_backward")
     return grads
 
 

@@ -116,3 +116,50 @@ def test_gradient_directional_derivative_longer_chain():
         fd = (oracle.classify_loss(plus, ls, x, y) - oracle.classify_loss(minus, ls, x, y)) / (2 * h)
         an = sum(float(np.sum(g * d)) for g, d in zip(grads, dirs))
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+# ------------------------------------------- one MPS per label (Sec. IV.A)
+def test_separate_identity_cores_closed_form():
+    n, chi, L, B = 40, 6, 4, 9
+    mps = synth.classifier_separate_mps(n, chi, L, seed=3, eps_std=0.0)
+    px = synth.pixels(B, n, seed=4).astype(np.float64)
+    ft, lam = oracle.classify_separate(mps, px)
+    ref = np.sum(np.log(np.cos(np.pi * px / 2) + np.sin(np.pi * px / 2)), axis=1)
+    assert np.allclose(np.log(ft) + lam[:, None], ref[:, None], rtol=0, atol=1e-10)
+
+
+def test_separate_equals_label_core_model_with_shared_cores():
+    """L MPS that share every core but the label site's, whose core is slice l
+    of a label core, score exactly as the one-MPS label-core classifier."""
+    n, chi, ls, L, B = 14, 5, 6, 4, 11
+    cores = synth.classifier_mps(n, chi, ls, L, seed=7, eps_std=0.2)
+    px = synth.pixels(B, n, seed=8)
+    mps = [[c if i != ls else np.ascontiguousarray(cores[ls][:, :, l, :]) for i, c in enumerate(cores)]
+           for l in range(L)]
+    ft, lam = oracle.classify_separate(mps, px)
+    ft_ref, lam_ref = oracle.classify(cores, ls, px)
+    assert np.allclose(ft * np.exp(lam - lam_ref)[:, None], ft_ref, rtol=1e-12, atol=1e-14)
+
+
+def test_separate_brute_force_tiny():
+    """2^n state vector of each MPS against the product state of the pixels."""
+    n, chi, L, B = 7, 3, 3, 5
+    mps = synth.classifier_separate_mps(n, chi, L, seed=9, eps_std=0.5)
+    px = synth.pixels(B, n, seed=10).astype(np.float64)
+    ft, lam = oracle.classify_separate(mps, px)
+    for l, cores in enumerate(mps):
+        psi = oracle.mps_state([c.astype(np.float64) for c in cores]).reshape([2] * n)
+        for b in range(B):
+            phi = [np.array([np.cos(np.pi * x / 2), np.sin(np.pi * x / 2)]) for x in px[b]]
+            f = psi
+            for v in phi:
+                f = np.tensordot(f, v, axes=([0], [0]))
+            assert ft[b, l] * np.exp(lam[b]) == pytest.approx(float(f), rel=1e-11)
+
+
+def test_separate_loss_equal_scores_is_log_L():
+    n, chi, L, B = 10, 4, 5, 6
+    one = synth.classifier_separate_mps(n, chi, 1, seed=11, eps_std=0.3)[0]
+    mps = [one] * L
+    px = synth.pixels(B, n, seed=12)
+    assert oracle.classify_separate_loss(mps, px, np.arange(B) % L) == pytest.approx(np.log(L), rel=1e-12)
