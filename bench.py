@@ -322,6 +322,19 @@ def run_extras(tn, synth, dev, stream):
             else:
                 entry[prec]["score_diff_vs_fp32_first32"] = _score_err(ft[:32], lam[:32], *ref)
             del ws
+        if chi == 64:
+            # training step: forward with checkpoints every 28 sites, loss head, adjoint backward of every MPS
+            for prec in ("fp32", "bf16"):
+                ws = tn.classifier_separate_workspace(mps, B, 28)
+
+                def sep_step():
+                    ft, lam, _ = tn.mps_classify_separate(mps, px, prec=prec, ckpt_every=28, workspace=ws)
+                    loss, dft = tn.mps_classify_loss(ft, y)
+                    tn.mps_classify_separate_backward(mps, px, dft, ws, prec=prec, ckpt_every=28)
+                ms = _time(sep_step, 2, 1, stream)
+                entry[prec]["train_step_ms"] = ms
+                entry[prec]["train_samples_per_s"] = B / (ms * 1e-3)
+                del ws
         sep["chi%d_L%d" % (chi, L)] = entry
         del mps
     out["classifier_separate"] = sep

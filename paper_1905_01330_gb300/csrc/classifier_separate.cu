@@ -9,6 +9,7 @@
 // back to each MPS's own log-scale and runs that MPS's adjoint sweep.
 #include <math.h>
 
+#include <mutex>
 #include <vector>
 
 #include "tn_internal.h"
@@ -44,8 +45,70 @@ __global__ void cls_sep_scale(const float* __restrict__ dftilde, const double* _
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Workspace: one single-MPS classifier workspace per MPS, then ftilde and
-// log-scale per MPS, then the scaled gradient of one MPS.
+// The MPS are independent: their sweeps run on SEP_STREAMS library-owned
+// streams of the current device (created once, non-blocking), forked from
+// and joined back into the caller's stream by events, so that several
+// sweeps (each a few dozen CTAs at batch 4096) share the GPU.
+constexpr int SEP_STREAMS = 8;
+std::mutex g_sep_lock;
+int g_sep_device = -1;
+cudaStream_t g_sep_streams[SEP_STREAMS];
+
+// Streams for the current device, or null (then everything runs on the
+// caller's stream) if they cannot be made or belong to another device.
+cudaStream_t* sep_streams() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> g(g_sep_lock);
+  if (g_sep_device == -1) {
+    for (int i = 0; i < SEP_STREAMS; ++i)
+      if (cudaStreamCreateWithFlags(&g_sep_streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaStreamDestroy(g_sep_streams[j]);
+        g_sep_device = -2;
+        return nullptr;
+      }
+    g_sep_device = dev;
+  }
+  return g_sep_device == dev ? g_sep_streams : nullptr;
+}
+
+// Runs body(l, stream) for every MPS: on the side streams when there are
+// several MPS, with the caller's stream waiting for all of them at the end.
+template <class F>
+int run_forked(int nl, cudaStream_t caller, F body) {
+  cudaStream_t* side = nl > 1 ? sep_streams() : nullptr;
+  if (!side) {
+    for (int l = 0; l < nl; ++l) {
+      const int rc = body(l, caller);
+      if (rc != TN_OK) return rc;
+    }
+    return TN_OK;
+  }
+  const int ns = nl < SEP_STREAMS ? nl : SEP_STREAMS;
+  cudaEvent_t fork = nullptr, join[SEP_STREAMS] = {};
+  auto done = [&](int rc) {
+    if (fork) cudaEventDestroy(fork);
+    for (int i = 0; i < ns; ++i)
+      if (join[i]) cudaEventDestroy(join[i]);
+    return rc;
+  };
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(fork, caller) != cudaSuccess)
+    return done(TN_ERR_CUDA);
+  for (int i = 0; i < ns; ++i)
+    if (cudaStreamWaitEvent(side[i], fork, 0) != cudaSuccess) return done(TN_ERR_CUDA);
+  int rc = TN_OK;
+  for (int l = 0; l < nl && rc == TN_OK; ++l) rc = body(l, side[l % ns]);
+  // join even after an error, so the caller's stream never runs ahead of work in flight
+  for (int i = 0; i < ns; ++i)
+    if (cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(join[i], side[i]) != cudaSuccess || cudaStreamWaitEvent(caller, join[i], 0) != cudaSuccess)
+      return done(TN_ERR_CUDA);
+  return done(rc);
+}
+
+// Workspace: one single-MPS classifier workspace per MPS, then ftilde,
+// log-scale and the scaled gradient of every MPS.
 struct SepLayout {
   std::vector<size_t> off, bytes;
   size_t ft_off, lam_off, d_off, total;
@@ -68,7 +131,7 @@ int sep_layout(const tn_mps* Ws, int nl, int batch, int ckpt_every, SepLayout* o
   o->ft_off = at;
   o->lam_off = o->ft_off + al256(sizeof(float) * (size_t)nl * (size_t)batch);
   o->d_off = o->lam_off + al256(sizeof(double) * (size_t)nl * (size_t)batch);
-  o->total = o->d_off + al256(sizeof(float) * (size_t)(batch > 0 ? batch : 1));
+  o->total = o->d_off + al256(sizeof(float) * (size_t)nl * (size_t)(batch > 0 ? batch : 1));
   return TN_OK;
 }
 
@@ -98,11 +161,11 @@ int tn_mps_classify_separate(const tn_mps* Ws, int n_mps, const float* pixels, i
   float* ft_each = reinterpret_cast<float*>(base + lay.ft_off);
   double* lam_each = reinterpret_cast<double*>(base + lay.lam_off);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int l = 0; l < n_mps; ++l) {
-    rc = tn_mps_classify(&Ws[l], Ws[l].n / 2, 1, pixels, batch, prec, ckpt_every, ft_each + (int64_t)l * batch,
-                         lam_each + (int64_t)l * batch, base + lay.off[(size_t)l], lay.bytes[(size_t)l], stream);
-    if (rc != TN_OK) return rc;
-  }
+  rc = run_forked(n_mps, s, [&](int l, cudaStream_t sl) {
+    return tn_mps_classify(&Ws[l], Ws[l].n / 2, 1, pixels, batch, prec, ckpt_every, ft_each + (int64_t)l * batch,
+                           lam_each + (int64_t)l * batch, base + lay.off[(size_t)l], lay.bytes[(size_t)l], sl);
+  });
+  if (rc != TN_OK) return rc;
   cls_sep_combine<<<(batch + 127) / 128, 128, 0, s>>>(ft_each, lam_each, batch, n_mps, ftilde, log_scale);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
@@ -134,16 +197,15 @@ int tn_mps_classify_separate_backward(const tn_mps* Ws, int n_mps, const float* 
   uint8_t* base = static_cast<uint8_t*>(workspace);
   double* lam_each = reinterpret_cast<double*>(base + lay.lam_off);
   float* d = reinterpret_cast<float*>(base + lay.d_off);
-  int64_t first = 0;  // dcores: the cores of MPS 0, then of MPS 1, ...
-  for (int l = 0; l < n_mps; ++l) {
-    cls_sep_scale<<<(batch + 127) / 128, 128, 0, s>>>(dftilde, lam_each, batch, n_mps, l, d);
-    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
-    rc = tn_mps_classify_backward(&Ws[l], Ws[l].n / 2, 1, pixels, batch, prec, ckpt_every, d, dcores + first,
-                                  base + lay.off[(size_t)l], lay.bytes[(size_t)l], stream);
-    if (rc != TN_OK) return rc;
-    first += Ws[l].n;
-  }
-  return TN_OK;
+  std::vector<int64_t> first((size_t)n_mps, 0);  // dcores: the cores of MPS 0, then of MPS 1, ...
+  for (int l = 1; l < n_mps; ++l) first[(size_t)l] = first[(size_t)l - 1] + Ws[l - 1].n;
+  return run_forked(n_mps, s, [&](int l, cudaStream_t sl) {
+    float* dl = d + (int64_t)l * batch;
+    cls_sep_scale<<<(batch + 127) / 128, 128, 0, sl>>>(dftilde, lam_each, batch, n_mps, l, dl);
+    if (cudaGetLastError() != cudaSuccess) return (int)TN_ERR_CUDA;
+    return tn_mps_classify_backward(&Ws[l], Ws[l].n / 2, 1, pixels, batch, prec, ckpt_every, dl,
+                                    dcores + first[(size_t)l], base + lay.off[(size_t)l], lay.bytes[(size_t)l], sl);
+  });
 }
 
 }  // extern "C"
