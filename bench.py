@@ -140,6 +140,38 @@ def cpu_oracle_sample(specs_h, count):
     return flops / dt, dt, flops, len(os.sched_getaffinity(0))
 
 
+def cpu_oracle_rows():
+    """The FP64 oracle on the host cores for the rows timed in the extras,
+    each once on a stated case (a few seconds in all): node splitting (numpy's
+    LAPACK SVD in float64), ncon of the N=20, chi=32 norm network, and the
+    classifier with one MPS per label on a 64-sample subset."""
+    import oracle
+    from paper_1905_01330_gb300 import synth
+    out = {}
+    rng = np.random.default_rng(7)
+    for name, shape, left, right, keep in (("split_node_two_site_chi128", (128, 2, 2, 128), [0, 1], [2, 3], 128),
+                                           ("split_node_n1000_keep5", (1000, 1000), [0], [1], 5)):
+        A = rng.standard_normal(shape).astype(np.float32)
+        t0 = time.perf_counter()
+        oracle.split_node(A, left, right, max_singular_values=keep)
+        out[name] = {"ms": 1e3 * (time.perf_counter() - t0)}
+    m = synth.random_mps(20, 2, 32, seed=1)
+    net = []
+    for base in (1000, 2000):
+        for i in range(20):
+            net.append((base + i if i > 0 else 0, 100 + i, base + i + 1 if i < 19 else 1))
+    t0 = time.perf_counter()
+    oracle.ncon(m + m, net)
+    out["ncon_mps_norm_n20_chi32"] = {"ms": 1e3 * (time.perf_counter() - t0)}
+    mps = synth.classifier_separate_mps(784, 32, 10, seed=122, eps_std=0.1)
+    px = synth.pixels(64, 784, seed=3)
+    t0 = time.perf_counter()
+    oracle.classify_separate(mps, px)
+    dt = time.perf_counter() - t0
+    out["classifier_separate_chi32_L10"] = {"samples_per_s": 64 / dt, "sample": "first 64 of 4096 samples"}
+    return out
+
+
 def _time(fn, reps, warm, stream):
     import torch
     for _ in range(warm):
@@ -665,6 +697,8 @@ def main():
         r, dt, fl, cores = cpu_oracle_sample(synth.contraction_specs(N_SPECS, seed=SEED), CPU_SAMPLE_SPECS)
         cpu = {"value": r / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                "sample": "first %d of the 2048 specs (%.2f GFLOP, %.1f s)" % (CPU_SAMPLE_SPECS, fl / 1e9, dt)}
+        if not args.no_extras:
+            cpu["other_rows"] = cpu_oracle_rows()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
