@@ -109,10 +109,22 @@ svd_round(float* __restrict__ W, float* __restrict__ V, int64_t L, int r, int rp
   if (p >= r || q >= r) return;  // the dummy slot of an odd r
   float* wp = W + (int64_t)p * L;
   float* wq = W + (int64_t)q * L;
+  float* vp = V + (int64_t)p * r;
+  float* vq = V + (int64_t)q * r;
   // columns of up to SVD_CACHE * SVD_THREADS entries stay in registers
-  // between the dot products and the rotation
+  // between the dot products and the rotation; V's two columns are loaded
+  // with W's, so their latency overlaps the reduction
   const bool cached = L <= (int64_t)SVD_CACHE * SVD_THREADS;
-  float xs[SVD_CACHE], ys[SVD_CACHE];
+  const bool vcached = r <= SVD_CACHE * SVD_THREADS;
+  float xs[SVD_CACHE], ys[SVD_CACHE], us[SVD_CACHE], ts[SVD_CACHE];
+  if (vcached) {
+#pragma unroll
+    for (int u = 0; u < SVD_CACHE; ++u) {
+      const int i = threadIdx.x + u * SVD_THREADS;
+      us[u] = i < r ? vp[i] : 0.0f;
+      ts[u] = i < r ? vq[i] : 0.0f;
+    }
+  }
   float a = 0.0f, b = 0.0f, g = 0.0f;
   if (cached) {
 #pragma unroll
@@ -137,6 +149,9 @@ svd_round(float* __restrict__ W, float* __restrict__ V, int64_t L, int r, int rp
   __shared__ int skip;
   block_sum3(a, b, g, sums);
   if (threadIdx.x == 0) {
+    // the angle in float64: with float32 c and s from float32 arithmetic the
+    // rounding of c^2 + s^2 is biased and the column norms drift by ~1e-4
+    // over the ~10^4 rotations a column of a 1000-column matrix takes
     const double al = sums[0], be = sums[1], ga = sums[2];
     const bool go = al > 0.0 && be > 0.0 && fabs(ga) > (double)tol * sqrt(al) * sqrt(be);
     if (go) {
@@ -168,12 +183,21 @@ svd_round(float* __restrict__ W, float* __restrict__ V, int64_t L, int r, int rp
       wq[i] = s * x + c * y;
     }
   }
-  float* vp = V + (int64_t)p * r;
-  float* vq = V + (int64_t)q * r;
-  for (int i = threadIdx.x; i < r; i += SVD_THREADS) {
-    const float x = vp[i], y = vq[i];
-    vp[i] = c * x - s * y;
-    vq[i] = s * x + c * y;
+  if (vcached) {
+#pragma unroll
+    for (int u = 0; u < SVD_CACHE; ++u) {
+      const int i = threadIdx.x + u * SVD_THREADS;
+      if (i < r) {
+        vp[i] = c * us[u] - s * ts[u];
+        vq[i] = s * us[u] + c * ts[u];
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < r; i += SVD_THREADS) {
+      const float x = vp[i], y = vq[i];
+      vp[i] = c * x - s * y;
+      vq[i] = s * x + c * y;
+    }
   }
 }
 
