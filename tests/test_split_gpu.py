@@ -107,6 +107,13 @@ def test_random_nodes(tn, shape, left, right):
     check(tn, rand(2, shape), left, right)
 
 
+@pytest.mark.parametrize("shape", [(256, 256), (512, 512), (700, 650)])
+def test_two_site_sizes(tn, shape):
+    """Square and near-square nodes of the sizes a two-site split of an MPS
+    sweep meets (chi = 128, 256): hundreds of rounds per sweep."""
+    check(tn, rand(9, shape), [0], [1])
+
+
 def test_strided_view(tn):
     base = rand(3, (8, 6, 10))
     At = torch.from_numpy(base).cuda().permute(2, 0, 1)[:, ::2]   # (10, 4, 6), non-contiguous
