@@ -434,7 +434,13 @@ def run_extras(tn, synth, dev, stream):
     ts = m + m
     val = float(tn.ncon(ts, net, prec="fp32"))
     ms_ncon = _time(lambda: tn.ncon(ts, net, prec="fp32"), 5, 2, stream)
-    out["ncon_mps_norm_n20_chi32"] = {"ms_per_call": ms_ncon, "steps": len(tn.ncon_plan([t.shape for t in ts], net)[0]),
+    nplan = tn.NconPlan(ts, net, prec="fp32")
+    ms_plan = _time(nplan.run, 10, 2, stream)
+    nplan.capture()
+    ms_graph = _time(nplan.replay, 20, 2, stream)
+    out["ncon_mps_norm_n20_chi32"] = {"ms_per_call": ms_ncon, "ms_per_call_plan": ms_plan,
+                                      "ms_per_call_plan_graph": ms_graph,
+                                      "steps": len(tn.ncon_plan([t.shape for t in ts], net)[0]),
                                       "log_norm": float(np.log(abs(val))),
                                       "log_norm_diff_vs_tn_mps_inner": float(abs(np.log(abs(val)) -
                                                                                (np.log(abs(r[0])) + r[1])))}

@@ -278,6 +278,74 @@ def ncon(tensors, network, con_order=None, out_order=None, prec: str = "fp32", s
     return ops[-1].permute(perm) if perm else ops[-1]
 
 
+class NconPlan:
+    """ncon planned once for fixed tensors (Appendix B): the steps of
+    tn_ncon_plan with their results allocated and every tn_contract /
+    tn_contract_ws argument built here, so run() is one C call per step and
+    can be captured in a CUDA graph (capture()/replay()). The tensors must stay
+    alive and in place; their values may change between runs."""
+
+    def __init__(self, tensors, network, con_order=None, out_order=None, prec: str = "fp32"):
+        self.lib = lib = load()
+        self.prec = PREC[prec]
+        steps, self.perm = ncon_plan([list(t.shape) for t in tensors], network, con_order, out_order, lib)
+        dev = tensors[0].device
+        ops = list(tensors)
+        self._keep = []
+        self.calls = []
+        for a, b, la, lb, shape in steps:
+            A = ops[a]
+            if b < 0:
+                d = A.shape[la[0]]
+                B = torch.from_numpy(np.eye(d, dtype=np.float32)).to(dev)
+                la, lb = [la[0], lb[0]], [0, 1]
+            else:
+                B = ops[b]
+            C = torch.empty(shape, dtype=torch.float32, device=dev)
+            da, db, dc = tensor_desc(A), tensor_desc(B), tensor_desc(C)
+            k = len(la)
+            ia = (ctypes.c_int * max(k, 1))(*la)
+            ib = (ctypes.c_int * max(k, 1))(*lb)
+            ws = None
+            if self.prec != PREC["fp32"]:
+                nb = lib.tn_contract_workspace_bytes(ctypes.byref(da), ia, ctypes.byref(db), ib, k,
+                                                     ctypes.byref(dc), self.prec)
+                ws = _workspace(nb, dev) if nb > 0 else None
+            self._keep += [A, B, C, da, db, dc, ia, ib, ws]
+            self.calls.append((ctypes.byref(da), ia, ctypes.byref(db), ib, k, ctypes.byref(dc), ws))
+            ops.append(C)
+        self.result = ops[-1].permute(self.perm) if self.perm else ops[-1]
+        self.graph = None
+
+    def run(self, stream=None):
+        """Runs every step on `stream` (default: the current stream); returns the result view."""
+        st = _stream(stream)
+        for da, ia, db, ib, k, dc, ws in self.calls:
+            if ws is not None:
+                _check(self.lib.tn_contract_ws(da, ia, db, ib, k, dc, self.prec, ctypes.c_void_p(ws.data_ptr()),
+                                               ws.numel(), st), "tn_contract_ws")
+            else:
+                _check(self.lib.tn_contract(da, ia, db, ib, k, dc, self.prec, st), "tn_contract")
+        return self.result
+
+    def capture(self):
+        """Records run() in a CUDA graph (after one eager run on a side stream)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.result
+
+
 def split_node(A: torch.Tensor, left_legs, right_legs, max_singular_values: int | None = None,
                max_truncation_err: float | None = None, full_svd: bool = False, stream=None,
                info: dict | None = None):

@@ -83,3 +83,26 @@ def test_larger_contraction_chain(tn):
 def test_invalid_network(tn):
     with pytest.raises(tn.TnError):
         tn.ncon([torch.zeros(2, 2, device="cuda"), torch.zeros(3, 2, device="cuda")], [(0, -1), (0, -2)])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 2e-2)])
+def test_plan_eager_and_graph(tn, prec, tol):
+    """NconPlan: planned once, run eagerly and replayed from a CUDA graph,
+    after the inputs' values change in place."""
+    shapes, net = random_network(500, n_tensors=5, n_edges=6, n_open=3, max_dim=6)
+    rng = np.random.default_rng(2)
+    hs = [rng.standard_normal(sh).astype(np.float32) for sh in shapes]
+    ts = [torch.from_numpy(h).cuda() for h in hs]
+    plan = tn.NconPlan(ts, net, prec=prec)
+    ref = oracle.ncon([h.astype(np.float64) for h in hs], net)
+    got = plan.run().double().cpu().numpy()
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+    plan.capture()
+    hs2 = [rng.standard_normal(sh).astype(np.float32) for sh in shapes]
+    for t, h in zip(ts, hs2):
+        t.copy_(torch.from_numpy(h))
+    got2 = plan.replay().double().cpu().numpy()
+    torch.cuda.synchronize()
+    ref2 = oracle.ncon([h.astype(np.float64) for h in hs2], net)
+    assert np.linalg.norm(got2 - ref2) <= tol * np.linalg.norm(ref2)
+    assert tn.sync_status() == 0
