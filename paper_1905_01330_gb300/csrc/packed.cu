@@ -479,23 +479,33 @@ struct ConvRegs {
 // proportionally less time.
 __device__ __forceinline__ int conv_rpw(int rv) { return rv >= PR ? 16 : ((((rv + 7) >> 3) + 1) & ~1); }
 
-// Entries past the operand's end are read at its last row or shared index
-// (always in bounds) and never used: no select waits on the loads, which
-// land while the current slab is rounded.
+// Row entries past the operand's end are read at its last row (always in
+// bounds), shared-index entries past K in the run's zero padding; neither is
+// used, so no select waits on the loads, which land while the current slab is
+// rounded.
 __device__ __forceinline__ void conv_fetch(const ConvIter& it, int cw, int l, ConvRegs& cr) {
   if (!it.valid() || it.mode == 0) return;
-  const int64_t k0 = it.k0(), rl = it.R - 1, kl = it.K - 1;
+  const int64_t k0 = it.k0(), rl = it.R - 1;
   if (it.mode == 1) {
     if (it.ks == 0) {
       const int rpw = conv_rpw(it.rv());
 #pragma unroll
       for (int i = 0; i < 8; ++i) cr.r[i] = __ldg(it.rtab + min(it.p0 + rpw * cw + (l >> 4) + 2 * i, rl));
     }
-    cr.k[0] = __ldg(it.ktab + min(k0 + 4 * (l & 15), kl));
+    cr.k[0] = __ldg(it.ktab + k0 + 4 * (l & 15));  // inside the padded run
   } else {
     if (it.ks == 0) cr.r[0] = __ldg(it.rtab + min(it.p0 + 4 * l, rl));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) cr.k[i] = __ldg(it.ktab + min(k0 + 8 * cw + i, kl));
+    // the run is 32-byte aligned and padded to whole slabs (fused_tables)
+    const int4* kp = reinterpret_cast<const int4*>(it.ktab + k0 + 8 * cw);
+    const int4 k03 = __ldg(kp), k47 = __ldg(kp + 1);
+    cr.k[0] = k03.x;
+    cr.k[1] = k03.y;
+    cr.k[2] = k03.z;
+    cr.k[3] = k03.w;
+    cr.k[4] = k47.x;
+    cr.k[5] = k47.y;
+    cr.k[6] = k47.z;
+    cr.k[7] = k47.w;
   }
 }
 
@@ -1197,8 +1207,13 @@ void fused_tables(const ContractDesc& d, std::vector<int32_t>* tab, int64_t* rta
   };
   *rtab_off = (int64_t)tab->size();
   run(R, nr, rdim, rstr);
+  // the shared-index run starts on a 32-byte boundary and is padded with
+  // zeros to whole 64-wide slabs, so a converter reads the 8 entries of its
+  // k-rows as two aligned 16-byte loads, never past the run
+  while (tab->size() % 8) tab->push_back(0);
   *ktab_off = (int64_t)tab->size();
   run(d.K, d.nk, d.kdim, kstr);
+  while ((tab->size() - (size_t)*ktab_off) % PK) tab->push_back(0);
 }
 
 int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,

@@ -31,7 +31,8 @@ struct PackJob {
                           // aligned), 0 none
   int32_t rg, nbv;        // pack: rows per block, and blocks packed at once (nbv * rg <= 128)
   const int32_t* rtab;    // device (fused P only): source offset of every row, R entries
-  const int32_t* ktab;    // and of every shared index, K entries
+  const int32_t* ktab;    // and of every shared index, K entries (32-byte aligned, zero-padded
+                          // to whole 64-wide slabs)
   int64_t rtab_off, ktab_off;  // host: their element offsets in the plan's table region, -1 none
   int32_t rdim[TN_MAX_RANK];
   int32_t kdim[TN_MAX_RANK];

@@ -143,7 +143,8 @@ def test_autotune_picks_a_schedule_and_caches_it(tn, prec):
     plan = tn.GroupPlan(specs, prec=prec)
     sched = plan.autotune()
     assert tn.sync_status() == 0
-    assert all(w in (64, 128) and lk in (0, 1) and s16 in (0, 1) for w, lk, s16 in sched.values())
+    widths = (64, 128, 256) if prec == "bf16" else (64, 128)   # 256-wide tiles are BF16 only
+    assert all(w in widths and lk in (0, 1) and s16 in (0, 1) for w, lk, s16 in sched.values())
     for sp in specs:
         sp[4].fill_(float("nan"))
     plan.run()
