@@ -540,6 +540,82 @@ class GroupPlan:
 # MPS classifier (Sec. IV.A)
 # ---------------------------------------------------------------------------
 
+class StagedGroupPlan:
+    """A grouped contraction fed from pinned host memory and drained back to it
+    in chunks. The specs' operands must fill one device buffer `dev_in` and
+    their results another, `dev_out`, in spec order (each chunk of consecutive
+    specs then owns one contiguous range of each). run(host_in, host_out)
+    copies chunk c's operands host -> device on one stream while chunk c-1 is
+    contracted (its own GroupPlan) on a second and chunk c-2's results go
+    device -> host on a third, so the two copy directions and the kernels
+    overlap; the caller's stream waits for the last copy. host_in / host_out
+    are pinned tensors laid out like dev_in / dev_out."""
+
+    def __init__(self, specs, dev_in: torch.Tensor, dev_out: torch.Tensor, chunks: int = 8, prec: str = "bf16",
+                 schedule=None):
+        if dev_in.dim() != 1 or dev_out.dim() != 1:
+            raise ValueError("dev_in and dev_out must be 1-D buffers")
+        esz = dev_in.element_size()
+        base_in, base_out = dev_in.data_ptr(), dev_out.data_ptr()
+
+        def span(t, base, n):
+            lo = (t.data_ptr() - base) // esz
+            if t.data_ptr() < base or lo + t.numel() > n:
+                raise ValueError("a spec tensor lies outside its buffer")
+            return lo, lo + t.numel()
+        weights = [A.numel() + B.numel() + C.numel() for A, _, B, _, C in specs]
+        total, acc = sum(weights), 0
+        bounds = [0]
+        for i, w in enumerate(weights):
+            acc += w
+            if len(bounds) < chunks and acc >= total * len(bounds) / chunks and i + 1 < len(specs):
+                bounds.append(i + 1)
+        bounds.append(len(specs))
+        self.dev_in, self.dev_out = dev_in, dev_out
+        self.parts = []
+        prev_in = prev_out = 0
+        for c in range(len(bounds) - 1):
+            sp = specs[bounds[c]:bounds[c + 1]]
+            if not sp:
+                continue
+            ins = [span(t, base_in, dev_in.numel()) for A, _, B, _, _ in sp for t in (A, B)]
+            outs = [span(C, base_out, dev_out.numel()) for *_, C in sp]
+            lo_in, hi_in = min(a for a, _ in ins), max(b for _, b in ins)
+            lo_out, hi_out = min(a for a, _ in outs), max(b for _, b in outs)
+            if lo_in < prev_in or lo_out < prev_out:
+                raise ValueError("operands and results must be laid out in spec order")
+            prev_in, prev_out = hi_in, hi_out
+            plan = GroupPlan(sp, prec=prec)
+            if schedule:
+                for cls, (w, lk, s16) in schedule.items():
+                    plan.set_schedule(cls, w, bool(lk), bool(s16))
+            self.parts.append((plan, lo_in, hi_in, lo_out, hi_out))
+        self.flops = sum(p[0].flops for p in self.parts)
+        dev = dev_in.device
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+
+    def run(self, host_in: torch.Tensor, host_out: torch.Tensor):
+        h2d, comp, d2h = self.streams
+        cur = torch.cuda.current_stream(self.dev_in.device)
+        for st in self.streams:
+            st.wait_stream(cur)
+        for plan, lo_in, hi_in, lo_out, hi_out in self.parts:
+            with torch.cuda.stream(h2d):
+                self.dev_in[lo_in:hi_in].copy_(host_in[lo_in:hi_in], non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(h2d)
+            comp.wait_event(ready)
+            with torch.cuda.stream(comp):
+                plan.run()
+                done = torch.cuda.Event()
+                done.record(comp)
+            d2h.wait_event(done)
+            with torch.cuda.stream(d2h):
+                host_out[lo_out:hi_out].copy_(self.dev_out[lo_out:hi_out], non_blocking=True)
+        for st in self.streams:
+            cur.wait_stream(st)
+
+
 def classifier_workspace(cores, label_site: int, n_labels: int, batch: int, ckpt_every: int) -> torch.Tensor:
     lib = load()
     ch, keep = chain_desc_classifier(cores, label_site)

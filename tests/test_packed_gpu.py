@@ -198,3 +198,49 @@ def test_fused_gemm_access_patterns(tn):
         assert tn.sync_status() == 0
         for (A, la, B, lb), sp in zip(host, specs):
             check(sp[4], A, la, B, lb, "bf16")
+
+
+def test_staged_plan_from_pinned_host(tn):
+    """StagedGroupPlan: operands in one device buffer and results in another
+    (spec order), fed from and drained to pinned host buffers chunk by chunk
+    on three streams; every result checked after two runs (the second with
+    new operand values in the host buffer)."""
+    st = synth.Stream(77)
+    # the two large specs first: chunks of equal weight are then [big], [thin], [20 small]
+    shapes = [((640, 4608), [1], (4608, 520), [0]), ((4096,), [0], (4096, 200), [0])]
+    shapes += [synth.contraction_spec(st, dims=(3, 8, 13, 24, 48, 64), cap=1 << 17) for _ in range(20)]
+
+    def layout(sizes):
+        offs, n = [], 0
+        for k in sizes:
+            offs.append(n)
+            n += (k + 63) // 64 * 64
+        return offs, n
+    in_sizes = [int(np.prod(sh)) for sa, _, sb, _ in shapes for sh in (sa, sb)]
+    outs = [tuple(sa[p] for p in range(len(sa)) if p not in la) + tuple(sb[p] for p in range(len(sb)) if p not in lb)
+            for sa, la, sb, lb in shapes]
+    in_offs, n_in = layout(in_sizes)
+    out_offs, n_out = layout([int(np.prod(o)) for o in outs])
+    dev_in, dev_out = torch.empty(n_in, device="cuda"), torch.empty(n_out, device="cuda")
+    specs = []
+    for i, (sa, la, sb, lb) in enumerate(shapes):
+        A = dev_in[in_offs[2 * i]:in_offs[2 * i] + in_sizes[2 * i]].view(sa)
+        B = dev_in[in_offs[2 * i + 1]:in_offs[2 * i + 1] + in_sizes[2 * i + 1]].view(sb)
+        C = dev_out[out_offs[i]:out_offs[i] + int(np.prod(outs[i]))].view(outs[i])
+        specs.append((A, list(la), B, list(lb), C))
+    staged = tn.StagedGroupPlan(specs, dev_in, dev_out, chunks=3, prec="bf16")
+    assert len(staged.parts) == 3
+    host_in = torch.empty(n_in, dtype=torch.float32, pin_memory=True)
+    host_out = torch.empty(n_out, dtype=torch.float32, pin_memory=True)
+    for seed in (1, 2):
+        host_in.copy_(torch.from_numpy(np.random.default_rng(seed).standard_normal(n_in).astype(np.float32)))
+        host_out.fill_(float("nan"))
+        staged.run(host_in, host_out)
+        torch.cuda.synchronize()
+        assert tn.sync_status() == 0
+        hi = host_in.numpy()
+        for i, (sa, la, sb, lb) in enumerate(shapes):
+            A = hi[in_offs[2 * i]:in_offs[2 * i] + in_sizes[2 * i]].reshape(sa)
+            B = hi[in_offs[2 * i + 1]:in_offs[2 * i + 1] + in_sizes[2 * i + 1]].reshape(sb)
+            C = host_out[out_offs[i]:out_offs[i] + int(np.prod(outs[i]))].view(outs[i])
+            check(C, A, la, B, lb, "bf16")
