@@ -207,3 +207,33 @@ def test_ncon_planner_without_gpu(libpath):
         with pytest.raises(tn.TnError) as e:
             tn.ncon_plan(shapes, net, co, oo, lib=lib)
         assert e.value.code == code
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_ncon_planner_steps_evaluate_the_network(libpath, seed):
+    """The host planner's steps, executed with the FP64 oracle's tensordot and
+    trace (CPU), give the oracle's ncon of the same random network (traces,
+    multi-edges, unconnected pieces), for the default and a shuffled order."""
+    import sys
+    import numpy as np
+    import oracle
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from ncon_nets import random_network
+    lib, tn = _bound(libpath)
+    shapes, net = random_network(600 + seed)
+    rng = np.random.default_rng(seed)
+    ts = [rng.standard_normal(sh) for sh in shapes]
+    edges = sorted({x for labels in net for x in labels if x >= 0})
+    for order in (None, list(rng.permutation(edges))):
+        steps, perm = tn.ncon_plan(shapes, net, con_order=order, lib=lib)
+        ops = list(ts)
+        for a, b, la, lb, shape in steps:
+            if b < 0:
+                r = oracle.trace(ops[a], la[0], lb[0])
+            else:
+                r = oracle.tensordot(ops[a], la, ops[b], lb)
+            assert list(np.shape(r)) == shape
+            ops.append(r)
+        got = np.transpose(ops[-1], perm) if perm else ops[-1]
+        ref = oracle.ncon(ts, net, con_order=order)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
