@@ -7,7 +7,10 @@ share no code; they share only the seeded inputs of
 
 The arithmetic lives in ``oracle.c`` (plain nested loops in float64, OpenMP
 over independent outputs); this module builds it with gcc and marshals numpy
-arrays through ctypes.
+arrays through ctypes. Three modules build on it: ``split.py`` (node
+splitting, its decomposition step numpy's LAPACK SVD), ``ncon.py`` (ncon over
+tensordot and trace) and ``classifier_separate.py`` (one MPS per label over
+the classifier sweep).
 """
 from __future__ import annotations
 
