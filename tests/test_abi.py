@@ -15,7 +15,8 @@ def declared_functions():
     for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if not hdr.endswith(".h"):
             continue
-        text = open(os.path.join(ROOT, "include", hdr)).read()
+        with open(os.path.join(ROOT, "include", hdr)) as f:
+            text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tn_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))

@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_the_slowest_time():
     world, port = 2, free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
