@@ -238,3 +238,39 @@ def test_ncon_planner_steps_evaluate_the_network(libpath, seed):
         got = np.transpose(ops[-1], perm) if perm else ops[-1]
         ref = oracle.ncon(ts, net, con_order=order)
         assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_separate_classifier_validation_without_gpu(libpath):
+    """tn_mps_classify_separate*: counts, lengths and pointers are checked on the
+    host before any CUDA call."""
+    lib, tn = _bound(libpath)
+    n, chi = 6, 4
+    bonds = [1] + [chi] * (n - 1) + [1]
+
+    def chain(nsites):
+        b = bonds[:nsites] + [1]
+        bond_arr = (ctypes.c_int64 * (nsites + 1))(*b)
+        ptr_arr = (ctypes.c_void_p * nsites)(*[0x1000 * (i + 1) for i in range(nsites)])
+        ch = tn.TnChain()
+        ch.n, ch.d = nsites, 2
+        ch.bond = ctypes.cast(bond_arr, ctypes.POINTER(ctypes.c_int64))
+        ch.cores = ctypes.cast(ptr_arr, ctypes.POINTER(ctypes.c_void_p))
+        return ch, (bond_arr, ptr_arr)
+    (c0, k0), (c1, k1), (c2, k2) = chain(n), chain(n), chain(n - 1)
+    two = (tn.TnChain * 2)(c0, c1)
+    mixed = (tn.TnChain * 2)(c0, c2)
+    assert lib.tn_mps_classify_separate_workspace_bytes(two, 2, 8, 1) > 0
+    assert lib.tn_mps_classify_separate_workspace_bytes(two, 0, 8, 1) == 0
+    assert lib.tn_mps_classify_separate_workspace_bytes(two, 65, 8, 1) == 0
+    assert lib.tn_mps_classify_separate_workspace_bytes(two, 2, -1, 1) == 0
+    px = ctypes.c_void_p(0x5000)
+    ft, lam = ctypes.c_void_p(0x6000), ctypes.c_void_p(0x7000)
+    # MPS of different lengths
+    assert lib.tn_mps_classify_separate(mixed, 2, px, 8, 0, 0, ft, lam, None, 0, None) == 2
+    # missing outputs
+    assert lib.tn_mps_classify_separate(two, 2, px, 8, 0, 0, None, lam, None, 0, None) == 1
+    # no workspace
+    assert lib.tn_mps_classify_separate(two, 2, px, 8, 0, 0, ft, lam, None, 0, None) == 6
+    # backward: checkpoints every >= 1 site required
+    table = (ctypes.c_void_p * (2 * n))(*[0x9000] * (2 * n))
+    assert lib.tn_mps_classify_separate_backward(two, 2, px, 8, 0, 0, ft, table, None, 0, None) == 1
