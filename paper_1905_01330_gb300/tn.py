@@ -6,6 +6,7 @@ built, or no GPU is present, the calls raise.
 """
 from __future__ import annotations
 
+import bisect
 import ctypes
 import os
 
@@ -540,6 +541,30 @@ class GroupPlan:
 # MPS classifier (Sec. IV.A)
 # ---------------------------------------------------------------------------
 
+def chunk_bounds(weights, chunks: int):
+    """Cuts a sequence of items with the given weights into at most `chunks`
+    runs of consecutive items of about equal total weight: returns the run
+    boundaries [0, ..., len(weights)]. Boundary k goes where the running
+    weight comes closest to k/chunks of the total (strictly after the
+    previous boundary and before the end); a run never splits an item, so
+    heavy items make fewer, unequal runs."""
+    n, cum, acc = len(weights), [], 0
+    for w in weights:
+        acc += w
+        cum.append(acc)
+    bounds = [0]
+    for k in range(1, chunks):
+        t = acc * k / chunks
+        j = bisect.bisect_left(cum, t)  # first item whose running weight reaches t
+        cands = list(range(max(bounds[-1] + 1, j), min(j + 2, n)))
+        if not cands and bounds[-1] + 1 < n:
+            cands = [bounds[-1] + 1]
+        if cands:
+            bounds.append(min(cands, key=lambda b: abs(cum[b - 1] - t)))
+    bounds.append(n)
+    return bounds
+
+
 class StagedGroupPlan:
     """A grouped contraction fed from pinned host memory and drained back to it
     in chunks. The specs' operands must fill one device buffer `dev_in` and
@@ -563,14 +588,7 @@ class StagedGroupPlan:
             if t.data_ptr() < base or lo + t.numel() > n:
                 raise ValueError("a spec tensor lies outside its buffer")
             return lo, lo + t.numel()
-        weights = [A.numel() + B.numel() + C.numel() for A, _, B, _, C in specs]
-        total, acc = sum(weights), 0
-        bounds = [0]
-        for i, w in enumerate(weights):
-            acc += w
-            if len(bounds) < chunks and acc >= total * len(bounds) / chunks and i + 1 < len(specs):
-                bounds.append(i + 1)
-        bounds.append(len(specs))
+        bounds = chunk_bounds([A.numel() + B.numel() + C.numel() for A, _, B, _, C in specs], chunks)
         self.dev_in, self.dev_out = dev_in, dev_out
         self.parts = []
         prev_in = prev_out = 0

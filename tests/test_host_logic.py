@@ -1,0 +1,40 @@
+"""Host logic without a GPU: the chunking of StagedGroupPlan and the bench's
+JSON line of the reference arm (the FP64 oracle on the host cores)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("weights,chunks,bounds", [
+    ([1] * 8, 4, [0, 2, 4, 6, 8]),
+    ([1] * 7, 3, [0, 2, 5, 7]),
+    ([10, 1, 1, 1], 3, [0, 1, 2, 4]),       # a heavy first item ends a run by itself
+    ([1, 1, 1, 10], 3, [0, 3, 4]),          # a heavy last item: fewer runs
+    ([5.68e6, 8.2e5] + [4e4] * 20, 3, [0, 1, 2, 22]),   # the staged-plan GPU test's specs
+    ([5], 8, [0, 1]),
+    ([], 4, [0, 0]),
+])
+def test_chunk_bounds(weights, chunks, bounds):
+    from paper_1905_01330_gb300.tn import chunk_bounds
+    got = chunk_bounds(weights, chunks)
+    assert got == bounds
+    assert all(a < b for a, b in zip(got, got[1:])) or not weights
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["dtype"] == "f64"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
