@@ -451,8 +451,8 @@ int tn_mps_classify_separate_backward(const tn_mps* Ws, int n_mps, const float* 
  *
  * Arithmetic: float32 one-sided Jacobi (Hestenes) on the r columns of
  * length max(M, N), the rotation angles computed in float64; singular values
- * are column norms. Columns of U (or of V when M < N) that belong to a zero
- * singular value are zeros. Workspace: tn_split_node_workspace_bytes (256-B
+ * are column norms. The singular vectors of a zero singular value on the
+ * longer side (columns of U when M >= N, rows of V^T when M < N) are zeros. Workspace: tn_split_node_workspace_bytes (256-B
  * aligned). Unlike the other entry points this call synchronises `stream`
  * (once per sweep and before the outputs, whose shapes depend on k).
  * Errors: TN_ERR_ARG (legs not a partition of A's, null outputs or kept),
