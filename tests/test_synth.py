@@ -39,3 +39,16 @@ def test_bonds_and_tfim_shapes():
     assert synth.mps_bonds(6, 2, 4) == [1, 2, 4, 4, 4, 2, 1]
     W = synth.tfim_mpo(4)
     assert [w.shape for w in W] == [(1, 3, 2, 2), (3, 3, 2, 2), (3, 3, 2, 2), (3, 1, 2, 2)]
+
+
+def test_classifier_separate_mps_is_seeded_and_near_identity():
+    a = synth.classifier_separate_mps(8, 4, 3, seed=5, eps_std=0.1)
+    b = synth.classifier_separate_mps(8, 4, 3, seed=5, eps_std=0.1)
+    assert len(a) == 3 and all(len(m) == 8 for m in a)
+    for ma, mb in zip(a, b):
+        for x, y in zip(ma, mb):
+            assert x.dtype == np.float32 and np.array_equal(x, y)
+    assert [c.shape for c in a[0]] == [(1, 2, 4)] + [(4, 2, 4)] * 6 + [(4, 2, 1)]
+    assert not np.array_equal(a[0][3], a[1][3])                 # each label its own MPS
+    eye = synth.classifier_separate_mps(8, 4, 2, seed=5, eps_std=0.0)[1][3]
+    assert np.array_equal(eye[:, 0, :], np.eye(4, dtype=np.float32))
