@@ -141,9 +141,12 @@ int tn_group_plan_upload(const tn_group_plan* plan, void* workspace, size_t byte
 int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, void* stream);
 void tn_group_plan_destroy(tn_group_plan* plan);
 /*
- * Grouped contraction that allocates nothing: the same contractions and
- * kernels as a plan's create + upload + run, with the work list kept in a
- * fixed 4 MiB array inside the library instead of a caller workspace. (The
+ * Grouped contraction that allocates nothing: the same results as a plan's
+ * create + upload + run, computed by the single-pass grouped kernels (the
+ * tcgen05 kernel for BF16 / BF16X3, the SIMT kernel for FP32; not the pack +
+ * GEMM launches or the small-first-operand FP32 kernel a plan may choose, so
+ * speed and rounding order can differ from a plan's), with the work list kept
+ * in a fixed 4 MiB array inside the library instead of a caller workspace. (The
  * paper has no counterpart; this is a convenience of the library.) It is for
  * callers that must not call cudaMalloc: code whose device memory all belongs
  * to another framework's pool, where an extra cudaMalloc can exceed the
@@ -159,6 +162,9 @@ void tn_group_plan_destroy(tn_group_plan* plan);
  *   Every GPU that loads libtn.so holds the array until the process exits.
  *   All calls share the array: calls whose work overlaps on the GPU (other
  *   streams or host threads) race on it; calls on one stream are ordered.
+ *   The work list goes to the array in three copies from the library's
+ *   pageable host staging arrays; a copy from pageable memory may block the
+ *   calling thread until the stream's earlier work has finished.
  * Errors: as tn_group_plan_create, plus TN_ERR_UNSUPPORTED (too large) and
  * TN_ERR_CUDA.
  */

@@ -201,14 +201,6 @@ int launch_sweep_chi(const SweepParams& p, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
-int launch_sweep(int chi, const SweepParams& p, cudaStream_t s);
-
-// The tensor-core images of one mode for both half-chains.
-int pack_images(const tn_mps* W, const struct ClsLayout& w, int mode, cudaStream_t s);
-
-// A sweep on the float32 kernel (prec FP32) or the tcgen05 kernel (else).
-int run_sweep(int prec, const struct ClsLayout& w, const SweepParams& p, cudaStream_t s);
-
 int launch_sweep(int chi, const SweepParams& p, cudaStream_t s) {
   if (p.t_end <= p.t_begin) return TN_OK;
   if (chi == 32) return launch_sweep_chi<32>(p, s);
@@ -217,131 +209,132 @@ int launch_sweep(int chi, const SweepParams& p, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------- label core
+// The label core C[a, s, l, c] meets the two half-chain vectors vL, vR:
+//   ftilde_b[l] = sum_{a,s} vL_b[a] Phi_s(x_b) G_b[a, s, l],  G_b[a, s, l] = sum_c C[a, s, l, c] vR_b[c],
+// with G one float32 contraction over c for the whole batch. Its adjoint,
+// for d_b = dLoss/dftilde_b and H_b[a, s, l] = vL_b[a] Phi_s(x_b) d_b[l]:
+//   gL_b[a] = sum_{s,l} d_b[l] Phi_s(x_b) G_b[a, s, l],
+//   gR_b[c] = sum_{a,s,l} H_b[a, s, l] C[a, s, l, c]   (a contraction over (a, s, l)),
+//   dC[a, s, l, c] = sum_b H_b[a, s, l] vR_b[c]         (a contraction over b).
+constexpr int LABEL_MAXL = 16;
+
 struct LabelParams {
   int32_t n, batch, ls, L, chi, DL, DR;
-  const float* C;       // (DL, 2, L, DR)
   const float* pixels;  // [batch, n]
   const float* vL;      // [batch, chi]
-  const float* vR;
   const double* lamL;
   const double* lamR;
+  const float* G;       // [batch, DL, 2, L]
   float* ftilde;        // [batch, L]
   double* log_scale;    // [batch]
   const float* dft;     // adjoint: [batch, L]
-  float* gL;            // adjoint: [batch, chi]
-  float* gR;
-  float* Y;             // adjoint: [batch, 2, L, DR]
+  float* gL;            // adjoint: [batch, chi] (zero past DL)
+  float* H;             // adjoint: [batch, DL, 2, L]
 };
 
-constexpr int LABEL_MAXL = 16;
-
-__global__ void __launch_bounds__(128) cls_label_fwd(const __grid_constant__ LabelParams p) {
-  const int b = blockIdx.x, tid = threadIdx.x;
-  __shared__ float red[LABEL_MAXL][128 / 32];
-  const float x = p.pixels[(int64_t)b * p.n + p.ls];
+// One warp per sample: ftilde_b[l] = sum_{a,s} vL_b[a] Phi_s G_b[a, s, l].
+__global__ void __launch_bounds__(256) cls_label_reduce(const __grid_constant__ LabelParams p) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= p.batch) return;
+  const float x = __ldg(p.pixels + (int64_t)b * p.n + p.ls);
   const float ph[2] = {cospif(0.5f * x), sinpif(0.5f * x)};
   const float* vL = p.vL + (int64_t)b * p.chi;
-  const float* vR = p.vR + (int64_t)b * p.chi;
+  const float* G = p.G + (int64_t)b * p.DL * 2 * p.L;
   float acc[LABEL_MAXL];
+#pragma unroll
   for (int l = 0; l < LABEL_MAXL; ++l) acc[l] = 0.0f;
-  for (int as = tid; as < p.DL * 2; as += blockDim.x) {
-    const int a = as >> 1, s = as & 1;
-    const float w = vL[a] * ph[s];
-    for (int l = 0; l < p.L; ++l) {
-      const float* Cr = p.C + ((int64_t)as * p.L + l) * p.DR;
-      float t = 0.0f;
-      for (int c = 0; c < p.DR; ++c) t = fmaf(Cr[c], vR[c], t);
-      acc[l] = fmaf(w, t, acc[l]);
-    }
+  for (int as = lane; as < p.DL * 2; as += 32) {
+    const float w = vL[as >> 1] * ph[as & 1];
+#pragma unroll
+    for (int l = 0; l < LABEL_MAXL; ++l)
+      if (l < p.L) acc[l] = fmaf(w, G[(int64_t)as * p.L + l], acc[l]);
   }
-  for (int l = 0; l < p.L; ++l) {
-    float v = acc[l];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((tid & 31) == 0) red[l][tid >> 5] = v;
+#pragma unroll
+  for (int l = 0; l < LABEL_MAXL; ++l)
+    for (int o = 16; o > 0; o >>= 1) acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], o);
+  if (lane < p.L) {
+    float v = acc[0];
+#pragma unroll
+    for (int l = 1; l < LABEL_MAXL; ++l)
+      if (lane == l) v = acc[l];
+    p.ftilde[(int64_t)b * p.L + lane] = v;
   }
-  __syncthreads();
-  if (tid < p.L) {
-    float v = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[tid][w];
-    p.ftilde[(int64_t)b * p.L + tid] = v;
-  }
-  if (tid == 0) p.log_scale[b] = p.lamL[b] + p.lamR[b];
+  if (lane == 0) p.log_scale[b] = p.lamL[b] + p.lamR[b];
 }
 
-// Adjoint of the label core for one sample: gL[a] = sum_{s,l,c} d_l Phi_s C[a,s,l,c] vR[c],
-// gR[c] = sum_{a,s,l} d_l vL[a] Phi_s C[a,s,l,c], Y[s,l,c] = d_l Phi_s vR[c].
-__global__ void __launch_bounds__(128) cls_label_bwd(const __grid_constant__ LabelParams p) {
-  const int b = blockIdx.x, tid = threadIdx.x;
-  const float x = p.pixels[(int64_t)b * p.n + p.ls];
+// One warp per sample: gL_b and H_b.
+__global__ void __launch_bounds__(256) cls_label_adjoint(const __grid_constant__ LabelParams p) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= p.batch) return;
+  const float x = __ldg(p.pixels + (int64_t)b * p.n + p.ls);
   const float ph[2] = {cospif(0.5f * x), sinpif(0.5f * x)};
   const float* vL = p.vL + (int64_t)b * p.chi;
-  const float* vR = p.vR + (int64_t)b * p.chi;
+  const float* G = p.G + (int64_t)b * p.DL * 2 * p.L;
+  float* H = p.H + (int64_t)b * p.DL * 2 * p.L;
   const float* d = p.dft + (int64_t)b * p.L;
-  for (int a = tid; a < p.chi; a += blockDim.x) {
+  for (int a = lane; a < p.chi; a += 32) {
     float acc = 0.0f;
     if (a < p.DL)
       for (int s = 0; s < 2; ++s)
         for (int l = 0; l < p.L; ++l) {
-          const float* Cr = p.C + (((int64_t)a * 2 + s) * p.L + l) * p.DR;
-          float t = 0.0f;
-          for (int c = 0; c < p.DR; ++c) t = fmaf(Cr[c], vR[c], t);
-          acc = fmaf(d[l] * ph[s], t, acc);
+          const int64_t i = ((int64_t)a * 2 + s) * p.L + l;
+          acc = fmaf(d[l] * ph[s], G[i], acc);
+          H[i] = vL[a] * ph[s] * d[l];
         }
     p.gL[(int64_t)b * p.chi + a] = acc;
   }
-  for (int c = tid; c < p.chi; c += blockDim.x) {
-    float acc = 0.0f;
-    if (c < p.DR)
-      for (int a = 0; a < p.DL; ++a)
-        for (int s = 0; s < 2; ++s) {
-          const float w = vL[a] * ph[s];
-          for (int l = 0; l < p.L; ++l) acc = fmaf(w * d[l], p.C[(((int64_t)a * 2 + s) * p.L + l) * p.DR + c], acc);
-        }
-    p.gR[(int64_t)b * p.chi + c] = acc;
-  }
-  for (int i = tid; i < 2 * p.L * p.DR; i += blockDim.x) {
-    const int c = i % p.DR, l = (i / p.DR) % p.L, s = i / (p.DR * p.L);
-    p.Y[(int64_t)b * 2 * p.L * p.DR + i] = d[l] * ph[s] * vR[c];
-  }
 }
 
-// Loss head: one CTA, samples strided over its threads, float64 partial sums
-// reduced in a fixed order.
-__global__ void __launch_bounds__(256)
+// dst[b, c] = src[b, c] for c < D, 0 for D <= c < chi.
+__global__ void cls_pad_rows(const float* __restrict__ src, int D, float* __restrict__ dst, int batch, int chi) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)batch * chi) return;
+  const int64_t b = i / chi;
+  const int c = (int)(i % chi);
+  dst[i] = c < D ? src[b * D + c] : 0.0f;
+}
+
+// Loss head: one CTA of 1024 threads, samples strided over the threads; the
+// softmax of the normalised scores (|z| <= 1) in float32, the norm and the
+// batch sum in float64, reduced in a fixed order (deterministic).
+constexpr int LOSS_THREADS = 1024;
+__global__ void __launch_bounds__(LOSS_THREADS)
 cls_loss_kernel(const float* __restrict__ ft, const int64_t* __restrict__ y, int batch, int L, double* loss,
                 float* dft) {
-  __shared__ double red[256];
+  __shared__ double red[LOSS_THREADS];
   double acc = 0.0;
-  for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+  for (int b = threadIdx.x; b < batch; b += LOSS_THREADS) {
     const float* f = ft + (int64_t)b * L;
     double nrm = 0.0;
     for (int l = 0; l < L; ++l) nrm += (double)f[l] * f[l];
     nrm = sqrt(nrm);
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    double z[LABEL_MAXL], pz[LABEL_MAXL], zmax = -1e300;
+    const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
+    float z[LABEL_MAXL], pz[LABEL_MAXL], zmax = -3.0e38f;
     for (int l = 0; l < L; ++l) {
       z[l] = f[l] * inv;
-      zmax = fmax(zmax, z[l]);
+      zmax = fmaxf(zmax, z[l]);
     }
-    double se = 0.0;
+    float se = 0.0f;
     for (int l = 0; l < L; ++l) {
-      pz[l] = exp(z[l] - zmax);
+      pz[l] = expf(z[l] - zmax);
       se += pz[l];
     }
     const int64_t yb = y[b];
-    acc += zmax + log(se) - z[yb];
+    acc += (double)(zmax + logf(se) - z[yb]);
     if (dft) {
-      double zg = 0.0;
+      float zg = 0.0f;
+      const float ise = 1.0f / se;
       for (int l = 0; l < L; ++l) {
-        pz[l] = pz[l] / se - (l == yb ? 1.0 : 0.0);
+        pz[l] = pz[l] * ise - (l == yb ? 1.0f : 0.0f);
         zg += z[l] * pz[l];
       }
-      for (int l = 0; l < L; ++l) dft[(int64_t)b * L + l] = (float)((pz[l] - z[l] * zg) * inv / batch);
+      const float sc = inv / (float)batch;
+      for (int l = 0; l < L; ++l) dft[(int64_t)b * L + l] = (pz[l] - z[l] * zg) * sc;
     }
   }
   red[threadIdx.x] = acc;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
+  for (int o = LOSS_THREADS / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
@@ -356,8 +349,11 @@ __global__ void cls_init_state(float* state, double* lam, int batch, int chi) {
 }
 
 // ----------------------------------------------------------------- layout
+// Workspace of one classifier. The forward leaves the half-chain vectors,
+// their log-scales, the per-step scales and the kept vectors here for the
+// backward.
 struct ClsLayout {
-  int n, ls, L, batch, chi, ck;
+  int n, ls, L, batch, chi, ck, ntiles;
   int T[2];        // steps per half
   int nck[2];      // kept vectors per half
   int seg_len;     // steps per backward segment
@@ -366,14 +362,23 @@ struct ClsLayout {
   float* ckpt[2];
   float* sc[2];
   float* g[2];
+  float* replay[2];     // running vector of a segment's recomputation [batch][chi]
+  double* replay_lam[2];
+  // float32 path
   float* seg;      // recomputed vectors of one segment [seg_len][batch][chi]
-  float* replay;   // running vector of the segment replay [batch][chi]
   float* X;        // [seg_len][batch][2 chi]
-  float* Y;        // [batch][2][L][chi]
-  uint8_t* plan_ws;
-  uint8_t* img[2][2];  // bf16 core images per half and mode (tensor-core sweeps)
-  size_t img_bytes;
+  uint8_t* plan_ws;  // every segment's grouped plan, one region each
   size_t plan_bytes;
+  int plan_count;
+  // tensor-core path
+  uint8_t* fimg[2];  // forward core images per half
+  uint8_t* aimg[2];  // adjoint core images per half
+  uint8_t* vseg[2];  // bf16 vector tiles of one segment per half
+  float* grad[2];    // [t][chi][2 chi] accumulated core gradients per half
+  // label core
+  float* labG;     // [batch][DL][2][L]
+  float* labH;     // [batch][DL][2][L]
+  float* gR;       // [batch][DR]
   size_t bytes;
 };
 
@@ -387,12 +392,14 @@ int chi_of(const tn_mps* W) {
 
 ClsLayout cls_layout(uint8_t* base, const tn_mps* W, int ls, int L, int batch, int ck) {
   ClsLayout w;
+  memset(&w, 0, sizeof(w));
   w.n = W->n;
   w.ls = ls;
   w.L = L;
   w.batch = batch;
   w.chi = chi_of(W);
   w.ck = ck;
+  w.ntiles = (batch + CLS_TILE - 1) / CLS_TILE;
   w.T[0] = ls;
   w.T[1] = W->n - 1 - ls;
   const int cke = ck > 0 ? ck : 1;
@@ -401,74 +408,44 @@ ClsLayout cls_layout(uint8_t* base, const tn_mps* W, int ls, int L, int batch, i
   w.seg_len = ck <= 1 ? std::max(Tmax, 1) : ck;
   size_t off = 0;
   auto take = [&](size_t b) { uint8_t* p = base ? base + off : nullptr; off += align256(b); return p; };
-  const size_t vec = sizeof(float) * (size_t)batch * w.chi;
+  const int chi = w.chi;
+  const size_t vec = sizeof(float) * (size_t)batch * chi;
+  const bool bwd = ck > 0;
   for (int h = 0; h < 2; ++h) {
     w.state[h] = reinterpret_cast<float*>(take(vec));
     w.lam[h] = reinterpret_cast<double*>(take(sizeof(double) * (size_t)batch));
     w.ckpt[h] = reinterpret_cast<float*>(take(vec * (size_t)w.nck[h]));
     w.sc[h] = reinterpret_cast<float*>(take(sizeof(float) * (size_t)batch * std::max(w.T[h], 1)));
-    w.g[h] = reinterpret_cast<float*>(take(vec));
+    w.g[h] = reinterpret_cast<float*>(take(bwd ? vec : 0));
+    w.replay[h] = reinterpret_cast<float*>(take(bwd ? vec : 0));
+    w.replay_lam[h] = reinterpret_cast<double*>(take(bwd ? sizeof(double) * (size_t)batch : 0));
   }
-  const bool bwd = ck > 0;
-  w.seg = reinterpret_cast<float*>(take(bwd && ck > 1 ? vec * (size_t)w.seg_len : 0));
-  w.replay = reinterpret_cast<float*>(take(bwd && ck > 1 ? vec : 0));
-  w.X = reinterpret_cast<float*>(take(bwd ? 2 * vec * (size_t)w.seg_len : 0));
-  w.Y = reinterpret_cast<float*>(take(bwd ? sizeof(float) * (size_t)batch * 2 * L * w.chi : 0));
-  // a segment's grouped plan: descriptors, split results to zero, and the
-  // unit map (each spec: at most 2 x 1 output tiles of 128 (2 chi <= 256)
+  // float32 backward: recomputed vectors and gradient operands of a segment,
+  // and one grouped plan per segment (descriptors, split results to zero and
+  // the unit map: each spec at most 2 x 1 output tiles of 128 (2 chi <= 256)
   // times ceil(batch / 2048) k ranges)
+  w.seg = reinterpret_cast<float*>(take(bwd && ck > 1 ? vec * (size_t)w.seg_len : 0));
+  w.X = reinterpret_cast<float*>(take(bwd ? 2 * vec * (size_t)w.seg_len : 0));
   const size_t units_per_spec = 2 * (size_t)((batch + 64 * MAX_SLABS_PER_UNIT - 1) / (64 * MAX_SLABS_PER_UNIT));
   w.plan_bytes = bwd ? align256(sizeof(ContractDesc) * (size_t)w.seg_len) + align256(sizeof(ZeroRange) * (size_t)w.seg_len) +
-                           sizeof(int32_t) * (size_t)w.seg_len * units_per_spec
+                           align256(sizeof(int32_t) * (size_t)w.seg_len * units_per_spec)
                      : 0;
-  w.plan_ws = take(w.plan_bytes);
-  w.img_bytes = cls_image_bytes(w.chi);
-  for (int h = 0; h < 2; ++h)
-    for (int m = 0; m < 2; ++m) w.img[h][m] = take(w.img_bytes * (size_t)w.T[h]);
+  w.plan_count = bwd ? (w.T[0] + w.seg_len - 1) / w.seg_len + (w.T[1] + w.seg_len - 1) / w.seg_len : 0;
+  w.plan_ws = take(w.plan_bytes * (size_t)w.plan_count);
+  // tensor-core path (sized for the split BF16x3 images, the larger)
+  for (int h = 0; h < 2; ++h) {
+    w.fimg[h] = take(cls_fwd_image_bytes(chi, 1) * (size_t)w.T[h]);
+    w.aimg[h] = take(bwd ? cls_adj_image_bytes(chi, 1) * (size_t)w.T[h] : 0);
+    w.vseg[h] = take(bwd ? cls_vtile_bytes(chi, 1) * (size_t)w.ntiles * (size_t)std::min(w.seg_len, std::max(w.T[h], 1)) : 0);
+    w.grad[h] = reinterpret_cast<float*>(take(bwd ? sizeof(float) * (size_t)w.T[h] * chi * 2 * chi : 0));
+  }
+  const int64_t DL = W->bond[ls], DR = W->bond[ls + 1];
+  const size_t lab = sizeof(float) * (size_t)batch * (size_t)(DL * 2 * L);
+  w.labG = reinterpret_cast<float*>(take(lab));
+  w.labH = reinterpret_cast<float*>(take(bwd ? lab : 0));
+  w.gR = reinterpret_cast<float*>(take(bwd ? sizeof(float) * (size_t)batch * DR : 0));
   w.bytes = off;
   return w;
-}
-
-int pack_images(const tn_mps* W, const ClsLayout& w, int mode, cudaStream_t s) {
-  for (int h = 0; h < 2; ++h) {
-    ClsPackParams pp;
-    memset(&pp, 0, sizeof(pp));
-    pp.n = W->n;
-    pp.half = h;
-    pp.mode = mode;
-    pp.chi = w.chi;
-    pp.kpad = w.chi < 64 ? 64 : w.chi;
-    pp.img_bytes = w.img_bytes;
-    for (int i = 0; i <= W->n; ++i) pp.bond[i] = (int32_t)W->bond[i];
-    for (int i = 0; i < W->n; ++i) pp.core[i] = W->cores[i];
-    pp.images = w.img[h][mode];
-    int rc = cls_pack(pp, w.T[h], s);
-    if (rc != TN_OK) return rc;
-  }
-  return TN_OK;
-}
-
-int run_sweep(int prec, const ClsLayout& w, const SweepParams& p, cudaStream_t s) {
-  if (prec == TN_PREC_FP32) return launch_sweep(w.chi, p, s);
-  ClsTcParams q;
-  memset(&q, 0, sizeof(q));
-  q.n = p.n;
-  q.batch = p.batch;
-  q.half = p.half;
-  q.mode = p.mode;
-  q.t_begin = p.t_begin;
-  q.t_end = p.t_end;
-  q.store_every = p.store_every;
-  q.store_base = p.store_base;
-  q.pixels = p.pixels;
-  q.state = p.state;
-  q.lam = p.lam;
-  q.store = p.store;
-  q.sc = p.sc;
-  q.xout = p.xout;
-  q.images = w.img[p.half][p.mode];
-  q.status = status_word();
-  return cls_sweep_tc_launch(w.chi, q, s);
 }
 
 int check_classifier(const tn_mps* W, int ls, int L, const float* pixels, int batch) {
@@ -500,6 +477,43 @@ SweepParams sweep_params(const tn_mps* W, const ClsLayout& w, const float* pixel
   return p;
 }
 
+// Both halves' cores packed into the tensor-core images of one kind.
+int pack_images(const tn_mps* W, const ClsLayout& w, int split, int adjoint, cudaStream_t s) {
+  ClsPackParams pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.n = W->n;
+  pp.chi = w.chi;
+  pp.split = split;
+  pp.adjoint = adjoint;
+  pp.T[0] = w.T[0];
+  pp.T[1] = w.T[1];
+  for (int i = 0; i <= W->n; ++i) pp.bond[i] = (int32_t)W->bond[i];
+  for (int i = 0; i < W->n; ++i) pp.core[i] = W->cores[i];
+  for (int h = 0; h < 2; ++h) pp.images[h] = adjoint ? w.aimg[h] : w.fimg[h];
+  pp.step_bytes = adjoint ? cls_adj_image_bytes(w.chi, split) : cls_fwd_image_bytes(w.chi, split);
+  return cls_pack(pp, s);
+}
+
+ClsTcParams tc_params(const tn_mps* W, const ClsLayout& w, const float* pixels) {
+  ClsTcParams q;
+  memset(&q, 0, sizeof(q));
+  q.n = W->n;
+  q.batch = w.batch;
+  q.ntiles = w.ntiles;
+  q.store_every = 1;
+  q.half_site[0] = 0;
+  q.half_dir[0] = 1;
+  q.half_site[1] = W->n - 1;
+  q.half_dir[1] = -1;
+  q.pixels = pixels;
+  for (int h = 0; h < 2; ++h) {
+    q.sc[h] = w.sc[h];
+    q.t_end[h] = w.T[h];
+  }
+  q.status = status_word();
+  return q;
+}
+
 tn_tensor strided(float* p, int rank, const int64_t* shape, const int64_t* stride) {
   tn_tensor t;
   memset(&t, 0, sizeof(t));
@@ -513,6 +527,37 @@ tn_tensor strided(float* p, int rank, const int64_t* shape, const int64_t* strid
   return t;
 }
 
+LabelParams label_params(const tn_mps* W, const ClsLayout& w, const float* pixels) {
+  LabelParams lp;
+  memset(&lp, 0, sizeof(lp));
+  lp.n = W->n;
+  lp.batch = w.batch;
+  lp.ls = w.ls;
+  lp.L = w.L;
+  lp.chi = w.chi;
+  lp.DL = (int)W->bond[w.ls];
+  lp.DR = (int)W->bond[w.ls + 1];
+  lp.pixels = pixels;
+  lp.vL = w.state[0];
+  lp.lamL = w.lam[0];
+  lp.lamR = w.lam[1];
+  lp.G = w.labG;
+  return lp;
+}
+
+// G[b, a, s, l] = sum_c vR[b, c] C[a, s, l, c] (float32).
+int label_G(const tn_mps* W, const ClsLayout& w, cudaStream_t s) {
+  const int64_t DL = W->bond[w.ls], DR = W->bond[w.ls + 1], B = w.batch, L = w.L;
+  const int64_t shv[2] = {B, DR}, stv[2] = {w.chi, 1};
+  const int64_t shc[4] = {DL, 2, L, DR}, stc[4] = {0, 0, 0, 0};
+  const int64_t shg[4] = {B, DL, 2, L}, stg[4] = {0, 0, 0, 0};
+  tn_tensor tv = strided(w.state[1], 2, shv, stv);
+  tn_tensor tc = strided(const_cast<float*>(W->cores[w.ls]), 4, shc, stc);
+  tn_tensor tg = strided(w.labG, 4, shg, stg);
+  const int lv[1] = {1}, lc[1] = {3};
+  return contract_internal(&tv, lv, &tc, lc, 1, &tg, TN_PREC_FP32, s);
+}
+
 }  // namespace
 }  // namespace tn
 
@@ -523,7 +568,8 @@ extern "C" {
 int tn_mps_classify_loss(const float* ftilde, const int64_t* labels, int batch, int n_labels, double* loss,
                          float* dftilde, void* stream) {
   if (!ftilde || !labels || !loss || batch < 1 || n_labels < 1 || n_labels > LABEL_MAXL) return TN_ERR_ARG;
-  cls_loss_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(ftilde, labels, batch, n_labels, loss, dftilde);
+  cls_loss_kernel<<<1, LOSS_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(ftilde, labels, batch, n_labels, loss,
+                                                                             dftilde);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
@@ -538,43 +584,47 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
   int rc = check_classifier(W, label_site, n_labels, pixels, batch);
   if (rc != TN_OK) return rc;
   if (!ftilde || !log_scale || ckpt_every < 0) return TN_ERR_ARG;
-  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16) return TN_ERR_UNSUPPORTED;
+  if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
   if (batch == 0) return TN_OK;
   ClsLayout w = cls_layout(static_cast<uint8_t*>(workspace), W, label_site, n_labels, batch, ckpt_every);
   if (!workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t nvec = (int64_t)batch * w.chi;
-  if (prec != TN_PREC_FP32 && (rc = pack_images(W, w, 0, s)) != TN_OK) return rc;
   for (int h = 0; h < 2; ++h) {
     cls_init_state<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(w.state[h], w.lam[h], batch, w.chi);
-    SweepParams p = sweep_params(W, w, pixels, h, 0);
-    p.t_begin = 0;
-    p.t_end = w.T[h];
-    if (ckpt_every > 0) {
-      p.store = w.ckpt[h];
-      p.store_every = ckpt_every;
-      p.store_base = 0;
-    }
-    if ((rc = run_sweep(prec, w, p, s)) != TN_OK) return rc;
+    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   }
-  LabelParams lp;
-  memset(&lp, 0, sizeof(lp));
-  lp.n = W->n;
-  lp.batch = batch;
-  lp.ls = label_site;
-  lp.L = n_labels;
-  lp.chi = w.chi;
-  lp.DL = (int)W->bond[label_site];
-  lp.DR = (int)W->bond[label_site + 1];
-  lp.C = W->cores[label_site];
-  lp.pixels = pixels;
-  lp.vL = w.state[0];
-  lp.vR = w.state[1];
-  lp.lamL = w.lam[0];
-  lp.lamR = w.lam[1];
+  if (prec == TN_PREC_FP32) {
+    for (int h = 0; h < 2; ++h) {
+      SweepParams p = sweep_params(W, w, pixels, h, 0);
+      p.t_begin = 0;
+      p.t_end = w.T[h];
+      if (ckpt_every > 0) {
+        p.store = w.ckpt[h];
+        p.store_every = ckpt_every;
+        p.store_base = 0;
+      }
+      if ((rc = launch_sweep(w.chi, p, s)) != TN_OK) return rc;
+    }
+  } else {
+    // both half-chains in one tcgen05 launch
+    const int split = prec == TN_PREC_BF16X3;
+    if ((rc = pack_images(W, w, split, 0, s)) != TN_OK) return rc;
+    ClsTcParams q = tc_params(W, w, pixels);
+    for (int h = 0; h < 2; ++h) {
+      q.state[h] = w.state[h];
+      q.lam[h] = w.lam[h];
+      q.images[h] = w.fimg[h];
+      if (ckpt_every > 0) q.store[h] = w.ckpt[h];
+    }
+    q.store_every = ckpt_every > 0 ? ckpt_every : 1;
+    if ((rc = cls_fwd_tc_launch(w.chi, split, q, s)) != TN_OK) return rc;
+  }
+  if ((rc = label_G(W, w, s)) != TN_OK) return rc;
+  LabelParams lp = label_params(W, w, pixels);
   lp.ftilde = ftilde;
   lp.log_scale = log_scale;
-  cls_label_fwd<<<batch, 128, 0, s>>>(lp);
+  cls_label_reduce<<<(unsigned)((batch + 7) / 8), 256, 0, s>>>(lp);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
@@ -591,6 +641,8 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
   if (!workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int chi = w.chi, n = W->n, ls = label_site, L = n_labels;
+  const int split = prec == TN_PREC_BF16X3;
+  if (prec != TN_PREC_FP32 && !cls_adj_tc_supported(chi, split)) return TN_ERR_UNSUPPORTED;
   if (batch == 0) {
     for (int i = 0; i < n; ++i) {
       const int64_t e = W->bond[i] * 2 * W->bond[i + 1] * (i == ls ? L : 1);
@@ -598,81 +650,118 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
     }
     return TN_OK;
   }
-  const int dprec = prec == TN_PREC_FP32 ? TN_PREC_FP32 : prec;
-  // reduced precisions run the sweeps on the tensor cores (bf16 operands)
-  const int sprec = prec == TN_PREC_FP32 ? TN_PREC_FP32 : TN_PREC_BF16;
-  if (sprec != TN_PREC_FP32) {
-    if ((rc = pack_images(W, w, 0, s)) != TN_OK) return rc;
-    if ((rc = pack_images(W, w, 1, s)) != TN_OK) return rc;
-  }
 
-  // label core: adjoints entering both half-chains, and dC = sum_b vL_b (x) Y_b
-  LabelParams lp;
-  memset(&lp, 0, sizeof(lp));
-  lp.n = n;
-  lp.batch = batch;
-  lp.ls = ls;
-  lp.L = L;
-  lp.chi = chi;
-  lp.DL = (int)W->bond[ls];
-  lp.DR = (int)W->bond[ls + 1];
-  lp.C = W->cores[ls];
-  lp.pixels = pixels;
-  lp.vL = w.state[0];
-  lp.vR = w.state[1];
-  lp.dft = dftilde;
-  lp.gL = w.g[0];
-  lp.gR = w.g[1];
-  lp.Y = w.Y;
-  cls_label_bwd<<<batch, 128, 0, s>>>(lp);
-  if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  // label core: the adjoints entering both half-chains, and dC
   {
-    const int64_t shv[2] = {batch, lp.DL}, stv[2] = {chi, 1};
-    const int64_t shy[4] = {batch, 2, L, lp.DR}, sty[4] = {2 * L * lp.DR, L * lp.DR, lp.DR, 1};
-    const int64_t shc[4] = {lp.DL, 2, L, lp.DR}, stc[4] = {0, 0, 0, 0};
-    tn_tensor tv = strided(w.state[0], 2, shv, stv);
-    tn_tensor ty = strided(w.Y, 4, shy, sty);
-    tn_tensor tc = strided(dcores[ls], 4, shc, stc);
+    if ((rc = label_G(W, w, s)) != TN_OK) return rc;
+    LabelParams lp = label_params(W, w, pixels);
+    lp.dft = dftilde;
+    lp.gL = w.g[0];
+    lp.H = w.labH;
+    cls_label_adjoint<<<(unsigned)((batch + 7) / 8), 256, 0, s>>>(lp);
+    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+    const int64_t B = batch, DL = lp.DL, DR = lp.DR;
+    const int64_t shh[4] = {B, DL, 2, L}, sth[4] = {0, 0, 0, 0};
+    const int64_t shc[4] = {DL, 2, L, DR}, stc[4] = {0, 0, 0, 0};
+    const int64_t shr[2] = {B, DR}, str[2] = {0, 0};
+    const int64_t shv[2] = {B, DR}, stv[2] = {chi, 1};
+    tn_tensor th = strided(w.labH, 4, shh, sth);
+    tn_tensor tc = strided(const_cast<float*>(W->cores[ls]), 4, shc, stc);
+    tn_tensor tr = strided(w.gR, 2, shr, str);
+    const int lh[3] = {1, 2, 3}, lc[3] = {0, 1, 2};
+    if ((rc = contract_internal(&th, lh, &tc, lc, 3, &tr, TN_PREC_FP32, s)) != TN_OK) return rc;
+    const int64_t nvec = B * chi;
+    cls_pad_rows<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(w.gR, (int)DR, w.g[1], batch, chi);
+    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+    tn_tensor tv = strided(w.state[1], 2, shv, stv);
+    tn_tensor td = strided(dcores[ls], 4, shc, stc);
     const int l0[1] = {0};
-    if ((rc = contract_internal(&tv, l0, &ty, l0, 1, &tc, dprec, s)) != TN_OK) return rc;
+    if ((rc = contract_internal(&th, l0, &tv, l0, 1, &td, TN_PREC_FP32, s)) != TN_OK) return rc;
   }
 
-  // each half-chain: segments from the label core outwards
-  for (int h = 0; h < 2; ++h) {
-    const int T = w.T[h];
-    if (T == 0) continue;
-    const int seg = ckpt_every <= 1 ? T : ckpt_every;
-    const int nseg = (T + seg - 1) / seg;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int t0 = sg * seg, t1 = std::min(T, t0 + seg);
-      const float* vecs;  // vectors entering steps t0..t1-1, [t - t0][batch][chi]
-      if (ckpt_every <= 1) {
-        vecs = w.ckpt[h] + (int64_t)t0 * batch * chi;
-      } else {
-        // recompute the segment from its kept vector, keeping the vector
-        // entering every step; the replay rewrites the same per-step scales
-        // (and the internal log-scale, which the backward does not read)
-        if (cudaMemcpyAsync(w.replay, w.ckpt[h] + (int64_t)sg * batch * chi, sizeof(float) * (size_t)batch * chi,
-                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  const int seg = ckpt_every <= 1 ? std::max(std::max(w.T[0], w.T[1]), 1) : ckpt_every;
+  int nseg[2];
+  for (int h = 0; h < 2; ++h) nseg[h] = (w.T[h] + seg - 1) / seg;
+  const int rounds = std::max(nseg[0], nseg[1]);
+  // segment of half h handled in round k (segments run from the label core outwards)
+  auto seg_range = [&](int h, int k, int* t0, int* t1) {
+    const int sg = nseg[h] - 1 - k;
+    if (sg < 0) {
+      *t0 = *t1 = 0;
+      return false;
+    }
+    *t0 = sg * seg;
+    *t1 = std::min(w.T[h], *t0 + seg);
+    return true;
+  };
+  const size_t vbytes = sizeof(float) * (size_t)batch * chi;
+
+  if (prec != TN_PREC_FP32) {
+    // tcgen05: per round, one launch recomputes both halves' segments (their
+    // bf16 vector tiles kept for the gradient products) and one launch runs
+    // both adjoint segments, accumulating every step's core gradient
+    if ((rc = pack_images(W, w, split, 0, s)) != TN_OK) return rc;
+    if ((rc = pack_images(W, w, split, 1, s)) != TN_OK) return rc;
+    for (int h = 0; h < 2; ++h)
+      if (w.T[h] > 0 &&
+          cudaMemsetAsync(w.grad[h], 0, sizeof(float) * (size_t)w.T[h] * chi * 2 * chi, s) != cudaSuccess)
+        return TN_ERR_CUDA;
+    for (int k = 0; k < rounds; ++k) {
+      ClsTcParams f = tc_params(W, w, pixels);
+      ClsTcParams a = tc_params(W, w, pixels);
+      for (int h = 0; h < 2; ++h) {
+        int t0, t1;
+        seg_range(h, k, &t0, &t1);
+        f.t_begin[h] = a.t_begin[h] = t0;
+        f.t_end[h] = a.t_end[h] = t1;
+        if (t1 > t0 && cudaMemcpyAsync(w.replay[h], w.ckpt[h] + (int64_t)(t0 / ckpt_every) * batch * chi, vbytes,
+                                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)
           return TN_ERR_CUDA;
-        SweepParams p = sweep_params(W, w, pixels, h, 0);
-        p.state = w.replay;
-        p.t_begin = t0;
-        p.t_end = t1;
-        p.store = w.seg;
-        p.store_every = 1;
-        p.store_base = t0;
-        if ((rc = run_sweep(sprec, w, p, s)) != TN_OK) return rc;
-        vecs = w.seg;
+        f.state[h] = w.replay[h];
+        f.lam[h] = w.replay_lam[h];
+        f.vseg[h] = w.vseg[h];
+        f.images[h] = w.fimg[h];
+        a.state[h] = w.g[h];
+        a.vseg[h] = w.vseg[h];
+        a.images[h] = w.aimg[h];
+        a.grad[h] = w.grad[h];
       }
-      // adjoint steps t1-1 .. t0: g <- adjoint step, X[t - t0] <- gradient operands
-      SweepParams p = sweep_params(W, w, pixels, h, 1);
-      p.state = w.g[h];
-      p.t_begin = t0;
-      p.t_end = t1;
-      p.xout = w.X;
-      if ((rc = run_sweep(sprec, w, p, s)) != TN_OK) return rc;
-      // core gradients of the segment: one grouped tensordot over the batch
+      if ((rc = cls_fwd_tc_launch(chi, split, f, s)) != TN_OK) return rc;
+      if ((rc = cls_adj_tc_launch(chi, split, a, s)) != TN_OK) return rc;
+    }
+    ClsScatterParams sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.n = n;
+    sp.chi = chi;
+    sp.T[0] = w.T[0];
+    sp.T[1] = w.T[1];
+    for (int i = 0; i <= n; ++i) sp.bond[i] = (int32_t)W->bond[i];
+    for (int i = 0; i < n; ++i) sp.dcore[i] = dcores[i];
+    sp.grad[0] = w.grad[0];
+    sp.grad[1] = w.grad[1];
+    return cls_scatter_grad(sp, s);
+  }
+
+  // float32: per half and segment (from the label core outwards) the
+  // recomputed vectors, the adjoint sweep writing the gradient operands, and
+  // one grouped tensordot over the batch for the segment's cores. The
+  // segments' plans are built and uploaded before the first sweep.
+  struct SegPlan {
+    int h, t0, t1;
+    const float* vecs;
+    tn_group_plan* plan;
+    uint8_t* ws;
+  };
+  std::vector<SegPlan> plans;
+  auto destroy_all = [&]() {
+    for (auto& sp : plans)
+      if (sp.plan) tn_group_plan_destroy(sp.plan);
+  };
+  for (int h = 0; h < 2; ++h)
+    for (int k = 0; k < nseg[h]; ++k) {
+      int t0, t1;
+      seg_range(h, k, &t0, &t1);
+      const float* vecs = ckpt_every <= 1 ? w.ckpt[h] + (int64_t)t0 * batch * chi : w.seg;
       std::vector<tn_contract_spec> specs((size_t)(t1 - t0));
       for (int t = t0; t < t1; ++t) {
         const int site = h == 0 ? t : n - 1 - t;
@@ -698,15 +787,48 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
           sp.B = strided(v, 2, shv, stv);
         }
       }
-      tn_group_plan* plan = nullptr;
-      if ((rc = group_plan_create_ex(specs.data(), (int)specs.size(), dprec, false, &plan)) != TN_OK) return rc;
-      rc = tn_group_plan_upload(plan, w.plan_ws, w.plan_bytes, s);
-      if (rc == TN_OK) rc = tn_group_plan_run(plan, w.plan_ws, w.plan_bytes, s);
-      tn_group_plan_destroy(plan);
-      if (rc != TN_OK) return rc;
+      SegPlan sp{h, t0, t1, vecs, nullptr, w.plan_ws + (size_t)plans.size() * w.plan_bytes};
+      if ((rc = group_plan_create_ex(specs.data(), (int)specs.size(), TN_PREC_FP32, false, &sp.plan)) != TN_OK) {
+        destroy_all();
+        return rc;
+      }
+      plans.push_back(sp);
+      if ((rc = tn_group_plan_upload(sp.plan, sp.ws, w.plan_bytes, s)) != TN_OK) {
+        destroy_all();
+        return rc;
+      }
     }
+  for (const SegPlan& sp : plans) {
+    const int h = sp.h, t0 = sp.t0, t1 = sp.t1;
+    if (ckpt_every > 1) {
+      // recompute the segment from its kept vector, keeping the vector
+      // entering every step; the replay rewrites the same per-step scales
+      if (cudaMemcpyAsync(w.replay[h], w.ckpt[h] + (int64_t)(t0 / ckpt_every) * batch * chi, vbytes,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        destroy_all();
+        return TN_ERR_CUDA;
+      }
+      SweepParams p = sweep_params(W, w, pixels, h, 0);
+      p.state = w.replay[h];
+      p.lam = w.replay_lam[h];
+      p.t_begin = t0;
+      p.t_end = t1;
+      p.store = w.seg;
+      p.store_every = 1;
+      p.store_base = t0;
+      if ((rc = launch_sweep(chi, p, s)) != TN_OK) break;
+    }
+    // adjoint steps t1-1 .. t0: g <- adjoint step, X[t - t0] <- gradient operands
+    SweepParams p = sweep_params(W, w, pixels, h, 1);
+    p.state = w.g[h];
+    p.t_begin = t0;
+    p.t_end = t1;
+    p.xout = w.X;
+    if ((rc = launch_sweep(chi, p, s)) != TN_OK) break;
+    if ((rc = tn_group_plan_run(sp.plan, sp.ws, w.plan_bytes, s)) != TN_OK) break;
   }
-  return TN_OK;
+  destroy_all();
+  return rc;
 }
 
 }  // extern "C"

@@ -5,7 +5,12 @@ Scores are compared per sample as vectors over labels, on the true scale
 f = ftilde * exp(log_scale): ||f - f*|| / ||f*||. Gradients per core:
 ||dW - dW*||_F / ||dW*||_F. float32 path tolerances: 1e-5 * sqrt(sites) for
 scores (independent float32 roundings per site), 1e-4 for gradients (sums of
-products over the batch on top of the sweep).
+products over the batch on top of the sweep). Split BF16x3 path: a step's
+products carry ~2^-16 relative error (the dropped lo*lo term and the rounding
+of lo), independent per site, so a random walk: median score error
+<= 2 * 2^-16 * sqrt(sites), largest <= 40 * 2^-16 * sqrt(sites) (the tail over
+samples is heavier: products of random matrices), gradients <= 8 * 2^-16 *
+sqrt(2 sites) per core (forward and adjoint walks).
 """
 import math
 
@@ -40,7 +45,8 @@ def score_err(ft, lam, ft_ref, lam_ref):
     return np.linalg.norm(got - ft_ref, axis=1) / np.linalg.norm(ft_ref, axis=1)
 
 
-@pytest.mark.parametrize("n,chi,ls,L,B", [(12, 8, 5, 3, 40), (50, 16, 25, 10, 70), (784, 32, 392, 10, 96)])
+@pytest.mark.parametrize("n,chi,ls,L,B", [(12, 8, 5, 3, 40), (50, 16, 25, 10, 70), (784, 32, 392, 10, 96),
+                                          (40, 128, 20, 10, 70)])
 def test_forward_fp32_parity(tn, n, chi, ls, L, B):
     cores = synth.classifier_mps(n, chi, ls, L, seed=31, eps_std=0.1)
     px = synth.pixels(B, n, seed=32)
@@ -191,3 +197,71 @@ def test_backward_bf16_parity(tn, ck):
     for i, (g, r) in enumerate(zip(grads, g_ref)):
         err = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
         assert err <= bf16_tol(2 * n), (i, err)
+
+
+# ------------------------------------------------------- split bf16x3 path
+U16 = 2.0 ** -16
+
+
+@pytest.mark.parametrize("n,chi,ls,L,B", [(12, 8, 5, 3, 40), (12, 8, 0, 3, 70), (12, 8, 11, 1, 70),
+                                          (60, 32, 30, 10, 300), (200, 64, 100, 10, 130),
+                                          (64, 128, 33, 10, 129)])
+def test_forward_bf16x3_parity(tn, n, chi, ls, L, B):
+    # ragged batches (not a multiple of the 128-sample tile), the label core
+    # at either end of the chain (one half-chain without steps), one label
+    cores = synth.classifier_mps(n, chi, ls, L, seed=81, eps_std=0.1)
+    px = synth.pixels(B, n, seed=82)
+    ft, lam, _ = tn.mps_classify([dev(c) for c in cores], ls, dev(px), prec="bf16x3", ckpt_every=0)
+    assert tn.sync_status() == 0
+    ft_ref, lam_ref = oracle.classify(cores, ls, px)
+    err = score_err(ft, lam, ft_ref, lam_ref)
+    assert np.median(err) <= 2 * U16 * math.sqrt(n), (np.median(err), err.max())
+    assert err.max() <= 40 * U16 * math.sqrt(n), (err.max(), np.median(err))
+
+
+@pytest.mark.parametrize("n,chi,ls,L,B,ck", [(12, 8, 5, 3, 40, 1), (12, 8, 0, 3, 70, 3), (40, 32, 20, 10, 300, 4),
+                                             (40, 64, 17, 10, 200, 5), (30, 64, 29, 1, 150, 7)])
+def test_backward_bf16x3_parity(tn, n, chi, ls, L, B, ck):
+    cores = synth.classifier_mps(n, chi, ls, L, seed=91, eps_std=0.1)
+    px = synth.pixels(B, n, seed=92)
+    y = synth.labels(B, L, seed=93)
+    _, g_ref = oracle.classify_grad(cores, ls, px, y)
+    dc = [dev(c) for c in cores]
+    ft, lam, ws = tn.mps_classify(dc, ls, dev(px), prec="bf16x3", ckpt_every=ck)
+    _, dft = tn.mps_classify_loss(ft, torch.from_numpy(y).cuda())
+    grads = tn.mps_classify_backward(dc, ls, dev(px), dft, ws, prec="bf16x3", ckpt_every=ck)
+    assert tn.sync_status() == 0
+    for i, (g, r) in enumerate(zip(grads, g_ref)):
+        nr = np.linalg.norm(r)
+        if nr == 0.0:
+            assert not g.any().item(), i
+            continue
+        err = np.linalg.norm(g.double().cpu().numpy() - r) / nr
+        assert err <= 8 * U16 * math.sqrt(2 * n), (i, err)
+
+
+def test_backward_bf16x3_chi128_is_unsupported(tn):
+    # the split adjoint's staging at chi = 128 does not fit in shared memory
+    n, chi, ls, L, B = 10, 128, 5, 2, 16
+    cores = synth.classifier_mps(n, chi, ls, L, seed=3, eps_std=0.1)
+    px = synth.pixels(B, n, seed=4)
+    dc = [dev(c) for c in cores]
+    ft, lam, ws = tn.mps_classify(dc, ls, dev(px), prec="bf16x3", ckpt_every=2)
+    with pytest.raises(tn.TnError) as e:
+        tn.mps_classify_backward(dc, ls, dev(px), torch.ones_like(ft), ws, prec="bf16x3", ckpt_every=2)
+    assert e.value.code == 3
+
+
+def test_backward_fp32_chi128(tn):
+    n, chi, ls, L, B = 16, 128, 8, 4, 40
+    cores = synth.classifier_mps(n, chi, ls, L, seed=95, eps_std=0.1)
+    px = synth.pixels(B, n, seed=96)
+    y = synth.labels(B, L, seed=97)
+    _, g_ref = oracle.classify_grad(cores, ls, px, y)
+    dc = [dev(c) for c in cores]
+    ft, lam, ws = tn.mps_classify(dc, ls, dev(px), prec="fp32", ckpt_every=3)
+    _, dft = tn.mps_classify_loss(ft, torch.from_numpy(y).cuda())
+    grads = tn.mps_classify_backward(dc, ls, dev(px), dft, ws, prec="fp32", ckpt_every=3)
+    for i, (g, r) in enumerate(zip(grads, g_ref)):
+        err = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
+        assert err <= 1e-4, (i, err)
