@@ -7,6 +7,17 @@
 // site to site. Larger bonds run each per-site contraction through
 // tn_contract's kernels (tcgen05 for BF16/BF16X3), with the environment in a
 // caller workspace, followed by a two-kernel rescale.
+//
+// The energy sweep carries <psi|psi> along as one more MPO channel: the MPO
+// is extended by a channel that maps to itself with the identity operator
+// (W'[w, w'] = W[w, w'] on the original channels, W'[wa, wb] = identity), so
+// the environment channel wa of L is the norm environment and one sweep of
+// three contractions per site gives both results. Its rescaling is deferred
+// and exact: after step (iii) the largest magnitude of the new environment
+// is found (one pass); the next site's step (ii) multiplies its output by
+// 2^-e, e the binary exponent of that maximum (the contractions are linear in
+// L, so scaling T2 scales everything downstream), and adds e ln 2 to the
+// float64 log-scale.
 #include <math.h>
 
 #include <algorithm>
@@ -296,6 +307,147 @@ tn_tensor tensor4(float* p, int64_t a, int64_t b, int64_t c, int64_t d) {
   return t;
 }
 
+// ---------------------------------------------------- energy sweep kernels
+constexpr int MPO_MAXN = 1024;   // sites of one extended-MPO build
+constexpr int MPO_MAXWD = 32;    // (extended MPO bond) x d of the step (ii) kernel
+
+// The extended MPO of every site: W'[w, w', s, s'] = W[w, w', s, s'] for
+// w < wa, w' < wb; W'[wa, wb, s, s'] = (s == s'); 0 elsewhere.
+struct MpoExtParams {
+  int32_t n, d;
+  int32_t wb[MPO_MAXN + 1];
+  const float* W[MPO_MAXN];
+  int64_t off[MPO_MAXN];
+  float* out;
+};
+
+__global__ void mpo_extend_kernel(const __grid_constant__ MpoExtParams p) {
+  const int i = blockIdx.x;
+  const int wa = p.wb[i], wb = p.wb[i + 1], d = p.d;
+  const int wa2 = wa + 1, wb2 = wb + 1;
+  float* o = p.out + p.off[i];
+  const int total = wa2 * wb2 * d * d;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int s2 = e % d, s = (e / d) % d, w2 = (e / (d * d)) % wb2, w = e / (d * d * wb2);
+    float v = 0.0f;
+    if (w < wa && w2 < wb) v = p.W[i][((w * wb + w2) * d + s) * d + s2];
+    else if (w == wa && w2 == wb) v = s == s2 ? 1.0f : 0.0f;
+    o[e] = v;
+  }
+}
+
+__device__ __forceinline__ int pow2_exponent(float m) {
+  if (!(m > 0.0f)) return 0;
+  const int ex = (__float_as_int(m) >> 23) & 0xff;
+  const int e = ex == 0 ? -126 : ex - 126;  // m * 2^-e in [1/2, 1)
+  return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+
+__device__ __forceinline__ void step_ii(const StepII& q, int64_t first, int64_t stride, bool log_thread) {
+  __shared__ float Ws[MPO_MAXWD][MPO_MAXWD];  // [(w, s)][(w', s')]
+  const int wad = q.wa * q.d, wbd = q.wb * q.d, d = q.d;
+  for (int e = threadIdx.x; e < wad * wbd; e += blockDim.x) {
+    const int k = e / wbd, m = e - k * wbd;
+    const int w = k / d, s = k - w * d, w2 = m / d, s2 = m - w2 * d;
+    Ws[k][m] = q.W[((w * q.wb + w2) * d + s) * d + s2];
+  }
+  __syncthreads();
+  int e = 0;
+  if (q.maxbits) e = pow2_exponent(__uint_as_float(*q.maxbits));
+  const float inv = __int_as_float((127 - e) << 23);
+  if (log_thread && q.maxbits) *q.lg += (double)e * 0.69314718055994530942;
+  const int64_t cols = q.Da * q.Db;
+  for (int64_t c = first; c < cols; c += stride) {
+    const int64_t a = c / q.Db, b = c - a * q.Db;
+    float t[MPO_MAXWD];
+#pragma unroll
+    for (int k = 0; k < MPO_MAXWD; ++k) {
+      if (k < wad) {
+        const int w = k / d, s = k - w * d;
+        t[k] = __ldg(q.T1 + (((int64_t)w * q.Da + a) * d + s) * q.Db + b);
+      }
+    }
+    for (int m = 0; m < wbd; ++m) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < MPO_MAXWD; ++k)
+        if (k < wad) acc = fmaf(Ws[k][m], t[k], acc);
+      q.T2[((int64_t)m * q.Da + a) * q.Db + b] = acc * inv;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) mpo_step_ii_kernel(const __grid_constant__ StepII q) {
+  step_ii(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+          blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Grouped form: blockIdx.y picks the chain's descriptor.
+__global__ void __launch_bounds__(256) mpo_step_ii_grouped(const StepII* __restrict__ descs) {
+  const StepII q = descs[blockIdx.y];
+  step_ii(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+          blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Energy sweep workspace: L0, L1 ((W+1) D^2), T1, T2 ((W+1) D d D), n max
+// slots, the log-scale, the extended MPO, and scratch for the packed bf16
+// operands of the largest contraction (sized for BF16X3).
+struct ExpectWs2 {
+  float *L0, *L1, *T1, *T2, *Wx;
+  unsigned* bits;
+  double* lg;
+  uint8_t* scratch;
+  size_t scratch_bytes;
+  size_t bytes;
+  std::vector<int64_t> woff;
+};
+
+ExpectWs2 expect2_layout(uint8_t* base, const tn_mps* psi, const tn_mpo* H) {
+  ExpectWs2 w;
+  int64_t Wm = 1;
+  for (int i = 0; i <= H->n; ++i) Wm = std::max(Wm, H->bond[i]);
+  const int64_t W1 = Wm + 1, D = max_bond(psi), d = psi->d;
+  size_t off = 0;
+  auto take = [&](size_t b) { uint8_t* p = base ? base + off : nullptr; off += align256(b); return p; };
+  w.L0 = reinterpret_cast<float*>(take(sizeof(float) * W1 * D * D));
+  w.L1 = reinterpret_cast<float*>(take(sizeof(float) * W1 * D * D));
+  w.T1 = reinterpret_cast<float*>(take(sizeof(float) * W1 * D * d * D));
+  w.T2 = reinterpret_cast<float*>(take(sizeof(float) * W1 * D * d * D));
+  w.bits = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)psi->n));
+  w.lg = reinterpret_cast<double*>(take(sizeof(double) * 2));
+  int64_t tot = 0;
+  for (int i = 0; i < H->n; ++i) {
+    w.woff.push_back(tot);
+    tot += (H->bond[i] + 1) * (H->bond[i + 1] + 1) * d * d;
+  }
+  w.Wx = reinterpret_cast<float*>(take(sizeof(float) * (size_t)tot));
+  // (i) (W+1) D x D by D x dD and (iii) (W+1) D x dD by dD x D, packed
+  w.scratch_bytes = std::max(packed_scratch_bound(W1 * D, d * D, D, TN_PREC_BF16X3),
+                             packed_scratch_bound(W1 * D, D, d * D, TN_PREC_BF16X3));
+  w.scratch = take(w.scratch_bytes);
+  w.bytes = off;
+  return w;
+}
+
+// L[w, 0, 0] = 1 for the first site's channels (the MPO's left boundary and
+// the norm channel), log-scale and max slots zeroed.
+__global__ void expect_init_kernel(float* L, int channels, double* lg, unsigned* bits, int nbits) {
+  for (int i = threadIdx.x; i < nbits; i += blockDim.x) bits[i] = 0u;
+  if (threadIdx.x < 2) lg[threadIdx.x] = 0.0;
+  if (threadIdx.x < channels) L[threadIdx.x] = 1.0f;
+}
+
+// result = {L[0] (energy channel), lg, L[1] (norm channel), lg} of the final
+// (wN + 1) x 1 x 1 environment (wN = 1).
+__global__ void expect_finish_kernel(const float* L, const double* lg, double* result) {
+  if (threadIdx.x == 0) {
+    result[0] = (double)L[0];
+    result[1] = lg[0];
+    result[2] = (double)L[1];
+    result[3] = lg[0];
+  }
+}
+
 bool small_ok(const tn_mps* bra, const tn_mps* ket) {
   return bra->n <= SMALL_MAXN && bra->d <= SMALL_PHYS && max_bond(bra) <= SMALL_D && max_bond(ket) <= SMALL_D;
 }
@@ -359,36 +511,38 @@ int inner_sweep(const tn_mps* bra, const tn_mps* ket, int prec, const InnerWs& w
   return TN_OK;
 }
 
-// Workspace of the MPO sweep: L0, L1 (wmax Dmax^2), T1, T2 (wmax Dmax d Dmax),
-// n max slots, one log-scale; the inner sweep reuses the front of it.
-struct ExpectWs {
-  float *L0, *L1, *T1, *T2;
-  unsigned* bits;
-  double* lg;
-  uint8_t* scratch;
-  size_t scratch_bytes;
-  size_t bytes;
-};
+}  // namespace
 
-ExpectWs expect_layout(uint8_t* base, int64_t D, int64_t W, int64_t d, int n) {
-  ExpectWs w;
-  size_t off = 0;
-  auto take = [&](size_t b) { uint8_t* p = base ? base + off : nullptr; off += align256(b); return p; };
-  w.L0 = reinterpret_cast<float*>(take(sizeof(float) * W * D * D));
-  w.L1 = reinterpret_cast<float*>(take(sizeof(float) * W * D * D));
-  w.T1 = reinterpret_cast<float*>(take(sizeof(float) * W * D * d * D));
-  w.T2 = reinterpret_cast<float*>(take(sizeof(float) * W * D * d * D));
-  w.bits = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)n));
-  w.lg = reinterpret_cast<double*>(take(sizeof(double) * 2));
-  // (i) W D x D by D x dD and (iii) W D x dD by dD x D, packed
-  w.scratch_bytes = std::max(packed_scratch_bound(W * D, d * D, D, TN_PREC_BF16X3),
-                             packed_scratch_bound(W * D, D, d * D, TN_PREC_BF16X3));
-  w.scratch = take(w.scratch_bytes);
-  w.bytes = off;
-  return w;
+int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, cudaStream_t s) {
+  if (count <= 0) return TN_OK;
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_cols + 255) / 256, 1024)), (unsigned)count);
+  mpo_step_ii_grouped<<<grid, 256, 0, s>>>(descs);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
-}  // namespace
+int launch_mpo_extend(const tn_mpo* H, float* out, const int64_t* off, cudaStream_t s) {
+  if (H->n > MPO_MAXN) return TN_ERR_UNSUPPORTED;
+  MpoExtParams mp;
+  memset(&mp, 0, sizeof(mp));
+  mp.n = H->n;
+  mp.d = H->d;
+  for (int i = 0; i <= H->n; ++i) mp.wb[i] = (int32_t)H->bond[i];
+  for (int i = 0; i < H->n; ++i) {
+    mp.W[i] = H->cores[i];
+    mp.off[i] = off[i];
+  }
+  mp.out = out;
+  mpo_extend_kernel<<<H->n, 128, 0, s>>>(mp);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+bool mpo_extend_supported(const tn_mpo* H) {
+  if (H->n > MPO_MAXN) return false;
+  for (int i = 0; i <= H->n; ++i)
+    if ((H->bond[i] + 1) * H->d > MPO_MAXWD) return false;
+  return true;
+}
+
 }  // namespace tn
 
 using namespace tn;
@@ -468,13 +622,8 @@ int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace
 }
 
 size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H) {
-  if (check_chain(psi) != TN_OK || !H || !H->bond) return 0;
-  int64_t W = 1;
-  for (int i = 0; i <= H->n; ++i) W = std::max(W, H->bond[i]);
-  const int64_t D = max_bond(psi);
-  const size_t a = expect_layout(nullptr, D, W, psi->d, psi->n).bytes;
-  const size_t b = inner_layout(nullptr, D, psi->d, psi->n).bytes;
-  return a + b;
+  if (check_chain(psi) != TN_OK || !H || !H->bond || H->n != psi->n) return 0;
+  return expect2_layout(nullptr, psi, H).bytes;
 }
 
 int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace, size_t ws_bytes,
@@ -486,28 +635,21 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
   for (int i = 0; i < H->n; ++i)
     if (H->bond[i + 1] < 1 || !H->cores[i]) return TN_ERR_ARG;
   if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  const int n = psi->n;
+  const int64_t d = psi->d;
+  if (!mpo_extend_supported(H)) return TN_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int64_t Wm = 1;
-  for (int i = 0; i <= H->n; ++i) Wm = std::max(Wm, H->bond[i]);
-  const int64_t D = max_bond(psi), d = psi->d;
-  const size_t need = tn_mps_expect_workspace_bytes(psi, H);
-  if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
-  uint8_t* base = static_cast<uint8_t*>(workspace);
-  ExpectWs w = expect_layout(base, D, Wm, d, psi->n);
-  InnerWs wi = inner_layout(base + w.bytes, D, d, psi->n);
+  ExpectWs2 w = expect2_layout(static_cast<uint8_t*>(workspace), psi, H);
+  if (!workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
 
-  // <psi|psi>
-  float* env = nullptr;
-  rc = inner_sweep(psi, psi, prec, wi, &env, s);
-  if (rc != TN_OK) return rc;
-
-  // <psi|H|psi>
-  init_sweep_kernel<<<1, 256, 0, s>>>(w.L0, w.lg, 1, w.bits, psi->n);
+  // the extended MPO (one more channel: the norm)
+  if ((rc = launch_mpo_extend(H, w.Wx, w.woff.data(), s)) != TN_OK) return rc;
+  expect_init_kernel<<<1, 256, 0, s>>>(w.L0, (int)(H->bond[0] + 1), w.lg, w.bits, n);
   if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   float* L = w.L0;
   float* L2 = w.L1;
-  for (int i = 0; i < psi->n; ++i) {
-    const int64_t Da = psi->bond[i], Db = psi->bond[i + 1], wa = H->bond[i], wb = H->bond[i + 1];
+  for (int i = 0; i < n; ++i) {
+    const int64_t Da = psi->bond[i], Db = psi->bond[i + 1], wa = H->bond[i] + 1, wb = H->bond[i + 1] + 1;
     // (i) T1[w, a', s, b] = sum_a L[w, a, a'] A[a, s, b]
     tn_tensor tL = tensor3(L, wa, Da, Da);
     tn_tensor tA = tensor3(psi->cores[i], Da, d, Db);
@@ -515,20 +657,37 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
     const int la1[1] = {1}, lb1[1] = {0};
     if ((rc = contract_internal(&tL, la1, &tA, lb1, 1, &tT1, prec, s, w.scratch, w.scratch_bytes)) != TN_OK)
       return rc;
-    // (ii) T2[w', s', a', b] = sum_{w,s} W[w, w', s, s'] T1[w, a', s, b]
-    tn_tensor tW = tensor4(H->cores[i], wa, wb, d, d);
-    tn_tensor tT2 = tensor4(w.T2, wb, d, Da, Db);
-    const int la2[2] = {0, 2}, lb2[2] = {0, 2};
-    if ((rc = contract_internal(&tW, la2, &tT1, lb2, 2, &tT2, TN_PREC_FP32, s)) != TN_OK) return rc;
+    // (ii) T2[w', s', a', b] = 2^-e sum_{w,s} W'[w, w', s, s'] T1[w, a', s, b]
+    StepII q;
+    memset(&q, 0, sizeof(q));
+    q.T1 = w.T1;
+    q.T2 = w.T2;
+    q.W = w.Wx + w.woff[(size_t)i];
+    q.Da = Da;
+    q.Db = Db;
+    q.wa = (int32_t)wa;
+    q.wb = (int32_t)wb;
+    q.d = (int32_t)d;
+    q.maxbits = i > 0 ? w.bits + (i - 1) : nullptr;
+    q.lg = w.lg;
+    const int64_t cols = Da * Db;
+    mpo_step_ii_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((cols + 255) / 256, 4096)), 256, 0, s>>>(q);
+    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
     // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] A[a', s', b']
+    tn_tensor tT2 = tensor4(w.T2, wb, d, Da, Db);
     tn_tensor tL2 = tensor3(L2, wb, Db, Db);
     const int la3[2] = {1, 2}, lb3[2] = {1, 0};
     if ((rc = contract_internal(&tT2, la3, &tA, lb3, 2, &tL2, prec, s, w.scratch, w.scratch_bytes)) != TN_OK)
       return rc;
-    if ((rc = rescale(L2, wb * Db * Db, w.bits + i, w.lg, s)) != TN_OK) return rc;
+    // the largest |L'|: applied, exactly, in the next site's step (ii)
+    if (i + 1 < n) {
+      const int64_t nl = wb * Db * Db;
+      absmax_kernel<<<(unsigned)std::min<int64_t>((nl + 255) / 256, 1024), 256, 0, s>>>(L2, nl, w.bits + i);
+      if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+    }
     std::swap(L, L2);
   }
-  finish_kernel<<<1, 32, 0, s>>>(L, w.lg, env, wi.lg, result);
+  expect_finish_kernel<<<1, 32, 0, s>>>(L, w.lg, result);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 

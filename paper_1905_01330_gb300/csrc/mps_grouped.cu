@@ -1,10 +1,12 @@
 // <psi_k|H|psi_k> and <psi_k|psi_k> for a batch of MPS with uneven bond
 // dimensions and one shared MPO (the environment sweep of Sec. II / Fig. 3a
-// applied to many chains at once). Every site step of every chain goes into
-// grouped contraction launches, so the launch count per site does not grow
-// with the batch: stage 1 = {norm: T = E psi, energy (i)}, stage 2 = {norm:
-// E' = psi T} and {energy (ii), float32}, stage 3 = {energy (iii)}, then one
-// grouped rescale of all 2*count new environments.
+// applied to many chains at once). The norm rides along as one more MPO
+// channel (the MPO extended by an identity channel, as in tn_mps_expect).
+// Every site step of every chain goes into grouped launches, so the launch
+// count per site does not grow with the batch: (i) one grouped contraction,
+// (ii) one grouped float32 kernel that also applies the previous site's
+// deferred power-of-two rescale, (iii) one grouped contraction, then one
+// grouped max-abs pass over the count new environments.
 #include <math.h>
 #include <string.h>
 
@@ -17,8 +19,8 @@
 namespace tn {
 namespace {
 
-// One environment to rescale after a site: x[0..n) /= max|x|, log(max) added
-// to *lg; *bits holds the running max (float bits) and starts at 0.
+// One environment whose largest magnitude is wanted after a site: *bits
+// holds the running max (float bits) and starts at 0.
 struct Segment {
   float* x;
   int64_t n;
@@ -48,19 +50,11 @@ __global__ void seg_absmax_kernel(const Segment* __restrict__ segs) {
   if (threadIdx.x == 0) atomicMax(s.bits, __float_as_uint(m));
 }
 
-__global__ void seg_scale_kernel(const Segment* __restrict__ segs) {
-  const Segment s = segs[blockIdx.y];
-  const float m = __uint_as_float(*s.bits);
-  const float sc = m > 0.0f ? m : 1.0f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x)
-    s.x[i] = s.x[i] / sc;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *s.lg += log((double)sc);
-}
-
-// Per chain: the two starting environments set to the 1x1 (x1) identity.
+// Per chain: the starting environment, 1 in each of its channels (the MPO's
+// left boundary and the norm channel).
 struct ChainInit {
-  float* E;
   float* L;
+  int32_t channels, pad;
 };
 
 __global__ void grouped_init_kernel(const ChainInit* __restrict__ c, int count, double* lg, int nlg,
@@ -69,15 +63,13 @@ __global__ void grouped_init_kernel(const ChainInit* __restrict__ c, int count, 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = t; i < nbits; i += stride) bits[i] = 0u;
   for (int64_t i = t; i < nlg; i += stride) lg[i] = 0.0;
-  for (int64_t i = t; i < count; i += stride) {
-    c[i].E[0] = 1.0f;
-    c[i].L[0] = 1.0f;
-  }
+  for (int64_t i = t; i < count; i += stride)
+    for (int w = 0; w < c[i].channels; ++w) c[i].L[w] = 1.0f;
 }
 
-// Per chain: where the final 1x1 environments ended.
+// Per chain: where the final environment ended (channel 0: the energy,
+// channel 1: the norm).
 struct ChainFinal {
-  const float* E;
   const float* L;
 };
 
@@ -85,9 +77,9 @@ __global__ void grouped_finish_kernel(const ChainFinal* __restrict__ f, int coun
                                       double* result) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
     result[4 * k + 0] = (double)f[k].L[0];
-    result[4 * k + 1] = lg[2 * k + 1];
-    result[4 * k + 2] = (double)f[k].E[0];
-    result[4 * k + 3] = lg[2 * k + 0];
+    result[4 * k + 1] = lg[k];
+    result[4 * k + 2] = (double)f[k].L[1];
+    result[4 * k + 3] = lg[k];
   }
 }
 
@@ -132,22 +124,27 @@ struct PlanDeleter {
 using PlanPtr = std::unique_ptr<tn_group_plan, PlanDeleter>;
 
 // Host-side layout of one grouped sweep: buffers of every chain, the site
-// plans (four per site, their work lists only), one packed-operand region
-// they share, and the per-site rescale tables.
+// plans (two per site, their work lists only), one packed-operand region
+// they share, the extended MPO, the step (ii) descriptors and the per-site
+// max-abs tables.
 struct GroupedSweep {
   struct ChainBufs {
-    float *E[2], *T, *L[2], *T1, *T2;
+    float *L[2], *T1, *T2;
   };
   int count = 0, n = 0;
   int64_t d = 0;
   std::vector<ChainBufs> bufs;
-  std::vector<PlanPtr> plans;         // site-major: 4 per site
+  std::vector<PlanPtr> plans;         // site-major: (i), (iii)
   std::vector<size_t> plan_off;       // workspace offset of each plan's work list
   std::vector<size_t> plan_bytes;
-  std::vector<Segment> segs;          // n * 2 * count
+  std::vector<Segment> segs;          // n * count
+  std::vector<StepII> steps;          // n * count
+  std::vector<int64_t> max_cols;      // per site: the largest Da Db of the batch
   std::vector<ChainInit> inits;
   std::vector<ChainFinal> finals;
-  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_init = 0, off_final = 0, off_packed = 0, total = 0;
+  std::vector<int64_t> woff;          // extended MPO of every site
+  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_steps = 0, off_init = 0, off_final = 0, off_packed = 0;
+  size_t off_w = 0, total = 0;
   size_t packed_bytes = 0;  // largest packed-operand region of one plan
   int64_t nbits = 0;
 };
@@ -171,6 +168,8 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
     if (H->bond[i + 1] < 1 || !H->cores[i]) return TN_ERR_ARG;
     Wm = std::max(Wm, H->bond[i + 1]);
   }
+  if (!mpo_extend_supported(H)) return TN_ERR_UNSUPPORTED;
+  const int64_t W1 = Wm + 1;
   g->count = count;
   g->n = n;
   g->d = d;
@@ -184,62 +183,72 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
   for (int k = 0; k < count; ++k) {
     const int64_t D = chain_max_bond(psis[k]);
     auto& b = g->bufs[(size_t)k];
-    b.E[0] = take(sizeof(float) * D * D);
-    b.E[1] = take(sizeof(float) * D * D);
-    b.T = take(sizeof(float) * D * d * D);
-    b.L[0] = take(sizeof(float) * Wm * D * D);
-    b.L[1] = take(sizeof(float) * Wm * D * D);
-    b.T1 = take(sizeof(float) * Wm * D * d * D);
-    b.T2 = take(sizeof(float) * Wm * D * d * D);
+    b.L[0] = take(sizeof(float) * W1 * D * D);
+    b.L[1] = take(sizeof(float) * W1 * D * D);
+    b.T1 = take(sizeof(float) * W1 * D * d * D);
+    b.T2 = take(sizeof(float) * W1 * D * d * D);
   }
+  int64_t wtot = 0;
+  for (int i = 0; i < n; ++i) {
+    g->woff.push_back(wtot);
+    wtot += (H->bond[i] + 1) * (H->bond[i + 1] + 1) * d * d;
+  }
+  g->off_w = off;
+  off += align256(sizeof(float) * (size_t)wtot);
+  const float* Wx = reinterpret_cast<const float*>(base + g->off_w);
   g->off_lg = off;
-  off += align256(sizeof(double) * 2 * (size_t)count);
+  off += align256(sizeof(double) * (size_t)count);
   g->off_bits = off;
-  g->nbits = (int64_t)n * 2 * count;
+  g->nbits = (int64_t)n * count;
   off += align256(sizeof(unsigned) * (size_t)g->nbits);
   double* lg = reinterpret_cast<double*>(base + g->off_lg);
   unsigned* bits = reinterpret_cast<unsigned*>(base + g->off_bits);
 
   // site plans
-  std::vector<tn_contract_spec> s1, s2a, s2b, s3;
+  std::vector<tn_contract_spec> s1, s3;
   for (int i = 0; i < n; ++i) {
     s1.clear();
-    s2a.clear();
-    s2b.clear();
     s3.clear();
-    const int64_t wa = H->bond[i], wb = H->bond[i + 1];
+    const int64_t wa = H->bond[i] + 1, wb = H->bond[i + 1] + 1;
+    int64_t mc = 1;
     for (int k = 0; k < count; ++k) {
       const tn_mps& m = psis[k];
       auto& b = g->bufs[(size_t)k];
       const int64_t Da = m.bond[i], Db = m.bond[i + 1];
       float* core = m.cores[i];
-      const int64_t shE[2] = {Da, Da}, shA[3] = {Da, d, Db}, shT[3] = {Da, d, Db}, shE2[2] = {Db, Db};
-      const tn_tensor tE = make_tensor(b.E[i & 1], 2, shE), tA = make_tensor(core, 3, shA);
-      const tn_tensor tT = make_tensor(b.T, 3, shT), tE2 = make_tensor(b.E[(i + 1) & 1], 2, shE2);
-      const int64_t shL[3] = {wa, Da, Da}, shT1[4] = {wa, Da, d, Db}, shW[4] = {wa, wb, d, d};
+      const int64_t shA[3] = {Da, d, Db};
+      const tn_tensor tA = make_tensor(core, 3, shA);
+      const int64_t shL[3] = {wa, Da, Da}, shT1[4] = {wa, Da, d, Db};
       const int64_t shT2[4] = {wb, d, Da, Db}, shL2[3] = {wb, Db, Db};
       const tn_tensor tL = make_tensor(b.L[i & 1], 3, shL), tT1 = make_tensor(b.T1, 4, shT1);
-      const tn_tensor tW = make_tensor(H->cores[i], 4, shW), tT2 = make_tensor(b.T2, 4, shT2);
+      const tn_tensor tT2 = make_tensor(b.T2, 4, shT2);
       const tn_tensor tL2 = make_tensor(b.L[(i + 1) & 1], 3, shL2);
-      // norm:  T[a, s, b'] = sum_a' E[a, a'] psi[a', s, b']
-      s1.push_back(make_spec(tE, {1}, tA, {0}, tT));
       // (i)   T1[w, a', s, b] = sum_a L[w, a, a'] psi[a, s, b]
       s1.push_back(make_spec(tL, {1}, tA, {0}, tT1));
-      // norm:  E'[b, b'] = sum_{a, s} psi[a, s, b] T[a, s, b']
-      s2a.push_back(make_spec(tA, {0, 1}, tT, {0, 1}, tE2));
-      // (ii)  T2[w', s', a', b] = sum_{w, s} W[w, w', s, s'] T1[w, a', s, b]
-      s2b.push_back(make_spec(tW, {0, 2}, tT1, {0, 2}, tT2));
+      // (ii)  T2[w', s', a', b] = 2^-e sum_{w, s} W'[w, w', s, s'] T1[w, a', s, b]
+      StepII q;
+      memset(&q, 0, sizeof(q));
+      q.T1 = b.T1;
+      q.T2 = b.T2;
+      q.W = Wx + g->woff[(size_t)i];
+      q.Da = Da;
+      q.Db = Db;
+      q.wa = (int32_t)wa;
+      q.wb = (int32_t)wb;
+      q.d = (int32_t)d;
+      q.maxbits = i > 0 ? bits + (size_t)count * (i - 1) + k : nullptr;
+      q.lg = lg + k;
+      g->steps.push_back(q);
+      mc = std::max(mc, Da * Db);
       // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] psi[a', s', b']
       s3.push_back(make_spec(tT2, {1, 2}, tA, {1, 0}, tL2));
-      g->segs.push_back(Segment{b.E[(i + 1) & 1], Db * Db, bits + (size_t)(2 * count) * i + 2 * k, lg + 2 * k});
-      g->segs.push_back(
-          Segment{b.L[(i + 1) & 1], wb * Db * Db, bits + (size_t)(2 * count) * i + 2 * k + 1, lg + 2 * k + 1});
+      g->segs.push_back(Segment{b.L[(i + 1) & 1], wb * Db * Db, bits + (size_t)count * i + k, lg + k});
     }
-    const std::vector<tn_contract_spec>* stages[4] = {&s1, &s2a, &s2b, &s3};
-    const int precs[4] = {prec, prec, TN_PREC_FP32, prec};
-    for (int j = 0; j < 4; ++j) {
+    g->max_cols.push_back(mc);
+    const std::vector<tn_contract_spec>* stages[2] = {&s1, &s3};
+    for (int j = 0; j < 2; ++j) {
       tn_group_plan* p = nullptr;
-      int rc = tn_group_plan_create(stages[j]->data(), (int)stages[j]->size(), precs[j], &p);
+      int rc = tn_group_plan_create(stages[j]->data(), (int)stages[j]->size(), prec, &p);
       if (rc != TN_OK) return rc;
       g->plans.emplace_back(p);
       const size_t bytes = group_plan_list_bytes(p);
@@ -255,11 +264,13 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
   off += align256(g->packed_bytes);
   g->off_segs = off;
   off += align256(sizeof(Segment) * g->segs.size());
+  g->off_steps = off;
+  off += align256(sizeof(StepII) * g->steps.size());
   g->inits.resize((size_t)count);
   g->finals.resize((size_t)count);
   for (int k = 0; k < count; ++k) {
-    g->inits[(size_t)k] = ChainInit{g->bufs[(size_t)k].E[0], g->bufs[(size_t)k].L[0]};
-    g->finals[(size_t)k] = ChainFinal{g->bufs[(size_t)k].E[n & 1], g->bufs[(size_t)k].L[n & 1]};
+    g->inits[(size_t)k] = ChainInit{g->bufs[(size_t)k].L[0], (int32_t)(H->bond[0] + 1), 0};
+    g->finals[(size_t)k] = ChainFinal{g->bufs[(size_t)k].L[n & 1]};
   }
   g->off_init = off;
   off += align256(sizeof(ChainInit) * (size_t)count);
@@ -293,7 +304,8 @@ int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int pr
   if (rc != TN_OK) return rc;
   if (ws_bytes < g.total) return TN_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // uploads: plan work lists, rescale segments, init and final tables
+  // uploads: plan work lists, max-abs segments, step (ii) descriptors, init
+  // and final tables; then the extended MPO
   for (size_t j = 0; j < g.plans.size(); ++j) {
     if (g.plan_bytes[j] == 0) continue;
     rc = group_plan_upload_shared(g.plans[j].get(), base + g.plan_off[j], g.plan_bytes[j], base + g.off_packed, s);
@@ -301,29 +313,37 @@ int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int pr
   }
   if (cudaMemcpyAsync(base + g.off_segs, g.segs.data(), sizeof(Segment) * g.segs.size(), cudaMemcpyHostToDevice,
                       s) != cudaSuccess ||
+      cudaMemcpyAsync(base + g.off_steps, g.steps.data(), sizeof(StepII) * g.steps.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
       cudaMemcpyAsync(base + g.off_init, g.inits.data(), sizeof(ChainInit) * g.inits.size(),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + g.off_final, g.finals.data(), sizeof(ChainFinal) * g.finals.size(),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return TN_ERR_CUDA;
+  if ((rc = launch_mpo_extend(H, reinterpret_cast<float*>(base + g.off_w), g.woff.data(), s)) != TN_OK) return rc;
   double* lg = reinterpret_cast<double*>(base + g.off_lg);
   unsigned* bits = reinterpret_cast<unsigned*>(base + g.off_bits);
-  grouped_init_kernel<<<64, 256, 0, s>>>(reinterpret_cast<const ChainInit*>(base + g.off_init), count, lg,
-                                         2 * count, bits, g.nbits);
+  grouped_init_kernel<<<64, 256, 0, s>>>(reinterpret_cast<const ChainInit*>(base + g.off_init), count, lg, count,
+                                         bits, g.nbits);
   if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   const Segment* segs = reinterpret_cast<const Segment*>(base + g.off_segs);
+  const StepII* steps = reinterpret_cast<const StepII*>(base + g.off_steps);
   for (int i = 0; i < g.n; ++i) {
-    for (int j = 0; j < 4; ++j) {
-      const size_t p = (size_t)i * 4 + j;
-      rc = group_plan_run_shared(g.plans[p].get(), base + g.plan_off[p], g.plan_bytes[p], s);
-      if (rc != TN_OK) return rc;
+    const size_t p0 = (size_t)i * 2;
+    if ((rc = group_plan_run_shared(g.plans[p0].get(), base + g.plan_off[p0], g.plan_bytes[p0], s)) != TN_OK)
+      return rc;
+    if ((rc = launch_mpo_step_ii_grouped(steps + (size_t)count * i, count, g.max_cols[(size_t)i], s)) != TN_OK)
+      return rc;
+    if ((rc = group_plan_run_shared(g.plans[p0 + 1].get(), base + g.plan_off[p0 + 1], g.plan_bytes[p0 + 1], s)) !=
+        TN_OK)
+      return rc;
+    if (i + 1 < g.n) {
+      int64_t longest = 1;
+      for (int k = 0; k < count; ++k) longest = std::max(longest, g.segs[(size_t)count * i + k].n);
+      const dim3 grid((unsigned)std::min<int64_t>((longest + 2047) / 2048, 64), (unsigned)count);
+      seg_absmax_kernel<<<grid, 256, 0, s>>>(segs + (size_t)count * i);
+      if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
     }
-    int64_t longest = 1;
-    for (int k = 0; k < 2 * count; ++k) longest = std::max(longest, g.segs[(size_t)(2 * count) * i + k].n);
-    const dim3 grid((unsigned)std::min<int64_t>((longest + 2047) / 2048, 64), (unsigned)(2 * count));
-    seg_absmax_kernel<<<grid, 256, 0, s>>>(segs + (size_t)(2 * count) * i);
-    seg_scale_kernel<<<grid, 256, 0, s>>>(segs + (size_t)(2 * count) * i);
-    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   }
   grouped_finish_kernel<<<(count + 127) / 128, 128, 0, s>>>(reinterpret_cast<const ChainFinal*>(base + g.off_final),
                                                            count, lg, result);

@@ -100,6 +100,27 @@ size_t group_plan_packed_bytes(const tn_group_plan* plan);
 int group_plan_upload_shared(const tn_group_plan* plan, void* lists, size_t bytes, void* packed, cudaStream_t s);
 int group_plan_run_shared(const tn_group_plan* plan, void* lists, size_t bytes, cudaStream_t s);
 
+// Step (ii) of an energy sweep with a deferred, exact rescale (mps.cu):
+//   T2[w', s', a', b] = 2^-e sum_{w,s} W'[w, w', s, s'] T1[w, a', s, b],
+// W' the MPO extended by the norm channel, e the binary exponent of *maxbits
+// (the largest |L| entering the site; null at the first site), e ln 2 added
+// to *lg by one thread.
+struct StepII {
+  const float* T1;
+  float* T2;
+  const float* W;
+  int64_t Da, Db;
+  int32_t wa, wb, d, pad;
+  const unsigned* maxbits;
+  double* lg;
+};
+int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, cudaStream_t s);
+// The extended MPO W' of every site of H into out + off[i] (floats):
+// W'[w, w', s, s'] = W[w, w', s, s'] on the original channels, the identity
+// on the added channel (bond + 1 of every bond).
+int launch_mpo_extend(const tn_mpo* H, float* out, const int64_t* off, cudaStream_t s);
+bool mpo_extend_supported(const tn_mpo* H);
+
 // Device status word (first error wins); defined in api.cu.
 int* status_word();
 
