@@ -103,3 +103,30 @@ def test_mpo_with_other_couplings_against_dense():
     # the MPO holds J and h rounded to float32
     ref = oracle.tfim_energy_dense(n, float(np.float32(0.7)), float(np.float32(1.3)), oracle.mps_state(cores))
     assert abs(v * math.exp(lg) - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+def test_stored_energy_values_are_the_oracles():
+    # tests/golden/energy_oracle.txt is written by make_energy_oracle.py from
+    # oracle.mpo_expect / oracle.mps_inner; recompute its cheapest row (the
+    # batch's chi = 64 state, N = 100) and check value and input fingerprint
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "energy_oracle.txt")
+    rows = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            rows[parts[0]] = [float(x) for x in parts[1:]]
+    chi, n, seed, e, le, v, lv, s, q = rows["batch0_chi64_n100"]
+    cores = synth.left_canonical_mps(int(n), 2, int(chi), seed=int(seed))
+    assert abs(sum(float(np.sum(c, dtype=np.float64)) for c in cores) - s) <= 1e-6 * abs(s)
+    assert abs(sum(float(np.sum(c.astype(np.float64) ** 2)) for c in cores) - q) <= 1e-9 * q
+    e2, le2 = oracle.mpo_expect(cores, synth.tfim_mpo(int(n)))
+    v2, lv2 = oracle.mps_inner(cores, cores)
+    assert abs(e2 * np.exp(le2) - e * np.exp(le)) <= 1e-12 * (2 * n)
+    assert abs(v2 * np.exp(lv2) - v * np.exp(lv)) <= 1e-12
+    # every stored state is left-canonical: its norm is 1 to float32 rounding
+    for key, (chi, n, seed, e, le, v, lv, s, q) in rows.items():
+        assert abs(v * np.exp(lv) - 1.0) <= n * 1e-6, key
+        assert abs(e * np.exp(le)) <= (2 * n - 1), key  # |E| <= ||H|| for a unit state
