@@ -343,36 +343,43 @@ __device__ __forceinline__ int pow2_exponent(float m) {
   return e < -126 ? -126 : (e > 126 ? 126 : e);
 }
 
+// Offsets are 32-bit: the host checks that T1 and T2 hold fewer than 2^31
+// elements. Thread c takes column (a', b) = (c / Db, c % Db).
 __device__ __forceinline__ void step_ii(const StepII& q, int64_t first, int64_t stride, bool log_thread) {
   __shared__ float Ws[MPO_MAXWD][MPO_MAXWD];  // [(w, s)][(w', s')]
+  __shared__ int32_t koff[MPO_MAXWD];         // T1 offset of (w, s): (w Da d + s) Db
   const int wad = q.wa * q.d, wbd = q.wb * q.d, d = q.d;
+  const int32_t Da = (int32_t)q.Da, Db = (int32_t)q.Db;
   for (int e = threadIdx.x; e < wad * wbd; e += blockDim.x) {
     const int k = e / wbd, m = e - k * wbd;
     const int w = k / d, s = k - w * d, w2 = m / d, s2 = m - w2 * d;
     Ws[k][m] = q.W[((w * q.wb + w2) * d + s) * d + s2];
+  }
+  for (int k = threadIdx.x; k < wad; k += blockDim.x) {
+    const int w = k / d, s = k - w * d;
+    koff[k] = (w * Da * d + s) * Db;
   }
   __syncthreads();
   int e = 0;
   if (q.maxbits) e = pow2_exponent(__uint_as_float(*q.maxbits));
   const float inv = __int_as_float((127 - e) << 23);
   if (log_thread && q.maxbits) *q.lg += (double)e * 0.69314718055994530942;
-  const int64_t cols = q.Da * q.Db;
-  for (int64_t c = first; c < cols; c += stride) {
-    const int64_t a = c / q.Db, b = c - a * q.Db;
+  const int32_t cols = Da * Db, mstride = Da * Db;
+  const float* __restrict__ T1 = q.T1;
+  float* __restrict__ T2 = q.T2;
+  for (int32_t c = (int32_t)first; c < cols; c += (int32_t)stride) {
+    const int32_t a = c / Db, b = c - a * Db;
+    const int32_t base1 = a * d * Db + b;
     float t[MPO_MAXWD];
 #pragma unroll
-    for (int k = 0; k < MPO_MAXWD; ++k) {
-      if (k < wad) {
-        const int w = k / d, s = k - w * d;
-        t[k] = __ldg(q.T1 + (((int64_t)w * q.Da + a) * d + s) * q.Db + b);
-      }
-    }
+    for (int k = 0; k < MPO_MAXWD; ++k)
+      if (k < wad) t[k] = __ldg(T1 + base1 + koff[k]);
     for (int m = 0; m < wbd; ++m) {
       float acc = 0.0f;
 #pragma unroll
       for (int k = 0; k < MPO_MAXWD; ++k)
         if (k < wad) acc = fmaf(Ws[k][m], t[k], acc);
-      q.T2[((int64_t)m * q.Da + a) * q.Db + b] = acc * inv;
+      T2[m * mstride + c] = acc * inv;
     }
   }
 }
@@ -638,6 +645,12 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
   const int n = psi->n;
   const int64_t d = psi->d;
   if (!mpo_extend_supported(H)) return TN_ERR_UNSUPPORTED;
+  {
+    int64_t Wm = 1;
+    for (int i = 0; i <= n; ++i) Wm = std::max(Wm, H->bond[i]);
+    const int64_t D = max_bond(psi);
+    if ((Wm + 1) * D * d * D >= (int64_t(1) << 31)) return TN_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ExpectWs2 w = expect2_layout(static_cast<uint8_t*>(workspace), psi, H);
   if (!workspace || ws_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;

@@ -170,6 +170,10 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
   }
   if (!mpo_extend_supported(H)) return TN_ERR_UNSUPPORTED;
   const int64_t W1 = Wm + 1;
+  for (int k = 0; k < count; ++k) {
+    const int64_t D = chain_max_bond(psis[k]);
+    if (W1 * D * d * D >= (int64_t(1) << 31)) return TN_ERR_UNSUPPORTED;  // 32-bit step (ii) offsets
+  }
   g->count = count;
   g->n = n;
   g->d = d;

@@ -262,9 +262,9 @@ pack_pair_kernel(const __grid_constant__ PackPair pp) {
 // GEMM (one per quadrant, all 128 columns: its tiles are narrow, and 14 warps
 // leave each sub-partition's register file 128 registers per thread)
 // BF16X3 promotes the TMEM accumulator into float32 registers every KC slabs
-// (256 shared indices): the tensor core's float32 accumulation truncates, and
+// (512 shared indices): the tensor core's float32 accumulation truncates, and
 // over long k that error would exceed the split's own rounding error.
-constexpr int KC = 4;
+constexpr int KC = 8;
 
 // Fused GEMM: eight converter warps copy each 128-row x 64-k float32 slab of
 // P through its leg strides into a ring of XSLOTS staging slots (cp.async,

@@ -14,6 +14,10 @@ the last-bit differences another host's LAPACK may leave in a few entries).
 relative to ||H|| <psi|psi>, ||H|| <= J (N - 1) + h N, with the per-sweep
 tolerances of the other sweep tests: float32 1e-5; split BF16x3
 2 * 2^-16 * sqrt(c); bf16 2 * 2^-8 * sqrt(c), c = 2N contractions.
+<psi|psi> is a sum of squares: the term the split drops (lo * lo, at most
+2^-18 of a product) and the rounding of each operand enter it as quadratic
+forms of one sign, so those errors add up over the c contractions instead of
+walking: its bound adds c * 2^-18 (BF16x3) or c * 2^-16 (bf16) to the walk.
 """
 import math
 import os
@@ -32,6 +36,11 @@ UNIT = {"fp32": None, "bf16x3": 2.0 ** -16, "bf16": 2.0 ** -8}
 
 def tol(prec, n):
     return 1e-5 if prec == "fp32" else 2.0 * UNIT[prec] * math.sqrt(2 * n)
+
+
+def norm_tol(prec, n):
+    bias = {"fp32": 0.0, "bf16x3": 2.0 ** -18, "bf16": 2.0 ** -16}[prec]
+    return tol(prec, n) + 2 * n * bias
 
 
 def golden():
@@ -69,7 +78,7 @@ def check(r, row, prec, what):
     h_norm = 1.0 * (n - 1) + 1.0 * n
     energy, norm = r[0] * math.exp(r[1]), r[2] * math.exp(r[3])
     assert abs(energy - row["energy"]) <= tol(prec, n) * h_norm * row["norm"], (what, prec, energy, row["energy"])
-    assert abs(norm - row["norm"]) <= tol(prec, n) * row["norm"], (what, prec, norm, row["norm"])
+    assert abs(norm - row["norm"]) <= norm_tol(prec, n) * row["norm"], (what, prec, norm, row["norm"])
 
 
 @pytest.mark.parametrize("key", ["chain_chi256_n100", "chain_chi512_n38", "chain_chi1024_n40"])
