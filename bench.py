@@ -570,6 +570,65 @@ def run_reference(args):
     return 0
 
 
+
+def run_case(args):
+    """One workload of the hot path, a warm-up call and one more, for profilers
+    (ncu launch lists and captures); prints the device status, no bench line.
+    Cases: classifier_forward, classifier_train, energy, mps_norm,
+    grouped_tensordot (the first --specs specs of the bench workload)."""
+    import torch
+    from paper_1905_01330_gb300 import build, synth, tn
+    build.build()
+    tn.load()
+    dev = torch.device("cuda", 0)
+    B, n, ls, L = 4096, 784, 392, 10
+    chi, prec = args.chi, args.prec
+    if args.case in ("classifier_forward", "classifier_train"):
+        px = torch.from_numpy(synth.pixels(B, n, seed=3)).to(dev)
+        y = torch.from_numpy(synth.labels(B, L, seed=4)).to(dev)
+        cores = [torch.from_numpy(c).to(dev) for c in synth.classifier_mps(n, chi, ls, L, seed=30 + chi, eps_std=0.1)]
+        ck = 28 if args.case == "classifier_train" else 0
+        ws = tn.classifier_workspace(cores, ls, L, B, ck)
+        for _ in range(2):
+            ft, lam, _ = tn.mps_classify(cores, ls, px, prec=prec, ckpt_every=ck, workspace=ws)
+            if ck:
+                loss, dft = tn.mps_classify_loss(ft, y)
+                tn.mps_classify_backward(cores, ls, px, dft, ws, prec=prec, ckpt_every=ck)
+    elif args.case == "energy":
+        # N = 100 TFIM energy; random N(0, 1/chi) cores drawn on the device (the
+        # sweep's work does not depend on the values: it rescales every site)
+        W = [torch.from_numpy(w).to(dev) for w in synth.tfim_mpo(100)]
+        bonds = synth.mps_bonds(100, 2, chi)
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        cores = [torch.randn(bonds[i], 2, bonds[i + 1], device=dev, generator=g) / chi ** 0.5 for i in range(100)]
+        res = torch.empty(4, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            tn.mps_expect(cores, W, prec=prec, out=res)
+    elif args.case == "mps_norm":
+        m = [torch.from_numpy(c).to(dev) for c in synth.random_mps(20, 2, 32, seed=1)]
+        res = torch.empty(2, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            tn.mps_inner(m, m, prec="fp32", out=res)
+    elif args.case == "grouped_tensordot":
+        specs_h = synth.contraction_specs(N_SPECS, seed=SEED)[:args.specs]
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(SEED)
+        specs = []
+        for sa, la, sb, lb in specs_h:
+            A = torch.randn(sa, device=dev, generator=gen)
+            Bt = torch.randn(sb, device=dev, generator=gen)
+            specs.append((A, list(la), Bt, list(lb), torch.empty(tn.result_shape(A, la, Bt, lb), device=dev)))
+        plan = tn.GroupPlan(specs, prec=prec)
+        for _ in range(2):
+            plan.run()
+    else:
+        raise SystemExit("unknown case " + args.case)
+    torch.cuda.synchronize()
+    status = tn.sync_status()
+    print("case %s chi %d prec %s status %d" % (args.case, chi, prec, status))
+    return 0 if status == 0 else 1
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -583,7 +642,14 @@ def main():
     ap.add_argument("--variants", default="bf16x3,fp32", help="other paths to time, comma separated, or none")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the classifier, MPS-norm and energy measurements")
+    ap.add_argument("--case", default=None,
+                    help="run one workload twice for a profiler (classifier_forward, classifier_train, energy, "
+                         "mps_norm, grouped_tensordot) instead of the bench")
+    ap.add_argument("--chi", type=int, default=64, help="bond dimension of --case")
+    ap.add_argument("--prec", default="bf16", help="precision of --case: fp32, bf16, bf16x3")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
 

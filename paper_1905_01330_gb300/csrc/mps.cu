@@ -344,20 +344,26 @@ __device__ __forceinline__ int pow2_exponent(float m) {
 }
 
 // Offsets are 32-bit: the host checks that T1 and T2 hold fewer than 2^31
-// elements. Thread c takes column (a', b) = (c / Db, c % Db).
+// elements. Thread c takes column (a', b) = (c / Db, c % Db); WD bounds both
+// (extended MPO bond) x d, so the sums unroll fully at the MPO's own size.
+template <int WD>
 __device__ __forceinline__ void step_ii(const StepII& q, int64_t first, int64_t stride, bool log_thread) {
-  __shared__ float Ws[MPO_MAXWD][MPO_MAXWD];  // [(w, s)][(w', s')]
-  __shared__ int32_t koff[MPO_MAXWD];         // T1 offset of (w, s): (w Da d + s) Db
+  __shared__ float Ws[WD][WD];     // [(w, s)][(w', s')], zero past the MPO
+  __shared__ int32_t koff[WD];     // T1 offset of (w, s): (w Da d + s) Db
   const int wad = q.wa * q.d, wbd = q.wb * q.d, d = q.d;
   const int32_t Da = (int32_t)q.Da, Db = (int32_t)q.Db;
-  for (int e = threadIdx.x; e < wad * wbd; e += blockDim.x) {
-    const int k = e / wbd, m = e - k * wbd;
-    const int w = k / d, s = k - w * d, w2 = m / d, s2 = m - w2 * d;
-    Ws[k][m] = q.W[((w * q.wb + w2) * d + s) * d + s2];
+  for (int e = threadIdx.x; e < WD * WD; e += blockDim.x) {
+    const int k = e / WD, m = e - k * WD;
+    float v = 0.0f;
+    if (k < wad && m < wbd) {
+      const int w = k / d, s = k - w * d, w2 = m / d, s2 = m - w2 * d;
+      v = q.W[((w * q.wb + w2) * d + s) * d + s2];
+    }
+    Ws[k][m] = v;
   }
-  for (int k = threadIdx.x; k < wad; k += blockDim.x) {
+  for (int k = threadIdx.x; k < WD; k += blockDim.x) {
     const int w = k / d, s = k - w * d;
-    koff[k] = (w * Da * d + s) * Db;
+    koff[k] = k < wad ? (w * Da * d + s) * Db : 0;
   }
   __syncthreads();
   int e = 0;
@@ -367,33 +373,66 @@ __device__ __forceinline__ void step_ii(const StepII& q, int64_t first, int64_t 
   const int32_t cols = Da * Db, mstride = Da * Db;
   const float* __restrict__ T1 = q.T1;
   float* __restrict__ T2 = q.T2;
+  // at the smallest width the whole MPO lives in registers
+  constexpr int WR = WD == 8 ? 8 : 1;
+  float wr[WR][WR];
+#pragma unroll
+  for (int k = 0; k < WR; ++k)
+#pragma unroll
+    for (int m = 0; m < WR; ++m) wr[k][m] = Ws[k][m];
+  int32_t ko[WD];
+#pragma unroll
+  for (int k = 0; k < WD; ++k) ko[k] = koff[k];
   for (int32_t c = (int32_t)first; c < cols; c += (int32_t)stride) {
     const int32_t a = c / Db, b = c - a * Db;
     const int32_t base1 = a * d * Db + b;
-    float t[MPO_MAXWD];
+    float t[WD];
 #pragma unroll
-    for (int k = 0; k < MPO_MAXWD; ++k)
-      if (k < wad) t[k] = __ldg(T1 + base1 + koff[k]);
-    for (int m = 0; m < wbd; ++m) {
-      float acc = 0.0f;
+    for (int k = 0; k < WD; ++k) t[k] = k < wad ? __ldg(T1 + base1 + ko[k]) : 0.0f;
 #pragma unroll
-      for (int k = 0; k < MPO_MAXWD; ++k)
-        if (k < wad) acc = fmaf(Ws[k][m], t[k], acc);
-      T2[m * mstride + c] = acc * inv;
+    for (int m = 0; m < WD; ++m) {
+      if (m < wbd) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < WD; ++k) acc = fmaf(WD == 8 ? wr[k % WR][m % WR] : Ws[k][m], t[k], acc);
+        T2[m * mstride + c] = acc * inv;
+      }
     }
   }
 }
 
+template <int WD>
 __global__ void __launch_bounds__(256) mpo_step_ii_kernel(const __grid_constant__ StepII q) {
-  step_ii(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
-          blockIdx.x == 0 && threadIdx.x == 0);
+  step_ii<WD>(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+              blockIdx.x == 0 && threadIdx.x == 0);
 }
 
 // Grouped form: blockIdx.y picks the chain's descriptor.
+template <int WD>
 __global__ void __launch_bounds__(256) mpo_step_ii_grouped(const StepII* __restrict__ descs) {
   const StepII q = descs[blockIdx.y];
-  step_ii(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
-          blockIdx.x == 0 && threadIdx.x == 0);
+  step_ii<WD>(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+              blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// The unroll width of step (ii): the smallest of 8, 16, 32 covering both
+// (extended MPO bond) x d.
+int step_ii_width(int64_t wad, int64_t wbd) {
+  const int64_t m = std::max(wad, wbd);
+  return m <= 8 ? 8 : (m <= 16 ? 16 : 32);
+}
+
+int launch_step_ii(const StepII& q, cudaStream_t s) {
+  const int64_t cols = q.Da * q.Db;
+  // a few columns per thread: the block's setup (the MPO into registers) is
+  // then spread over more work
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cols + 1023) / 1024, 1216));
+  switch (step_ii_width((int64_t)q.wa * q.d, (int64_t)q.wb * q.d)) {
+    case 8: mpo_step_ii_kernel<8><<<grid, 256, 0, s>>>(q); break;
+    case 16: mpo_step_ii_kernel<16><<<grid, 256, 0, s>>>(q); break;
+    default: mpo_step_ii_kernel<32><<<grid, 256, 0, s>>>(q); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
 // Energy sweep workspace: L0, L1 ((W+1) D^2), T1, T2 ((W+1) D d D), n max
@@ -520,10 +559,15 @@ int inner_sweep(const tn_mps* bra, const tn_mps* ket, int prec, const InnerWs& w
 
 }  // namespace
 
-int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, cudaStream_t s) {
+int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, int64_t wad, int64_t wbd,
+                               cudaStream_t s) {
   if (count <= 0) return TN_OK;
   const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_cols + 255) / 256, 1024)), (unsigned)count);
-  mpo_step_ii_grouped<<<grid, 256, 0, s>>>(descs);
+  switch (step_ii_width(wad, wbd)) {
+    case 8: mpo_step_ii_grouped<8><<<grid, 256, 0, s>>>(descs); break;
+    case 16: mpo_step_ii_grouped<16><<<grid, 256, 0, s>>>(descs); break;
+    default: mpo_step_ii_grouped<32><<<grid, 256, 0, s>>>(descs); break;
+  }
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
@@ -683,9 +727,7 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
     q.d = (int32_t)d;
     q.maxbits = i > 0 ? w.bits + (i - 1) : nullptr;
     q.lg = w.lg;
-    const int64_t cols = Da * Db;
-    mpo_step_ii_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((cols + 255) / 256, 4096)), 256, 0, s>>>(q);
-    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+    if ((rc = launch_step_ii(q, s)) != TN_OK) return rc;
     // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] A[a', s', b']
     tn_tensor tT2 = tensor4(w.T2, wb, d, Da, Db);
     tn_tensor tL2 = tensor3(L2, wb, Db, Db);

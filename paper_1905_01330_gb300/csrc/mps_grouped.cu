@@ -336,7 +336,9 @@ int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int pr
     const size_t p0 = (size_t)i * 2;
     if ((rc = group_plan_run_shared(g.plans[p0].get(), base + g.plan_off[p0], g.plan_bytes[p0], s)) != TN_OK)
       return rc;
-    if ((rc = launch_mpo_step_ii_grouped(steps + (size_t)count * i, count, g.max_cols[(size_t)i], s)) != TN_OK)
+    const StepII& q0 = g.steps[(size_t)count * i];
+    if ((rc = launch_mpo_step_ii_grouped(steps + (size_t)count * i, count, g.max_cols[(size_t)i],
+                                         (int64_t)q0.wa * q0.d, (int64_t)q0.wb * q0.d, s)) != TN_OK)
       return rc;
     if ((rc = group_plan_run_shared(g.plans[p0 + 1].get(), base + g.plan_off[p0 + 1], g.plan_bytes[p0 + 1], s)) !=
         TN_OK)

@@ -1309,8 +1309,13 @@ int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_
   memset(&pp, 0, sizeof(pp));
   pp.a = ja;
   pp.b = jb;
-  pp.per_a = blocks_per_unit(ja);
-  pp.per_b = blocks_per_unit(jb);
+  // one contraction alone on the GPU: units of fewer blocks when that is
+  // what it takes to give every SM a few (a large operand in units of 8
+  // blocks left two thirds of the SMs idle and the rest latency-bound)
+  const int64_t blocks = (int64_t)ja.tiles * ja.slabs + (int64_t)jb.tiles * jb.slabs;
+  const int32_t cap = (int32_t)std::max<int64_t>(1, blocks / (4 * (int64_t)sm_count()));
+  pp.per_a = std::min(blocks_per_unit(ja), cap);
+  pp.per_b = std::min(blocks_per_unit(jb), cap);
   const int64_t na = (ja.tiles * (int64_t)ja.slabs + pp.per_a - 1) / pp.per_a;
   const int64_t nb = (jb.tiles * (int64_t)jb.slabs + pp.per_b - 1) / pp.per_b;
   if (na + nb > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;

@@ -114,7 +114,9 @@ struct StepII {
   const unsigned* maxbits;
   double* lg;
 };
-int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, cudaStream_t s);
+// wad, wbd: (extended MPO bond) x d on either side of the site.
+int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, int64_t wad, int64_t wbd,
+                               cudaStream_t s);
 // The extended MPO W' of every site of H into out + off[i] (floats):
 // W'[w, w', s, s'] = W[w, w', s, s'] on the original channels, the identity
 // on the added channel (bond + 1 of every bond).
