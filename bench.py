@@ -524,10 +524,14 @@ def run_extras(tn, synth, dev, stream):
     rows = [golden["batch%d_chi%d_n100" % (k, chis[k])] for k in range(4)]
     sub = [[torch.from_numpy(c).to(dev) for c in synth.left_canonical_mps(100, 2, r["chi"], seed=r["seed"])] for r in rows]
     for prec in ("bf16x3", "fp32", "bf16"):
-        ms = _time(lambda: tn.mps_expect_grouped(states, W, prec=prec, out=res), 2, 1, stream)
+        # planned once (host layout and tables), then each run only launches
+        plan = tn.ExpectGroupedPlan(states, W, prec=prec)
+        ms = _time(lambda: plan.run(out=res), 3, 1, stream)
+        ms_oneshot = _time(lambda: tn.mps_expect_grouped(states, W, prec=prec, out=res), 2, 1, stream)
+        del plan
         r4 = tn.mps_expect_grouped(sub, W, prec=prec).cpu().numpy()
         errs = [abs(r4[k, 0] * np.exp(r4[k, 1]) - row["energy"]) / (199.0 * row["norm"]) for k, row in enumerate(rows)]
-        en[prec] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+        en[prec] = {"ms": ms, "ms_plan_and_run": ms_oneshot, "tflops": flops / (ms * 1e-3) / 1e12,
                     "max_err_vs_oracle_over_energy_scale": float(max(errs))}
     out["tfim_energy_batch64_n100_chi64_512"] = en
     del states, sub
@@ -574,8 +578,8 @@ def run_reference(args):
 def run_case(args):
     """One workload of the hot path, a warm-up call and one more, for profilers
     (ncu launch lists and captures); prints the device status, no bench line.
-    Cases: classifier_forward, classifier_train, energy, mps_norm,
-    grouped_tensordot (the first --specs specs of the bench workload)."""
+    Cases: classifier_forward, classifier_train, energy, energy_batch,
+    mps_norm, grouped_tensordot (the first --specs specs of the bench workload)."""
     import torch
     from paper_1905_01330_gb300 import build, synth, tn
     build.build()
@@ -605,6 +609,19 @@ def run_case(args):
         res = torch.empty(4, dtype=torch.float64, device=dev)
         for _ in range(2):
             tn.mps_expect(cores, W, prec=prec, out=res)
+    elif args.case == "energy_batch":
+        # the 64-MPS batch (bonds U{64, ..., 512}, seed 50), random N(0, 1/chi) cores on the device
+        W = [torch.from_numpy(w).to(dev) for w in synth.tfim_mpo(100)]
+        g = torch.Generator(device=dev)
+        g.manual_seed(50)
+        states = []
+        for c in synth.uneven_chis(64, seed=50):
+            bonds = synth.mps_bonds(100, 2, c)
+            states.append([torch.randn(bonds[i], 2, bonds[i + 1], device=dev, generator=g) / c ** 0.5
+                           for i in range(100)])
+        res = torch.empty(len(states), 4, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            tn.mps_expect_grouped(states, W, prec=prec, out=res)
     elif args.case == "mps_norm":
         m = [torch.from_numpy(c).to(dev) for c in synth.random_mps(20, 2, 32, seed=1)]
         res = torch.empty(2, dtype=torch.float64, device=dev)
@@ -644,7 +661,7 @@ def main():
                     help="skip the classifier, MPS-norm and energy measurements")
     ap.add_argument("--case", default=None,
                     help="run one workload twice for a profiler (classifier_forward, classifier_train, energy, "
-                         "mps_norm, grouped_tensordot) instead of the bench")
+                         "energy_batch, mps_norm, grouped_tensordot) instead of the bench")
     ap.add_argument("--chi", type=int, default=64, help="bond dimension of --case")
     ap.add_argument("--prec", default="bf16", help="precision of --case: fp32, bf16, bf16x3")
     args = ap.parse_args()

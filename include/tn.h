@@ -285,14 +285,21 @@ int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace
  *   (i)   T1[w, a', s, b]   = sum_a      L[w, a, a'] psi_i[a, s, b]
  *   (ii)  T2[w', s', a', b] = sum_{w, s} W_i[w, w', s, s'] T1[w, a', s, b]
  *   (iii) L'[w', b, b']     = sum_{a',s'} T2[w', s', a', b] psi_i[a', s', b']
- * with the same per-site rescaling and float64 log-scale as tn_mps_inner;
  * (i) and (iii) use `prec`, (ii) (contraction length w*d) runs in float32.
+ * <psi|psi> is carried in the same sweep as one more MPO channel (the MPO
+ * extended by a channel that maps to itself with the identity operator);
+ * after every site the environment is scaled by 2^-e, e the binary exponent
+ * of its largest magnitude (applied exactly, in the next site's step (ii)),
+ * and e ln 2 is added to the float64 log-scale shared by both results.
+ * The MPO's bonds must satisfy (bond + 1) * d <= 32, n <= 1024 and
+ * (bond + 1) * D * d * D < 2^31 for the largest MPS bond D (else
+ * TN_ERR_UNSUPPORTED).
  *   result: DEVICE pointer to 4 doubles {e_value, e_log_scale, n_value,
  *           n_log_scale}: <psi|H|psi> = e_value * exp(e_log_scale) and
  *           <psi|psi> = n_value * exp(n_log_scale); the energy per the
  *           normalised state is their ratio.
  *   workspace: DEVICE scratch of tn_mps_expect_workspace_bytes() bytes.
- * Errors: as tn_mps_inner.
+ * Errors: as tn_mps_inner, plus TN_ERR_UNSUPPORTED.
  */
 size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H);
 int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace, size_t ws_bytes,
@@ -301,10 +308,9 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
 /*
  * tn_mps_expect for a batch of `count` MPS sharing one MPO (same n and d for
  * all; bond dimensions may differ from state to state). Each site step runs
- * as grouped launches over the whole batch: {norm T, (i)} in one launch,
- * the norm environment update and (ii) in one each, (iii) in one, then one
- * grouped rescale of all 2*count environments, so a sweep is a fixed
- * number of launches per site whatever the batch size.
+ * as grouped launches over the whole batch ((i), (ii), (iii) and one max-abs
+ * pass, the norm carried as an extra MPO channel as in tn_mps_expect), so a
+ * sweep is a fixed number of launches per site whatever the batch size.
  *   psis:   HOST array of `count` chains.
  *   result: DEVICE pointer to 4*count doubles, {e_value, e_log_scale,
  *           n_value, n_log_scale} per state, as tn_mps_expect.
@@ -319,6 +325,26 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
 size_t tn_mps_expect_grouped_workspace_bytes(const tn_mps* psis, int count, const tn_mpo* H, int prec);
 int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
                           size_t ws_bytes, double* result, void* stream);
+
+/*
+ * tn_mps_expect_grouped in two parts, for a batch evaluated many times:
+ * _plan builds the host layout of the sweep (per site the grouped work lists
+ * of steps (i) and (iii), the step (ii) descriptors, the max-abs tables) in
+ * `workspace` and uploads its tables on `stream` (host -> device copies from
+ * pageable memory); _run only launches (one extended-MPO build, per site two
+ * grouped contractions, one grouped float32 step and one max-abs pass, then
+ * the finisher) and writes `result` as tn_mps_expect_grouped does. The plan
+ * keeps the device pointers of the states' and the MPO's cores and the
+ * workspace (which must stay allocated and unused by others); the values
+ * behind them are read at every run. Errors: as tn_mps_expect_grouped;
+ * _run: TN_ERR_ARG (null plan or result), TN_ERR_CUDA. Plans are not
+ * thread-safe; runs of one plan on different streams race on its workspace.
+ */
+typedef struct tn_expect_plan tn_expect_plan;
+int tn_mps_expect_grouped_plan(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
+                               size_t ws_bytes, tn_expect_plan** plan, void* stream);
+int tn_mps_expect_grouped_run(const tn_expect_plan* plan, double* result, void* stream);
+void tn_mps_expect_grouped_destroy(tn_expect_plan* plan);
 
 /* ------------------------------------------------------------------------ */
 /* MPS image classifier (Sec. IV.A)                                          */

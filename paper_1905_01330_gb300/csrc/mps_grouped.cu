@@ -298,33 +298,30 @@ size_t tn_mps_expect_grouped_workspace_bytes(const tn_mps* psis, int count, cons
   return g.total;
 }
 
-int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
-                          size_t ws_bytes, double* result, void* stream) {
-  if (!result) return TN_ERR_ARG;
-  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
-  uint8_t* base = static_cast<uint8_t*>(workspace);
-  GroupedSweep g;
-  int rc = build_sweep(psis, count, H, prec, base, &g);
-  if (rc != TN_OK) return rc;
-  if (ws_bytes < g.total) return TN_ERR_WORKSPACE;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // uploads: plan work lists, max-abs segments, step (ii) descriptors, init
-  // and final tables; then the extended MPO
-  for (size_t j = 0; j < g.plans.size(); ++j) {
-    if (g.plan_bytes[j] == 0) continue;
-    rc = group_plan_upload_shared(g.plans[j].get(), base + g.plan_off[j], g.plan_bytes[j], base + g.off_packed, s);
-    if (rc != TN_OK) return rc;
-  }
-  if (cudaMemcpyAsync(base + g.off_segs, g.segs.data(), sizeof(Segment) * g.segs.size(), cudaMemcpyHostToDevice,
-                      s) != cudaSuccess ||
-      cudaMemcpyAsync(base + g.off_steps, g.steps.data(), sizeof(StepII) * g.steps.size(), cudaMemcpyHostToDevice,
-                      s) != cudaSuccess ||
-      cudaMemcpyAsync(base + g.off_init, g.inits.data(), sizeof(ChainInit) * g.inits.size(),
-                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(base + g.off_final, g.finals.data(), sizeof(ChainFinal) * g.finals.size(),
-                      cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return TN_ERR_CUDA;
-  if ((rc = launch_mpo_extend(H, reinterpret_cast<float*>(base + g.off_w), g.woff.data(), s)) != TN_OK) return rc;
+}  // extern "C"
+
+// A planned grouped sweep: the host layout (site plans, tables) built and its
+// tables uploaded once; every run only launches. The MPO's core pointers are
+// kept (its extension is rebuilt at every run, so values changed in place
+// are picked up, as are the states' core values).
+struct tn_expect_plan {
+  tn::GroupedSweep g;
+  uint8_t* base;
+  size_t bytes;
+  std::vector<int64_t> hbond;
+  std::vector<float*> hcores;
+  tn_mpo H;
+};
+
+namespace tn {
+namespace {
+
+int run_sweep(const tn_expect_plan* pl, double* result, cudaStream_t s) {
+  const GroupedSweep& g = pl->g;
+  uint8_t* base = pl->base;
+  const int count = g.count;
+  int rc;
+  if ((rc = launch_mpo_extend(&pl->H, reinterpret_cast<float*>(base + g.off_w), g.woff.data(), s)) != TN_OK) return rc;
   double* lg = reinterpret_cast<double*>(base + g.off_lg);
   unsigned* bits = reinterpret_cast<unsigned*>(base + g.off_bits);
   grouped_init_kernel<<<64, 256, 0, s>>>(reinterpret_cast<const ChainInit*>(base + g.off_init), count, lg, count,
@@ -354,6 +351,68 @@ int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int pr
   grouped_finish_kernel<<<(count + 127) / 128, 128, 0, s>>>(reinterpret_cast<const ChainFinal*>(base + g.off_final),
                                                            count, lg, result);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace tn
+
+extern "C" {
+
+int tn_mps_expect_grouped_plan(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
+                               size_t ws_bytes, tn_expect_plan** plan, void* stream) {
+  if (!plan) return TN_ERR_ARG;
+  *plan = nullptr;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
+  std::unique_ptr<tn_expect_plan> pl(new tn_expect_plan());
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  GroupedSweep& g = pl->g;
+  int rc = build_sweep(psis, count, H, prec, base, &g);
+  if (rc != TN_OK) return rc;
+  if (ws_bytes < g.total) return TN_ERR_WORKSPACE;
+  pl->base = base;
+  pl->bytes = ws_bytes;
+  pl->hbond.assign(H->bond, H->bond + H->n + 1);
+  pl->hcores.assign(H->cores, H->cores + H->n);
+  pl->H = *H;
+  pl->H.bond = pl->hbond.data();
+  pl->H.cores = pl->hcores.data();
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // uploads: plan work lists, max-abs segments, step (ii) descriptors, init
+  // and final tables
+  for (size_t j = 0; j < g.plans.size(); ++j) {
+    if (g.plan_bytes[j] == 0) continue;
+    rc = group_plan_upload_shared(g.plans[j].get(), base + g.plan_off[j], g.plan_bytes[j], base + g.off_packed, s);
+    if (rc != TN_OK) return rc;
+  }
+  if (cudaMemcpyAsync(base + g.off_segs, g.segs.data(), sizeof(Segment) * g.segs.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(base + g.off_steps, g.steps.data(), sizeof(StepII) * g.steps.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(base + g.off_init, g.inits.data(), sizeof(ChainInit) * g.inits.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + g.off_final, g.finals.data(), sizeof(ChainFinal) * g.finals.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  *plan = pl.release();
+  return TN_OK;
+}
+
+int tn_mps_expect_grouped_run(const tn_expect_plan* plan, double* result, void* stream) {
+  if (!plan || !result) return TN_ERR_ARG;
+  return run_sweep(plan, result, static_cast<cudaStream_t>(stream));
+}
+
+void tn_mps_expect_grouped_destroy(tn_expect_plan* plan) { delete plan; }
+
+int tn_mps_expect_grouped(const tn_mps* psis, int count, const tn_mpo* H, int prec, void* workspace,
+                          size_t ws_bytes, double* result, void* stream) {
+  if (!result) return TN_ERR_ARG;
+  tn_expect_plan* plan = nullptr;
+  int rc = tn_mps_expect_grouped_plan(psis, count, H, prec, workspace, ws_bytes, &plan, stream);
+  if (rc != TN_OK) return rc;
+  rc = tn_mps_expect_grouped_run(plan, result, stream);
+  tn_mps_expect_grouped_destroy(plan);
+  return rc;
 }
 
 }  // extern "C"

@@ -107,6 +107,10 @@ def _signatures():
                                                                     ctypes.POINTER(TnChain), i32]),
         "tn_mps_expect_grouped": (i32, [ctypes.POINTER(TnChain), i32, ctypes.POINTER(TnChain), i32, vp,
                                         ctypes.c_size_t, vp, vp]),
+        "tn_mps_expect_grouped_plan": (i32, [ctypes.POINTER(TnChain), i32, ctypes.POINTER(TnChain), i32, vp,
+                                             ctypes.c_size_t, ctypes.POINTER(vp), vp]),
+        "tn_mps_expect_grouped_run": (i32, [vp, vp, vp]),
+        "tn_mps_expect_grouped_destroy": (None, [vp]),
         "tn_mps_expect": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_classify_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), i32, i32, i32, i32]),
         "tn_mps_classify": (i32, [ctypes.POINTER(TnChain), i32, i32, vp, i32, i32, i32, vp, vp, vp,
@@ -423,6 +427,48 @@ def mps_expect(psi, mpo, prec: str = "fp32", stream=None, out: torch.Tensor | No
                              ws.numel(), ctypes.c_void_p(res.data_ptr()), _stream(stream)), "tn_mps_expect")
     res._tn_keep = (ws, kp, kh)
     return res
+
+
+class ExpectGroupedPlan:
+    """tn_mps_expect_grouped planned once (tn_mps_expect_grouped_plan): the
+    host layout and its uploaded tables are kept, and run() only launches.
+    The states' and the MPO's tensors are read at every run (values changed
+    in place are picked up); they must stay allocated."""
+
+    def __init__(self, psis, mpo, prec: str = "fp32", stream=None):
+        lib = load()
+        count = len(psis)
+        arr = (TnChain * count)()
+        keep = []
+        for k, cores in enumerate(psis):
+            c, kc = chain_desc(cores)
+            arr[k] = c
+            keep.append(kc)
+        ch, kh = chain_desc(mpo, phys_axis=2)
+        self.count = count
+        self.device = psis[0][0].device
+        nbytes = lib.tn_mps_expect_grouped_workspace_bytes(arr, count, ctypes.byref(ch), PREC[prec])
+        if nbytes == 0:
+            raise TnError(1, "tn_mps_expect_grouped_workspace_bytes (invalid chains or MPO)")
+        self.ws = _workspace(nbytes, self.device)
+        handle = ctypes.c_void_p()
+        _check(lib.tn_mps_expect_grouped_plan(arr, count, ctypes.byref(ch), PREC[prec],
+                                              ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                              ctypes.byref(handle), _stream(stream)), "tn_mps_expect_grouped_plan")
+        self.handle = handle
+        self._keep = (arr, keep, ch, kh, psis, mpo)
+
+    def run(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """[count, 4] float64 {e_value, e_log_scale, n_value, n_log_scale} per state."""
+        res = out if out is not None else torch.empty(self.count, 4, dtype=torch.float64, device=self.device)
+        _check(load().tn_mps_expect_grouped_run(self.handle, ctypes.c_void_p(res.data_ptr()), _stream(stream)),
+               "tn_mps_expect_grouped_run")
+        return res
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_mps_expect_grouped_destroy(self.handle)
+            self.handle = None
 
 
 def mps_expect_grouped(psis, mpo, prec: str = "fp32", stream=None, out: torch.Tensor | None = None):

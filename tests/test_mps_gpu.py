@@ -174,3 +174,25 @@ def test_grouped_energy_rejects_mismatched_lengths(tn):
     b = to_dev(synth.random_mps(9, 2, 4, seed=2))
     with pytest.raises(tn.TnError):
         tn.mps_expect_grouped([a, b], to_dev(W))
+
+
+def test_grouped_energy_plan_runs_like_the_one_shot_call(tn):
+    # planned once, run twice; core values changed in place are read by the next run
+    n = 10
+    states = [[torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in synth.random_mps(n, 2, chi, seed=80 + chi)]
+              for chi in (4, 16, 8)]
+    W = to_dev(synth.tfim_mpo(n))
+    plan = tn.ExpectGroupedPlan(states, W, prec="fp32")
+    a = plan.run().cpu().numpy()
+    b = plan.run().cpu().numpy()
+    ref = tn.mps_expect_grouped(states, W, prec="fp32").cpu().numpy()
+    assert np.array_equal(a, b)
+    for k in range(3):
+        for j in (0, 2):
+            assert rel(a[k, j] * math.exp(a[k, j + 1]), ref[k, j] * math.exp(ref[k, j + 1])) <= 1e-6
+    states[1][3].mul_(2.0)  # <psi|H|psi> and <psi|psi> of state 1 scale by 4
+    c = plan.run().cpu().numpy()
+    assert tn.sync_status() == 0
+    for j in (0, 2):
+        assert rel(c[1, j] * math.exp(c[1, j + 1]), 4.0 * a[1, j] * math.exp(a[1, j + 1])) <= 1e-5
+        assert rel(c[0, j] * math.exp(c[0, j + 1]), a[0, j] * math.exp(a[0, j + 1])) <= 1e-12
