@@ -562,7 +562,9 @@ int inner_sweep(const tn_mps* bra, const tn_mps* ket, int prec, const InnerWs& w
 int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, int64_t wad, int64_t wbd,
                                cudaStream_t s) {
   if (count <= 0) return TN_OK;
-  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_cols + 255) / 256, 1024)), (unsigned)count);
+  // a few columns per thread and at most 64 blocks per chain: the small
+  // chains' blocks would otherwise mostly start, load the MPO and leave
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_cols + 1023) / 1024, 64)), (unsigned)count);
   switch (step_ii_width(wad, wbd)) {
     case 8: mpo_step_ii_grouped<8><<<grid, 256, 0, s>>>(descs); break;
     case 16: mpo_step_ii_grouped<16><<<grid, 256, 0, s>>>(descs); break;
