@@ -501,7 +501,7 @@ def mps_expect_grouped(psis, mpo, prec: str = "fp32", stream=None, out: torch.Te
 class GroupPlan:
     """A grouped contraction (tn_group_plan_*): specs = [(A, legsA, B, legsB, C), ...]."""
 
-    def __init__(self, specs, prec: str = "bf16", stream=None):
+    def __init__(self, specs, prec: str = "bf16", stream=None, device=None):
         lib = load()
         arr = (TnContractSpec * max(len(specs), 1))()
         for i, (A, la, B, lb, C) in enumerate(specs):
@@ -518,7 +518,10 @@ class GroupPlan:
         self._h = h
         self.prec = prec
         nbytes = lib.tn_group_plan_workspace_bytes(h)
-        dev = specs[0][0].device if specs else torch.device("cuda")
+        # the workspace lives on the GPU; the operands and results may also be
+        # pinned host tensors (device-accessible through unified addressing)
+        dev = device if device is not None else (specs[0][0].device if specs and specs[0][0].is_cuda
+                                                 else torch.device("cuda"))
         self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
         self.ws_bytes = self.workspace.numel()
         self.flops = lib.tn_group_plan_flops(h)
