@@ -79,7 +79,10 @@ struct Cfg {
   static constexpr int ARING_RAW = (SMEM_BUDGET - XTS - 2 * VTS) / ASET;
   static constexpr int ARING = ARING_RAW > 8 ? 8 : ARING_RAW;
   static constexpr int A2OFF = CHI < 64 ? 64 : CHI;  // TMEM column of the gradient accumulator
-  static constexpr uint32_t ACOLS = (uint32_t)pow2ceil(A2OFF + MH * KPAD);
+  // two gradient accumulators when they fit (step q's is drained while step
+  // q + 1's products run), else one
+  static constexpr int A2BUF = A2OFF + 2 * MH * KPAD <= 512 ? 2 : 1;
+  static constexpr uint32_t ACOLS = (uint32_t)pow2ceil(A2OFF + A2BUF * MH * KPAD);
 };
 
 struct __align__(8) Bars {
@@ -293,6 +296,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) cls_fwd_tc(const __grid_constant_
     for (int k = 0; k < C::HC; ++k) v[k] = live ? p.state[h][(int64_t)b * CHI + c0 + k] : 0.0f;
     double lam0 = (live && hc == 0) ? p.lam[h][b] : 0.0;
     int lam_e = 0;
+    // scale of the vector in the tile not yet applied (deferred mode)
+    int e_prev = 0;
+    const bool defer = p.vseg[h] == nullptr;
     auto write_vtile = [&]() {
 #pragma unroll
       for (int g8 = 0; g8 < C::HC / 8; ++g8) {
@@ -313,57 +319,63 @@ __global__ void __launch_bounds__(NTHREADS, 1) cls_fwd_tc(const __grid_constant_
 
     bool ok = true;
     int gs = 0;  // slabs consumed (thread 0)
-    for (int q = 0; q < nsteps && ok; ++q) {
-      const int t = t0 + q;
-      if (tid == 0) {
-        // the vector entering step t, for the adjoint's gradient product
-        if (p.vseg[h]) bulk_copy_s2g(p.vseg[h] + ((size_t)q * p.ntiles + tile) * C::VTS, vaddr, C::VTS);
-        bool w = true;
-        for (int ks = 0; ks < C::KSL && w; ++ks, ++gs) {
-          const int slot = gs % C::FRING;
-          w = ptx::mbar_wait(ptx::smem_addr(&x.full[slot]), (uint32_t)((gs / C::FRING) & 1), p.status);
-          if (!w) break;
-          ptx::tc_fence_after();
-          const uint32_t bs = raddr + (uint32_t)(slot * C::FSET);
+    // thread 0: the MMAs of step qq (issued as soon as the tile holds its vector)
+    auto issue = [&](int qq) {
+      // the vector entering step t0 + qq, for the adjoint's gradient product
+      if (p.vseg[h]) bulk_copy_s2g(p.vseg[h] + ((size_t)qq * p.ntiles + tile) * C::VTS, vaddr, C::VTS);
+      bool w = true;
+      for (int ks = 0; ks < C::KSL && w; ++ks, ++gs) {
+        const int slot = gs % C::FRING;
+        w = ptx::mbar_wait(ptx::smem_addr(&x.full[slot]), (uint32_t)((gs / C::FRING) & 1), p.status);
+        if (!w) break;
+        ptx::tc_fence_after();
+        const uint32_t bs = raddr + (uint32_t)(slot * C::FSET);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t ao = vaddr + (uint32_t)(ks * SLAB_V + kk * 32);
-            const uint64_t ah = ptx::sw128_kmajor_desc(ao), bh = ptx::sw128_kmajor_desc(bs + kk * 32);
-            ptx::mma_bf16(tmem, ah, bh, idesc, (ks | kk) ? 1u : 0u);
-            if (SPLIT) {
-              ptx::mma_bf16(tmem, ptx::sw128_kmajor_desc(ao + C::VT), bh, idesc, 1u);
-              ptx::mma_bf16(tmem, ah, ptx::sw128_kmajor_desc(bs + C::FSLAB + kk * 32), idesc, 1u);
-            }
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t ao = vaddr + (uint32_t)(ks * SLAB_V + kk * 32);
+          const uint64_t ah = ptx::sw128_kmajor_desc(ao), bh = ptx::sw128_kmajor_desc(bs + kk * 32);
+          ptx::mma_bf16(tmem, ah, bh, idesc, (ks | kk) ? 1u : 0u);
+          if (SPLIT) {
+            ptx::mma_bf16(tmem, ptx::sw128_kmajor_desc(ao + C::VT), bh, idesc, 1u);
+            ptx::mma_bf16(tmem, ah, ptx::sw128_kmajor_desc(bs + C::FSLAB + kk * 32), idesc, 1u);
           }
-          ptx::mma_commit(ptx::smem_addr(&x.empty[slot]));
         }
-        if (w) ptx::mma_commit(ptx::smem_addr(&x.acc_full));
-        else {
-          x.abort = 1;
-          ptx::mbar_arrive(ptx::smem_addr(&x.acc_full));
-        }
-        bulk_wait_read();
+        ptx::mma_commit(ptx::smem_addr(&x.empty[slot]));
+      }
+      if (w) ptx::mma_commit(ptx::smem_addr(&x.acc_full));
+      else {
+        x.abort = 1;
         ptx::mbar_arrive(ptx::smem_addr(&x.acc_full));
       }
-      __syncwarp();
+      bulk_wait_read();
+      ptx::mbar_arrive(ptx::smem_addr(&x.acc_full));
+    };
+    if (nsteps > 0 && tid == 0) issue(0);
+    __syncwarp();
+    for (int q = 0; q < nsteps && ok; ++q) {
+      const int t = t0 + q;
       // pixels of the next PXS steps (the epilogue threads only)
       if (q % PXS == 0) {
         stage_pixels(st.px, p.pixels, n, B, b0, q, nsteps, site_of);
         epi_barrier();
       }
-      // keep the float32 vector entering step t
+      // keep the float32 vector entering step t (v holds it times 2^e_prev)
       if (p.store[h] && live && ((t - p.store_base[h]) % p.store_every) == 0) {
         float* dst = p.store[h] + ((int64_t)((t - p.store_base[h]) / p.store_every) * B + b) * CHI + c0;
+        const float ip = pow2f(-e_prev);
 #pragma unroll
-        for (int k = 0; k < C::HC; k += 4) *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+        for (int k = 0; k < C::HC; k += 4)
+          *reinterpret_cast<float4*>(dst + k) = make_float4(v[k] * ip, v[k + 1] * ip, v[k + 2] * ip, v[k + 3] * ip);
       }
       const float xp = st.px[q % PXS][r];
       const float f0 = cospif(0.5f * xp), f1 = sinpif(0.5f * xp);
       const bool waited = ptx::mbar_wait(ptx::smem_addr(&x.acc_full), (uint32_t)(q & 1), p.status);
       if (!__all_sync(0xffffffffu, waited)) x.abort = 1;
-      float m = 0.0f;
       if (waited) {
         ptx::tc_fence_after();
+        // the MMA read v_t 2^e_prev: the step's output times 2^-e_prev is u_t itself (exact)
+        const float ip = pow2f(-e_prev);
+        const float g0 = f0 * ip, g1 = f1 * ip;
 #pragma unroll
         for (int c = 0; c < C::HC; c += LDN) {
           uint32_t u0[LDN], u1[LDN];
@@ -371,27 +383,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) cls_fwd_tc(const __grid_constant_
           tmem_ld<LDN>(lane_base + (uint32_t)(CHI + c0 + c), u1);
           ptx::tmem_ld_wait();
 #pragma unroll
-          for (int e = 0; e < LDN; ++e) {
-            v[c + e] = f0 * __uint_as_float(u0[e]) + f1 * __uint_as_float(u1[e]);
-            m = fmaxf(m, fabsf(v[c + e]));
-          }
+          for (int e = 0; e < LDN; ++e) v[c + e] = g0 * __uint_as_float(u0[e]) + g1 * __uint_as_float(u1[e]);
         }
       }
-      // the sample's largest magnitude over both column halves
-      st.pmax[hc][r] = m;
-      ptx::named_barrier(2 + (warp & 3), 64);
-      m = fmaxf(st.pmax[0][r], st.pmax[1][r]);
-      const int e = scale_exponent(m);
-      const float inv = pow2f(-e);
+      // the step's scale 2^e_t from the sample's largest |u_t| over both
+      // column halves. Without a vector-image store it is applied one step
+      // late (the next MMA reads u_t itself, bf16(u_t) = bf16(v_{t+1}) 2^e_t),
+      // so the exchange runs while that MMA does; the recomputation keeps
+      // the normalised v_{t+1} in the tile it stores for the gradients.
+      auto exchange = [&]() {
+        float m = 0.0f;
 #pragma unroll
-      for (int k = 0; k < C::HC; ++k) v[k] *= inv;
-      lam_e += e;
-      if (hc == 0 && live) p.sc[h][(int64_t)t * B + b] = pow2f(e);
+        for (int k = 0; k < C::HC; ++k) m = fmaxf(m, fabsf(v[k]));
+        st.pmax[hc][r] = m;
+        ptx::named_barrier(2 + (warp & 3), 64);
+        m = fmaxf(st.pmax[0][r], st.pmax[1][r]);
+        const int e = scale_exponent(m);
+        lam_e += e;
+        if (hc == 0 && live) p.sc[h][(int64_t)t * B + b] = pow2f(e);
+        return e;
+      };
+      if (!defer) {
+        const float inv = pow2f(-exchange());
+#pragma unroll
+        for (int k = 0; k < C::HC; ++k) v[k] *= inv;
+      }
       write_vtile();
       ptx::fence_proxy_async_smem();
       ptx::tc_fence_before();
       ok = ptx::named_barrier_or(1, NEPI, *(volatile int32_t*)&x.abort != 0) == false;
       ptx::tc_fence_after();
+      if (tid == 0 && ok && q + 1 < nsteps) issue(q + 1);
+      __syncwarp();
+      if (defer) e_prev = exchange();
+    }
+    {
+      const float ip = pow2f(-e_prev);
+#pragma unroll
+      for (int k = 0; k < C::HC; ++k) v[k] *= ip;
     }
     if (live) {
 #pragma unroll
@@ -544,63 +573,87 @@ __global__ void __launch_bounds__(NTHREADS, 1) cls_adj_tc(const __grid_constant_
     constexpr int LDN = C::HC >= 32 ? 32 : 16;
     constexpr int GLD = C::KPAD / 2 >= 32 ? 32 : 16;  // gradient columns per TMEM load
     const int mrow = r;  // gradient row (x column) of this lane in M half 0
+    // this tile's share of step t's core gradient, from accumulator `buf`
+    auto drain_grad = [&](int t, int buf) {
+      float* gbase = p.grad[h] + (size_t)t * CHI * 2 * CHI;
+#pragma unroll
+      for (int mh = 0; mh < C::MH; ++mh) {
+        const int m = mh * 128 + mrow;
+        if (m < 2 * CHI) {
+#pragma unroll
+          for (int c = 0; c < C::KPAD / 2; c += GLD) {
+            const int k0 = hc * (C::KPAD / 2) + c;
+            if (k0 < CHI) {
+              uint32_t u[GLD];
+              tmem_ld<GLD>(lane_base + (uint32_t)(C::A2OFF + buf * C::MH * C::KPAD + mh * C::KPAD + k0), u);
+              ptx::tmem_ld_wait();
+#pragma unroll
+              for (int e = 0; e < GLD; ++e)
+                if (k0 + e < CHI) red_add(gbase + (size_t)(k0 + e) * 2 * CHI + m, __uint_as_float(u[e]));
+            }
+          }
+        }
+      }
+    };
 
     bool ok = true;
     int gs = 0;
+    // thread 0: both products of step qq (issued as soon as the x tile holds its operand)
+    auto issue = [&](int qq) {
+      bool w = true;
+      // g'[b, k] = sum_m x[b, m] L[k, m]
+      for (int ks = 0; ks < C::XSL && w; ++ks, ++gs) {
+        const int slot = gs % C::ARING;
+        w = ptx::mbar_wait(ptx::smem_addr(&x.full[slot]), (uint32_t)((gs / C::ARING) & 1), p.status);
+        if (!w) break;
+        ptx::tc_fence_after();
+        const uint32_t bs = caddr + (uint32_t)(slot * C::ASET);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t ao = xaddr + (uint32_t)(ks * SLAB_V + kk * 32);
+          const uint64_t ah = ptx::sw128_kmajor_desc(ao), bh = ptx::sw128_kmajor_desc(bs + kk * 32);
+          ptx::mma_bf16(tmem, ah, bh, idesc1, (ks | kk) ? 1u : 0u);
+          if (SPLIT) {
+            ptx::mma_bf16(tmem, ptx::sw128_kmajor_desc(ao + C::XPART), bh, idesc1, 1u);
+            ptx::mma_bf16(tmem, ah, ptx::sw128_kmajor_desc(bs + C::ASLAB + kk * 32), idesc1, 1u);
+          }
+        }
+        ptx::mma_commit(ptx::smem_addr(&x.empty[slot]));
+      }
+      // dL[m, k] = sum_b x[b, m] v[b, k]: both operands MN-major (the
+      // K-major x tile read transposed; the v tile as the forward wrote it)
+      const int vs = qq & 1;
+      if (w) w = ptx::mbar_wait(ptx::smem_addr(&x.vfull[vs]), (uint32_t)((qq >> 1) & 1), p.status);
+      if (w) {
+        ptx::tc_fence_after();
+        const uint32_t vb = vaddr + (uint32_t)(vs * C::VTS);
+#pragma unroll
+        for (int mh = 0; mh < C::MH; ++mh) {
+          const uint32_t d = tmem + (uint32_t)(C::A2OFF + ((qq & 1) % C::A2BUF) * C::MH * C::KPAD + mh * C::KPAD);
+#pragma unroll
+          for (int kk = 0; kk < TS / 16; ++kk) {
+            const uint32_t ao = xaddr + (uint32_t)(mh * 2 * SLAB_V + kk * 2048);
+            const uint32_t bo = vb + (uint32_t)(kk * 2048);
+            const uint64_t ah = ptx::sw128_mnmajor_desc(ao, SLAB_V, 1024);
+            const uint64_t bh = ptx::sw128_mnmajor_desc(bo, SLAB_V, 1024);
+            ptx::mma_bf16(d, ah, bh, idesc2, kk ? 1u : 0u);
+            if (SPLIT) {
+              ptx::mma_bf16(d, ptx::sw128_mnmajor_desc(ao + C::XPART, SLAB_V, 1024), bh, idesc2, 1u);
+              ptx::mma_bf16(d, ah, ptx::sw128_mnmajor_desc(bo + C::VT, SLAB_V, 1024), idesc2, 1u);
+            }
+          }
+        }
+        ptx::mma_commit(ptx::smem_addr(&x.vempty[vs]));
+        ptx::mma_commit(ptx::smem_addr(&x.acc_full));
+      } else {
+        x.abort = 1;
+        ptx::mbar_arrive(ptx::smem_addr(&x.acc_full));
+      }
+    };
+    if (nsteps > 0 && tid == 0) issue(0);
+    __syncwarp();
     for (int q = 0; q < nsteps && ok; ++q) {
       const int t = step_t(q);
-      if (tid == 0) {
-        bool w = true;
-        // g'[b, k] = sum_m x[b, m] L[k, m]
-        for (int ks = 0; ks < C::XSL && w; ++ks, ++gs) {
-          const int slot = gs % C::ARING;
-          w = ptx::mbar_wait(ptx::smem_addr(&x.full[slot]), (uint32_t)((gs / C::ARING) & 1), p.status);
-          if (!w) break;
-          ptx::tc_fence_after();
-          const uint32_t bs = caddr + (uint32_t)(slot * C::ASET);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t ao = xaddr + (uint32_t)(ks * SLAB_V + kk * 32);
-            const uint64_t ah = ptx::sw128_kmajor_desc(ao), bh = ptx::sw128_kmajor_desc(bs + kk * 32);
-            ptx::mma_bf16(tmem, ah, bh, idesc1, (ks | kk) ? 1u : 0u);
-            if (SPLIT) {
-              ptx::mma_bf16(tmem, ptx::sw128_kmajor_desc(ao + C::XPART), bh, idesc1, 1u);
-              ptx::mma_bf16(tmem, ah, ptx::sw128_kmajor_desc(bs + C::ASLAB + kk * 32), idesc1, 1u);
-            }
-          }
-          ptx::mma_commit(ptx::smem_addr(&x.empty[slot]));
-        }
-        // dL[m, k] = sum_b x[b, m] v[b, k]: both operands MN-major (the
-        // K-major x tile read transposed; the v tile as the forward wrote it)
-        const int vs = q & 1;
-        if (w) w = ptx::mbar_wait(ptx::smem_addr(&x.vfull[vs]), (uint32_t)((q >> 1) & 1), p.status);
-        if (w) {
-          ptx::tc_fence_after();
-          const uint32_t vb = vaddr + (uint32_t)(vs * C::VTS);
-#pragma unroll
-          for (int mh = 0; mh < C::MH; ++mh) {
-            const uint32_t d = tmem + (uint32_t)(C::A2OFF + mh * C::KPAD);
-#pragma unroll
-            for (int kk = 0; kk < TS / 16; ++kk) {
-              const uint32_t ao = xaddr + (uint32_t)(mh * 2 * SLAB_V + kk * 2048);
-              const uint32_t bo = vb + (uint32_t)(kk * 2048);
-              const uint64_t ah = ptx::sw128_mnmajor_desc(ao, SLAB_V, 1024);
-              const uint64_t bh = ptx::sw128_mnmajor_desc(bo, SLAB_V, 1024);
-              ptx::mma_bf16(d, ah, bh, idesc2, kk ? 1u : 0u);
-              if (SPLIT) {
-                ptx::mma_bf16(d, ptx::sw128_mnmajor_desc(ao + C::XPART, SLAB_V, 1024), bh, idesc2, 1u);
-                ptx::mma_bf16(d, ah, ptx::sw128_mnmajor_desc(bo + C::VT, SLAB_V, 1024), idesc2, 1u);
-              }
-            }
-          }
-          ptx::mma_commit(ptx::smem_addr(&x.vempty[vs]));
-          ptx::mma_commit(ptx::smem_addr(&x.acc_full));
-        } else {
-          x.abort = 1;
-          ptx::mbar_arrive(ptx::smem_addr(&x.acc_full));
-        }
-      }
-      __syncwarp();
       // pixels of steps q + 1 .. q + PXS (the x of the next step needs them)
       if ((q + 1) % PXS == 0 && q + 1 < nsteps) {
         stage_pixels(st.px, p.pixels, n, B, b0, q + 1, nsteps, site_of);
@@ -618,32 +671,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) cls_adj_tc(const __grid_constant_
 #pragma unroll
           for (int e = 0; e < LDN; ++e) g[c + e] = __uint_as_float(u[e]);
         }
-        // this tile's share of the step's core gradient
-        float* gbase = p.grad[h] + (size_t)t * CHI * 2 * CHI;
-#pragma unroll
-        for (int mh = 0; mh < C::MH; ++mh) {
-          const int m = mh * 128 + mrow;
-          if (m < 2 * CHI) {
-#pragma unroll
-            for (int c = 0; c < C::KPAD / 2; c += GLD) {
-              const int k0 = hc * (C::KPAD / 2) + c;
-              if (k0 < CHI) {
-                uint32_t u[GLD];
-                tmem_ld<GLD>(lane_base + (uint32_t)(C::A2OFF + mh * C::KPAD + k0), u);
-                ptx::tmem_ld_wait();
-#pragma unroll
-                for (int e = 0; e < GLD; ++e)
-                  if (k0 + e < CHI) red_add(gbase + (size_t)(k0 + e) * 2 * CHI + m, __uint_as_float(u[e]));
-              }
-            }
-          }
-        }
+        if (C::A2BUF == 1) drain_grad(t, 0);
         if (q + 1 < nsteps) write_xtile(q + 1);
       }
       ptx::fence_proxy_async_smem();
       ptx::tc_fence_before();
       ok = ptx::named_barrier_or(1, NEPI, *(volatile int32_t*)&x.abort != 0) == false;
       ptx::tc_fence_after();
+      if (tid == 0 && ok && q + 1 < nsteps) issue(q + 1);
+      __syncwarp();
+      // with two accumulators this step's gradient is drained while the next
+      // step's products run (its buffer is rewritten two steps later, after
+      // the next barrier)
+      if (C::A2BUF == 2 && waited && ok) drain_grad(t, q & 1);
     }
     if (live) {
 #pragma unroll
