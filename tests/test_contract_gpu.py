@@ -264,7 +264,7 @@ def test_full_size_grouped_sampled(tn):
     sizes = [2 * np.prod(synth.spec_sizes(s)) for s in specs_h]
     order = np.argsort(sizes)[::-1]
     chosen = list(order[:3]) + [int(order[len(order) // 2]), int(order[-1])] + [rng.below(2048) for _ in range(3)]
-    for prec in ("bf16", "bf16x3"):
+    for prec in ("bf16", "bf16x3", "fp32"):
         plan = tn.GroupPlan(specs, prec=prec)
         plan.run()
         torch.cuda.synchronize()
@@ -281,3 +281,29 @@ def test_full_size_grouped_sampled(tn):
             K = int(np.prod([A.shape[p] for p in la]))
             assert np.all(np.abs(got - ref) <= comp_coef(prec, K) * aref + 1e-30), (prec, si)
         del plan
+
+
+def test_grouped_plan_on_pinned_host_operands(tn):
+    """A plan whose operands and results are pinned host tensors (read and
+    written by the kernels through unified addressing; the workspace on the
+    GPU) gives the device plan's results."""
+    specs_h = synth.contraction_specs(12, seed=5, dims=(8, 16, 24), cap=1 << 14)
+    dev_specs, host_specs = [], []
+    for i, (sa, la, sb, lb) in enumerate(specs_h):
+        A = torch.from_numpy(synth.normal_f32(300 + i, sa))
+        B = torch.from_numpy(synth.normal_f32(400 + i, sb))
+        shape = tn.result_shape(A, la, B, lb)
+        host_specs.append((A.pin_memory(), list(la), B.pin_memory(), list(lb),
+                           torch.full(shape, float("nan")).pin_memory()))
+        dev_specs.append((A.cuda(), list(la), B.cuda(), list(lb), torch.empty(shape, device="cuda")))
+    for prec in ("bf16", "fp32"):
+        pd = tn.GroupPlan(dev_specs, prec=prec)
+        ph = tn.GroupPlan(host_specs, prec=prec, device=torch.device("cuda"))
+        pd.run()
+        ph.run()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == 0
+        for (_, _, _, _, Cd), (_, _, _, _, Ch) in zip(dev_specs, host_specs):
+            ref = Cd.cpu()
+            assert torch.isfinite(Ch).all()
+            assert (Ch - ref).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item()), prec
