@@ -778,6 +778,24 @@ def main():
         tm, pp, _ = timed(plans[p], max(2, args.steps // 2), 1)
         variants[p] = {"ms_per_step": tm / max(2, args.steps // 2), "tflops": flops / (tm / max(2, args.steps // 2) * 1e-3) / 1e12}
     variants["bf16"] = {"ms_per_step": ms_per_step, "tflops": flops / (ms_per_step * 1e-3) / 1e12}
+    if rank == 0 and not args.no_cpu_baseline:
+        # each path's error against the FP64 oracle on five of the workload's
+        # contractions (the smallest two and three from the middle of the
+        # flop-sorted list), normwise against || |A||B| ||_F
+        import oracle
+        fl = [2.0 * np.prod(synth.spec_sizes(sp)) for sp in specs_h]
+        order = np.argsort(fl)
+        pick = [int(order[0]), int(order[1])] + [int(order[len(order) // 2 + i]) for i in range(3)]
+        ref = {}
+        for si in pick:
+            At, la, Bt, lb, _ = specs[si]
+            a, b = At.cpu().numpy(), Bt.cpu().numpy()
+            ref[si] = (oracle.tensordot(a, la, b, lb), np.linalg.norm(oracle.tensordot(np.abs(a), la, np.abs(b), lb)))
+        for p in ["bf16"] + var_list:
+            plans[p].run()
+            torch.cuda.synchronize(dev)
+            errs = [float(np.linalg.norm(specs[si][4].double().cpu().numpy() - ref[si][0]) / ref[si][1]) for si in pick]
+            variants[p]["err_vs_oracle_5_specs"] = {"max": max(errs), "normwise_against": "|| |A||B| ||_F"}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -843,6 +861,22 @@ def main():
                 "tensor_tflops": flops / (launch_ms * 1e-3) / 1e12,
                 "tensor_frac": flops / (launch_ms * 1e-3) / 1e12 / bf16_peak}
 
+    # the large contractions of the workload (>= 1 GFLOP each): one grouped
+    # plan of just those, its tensor-pipe fraction
+    large = None
+    if rank == 0 and not args.no_extras:
+        big_idx = [i for i, sp in enumerate(specs_h) if 2.0 * np.prod(synth.spec_sizes(sp)) >= 1e9]
+        if big_idx:
+            lp = tn.GroupPlan([specs[i] for i in big_idx], prec="bf16")
+            lp.autotune()
+            lt_ms, _, _ = timed(lp, 5, 2)
+            lflops = lp.flops
+            large = {"specs": len(big_idx), "tflop": lflops / 1e12, "share_of_workload_flops": lflops / flops,
+                     "ms": lt_ms / 5, "tflops": lflops / (lt_ms / 5 * 1e-3) / 1e12,
+                     "tensor_frac": lflops / (lt_ms / 5 * 1e-3) / 1e12 / bf16_peak,
+                     "hbm_gbs": lp.bytes / (lt_ms / 5 * 1e-3) / 1e9}
+            del lp
+
     extras = None
     if rank == 0 and not args.no_extras:
         extras = run_extras(tn, synth, dev, stream)
@@ -862,7 +896,8 @@ def main():
                 "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": workload_config(args.specs),
                 "gpu_launches": args.steps * plan.launches, "clocks": clocks, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu, "variants": variants, "schedules": schedules,
-                "tensor_peak_frac": value / world / bf16_peak, "extras": extras}
+                "tensor_peak_frac": value / world / bf16_peak, "large_contractions_subset": large,
+                "extras": extras}
         print(json.dumps(line), flush=True)
     tndist.finish()
     return 0
