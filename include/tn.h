@@ -359,22 +359,25 @@ void tn_mps_expect_grouped_destroy(tn_expect_plan* plan);
  * (bond[ls], 2, n_labels, bond[ls+1]); every bond <= 128, d = 2.
  * The sweep runs from both ends towards the label core: the left vector after
  * sites 0..ls-1 and the right vector after sites n-1..ls+1 (each step
- * v' = sum_s Phi_s(x_i) v.W_i[:, s, :]) are divided per sample by their
- * largest magnitude after every site, the logs of those factors summed in
- * float64, and met at the label core.
+ * v' = sum_s Phi_s(x_i) v.W_i[:, s, :]) are rescaled per sample after every
+ * site (float32 path: divided by their largest magnitude; tensor-core paths:
+ * multiplied by 2^-e, e the binary exponent of that magnitude, exactly), the
+ * logs of the factors summed in float64, and met at the label core (a
+ * float32 contraction over the batch).
  *   pixels:  DEVICE [batch, n] float32, row-major.
  *   ftilde:  DEVICE [batch, n_labels] float32; log_scale: DEVICE [batch]
  *            float64. score_l(b) = ftilde[b, l] * exp(log_scale[b]).
- *   prec:    TN_PREC_FP32 (float32 on the CUDA cores) or TN_PREC_BF16 (bf16
- *            operands, float32 accumulation on tcgen05, when every inner
- *            bond is the same chi in {32, 64, 128}).
+ *   prec:    TN_PREC_FP32 (float32 on the CUDA cores), TN_PREC_BF16 (bf16
+ *            operands, float32 accumulation on tcgen05) or TN_PREC_BF16X3
+ *            (split bf16 operands, hi*hi + lo*hi + hi*lo); both half-chains
+ *            run in one launch, bonds padded to chi in {32, 64, 128}.
  *   ckpt_every: the forward keeps the per-sample sweep vector every
  *            ckpt_every sites (1 = every site) for the backward pass, which
  *            recomputes the vectors in between; 0 keeps none (no backward).
  *   workspace: DEVICE scratch of tn_mps_classify_workspace_bytes(); it holds
  *            the forward's state for tn_mps_classify_backward.
  * Errors: TN_ERR_ARG, TN_ERR_SHAPE (bonds or label core inconsistent),
- * TN_ERR_UNSUPPORTED (bond > 128, d != 2, BF16 on uneven bonds),
+ * TN_ERR_UNSUPPORTED (bond > 128, d != 2),
  * TN_ERR_WORKSPACE, TN_ERR_CUDA.
  */
 size_t tn_mps_classify_workspace_bytes(const tn_mps* W, int label_site, int n_labels, int batch,
@@ -393,12 +396,20 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
  * vector leaving it,
  *   dW_i[a, s, c] = sum_b v_b[a] Phi_s(x_bi) g_b[c] / scale_bi,
  *   g_b <- sum_{s,c} W_i[a, s, c] Phi_s(x_bi) g_b[c] / scale_bi,
- * done as one adjoint sweep per half-chain and, per checkpoint segment, one
- * grouped tensordot over the batch for the segment's cores.
+ * done per checkpoint segment: TN_PREC_BF16 / TN_PREC_BF16X3 run one launch
+ * that recomputes both halves' segments and one adjoint launch that also
+ * accumulates every step's dW (the products over the segment's samples on
+ * tcgen05, float32 reductions into a workspace buffer, then one scatter);
+ * TN_PREC_FP32 runs the float32 adjoint sweep and one grouped tensordot over
+ * the batch per segment.
  *   dcores: host table of n DEVICE pointers, each shaped like its core
  *           (overwritten).
- *   prec:   arithmetic of the sweeps and of the batch contractions.
- * Errors: as tn_mps_classify.
+ *   prec:   arithmetic of the sweeps and of the gradient products (the label
+ *           core's contractions run in float32). TN_PREC_BF16X3 needs chi <=
+ *           64 (its staging at chi = 128 does not fit in shared memory).
+ * Errors: as tn_mps_classify, plus TN_ERR_UNSUPPORTED for TN_PREC_BF16X3 at
+ * chi = 128. The gradient reductions are float32 atomics: results agree
+ * between runs to rounding, not bit for bit.
  */
 int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, const float* pixels,
                              int batch, int prec, int ckpt_every, const float* dftilde,
