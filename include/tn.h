@@ -178,24 +178,30 @@ double tn_group_plan_bytes(const tn_group_plan* plan);
  * results are accumulated over split k ranges] [the pack kernel, for BF16 /
  * BF16X3 plans] and the contraction kernel -- for BF16 / BF16X3 plans the
  * GEMM on packed operands and / or, for BF16 contractions whose narrower
- * operand has at most 64 rows, the fused GEMM that reads the wider operand as
+ * operand has at most 64 rows, a fused GEMM that reads the wider operand as
  * float32 and rounds it to bf16 in shared memory (it is read by exactly one
- * work unit, so it is never packed). */
+ * work unit, so it is never packed): the TMA one, which loads each tile of
+ * it as one box of a tensor map over its legs (the leg permutation done by
+ * the copy), when the operand is in device memory with a unit-stride last
+ * free or shared leg, at most five legs longer than 1 and 16-byte strides,
+ * else the one whose warps copy it element-wise through offset tables. */
 int tn_group_plan_launches(const tn_group_plan* plan);
 /* Runs launch `index` (0 .. launches-1) of that sequence alone, so each can
  * be timed by itself; running them all in order is one tn_group_plan_run.
  * Errors: TN_ERR_ARG (index out of range), as tn_group_plan_run. */
 int tn_group_plan_run_launch(const tn_group_plan* plan, void* workspace, size_t bytes, int index, void* stream);
 /* "zero", "pack", "gemm" (packed bf16 blocks), "gemm_fused" (wider operand
- * rounded inside the GEMM) or "contract" (single-pass kernel) for launch
- * `index`; NULL when out of range. */
+ * copied through offset tables and rounded inside the GEMM), "gemm_tma"
+ * (wider operand loaded in tensor-map boxes and rounded inside the GEMM) or
+ * "contract" (single-pass kernel) for launch `index`; NULL when out of
+ * range. */
 const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index);
 /* Algorithmic bytes of launch `index`: what it must move at the least, each
  * operand element read once and each result written once -- zero: 4 B per
  * zeroed result; pack: 4 B read + 2 B (BF16) or 4 B (BF16X3, hi and lo)
  * written per packed operand element; gemm: 2 B (4 B) per packed operand
- * element + 4 B per result; gemm_fused: 4 B per element of the float32
- * operand + 2 B per packed element + 4 B per result; contract: 4 B per
+ * element + 4 B per result; gemm_fused and gemm_tma: 4 B per element of the
+ * float32 operand + 2 B per packed element + 4 B per result; contract: 4 B per
  * operand element and per result. -1 when `index` is out of range. */
 double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index);
 /*

@@ -76,6 +76,13 @@ struct tn_group_plan {
   // its row and shared-index runs in `ctab`, -1 for the others
   std::vector<int32_t> ctab;
   std::vector<int64_t> ctab_r, ctab_k;
+  // the fused TMA GEMM's tiling of every contraction whose P allows one
+  // (BF16, narrower side at most 64 rows, P in device memory): its box and
+  // the index of P's tensor map in `tmaps`, -1 for the others
+  std::vector<tn::TmaBox> boxes;
+  std::vector<int64_t> box_map;
+  std::vector<tn::TmaMap> tmaps;
+  int64_t tma_tiles = 0;               // first unit of the fused TMA GEMM (after the other fused ones)
   double flops = 0.0, bytes = 0.0;
 };
 
@@ -231,7 +238,8 @@ int build_packed(tn_group_plan* p, bool allow_fuse = true) {
     const tn::PackedSchedule& sc = p->sched[spec_class(d)];
     plan_units_packed(&d, sc.long_k != 0);
     const int64_t rt = p->ctab_r.empty() ? -1 : p->ctab_r[i], kt = p->ctab_k.empty() ? -1 : p->ctab_k[i];
-    const int rc = plan_packed(d, p->prec, sc, allow_fuse, rt, kt, &p->pp);
+    const int64_t bm = p->box_map.empty() ? -1 : p->box_map[i];
+    const int rc = plan_packed(d, p->prec, sc, allow_fuse, rt, kt, bm >= 0 ? &p->boxes[i] : nullptr, bm, &p->pp);
     if (rc != TN_OK) return rc;
   }
   // largest units first: tensor time plus memory time of one unit
@@ -240,26 +248,30 @@ int build_packed(tn_group_plan* p, bool allow_fuse = true) {
     const double k = 64.0 * std::min<int64_t>(g.slabs, g.slabs_per_split);
     return 2.0 * pr * qr * k / 1500.0 + (2.0 * (pr + qr) * k + 4.0 * pr * qr) / 5.0;
   };
+  // launch of a GEMM: 0 on packed P, 1 fused (converters' copies), 2 fused TMA
+  auto kind = [](const GemmDesc& g) { return g.pjob < 0 ? 0 : (g.tmap_idx < 0 ? 1 : 2); };
   std::stable_sort(p->pp.gemms.begin(), p->pp.gemms.end(), [&](const GemmDesc& a, const GemmDesc& b) {
-    if ((a.pjob >= 0) != (b.pjob >= 0)) return a.pjob < 0;
+    if (kind(a) != kind(b)) return kind(a) < kind(b);
     return cost(a) > cost(b);
   });
-  int64_t t = 0, base = 0;
-  p->packed_tiles = -1;
+  // each launch numbers its units from 0
+  int64_t t = 0, start[3] = {-1, -1, -1};
   for (auto& g : p->pp.gemms) {
-    if (g.pjob >= 0 && p->packed_tiles < 0) p->packed_tiles = base = t;
-    g.tile_begin = t - base;
+    const int k = kind(g);
+    if (start[k] < 0) start[k] = t;
+    g.tile_begin = t - start[k];
     t += (int64_t)g.tiles_p * g.tiles_q * g.splits;
     if (g.splits > 1) p->zero_ranges.push_back(ZeroRange{g.C, g.RP * g.RQ});
   }
-  if (p->packed_tiles < 0) p->packed_tiles = t;
+  p->tma_tiles = start[2] < 0 ? t : start[2];
+  p->packed_tiles = start[1] < 0 ? p->tma_tiles : start[1];
   p->total_tiles = t;
   if (t > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
   p->unit_desc.assign((size_t)t, 0);
   for (size_t i = 0; i < p->pp.gemms.size(); ++i) {
     const GemmDesc& g = p->pp.gemms[i];
     const int64_t n = (int64_t)g.tiles_p * g.tiles_q * g.splits;
-    const int64_t b = g.tile_begin + (g.pjob >= 0 ? p->packed_tiles : 0);
+    const int64_t b = g.tile_begin + start[kind(g)];
     std::fill(p->unit_desc.begin() + b, p->unit_desc.begin() + b + n, (int32_t)i);
   }
   return TN_OK;
@@ -319,19 +331,32 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
     if (prec == TN_PREC_BF16) {
       p->ctab_r.assign(p->descs.size(), -1);
       p->ctab_k.assign(p->descs.size(), -1);
-      for (size_t i = 0; i < p->descs.size(); ++i)
-        if (std::min(p->descs[i].M, p->descs[i].N) <= 128)
-          tn::fused_tables(p->descs[i], &p->ctab, &p->ctab_r[i], &p->ctab_k[i]);
+      p->boxes.assign(p->descs.size(), tn::TmaBox());
+      p->box_map.assign(p->descs.size(), -1);
+      for (size_t i = 0; i < p->descs.size(); ++i) {
+        const ContractDesc& d = p->descs[i];
+        tn::TmaMap m;
+        if (std::min(d.M, d.N) <= 64 && tn::plan_tma_box(d, &p->boxes[i], &m)) {
+          p->box_map[i] = (int64_t)p->tmaps.size();
+          p->tmaps.push_back(m);
+        } else if (std::min(d.M, d.N) <= 128) {
+          tn::fused_tables(d, &p->ctab, &p->ctab_r[i], &p->ctab_k[i]);
+        }
+      }
     }
     // the workspace is laid out for the schedule with the longest lists
-    // (64-wide tiles, 32-slab k ranges), so any schedule fits it
+    // (64-wide tiles, 32-slab k ranges), nothing fused (the most packed
+    // bytes) or everything that can be (the fused TMA GEMM's tiles may be
+    // shorter than 128 rows), so any schedule fits it
     for (auto& sc : p->sched) sc = tn::PackedSchedule{64, 0, 0};
-    int rc = build_packed(p, false);
-    if (rc != TN_OK) { delete p; return rc; }
-    p->reserve_zero = p->zero_ranges.size();
-    p->reserve_units = p->unit_desc.size();
-    p->reserve_punits = p->pp.units.size();
-    p->reserve_packed = p->pp.packed_bytes;
+    for (int f = 0; f < 2; ++f) {
+      int rc = build_packed(p, f == 1);
+      if (rc != TN_OK) { delete p; return rc; }
+      p->reserve_zero = std::max(p->reserve_zero, p->zero_ranges.size());
+      p->reserve_units = std::max(p->reserve_units, p->unit_desc.size());
+      p->reserve_punits = std::max(p->reserve_punits, p->pp.units.size());
+      p->reserve_packed = std::max(p->reserve_packed, p->pp.packed_bytes);
+    }
     for (int c = 0; c < 3; ++c) p->sched[c] = default_schedule(c);
     {
       std::lock_guard<std::mutex> lk(g_tune_lock);
@@ -339,7 +364,7 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
       if (it != g_tune_cache.end())
         for (int c = 0; c < 3; ++c) p->sched[c] = it->second.sc[c];
     }
-    rc = build_packed(p);
+    const int rc = build_packed(p);
     if (rc != TN_OK) { delete p; return rc; }
     *plan = p;
     return TN_OK;
@@ -382,7 +407,8 @@ extern "C" {
 
 // Workspace layout (each part 256-byte aligned): descriptors (ContractDesc,
 // or GemmDesc when packed) | zero ranges | unit -> descriptor map |
-// (packed:) pack jobs | pack units | packed blocks.
+// (packed:) pack jobs | pack units | offset tables | tensor maps | the
+// GEMMs' unit counters | packed blocks.
 static size_t zero_offset(const tn_group_plan* plan) {
   return plan->packed ? align256(sizeof(GemmDesc) * plan->pp.gemms.size())
                       : align256(sizeof(ContractDesc) * plan->descs.size());
@@ -401,8 +427,14 @@ static size_t punits_offset(const tn_group_plan* plan) {
 static size_t tables_offset(const tn_group_plan* plan) {
   return punits_offset(plan) + align256(sizeof(PackUnit) * plan->reserve_punits);
 }
-static size_t packed_offset(const tn_group_plan* plan) {
+static size_t tmaps_offset(const tn_group_plan* plan) {
   return tables_offset(plan) + align256(sizeof(int32_t) * plan->ctab.size());
+}
+static size_t ctr_offset(const tn_group_plan* plan) {
+  return tmaps_offset(plan) + align256(sizeof(tn::TmaMap) * plan->tmaps.size());
+}
+static size_t packed_offset(const tn_group_plan* plan) {
+  return ctr_offset(plan) + (plan->packed ? 256 : 0);
 }
 
 size_t tn_group_plan_workspace_bytes(const tn_group_plan* plan) {
@@ -438,6 +470,20 @@ static int check_ws(const tn_group_plan* plan, void* ws, size_t bytes) {
 
 // Upload with the packed blocks at `packed` (inside the workspace, or a
 // separate region shared by plans that run one after another).
+// The schedule-independent lists: the fused GEMM's offset tables and the
+// fused TMA GEMM's tensor maps.
+static int upload_tables(const tn_group_plan* plan, uint8_t* base, cudaStream_t s) {
+  if (!plan->ctab.empty() &&
+      cudaMemcpyAsync(base + tables_offset(plan), plan->ctab.data(), sizeof(int32_t) * plan->ctab.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  if (!plan->tmaps.empty() &&
+      cudaMemcpyAsync(base + tmaps_offset(plan), plan->tmaps.data(), sizeof(tn::TmaMap) * plan->tmaps.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TN_ERR_CUDA;
+  return TN_OK;
+}
+
 static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* packed, cudaStream_t s,
                        bool with_tables = true) {
   // pageable sources: each call returns once the bytes are staged, so the
@@ -449,6 +495,7 @@ static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* pack
     for (auto& e : g) {
       e.P = packed + e.P_off;
       e.Q = packed + e.Q_off;
+      e.tmap = e.tmap_idx >= 0 ? base + tmaps_offset(plan) + sizeof(tn::TmaMap) * (size_t)e.tmap_idx : nullptr;
     }
     std::vector<PackJob> j = plan->pp.jobs;
     const int32_t* tabs = reinterpret_cast<const int32_t*>(base + tables_offset(plan));
@@ -458,10 +505,7 @@ static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* pack
       j[i].rtab = j[i].rtab_off >= 0 ? tabs + j[i].rtab_off : nullptr;
       j[i].ktab = j[i].ktab_off >= 0 ? tabs + j[i].ktab_off : nullptr;
     }
-    if (with_tables && !plan->ctab.empty() &&
-        cudaMemcpyAsync(base + tables_offset(plan), plan->ctab.data(), sizeof(int32_t) * plan->ctab.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return TN_ERR_CUDA;
+    if (with_tables && upload_tables(plan, base, s) != TN_OK) return TN_ERR_CUDA;
     if ((!g.empty() && cudaMemcpyAsync(base, g.data(), sizeof(GemmDesc) * g.size(), cudaMemcpyHostToDevice, s) !=
                            cudaSuccess) ||
         (!j.empty() && cudaMemcpyAsync(base + jobs_offset(plan), j.data(), sizeof(PackJob) * j.size(),
@@ -536,8 +580,8 @@ int tn_group_plan_run(const tn_group_plan* plan, void* workspace, size_t bytes, 
 // The launch sequence of a run: [zeroing of split results] [pack] then the
 // contraction kernel (single-pass), or the GEMM on packed P and / or the
 // fused GEMM.
-enum LaunchKind { L_ZERO, L_PACK, L_CONTRACT, L_FUSED };
-constexpr int MAX_LAUNCHES = 4;
+enum LaunchKind { L_ZERO, L_PACK, L_CONTRACT, L_FUSED, L_TMA };
+constexpr int MAX_LAUNCHES = 5;
 
 static int launch_list(const tn_group_plan* plan, LaunchKind* kinds) {
   int n = 0;
@@ -546,7 +590,8 @@ static int launch_list(const tn_group_plan* plan, LaunchKind* kinds) {
   if (plan->packed) {
     if (!plan->pp.units.empty()) kinds[n++] = L_PACK;
     if (plan->packed_tiles > 0) kinds[n++] = L_CONTRACT;
-    if (plan->total_tiles > plan->packed_tiles) kinds[n++] = L_FUSED;
+    if (plan->tma_tiles > plan->packed_tiles) kinds[n++] = L_FUSED;
+    if (plan->total_tiles > plan->tma_tiles) kinds[n++] = L_TMA;
     return n;
   }
   kinds[n++] = L_CONTRACT;
@@ -572,12 +617,17 @@ static int run_one(const tn_group_plan* plan, void* workspace, LaunchKind k, cud
     case L_FUSED:
       return launch_fused_gemm(reinterpret_cast<const GemmDesc*>(base), map + plan->packed_tiles,
                                reinterpret_cast<const PackJob*>(base + jobs_offset(plan)),
-                               plan->total_tiles - plan->packed_tiles, s);
+                               plan->tma_tiles - plan->packed_tiles, s);
+    case L_TMA:
+      return launch_tma_gemm(reinterpret_cast<const GemmDesc*>(base), map + plan->tma_tiles,
+                             plan->total_tiles - plan->tma_tiles,
+                             reinterpret_cast<uint32_t*>(base + ctr_offset(plan)) + 1, s);
     default:
       break;
   }
   if (plan->packed)
-    return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->packed_tiles, plan->prec, s);
+    return launch_packed_gemm(reinterpret_cast<const GemmDesc*>(base), map, plan->packed_tiles, plan->prec,
+                              reinterpret_cast<uint32_t*>(base + ctr_offset(plan)), s);
   const ContractDesc* g = reinterpret_cast<const ContractDesc*>(base);
   if (plan->prec == TN_PREC_FP32 && plan->skinny)
     return launch_contract_skinny_grouped(g, (int)plan->descs.size(), plan->max_n, s);
@@ -622,6 +672,7 @@ const char* tn_group_plan_launch_name(const tn_group_plan* plan, int index) {
     case L_ZERO: return "zero";
     case L_PACK: return "pack";
     case L_FUSED: return "gemm_fused";
+    case L_TMA: return "gemm_tma";
     default: return plan->packed ? "gemm" : "contract";
   }
 }
@@ -644,6 +695,7 @@ double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index) {
       return b;
     }
     case L_FUSED:
+    case L_TMA:
     case L_CONTRACT:
       break;
   }
@@ -652,10 +704,11 @@ double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index) {
       b += 4.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
     return b;
   }
-  const bool fused = kinds[index] == L_FUSED;
+  const int want = kinds[index] == L_CONTRACT ? 0 : (kinds[index] == L_FUSED ? 1 : 2);
+  const bool fused = want > 0;
   const double pe = plan->prec == TN_PREC_BF16X3 ? 4.0 : 2.0;  // packed bytes per element
   for (const auto& g : plan->pp.gemms) {
-    if ((g.pjob >= 0) != fused) continue;
+    if ((g.pjob < 0 ? 0 : (g.tmap_idx < 0 ? 1 : 2)) != want) continue;
     const double K = (double)g.K;
     b += (fused ? 4.0 : pe) * (double)g.RP * K + pe * (double)g.RQ * K + 4.0 * (double)g.RP * (double)g.RQ;
   }
@@ -679,10 +732,8 @@ int tn_group_plan_autotune(tn_group_plan* plan, void* workspace, size_t bytes, v
     return TN_ERR_CUDA;
   }
   // one candidate: rebuild, upload, one warm run, the mean of two timed runs
-  // the offset tables do not depend on the schedule: uploaded once
-  if (!plan->ctab.empty() &&
-      cudaMemcpyAsync(base + tables_offset(plan), plan->ctab.data(), sizeof(int32_t) * plan->ctab.size(),
-                      cudaMemcpyHostToDevice, s) != cudaSuccess) {
+  // the offset tables and tensor maps do not depend on the schedule: uploaded once
+  if (upload_tables(plan, base, s) != TN_OK) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return TN_ERR_CUDA;

@@ -20,6 +20,7 @@
 // other one its N side, whose width per tile is cut to the rows present
 // (multiple of 16), so a contraction with one thin side streams its wide
 // operand at memory speed instead of filling a 128x128 tile with padding.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string.h>
@@ -118,8 +119,9 @@ __device__ __forceinline__ void block_tables(const PackJob& J, const VBlock& v, 
   // shared indices from thread 128 on, so one block's rows and shared
   // indices are decoded by different threads at once
   for (int e = t ^ PR; e < v.nb * PK; e += PACK_THREADS) {
-    const int64_t k = (int64_t)(v.slab0 + (e >> 6)) * PK + (e & (PK - 1));
-    sm.koff[sl][e] = k < J.K ? (int32_t)leg_offset((uint32_t)k, J.nk, J.kdim, J.kstr) : 0;
+    const int p = e & (PK - 1);
+    const int64_t k = (int64_t)(v.slab0 + (e >> 6)) * J.kw + p;
+    sm.koff[sl][e] = (p < J.kw && k < J.K) ? (int32_t)leg_offset((uint32_t)k, J.nk, J.kdim, J.kstr) : 0;
   }
 }
 
@@ -156,8 +158,8 @@ __device__ __forceinline__ void block_load(const PackJob& J, const VBlock& v, in
 #pragma unroll
     for (int j = 0; j < 8; ++j) cr.v[c][j] = 0.0f;
     if (bl >= v.nb || r >= v.rv) continue;
-    const int64_t kb = (int64_t)(v.slab0 + bl) * PK;
-    const int kv = (int)(J.K - kb < PK ? J.K - kb : PK);
+    const int64_t kb = (int64_t)(v.slab0 + bl) * J.kw;
+    const int kv = (int)(J.K - kb < J.kw ? J.K - kb : J.kw);
     const int32_t* koff = sm.koff[sl] + bl * PK;
     const int k0 = grp * 8;
     const float* rowp = src + roff[r];
@@ -294,28 +296,66 @@ constexpr int XSLOTS = 4;
 constexpr int XDIST = XSLOTS - 1;          // slabs copied ahead of the rounding
 constexpr int XSLOT_BYTES = PR * PK * 4;   // 32 KB
 constexpr int XPART = XSLOT_BYTES / CONV_WARPS;  // one converter warp's part of a slot (4 KB)
+// Fused TMA GEMM: the same staging memory as a ring of bytes, each box at the
+// next 128-byte boundary (wrapping to the ring's start rather than past its
+// end), at most XBOXES boxes in it at once: more small boxes in flight than
+// fixed slots would hold.
+constexpr uint32_t XRING = XSLOTS * XSLOT_BYTES;  // 128 KB
+constexpr int XBOXES = 8;
+static_assert((XRING & (XRING - 1)) == 0, "ring size: a power of two");
 
+// Ring position of the next box of `bytes` (rounded up to 128): advances the
+// running position `v` (which counts the skipped tails too) and returns the
+// box's start on it.
+__device__ __forceinline__ uint64_t ring_take(uint64_t& v, uint32_t bytes) {
+  const uint32_t b = (bytes + 127u) & ~127u;
+  const uint32_t off = (uint32_t)(v & (XRING - 1));
+  if (off + b > XRING) v += XRING - off;
+  const uint64_t start = v;
+  v += b;
+  return start;
+}
+
+// FUSE: 0 -- P and Q packed; 1 -- P gathered by the converters' own copies
+// (cp.async through offset tables); 2 -- P tiles loaded as boxes of its
+// tensor map by one TMA warp, the converters only round.
 template <int SPLIT, int FUSE>
 struct GCfg {
   static constexpr int OPS = SPLIT ? 4 : 2;            // P hi, Q hi (, P lo, Q lo)
   // BF16 on packed operands: tiles up to 256 wide (Q up to two 128-row blocks)
   static constexpr bool WIDE = !SPLIT && !FUSE;
   static constexpr int STAGES = FUSE ? 3 : (SPLIT ? 3 : 4);
-  // fused: P 16 KB + Q at most 64 rows (8 KB); wide: P 16 KB + Q 32 KB
-  static constexpr int STAGE_BYTES = FUSE ? PBLOCK + PBLOCK / 2 : (WIDE ? 3 * PBLOCK : OPS * PBLOCK);
+  // fused: P 16 KB + Q at most 64 rows (8 KB); fused TMA: P only (Q has a
+  // ring of its own); wide: P 16 KB + Q 32 KB
+  static constexpr int STAGE_BYTES =
+      FUSE == 2 ? PBLOCK : (FUSE ? PBLOCK + PBLOCK / 2 : (WIDE ? 3 * PBLOCK : OPS * PBLOCK));
+  // fused TMA GEMM: Q's blocks (at most 64 rows, 8 KB) in QSLOTS slots of
+  // their own, copied as far ahead as the slots allow -- not gated by the
+  // rounding of P, so their latency stays off the stages' turnaround
+  static constexpr int QSLOTS = FUSE == 2 ? 4 : 0;
+  static constexpr int QDIV = QSLOTS > 0 ? QSLOTS : 1;
+  static constexpr int QSLOT_BYTES = PBLOCK / 2;
   static constexpr int ACC_COLS = WIDE ? 256 : 128;   // columns of one accumulator
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS; // two accumulators
   static constexpr int CONV = FUSE ? CONV_WARPS : 0;
-  static constexpr int EPI0 = 2 + CONV;                // first epilogue warp
+  static constexpr int TMAW = FUSE == 2 ? 1 : 0;       // the warp issuing P's box loads
+  // fused TMA GEMM: the converter warps form RGROUPS groups, each rounding
+  // every RGROUPS-th box (two groups of four measured slower than one of
+  // eight: the rounding is bound by throughput, not latency)
+  static constexpr int RGROUPS = 1;
+  static constexpr int RW = CONV / RGROUPS;            // warps rounding one box
+  static constexpr int EPI0 = 2 + TMAW + CONV;         // first epilogue warp
   static constexpr int EPI = FUSE ? 4 : 8;             // epilogue warps
   static constexpr int ECOLS = ACC_COLS * 4 / EPI;     // at most this many accumulator columns per warp
-  static constexpr int THREADS = 32 * (2 + CONV + EPI);
+  static constexpr int THREADS = 32 * (2 + TMAW + CONV + EPI);
   // BF16 on packed operands: each epilogue warp transposes its 32 x 32 blocks
   // through shared memory (16-byte chunks of a row XOR-permuted by row % 8:
   // 16-byte accesses conflict-free both ways), so a store instruction writes
   // four whole 128-byte row segments of C instead of 16 bytes in each of 32
   // rows
-  static constexpr bool TR = !SPLIT && !FUSE;
+  // (and the fused TMA GEMM: its thin tiles' rows are short, so per-row
+  // stores would touch 32 lines per instruction)
+  static constexpr bool TR = !SPLIT && FUSE != 1;
   static constexpr int TR_BYTES = TR ? EPI * 32 * 32 * 4 : 0;
   static_assert(!(SPLIT && FUSE), "the fused GEMM is BF16 only");
 };
@@ -324,12 +364,103 @@ template <int S>
 struct GemmAux {
   uint64_t full[S];          // stage s holds its blocks
   uint64_t empty[S];         // the MMAs reading stage s are complete
+  uint64_t xfull[XBOXES];    // fused TMA GEMM: box j (mod XBOXES) has landed in the ring
+  uint64_t xempty[XBOXES];   // ... and the converters have rounded it
+  uint64_t qfull[8];         // fused TMA GEMM: Q slot j holds its block
+  uint64_t qempty[8];        // ... and the MMAs reading it are complete
+  uint64_t uqfull[16];       // fused TMA GEMM: unit slot j (mod 16) is posted
+  uint64_t uqempty[16];      // ... and every role has read it
+  volatile int32_t uq[16];   // the posted units (-1: no more)
   uint64_t acc_full[2];      // accumulator b holds a finished chunk
   uint64_t acc_empty[2];     // the epilogue has drained accumulator b
   uint64_t final_bar;
   uint32_t tmem_base;
   volatile int32_t abort;
 };
+
+// This CTA's sequence of work units. Static: units blockIdx.x + n *
+// gridDim.x. Dynamic (grouped launches of the GEMM on packed P and of the
+// fused TMA GEMM): the first role to need a unit (the leader: the copy warp,
+// or the box-load warp) claims units from a global counter, UQ_AHEAD ahead
+// of the one it works on, and posts them in a ring of 16 slots; every other
+// role (followers: one thread, or a whole warp of which lane 0 answers) reads
+// them in order -- so a CTA that finishes early takes more units, and the
+// launch ends when the work does rather than when the CTA with the most
+// static units does. A follower reads unit n + 1 when it starts unit
+// n (to load its descriptor early): claims stay at most UQ_AHEAD + 1 units
+// ahead of the slowest role, within the ring. -1: none left.
+constexpr int UQ = 16, UQ_AHEAD = 2;
+
+template <int S>
+struct UnitSeq {
+  GemmAux<S>* x;
+  uint32_t* ctr;
+  int* status;
+  int64_t total;
+  uint32_t n, claimed;
+  int mode;  // 0 static, 1 leader, 2 follower thread, 3 follower warp
+  bool ended;
+
+  __device__ __forceinline__ void claim() {
+    if (ended) return;
+    const uint32_t k = claimed, sl = k % UQ;
+    if (!ptx::mbar_wait(ptx::smem_addr(&x->uqempty[sl]), ((k / UQ) & 1u) ^ 1u, status)) {
+      x->abort = 1;
+      ended = true;
+      return;
+    }
+    const uint32_t u = atomicAdd(ctr, 1u);
+    const int32_t v = (int64_t)u < total ? (int32_t)u : -1;
+    x->uq[sl] = v;
+    ptx::mbar_arrive(ptx::smem_addr(&x->uqfull[sl]));
+    ++claimed;
+    if (v < 0) ended = true;
+  }
+  __device__ __forceinline__ int64_t read(uint32_t k) {
+    const uint32_t sl = k % UQ;
+    if (mode == 1) return k < claimed ? (int64_t)x->uq[sl] : -1;
+    bool ok = ptx::mbar_wait(ptx::smem_addr(&x->uqfull[sl]), (k / UQ) & 1u, status);
+    if (mode == 3) ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+      x->abort = 1;
+      return -1;
+    }
+    const int32_t v = x->uq[sl];
+    if (mode == 3) __syncwarp();
+    if (mode == 2 || (threadIdx.x & 31) == 0) ptx::mbar_arrive(ptx::smem_addr(&x->uqempty[sl]));
+    return v;
+  }
+  __device__ __forceinline__ int64_t at_static(uint32_t k) const {
+    const int64_t u = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
+    return u < total ? u : -1;
+  }
+  __device__ __forceinline__ int64_t first() {
+    n = 0;
+    if (mode == 0) return at_static(0);
+    if (mode == 1)
+      for (int k = 0; k <= UQ_AHEAD; ++k) claim();
+    return read(0);
+  }
+  __device__ __forceinline__ int64_t next() {
+    ++n;
+    if (mode == 0) return at_static(n);
+    if (mode == 1) claim();
+    return read(n);
+  }
+};
+
+template <int S>
+__device__ __forceinline__ UnitSeq<S> unit_seq(GemmAux<S>& x, uint32_t* ctr, int* status, int64_t total, int mode) {
+  UnitSeq<S> q;
+  q.x = &x;
+  q.ctr = ctr;
+  q.status = status;
+  q.total = total;
+  q.n = q.claimed = 0;
+  q.mode = mode;
+  q.ended = false;
+  return q;
+}
 
 // Offsets of the 4-byte fallback copies (each converter warp its own).
 struct ConvTables {
@@ -340,10 +471,12 @@ struct ConvTables {
 template <int SPLIT, int FUSE>
 constexpr size_t gemm_smem_bytes() {
   using C = GCfg<SPLIT, FUSE>;
-  return 1024 + (size_t)C::STAGES * C::STAGE_BYTES +
-         (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables) : 0) + (size_t)C::TR_BYTES +
+  return 1024 + (size_t)C::STAGES * C::STAGE_BYTES + (size_t)C::QSLOTS * C::QSLOT_BYTES +
+         (FUSE ? (size_t)XSLOTS * XSLOT_BYTES : 0) + (FUSE == 1 ? sizeof(ConvTables) : 0) + (size_t)C::TR_BYTES +
          sizeof(GemmAux<C::STAGES>);
 }
+static_assert(GCfg<0, 2>::QSLOTS <= 8, "Q slots: barrier pairs");
+static_assert(gemm_smem_bytes<0, 2>() <= 227 * 1024, "fused TMA GEMM: shared memory");
 
 struct GUnit {
   int64_t p0, q0;        // first row of P and of Q
@@ -351,13 +484,15 @@ struct GUnit {
 };
 
 // Unit u of descriptor d (u < 2^31: the host rejects larger launches); 32-bit
-// division, far cheaper on the device than 64-bit.
-__device__ __forceinline__ GUnit gunit(const GemmDesc& d, int64_t u) {
+// division, far cheaper on the device than 64-bit. D: GemmDesc or one of the
+// per-role views below.
+template <class D>
+__device__ __forceinline__ GUnit gunit(const D& d, int64_t u) {
   GUnit g;
   const uint32_t uu = (uint32_t)u, nq = (uint32_t)d.tiles_q, np = (uint32_t)d.tiles_p;
   const uint32_t rest = uu / nq, tq = uu - rest * nq;
   const uint32_t split = rest / np, tp = rest - split * np;
-  g.p0 = (int64_t)tp * PR;
+  g.p0 = (int64_t)tp * d.ph;
   g.q0 = (int64_t)tq * d.q_tile;
   g.ks0 = (int32_t)(split * (uint32_t)d.slabs_per_split);
   g.nks = (int32_t)(d.slabs - g.ks0 < d.slabs_per_split ? d.slabs - g.ks0 : d.slabs_per_split);
@@ -381,7 +516,7 @@ __device__ __forceinline__ GemmDesc load_desc(const GemmDesc& single, const Gemm
 struct EpiDesc {
   float* C;
   int64_t ci, cj, RP, RQ, tile_begin;
-  int32_t tiles_q, tiles_p, slabs, slabs_per_split, q_tile, splits, store16;
+  int32_t tiles_q, tiles_p, slabs, slabs_per_split, q_tile, splits, store16, ph;
 };
 
 __device__ __forceinline__ EpiDesc load_epi(const GemmDesc& single, const GemmDesc* descs, const int32_t* map,
@@ -401,19 +536,63 @@ __device__ __forceinline__ EpiDesc load_epi(const GemmDesc& single, const GemmDe
   e.q_tile = d->q_tile;
   e.splits = d->splits;
   e.store16 = d->store16;
+  e.ph = d->ph;
   return e;
 }
 
-__device__ __forceinline__ GUnit gunit(const EpiDesc& d, int64_t u) {
-  GUnit g;
-  const uint32_t uu = (uint32_t)u, nq = (uint32_t)d.tiles_q, np = (uint32_t)d.tiles_p;
-  const uint32_t rest = uu / nq, tq = uu - rest * nq;
-  const uint32_t split = rest / np, tp = rest - split * np;
-  g.p0 = (int64_t)tp * PR;
-  g.q0 = (int64_t)tq * d.q_tile;
-  g.ks0 = (int32_t)(split * (uint32_t)d.slabs_per_split);
-  g.nks = (int32_t)(d.slabs - g.ks0 < d.slabs_per_split ? d.slabs - g.ks0 : d.slabs_per_split);
-  return g;
+// What the fused TMA GEMM's box-load warp reads of a unit's descriptor.
+struct TmaDesc {
+  const void* tmap;
+  int64_t tile_begin;
+  int32_t tiles_q, tiles_p, slabs, slabs_per_split, q_tile, ph, kw, bkmask, bk0, bk1, bkstep, nsb;
+  uint32_t bdim[5], bplace[5];
+};
+
+__device__ __forceinline__ TmaDesc load_tma(const GemmDesc* descs, const int32_t* map, int64_t u) {
+  const GemmDesc* d = descs + __ldg(map + u);
+  TmaDesc e;
+  e.tmap = d->tmap;
+  e.tile_begin = d->tile_begin;
+  e.tiles_q = d->tiles_q;
+  e.tiles_p = d->tiles_p;
+  e.slabs = d->slabs;
+  e.slabs_per_split = d->slabs_per_split;
+  e.q_tile = d->q_tile;
+  e.ph = d->ph;
+  e.kw = d->kw;
+  e.bkmask = d->bkmask;
+  e.bk0 = d->bk0;
+  e.bk1 = d->bk1;
+  e.bkstep = d->bkstep;
+  e.nsb = d->nsb;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    e.bdim[i] = d->bdim[i];
+    e.bplace[i] = d->bplace[i];
+  }
+  return e;
+}
+
+// What its rounding warps read.
+struct RoundDesc {
+  int64_t tile_begin;
+  int32_t tiles_q, tiles_p, slabs, slabs_per_split, q_tile, ph, kw, p_mn, nsb;
+};
+
+__device__ __forceinline__ RoundDesc load_round(const GemmDesc* descs, const int32_t* map, int64_t u) {
+  const GemmDesc* d = descs + __ldg(map + u);
+  RoundDesc e;
+  e.tile_begin = d->tile_begin;
+  e.tiles_q = d->tiles_q;
+  e.tiles_p = d->tiles_p;
+  e.slabs = d->slabs;
+  e.slabs_per_split = d->slabs_per_split;
+  e.q_tile = d->q_tile;
+  e.ph = d->ph;
+  e.kw = d->kw;
+  e.p_mn = d->p_mn;
+  e.nsb = d->nsb;
+  return e;
 }
 
 // Walks this CTA's (unit, slab) pairs in the order the copy warp and the MMA
@@ -636,35 +815,147 @@ __device__ __forceinline__ void conv_round(uint32_t w, int cw, int l, const uint
   }
 }
 
+// Fused TMA GEMM: warp wi of the NW warps rounding one staged box (shared
+// address xs) writes its part of the bf16 P tile (shared address pt).
+// p_mn = 0: the box is ph rows x nsb * kw shared indices, row-major along k,
+// covering nsb slabs; slab j of row r goes to row j * ceil8(ph) + r of the
+// tile (the MMA reads slab j's k-block from that row on). Lane l takes
+// shared indices 4q .. 4q+3 (q = l % 16) of each slab of rows r0 + 2 NW i
+// (r0 = 2 wi + l / 16) and writes them K-major (zeros at q >= kw / 4): rows
+// 2 NW apart are 2 NW / 8 swizzle atoms (of 1 KB) apart at the same position
+// in their atom, as are k-blocks (ceil8(ph) rows apart), so both addresses
+// advance by steps. At most 8 (slab, row) pairs per lane: nsb * ceil(ph / 16)
+// <= 8 (the planner's bound). p_mn = 1 (one slab): the box is kw k-rows x ph
+// rows, row-major along the rows; lane l takes rows 4l .. 4l+3 of the k-rows
+// of 8-row groups wi + NW j and writes them MN-major (zeros at k >= kw). Rows
+// past ph are left as they are: their products are never stored. Both read
+// each 16-byte run of the box with consecutive lanes on consecutive runs, and
+// write whole 128-byte rows of the tile per 16 lanes: no bank conflicts.
+// Loads go out 8 at a time before their conversions.
+template <int NW>
+__device__ __forceinline__ void round_box(int p_mn, int ph, int kw, int nsb, int wi, int l, uint32_t xs,
+                                          uint32_t pt) {
+  float4 v[8];
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!p_mn) {
+    static_assert((2 * NW) % 8 == 0, "rows of one step: whole swizzle atoms");
+    const int q = l & 15, r0 = 2 * wi + (l >> 4);
+    const bool kin = q < (kw >> 2);
+    const int wrow = nsb * kw;                          // floats per staged row
+    const uint32_t ld0 = xs + (uint32_t)((r0 * wrow + 4 * q) * 4);
+    const uint32_t ldrow = (uint32_t)(2 * NW * wrow * 4), ldslab = (uint32_t)(kw * 4);
+    const uint32_t st0 = pt + sw128_chunk(r0, q >> 1) + 8 * (q & 1);
+    constexpr uint32_t strow = 2 * NW / 8 * 1024;
+    const uint32_t stslab = (uint32_t)(((ph + 7) & ~7) * 128);
+    const int nrows = ph - r0;  // this lane's rows: r0 + 2 NW i < ph
+    const int ni = (ph - 2 * wi + 2 * NW - 1) / (2 * NW);  // row steps of this warp (uniform)
+    if (ni <= 0) return;
+    if (nsb == 1) {
+#pragma unroll
+      for (int h = 0; h < 64 / NW; h += 8) {
+        if (h >= ni) break;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int ii = h + i;
+          v[i] = (2 * NW * ii < nrows && kin) ? ptx::ld_shared_v4(ld0 + (uint32_t)ii * ldrow) : zero;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int ii = h + i;
+          if (2 * NW * ii < nrows)
+            ptx::st_shared_v2(st0 + (uint32_t)ii * strow, bf16x2_rn(v[i].x, v[i].y), bf16x2_rn(v[i].z, v[i].w));
+        }
+      }
+    } else {
+      // (slab j, row step i) pairs t = j * ni + i, t < nsb * ni <= 8
+      const int nt = nsb * ni;
+      int j = 0, i = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        v[t] = (t < nt && 2 * NW * i < nrows && kin)
+                   ? ptx::ld_shared_v4(ld0 + (uint32_t)i * ldrow + (uint32_t)j * ldslab)
+                   : zero;
+        if (++i == ni) { i = 0; ++j; }
+      }
+      j = 0;
+      i = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (t < nt && 2 * NW * i < nrows)
+          ptx::st_shared_v2(st0 + (uint32_t)i * strow + (uint32_t)j * stslab, bf16x2_rn(v[t].x, v[t].y),
+                            bf16x2_rn(v[t].z, v[t].w));
+        if (++i == ni) { i = 0; ++j; }
+      }
+    }
+  } else {
+    const int m = 4 * l;
+    if (m >= ph) return;
+    const uint32_t ldstep = (uint32_t)(ph * 4);
+    const int mg = (m & 63) >> 3;
+#pragma unroll
+    for (int gi = 0; gi < 8 / NW; ++gi) {
+      const int g = wi + NW * gi;  // 8-row k group
+      const uint32_t ld0 = xs + (uint32_t)((8 * g * ph + m) * 4);
+      const int kin = kw - 8 * g;  // k-rows of the group inside the box
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) v[jj] = jj < kin ? ptx::ld_shared_v4(ld0 + (uint32_t)jj * ldstep) : zero;
+      const uint32_t st0 = pt + (uint32_t)((m >> 6) * MN_HALF + g * MN_KGROUP + (m & 7) * 2);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        ptx::st_shared_v2(st0 + jj * 128 + ((mg ^ jj) << 4), bf16x2_rn(v[jj].x, v[jj].y),
+                          bf16x2_rn(v[jj].z, v[jj].w));
+    }
+  }
+}
+
 template <int SPLIT, int FUSE>
 __global__ void __launch_bounds__(GCfg<SPLIT, FUSE>::THREADS, 1)
 packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __restrict__ descs,
                    const int32_t* __restrict__ map, const PackJob* __restrict__ jobs, int64_t total_units,
-                   int* status) {
+                   uint32_t* unit_ctr, int* status) {
   using Cf = GCfg<SPLIT, FUSE>;
   constexpr int S = Cf::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // after the stages: fused -- staging slots, then the tables; BF16 on
-  // packed operands -- the epilogue's transpose buffers; then the barriers
-  uint8_t* xstage = smem + (size_t)S * Cf::STAGE_BYTES;
+  // after the stages: fused TMA -- Q's slots; fused -- the staging slots
+  // (or ring), then (converters' copies) their tables; BF16 on packed
+  // operands -- the epilogue's transpose buffers; then the barriers
+  uint8_t* qring = smem + (size_t)S * Cf::STAGE_BYTES;
+  uint8_t* xstage = qring + (size_t)Cf::QSLOTS * Cf::QSLOT_BYTES;
   ConvTables& tb = *reinterpret_cast<ConvTables*>(xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES : 0));
-  float* trbuf = reinterpret_cast<float*>(xstage);
-  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(
-      xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES + sizeof(ConvTables) : 0) + Cf::TR_BYTES);
-  const uint32_t stage0 = ptx::smem_addr(smem);
+  uint8_t* trb = xstage + (FUSE ? (size_t)XSLOTS * XSLOT_BYTES : 0) + (FUSE == 1 ? sizeof(ConvTables) : 0);
+  float* trbuf = reinterpret_cast<float*>(trb);
+  GemmAux<S>& x = *reinterpret_cast<GemmAux<S>*>(trb + Cf::TR_BYTES);
+  const uint32_t stage0 = ptx::smem_addr(smem), qring0 = ptx::smem_addr(qring);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
-      // fused: the copy warp's transaction arrival and one per converter warp
-      ptx::mbar_init(ptx::smem_addr(&x.full[s]), 1 + Cf::CONV);
+      // the copy warp's transaction arrival (unless Q has its own slots) and
+      // one per converter warp rounding the stage's P
+      ptx::mbar_init(ptx::smem_addr(&x.full[s]), (FUSE == 2 ? 0 : 1) + Cf::RW);
       ptx::mbar_init(ptx::smem_addr(&x.empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_addr(&x.acc_full[b]), 1);
       ptx::mbar_init(ptx::smem_addr(&x.acc_empty[b]), Cf::EPI);
     }
+    if (unit_ctr)
+      for (int q = 0; q < UQ; ++q) {
+        ptx::mbar_init(ptx::smem_addr(&x.uqfull[q]), 1);  // the leader's post
+        // every other role's read: MMA issuer, epilogue warps (and, fused
+        // TMA, the copy thread and the rounding warps)
+        ptx::mbar_init(ptx::smem_addr(&x.uqempty[q]), FUSE == 2 ? 2 + Cf::CONV + Cf::EPI : 1 + Cf::EPI);
+      }
+    for (int q = 0; q < Cf::QSLOTS; ++q) {
+      ptx::mbar_init(ptx::smem_addr(&x.qfull[q]), 1);   // the copy's transaction arrival
+      ptx::mbar_init(ptx::smem_addr(&x.qempty[q]), 1);  // the MMA issuer's commit
+    }
+    if (FUSE == 2)
+      for (int q = 0; q < XBOXES; ++q) {
+        ptx::mbar_init(ptx::smem_addr(&x.xfull[q]), 1);           // the TMA warp's transaction arrival
+        ptx::mbar_init(ptx::smem_addr(&x.xempty[q]), Cf::RW);     // one per warp rounding the box
+      }
     ptx::mbar_init(ptx::smem_addr(&x.final_bar), 1);
     x.abort = 0;
     ptx::fence_mbar_init();
@@ -684,10 +975,13 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       uint32_t gs = 0;
       // each role loads the descriptor of its next unit while the current
       // one runs, so unit boundaries do not wait on global-memory latency
-      GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
-      for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
+      UnitSeq<S> us = unit_seq(x, unit_ctr, status, total_units, !unit_ctr ? 0 : (FUSE == 2 ? 2 : 1));
+      int64_t u = us.first(), un = 0;
+      GemmDesc dn = load_desc(single, descs, map, u >= 0 ? u : 0);
+      for (; u >= 0 && !x.abort; u = un) {
         const GemmDesc d = dn;
-        if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
+        un = us.next();
+        if (un >= 0) dn = load_desc(single, descs, map, un);
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qleft = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
         // a 256-wide tile takes its Q rows from two consecutive 128-row blocks
@@ -698,7 +992,21 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         // a 64-row tile starts 64 rows (8 atoms, 8 KB) into its 128-row block
         const uint8_t* qbase = d.Q + ((g.q0 / PR) * d.slabs + g.ks0) * d.Q_block + (g.q0 % PR) * 128;
         bool ok = true;
-        for (int ks = 0; ks < g.nks; ++ks, ++gs) {
+        const int step = FUSE == 2 ? d.nsb : 1;  // slabs per stage
+        for (int ks = 0; ks < g.nks; ks += step, ++gs) {
+          if (FUSE == 2) {
+            // Q alone (the box's slabs: consecutive blocks), into its own slot
+            const int qs = (int)(gs % Cf::QDIV);
+            if (!ptx::mbar_wait(ptx::smem_addr(&x.qempty[qs]), ((gs / Cf::QDIV) & 1u) ^ 1u, status)) {
+              ok = false;
+              break;
+            }
+            const uint32_t qf = ptx::smem_addr(&x.qfull[qs]);
+            const uint32_t qbytes = (uint32_t)(step - 1) * (uint32_t)d.Q_block + qb;
+            ptx::mbar_arrive_expect_tx(qf, qbytes);
+            ptx::bulk_copy_g2s(qring0 + (uint32_t)qs * Cf::QSLOT_BYTES, qbase + ks * d.Q_block, qbytes, qf);
+            continue;
+          }
           const int s = (int)(gs % S);
           if (!ptx::mbar_wait(ptx::smem_addr(&x.empty[s]), ((gs / S) & 1u) ^ 1u, status)) { ok = false; break; }
           const uint32_t full = ptx::smem_addr(&x.full[s]);
@@ -715,23 +1023,36 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         if (!ok) { x.abort = 1; break; }
       }
       // copies still in flight land before the CTA can exit
-      const uint32_t first = gs > (uint32_t)S ? gs - (uint32_t)S : 0u;
-      for (uint32_t q = first; q < gs; ++q)
-        ptx::mbar_wait(ptx::smem_addr(&x.full[q % S]), (q / S) & 1u, status);
+      if (FUSE == 2) {
+        const uint32_t first = gs > (uint32_t)Cf::QDIV ? gs - (uint32_t)Cf::QDIV : 0u;
+        for (uint32_t q = first; q < gs; ++q)
+          ptx::mbar_wait(ptx::smem_addr(&x.qfull[q % Cf::QDIV]), (q / Cf::QDIV) & 1u, status);
+      } else {
+        const uint32_t first = gs > (uint32_t)S ? gs - (uint32_t)S : 0u;
+        for (uint32_t q = first; q < gs; ++q)
+          ptx::mbar_wait(ptx::smem_addr(&x.full[q % S]), (q / S) & 1u, status);
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t gs = 0, gc = 0;
-      GemmDesc dn = load_desc(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
-      for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
+      UnitSeq<S> us = unit_seq(x, unit_ctr, status, total_units, unit_ctr ? 2 : 0);
+      int64_t u = us.first(), un = 0;
+      GemmDesc dn = load_desc(single, descs, map, u >= 0 ? u : 0);
+      for (; u >= 0 && !x.abort; u = un) {
         const GemmDesc d = dn;
-        if (u + gridDim.x < total_units) dn = load_desc(single, descs, map, u + gridDim.x);
+        un = us.next();
+        if (un >= 0) dn = load_desc(single, descs, map, un);
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qrows = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
         const int nmma = (int)((qrows + 15) & ~int64_t(15));
         const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, FUSE ? d.p_mn : 0, 0);
         const int chunk = SPLIT ? KC : g.nks;
+        const int step = FUSE == 2 ? d.nsb : 1;  // slabs per stage
+        // fused TMA: slab j of a stage at row j * ceil8(ph) of the P tile,
+        // and Q's block j after the first j blocks of its slot
+        const uint32_t pslab = (uint32_t)(((d.ph + 7) & ~7) * 128), qslab = (uint32_t)d.Q_block;
         bool ok = true;
         for (int c0 = 0; c0 < g.nks && ok; c0 += chunk, ++gc) {
           const int b = (int)(gc & 1);
@@ -739,25 +1060,36 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
           ptx::tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)(b * Cf::ACC_COLS);
           const int c1 = min(g.nks, c0 + chunk);
-          for (int ks = c0; ks < c1; ++ks, ++gs) {
-            const int s = (int)(gs % S);
+          for (int ks = c0; ks < c1; ks += step, ++gs) {
+            const int s = (int)(gs % S), qs = (int)(gs % Cf::QDIV);
             if (!ptx::mbar_wait(ptx::smem_addr(&x.full[s]), (gs / S) & 1u, status)) { ok = false; break; }
+            if (FUSE == 2 && !ptx::mbar_wait(ptx::smem_addr(&x.qfull[qs]), (gs / Cf::QDIV) & 1u, status)) {
+              ok = false;
+              break;
+            }
             ptx::tc_fence_after();
             const uint32_t st = stage0 + (uint32_t)s * Cf::STAGE_BYTES;
+            const uint32_t qst = FUSE == 2 ? qring0 + (uint32_t)qs * Cf::QSLOT_BYTES : st + PBLOCK;
+            for (int j = 0; j < step; ++j) {
+              const uint32_t pj = st + (uint32_t)j * pslab, qj = qst + (uint32_t)j * qslab;
 #pragma unroll
-            for (int kk = 0; kk < PK / 16; ++kk) {
-              const uint64_t pd = (FUSE && d.p_mn) ? ptx::sw128_mnmajor_desc(st + kk * 2 * MN_KGROUP, MN_HALF, MN_KGROUP)
-                                                   : ptx::sw128_kmajor_desc(st + kk * 32);
-              const uint64_t qd = ptx::sw128_kmajor_desc(st + PBLOCK + kk * 32);
-              ptx::mma_bf16(dt, pd, qd, idesc, (ks == c0 && kk == 0) ? 0u : 1u);
-              if (SPLIT) {
-                const uint64_t pl = ptx::sw128_kmajor_desc(st + 2 * PBLOCK + kk * 32);
-                const uint64_t ql = ptx::sw128_kmajor_desc(st + 3 * PBLOCK + kk * 32);
-                ptx::mma_bf16(dt, pd, ql, idesc, 1u);
-                ptx::mma_bf16(dt, pl, qd, idesc, 1u);
+              for (int kk = 0; kk < PK / 16; ++kk) {
+                if (16 * kk >= d.kw) break;  // positions past kw are zeros on both sides
+                const uint64_t pd = (FUSE && d.p_mn)
+                                        ? ptx::sw128_mnmajor_desc(pj + kk * 2 * MN_KGROUP, MN_HALF, MN_KGROUP)
+                                        : ptx::sw128_kmajor_desc(pj + kk * 32);
+                const uint64_t qd = ptx::sw128_kmajor_desc(qj + kk * 32);
+                ptx::mma_bf16(dt, pd, qd, idesc, (ks == c0 && j == 0 && kk == 0) ? 0u : 1u);
+                if (SPLIT) {
+                  const uint64_t pl = ptx::sw128_kmajor_desc(st + 2 * PBLOCK + kk * 32);
+                  const uint64_t ql = ptx::sw128_kmajor_desc(st + 3 * PBLOCK + kk * 32);
+                  ptx::mma_bf16(dt, pd, ql, idesc, 1u);
+                  ptx::mma_bf16(dt, pl, qd, idesc, 1u);
+                }
               }
             }
             ptx::mma_commit(ptx::smem_addr(&x.empty[s]));
+            if (FUSE == 2) ptx::mma_commit(ptx::smem_addr(&x.qempty[qs]));
           }
           if (!ok) break;
           ptx::mma_commit(ptx::smem_addr(&x.acc_full[b]));
@@ -768,7 +1100,112 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       ptx::mma_commit(ptx::smem_addr(&x.final_bar));
       ptx::mbar_wait(ptx::smem_addr(&x.final_bar), 0u, status);
     }
-  } else if (FUSE && warp < Cf::EPI0) {
+  } else if (FUSE == 2 && warp == 2) {
+    // ------------------------------------------------------------ P box loads
+    // one box per slab into the staging ring, as far ahead of the rounding
+    // as the ring's bytes and its XBOXES barrier pairs allow; the box's
+    // coordinates are the mixed-radix digits of its first row and first
+    // shared index over P's legs
+    if (lane == 0) {
+      const uint32_t xs0 = ptx::smem_addr(xstage);
+      uint32_t gx = 0, old = 0;  // next box; oldest box not known to be rounded
+      uint64_t v = 0, vs[XBOXES];
+      for (int q = 0; q < XBOXES; ++q) vs[q] = 0;
+      UnitSeq<S> us = unit_seq(x, unit_ctr, status, total_units, 1);
+      int64_t u = us.first(), un = 0;
+      TmaDesc dn = load_tma(descs, map, u >= 0 ? u : 0);
+      for (; u >= 0 && !x.abort; u = un) {
+        const TmaDesc d = dn;
+        un = us.next();
+        if (un >= 0) dn = load_tma(descs, map, un);
+        const GUnit g = gunit(d, u - d.tile_begin);
+        // the unit's first box by division, the next ones by stepping the
+        // shared legs' coordinates like an odometer (no division per slab)
+        int32_t c[5];
+        const uint32_t r0 = (uint32_t)g.p0, k0 = (uint32_t)g.ks0 * (uint32_t)d.kw;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) c[i] = (int32_t)((((d.bkmask >> i) & 1) ? k0 : r0) / d.bplace[i] % d.bdim[i]);
+        const uint32_t bytes = (uint32_t)(d.ph * d.kw * d.nsb * 4);
+        bool ok = true;
+        for (int ks = 0; ks < g.nks; ks += d.nsb, ++gx) {
+          if (ks > 0) {
+            int32_t add = d.bkstep;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              if (i < d.bk0 || i > d.bk1 || add == 0) continue;
+              c[i] += add;
+              add = 0;
+              if (c[i] >= (int32_t)d.bdim[i]) {
+                c[i] -= (int32_t)d.bdim[i];
+                add = 1;
+              }
+            }
+          }
+          // room for the box: the boxes it would overwrite, and the one whose
+          // barriers it takes, have been rounded
+          const uint64_t start = ring_take(v, bytes);
+          while (old < gx && (gx - old >= (uint32_t)XBOXES || start + bytes - vs[old % XBOXES] > XRING)) {
+            if (!ptx::mbar_wait(ptx::smem_addr(&x.xempty[old % XBOXES]), (old / XBOXES) & 1u, status)) {
+              ok = false;
+              break;
+            }
+            ++old;
+          }
+          if (!ok) break;
+          const int sl = (int)(gx % XBOXES);
+          vs[sl] = start;
+          const uint32_t xf = ptx::smem_addr(&x.xfull[sl]);
+          ptx::mbar_arrive_expect_tx(xf, bytes);
+          ptx::tma_load_5d(xs0 + (uint32_t)(start & (XRING - 1)), d.tmap, c[0], c[1], c[2], c[3], c[4], xf);
+        }
+        if (!ok) {
+          x.abort = 1;
+          break;
+        }
+      }
+      // boxes still in flight land before the CTA can exit
+      for (uint32_t q = old; q < gx; ++q) ptx::mbar_wait(ptx::smem_addr(&x.xfull[q % XBOXES]), (q / XBOXES) & 1u, status);
+    }
+  } else if (FUSE == 2 && warp < Cf::EPI0) {
+    // ------------------------------------------------------------ rounding
+    const int cw = warp - 2 - Cf::TMAW;
+    const uint32_t xs0 = ptx::smem_addr(xstage);
+    const uint32_t grp = (uint32_t)(cw / Cf::RW);  // this warp rounds boxes grp, grp + RGROUPS, ..
+    const int wi = cw % Cf::RW;
+    uint32_t gx = 0;
+    uint64_t v = 0;  // the ring positions, taken in the TMA warp's order
+    bool ok = true;
+    UnitSeq<S> us = unit_seq(x, unit_ctr, status, total_units, 3);
+    int64_t u = us.first(), un = 0;
+    RoundDesc dn = load_round(descs, map, u >= 0 ? u : 0);
+    for (; u >= 0 && ok && !x.abort; u = un) {
+      const RoundDesc d = dn;
+      un = us.next();
+      if (un >= 0) dn = load_round(descs, map, un);
+      const GUnit g = gunit(d, u - d.tile_begin);
+      const uint32_t bytes = (uint32_t)(d.ph * d.kw * d.nsb * 4);
+      for (int ks = 0; ks < g.nks; ks += d.nsb, ++gx) {
+        const uint64_t start = ring_take(v, bytes);
+        if (gx % Cf::RGROUPS != grp) continue;
+        const int sl = (int)(gx % XBOXES), s = (int)(gx % S);
+        const bool w = ptx::mbar_wait(ptx::smem_addr(&x.xfull[sl]), (gx / XBOXES) & 1u, status) &&
+                       ptx::mbar_wait(ptx::smem_addr(&x.empty[s]), ((gx / S) & 1u) ^ 1u, status);
+        if (!__all_sync(0xffffffffu, w)) {
+          ok = false;
+          break;
+        }
+        round_box<Cf::RW>(d.p_mn, d.ph, d.kw, d.nsb, wi, lane, xs0 + (uint32_t)(start & (XRING - 1)),
+                          stage0 + (uint32_t)s * Cf::STAGE_BYTES);
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::mbar_arrive(ptx::smem_addr(&x.full[s]));
+          ptx::mbar_arrive(ptx::smem_addr(&x.xempty[sl]));
+        }
+      }
+    }
+    if (!ok) x.abort = 1;
+  } else if (FUSE == 1 && warp < Cf::EPI0) {
     // ------------------------------------------------------------ converters
     const int cw = warp - 2;
     const uint32_t xs0 = ptx::smem_addr(xstage);
@@ -829,12 +1266,17 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
     const int grp = (warp - Cf::EPI0) >> 2;  // column group of this warp (eight warps: two groups)
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     uint32_t gc = 0;
-    EpiDesc dn = load_epi(single, descs, map, blockIdx.x < total_units ? blockIdx.x : 0);
-    for (int64_t u = blockIdx.x; u < total_units && !x.abort; u += gridDim.x) {
+    UnitSeq<S> us = unit_seq(x, unit_ctr, status, total_units, unit_ctr ? 3 : 0);
+    int64_t u = us.first(), un = 0;
+    EpiDesc dn = load_epi(single, descs, map, u >= 0 ? u : 0);
+    for (; u >= 0 && !x.abort; u = un) {
       const EpiDesc d = dn;
-      if (u + gridDim.x < total_units) dn = load_epi(single, descs, map, u + gridDim.x);
+      un = us.next();
+      if (un >= 0) dn = load_epi(single, descs, map, un);
       const GUnit g = gunit(d, u - d.tile_begin);
       const int64_t i = g.p0 + quad * 32 + lane;            // row of P this thread owns
+      // rows of this tile: ph of them (fewer at P's end)
+      const int64_t rend = d.RP - g.p0 < d.ph ? d.RP : g.p0 + d.ph;
       const int64_t qcols = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
       // columns of the tile this warp drains: eight warps split the tile
       // width in two (the 64-column reads of the 16x256b shape: in 64s)
@@ -857,7 +1299,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
       // 16-byte stores along a row of C, or, with the roles swapped, one
       // store per column with the warp's lanes on consecutive addresses.
       auto emit = [&](int col, const float* r) {
-        if (i >= d.RP) return;
+        if (i >= rend) return;
         const int64_t nrem = qcols - col;
         if (d.cj == 1) {
           float* dst = C + i * d.ci + g.q0 + col;
@@ -899,7 +1341,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         for (int it = 0; it < 8; ++it) {
           const int rr = it * 4 + (lane >> 3);
           const int64_t row = g.p0 + quad * 32 + rr;
-          if (row >= d.RP || 4 * q >= nrem) continue;
+          if (row >= rend || 4 * q >= nrem) continue;
           const float4 v4 = *reinterpret_cast<const float4*>(tr + rr * 32 + ((q ^ (rr & 7)) << 2));
           emit4(C + row * d.ci + g.q0 + col + 4 * q, vec, nrem - 4 * q, accumulate, v4.x, v4.y, v4.z, v4.w);
         }
@@ -920,7 +1362,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int64_t rr = row + 8 * e;
-            if (rr >= d.RP || c >= qcols) continue;
+            if (rr >= rend || c >= qcols) continue;
             float* dst = C + rr * d.ci + g.q0 + c;
             const float a = r[4 * j + 2 * e], bq = r[4 * j + 2 * e + 1];
             if (accumulate) {
@@ -1052,7 +1494,7 @@ int sm_count() {
 
 template <int SPLIT, int FUSE>
 int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* map, const PackJob* jobs,
-                int64_t units, cudaStream_t s) {
+                int64_t units, cudaStream_t s, uint32_t* unit_ctr = nullptr) {
   const size_t smem = gemm_smem_bytes<SPLIT, FUSE>();
   static bool attr = false;
   if (!attr) {
@@ -1064,7 +1506,7 @@ int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* ma
   const int64_t sms = sm_count();
   const unsigned grid = (unsigned)(units < sms ? units : sms);
   packed_gemm_kernel<SPLIT, FUSE>
-      <<<grid, GCfg<SPLIT, FUSE>::THREADS, smem, s>>>(single, descs, map, jobs, units, status_word());
+      <<<grid, GCfg<SPLIT, FUSE>::THREADS, smem, s>>>(single, descs, map, jobs, units, unit_ctr, status_word());
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
@@ -1078,14 +1520,17 @@ int launch_pack(const PackJob* jobs, const PackUnit* units, int64_t nunits, cuda
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 
-int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, int prec, cudaStream_t s) {
+int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, int prec, uint32_t* unit_ctr,
+                       cudaStream_t s) {
   if (units <= 0) return TN_OK;
   if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
+  // the launch's CTAs claim units from this counter
+  if (unit_ctr && cudaMemsetAsync(unit_ctr, 0, sizeof(uint32_t), s) != cudaSuccess) return TN_ERR_CUDA;
   GemmDesc none;
   memset(&none, 0, sizeof(none));
-  if (prec == TN_PREC_BF16) return launch_gemm<0, 0>(none, descs, map, nullptr, units, s);
-  if (prec == TN_PREC_BF16X3) return launch_gemm<1, 0>(none, descs, map, nullptr, units, s);
-  return TN_ERR_ARG;
+  if (prec == TN_PREC_BF16) return launch_gemm<0, 0>(none, descs, map, nullptr, units, s, unit_ctr);
+  return launch_gemm<1, 0>(none, descs, map, nullptr, units, s, unit_ctr);
 }
 
 int launch_fused_gemm(const GemmDesc* descs, const int32_t* map, const PackJob* jobs, int64_t units,
@@ -1096,6 +1541,17 @@ int launch_fused_gemm(const GemmDesc* descs, const int32_t* map, const PackJob* 
   GemmDesc none;
   memset(&none, 0, sizeof(none));
   return launch_gemm<0, 1>(none, descs, map, jobs, units, s);
+}
+
+int launch_tma_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, uint32_t* unit_ctr, cudaStream_t s) {
+  if (units <= 0) return TN_OK;
+  if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (!descs || !map || !unit_ctr) return TN_ERR_ARG;
+  // the launch's CTAs claim units from this counter
+  if (cudaMemsetAsync(unit_ctr, 0, sizeof(uint32_t), s) != cudaSuccess) return TN_ERR_CUDA;
+  GemmDesc none;
+  memset(&none, 0, sizeof(none));
+  return launch_gemm<0, 2>(none, descs, map, nullptr, units, s, unit_ctr);
 }
 
 namespace {
@@ -1109,6 +1565,7 @@ PackJob make_job(const ContractDesc& d, const float* src, int64_t R, int nr, con
   j.R = R;
   j.K = d.K;
   j.tiles = (int32_t)((R + PR - 1) / PR);
+  j.kw = PK;
   j.slabs = (int32_t)((d.K + PK - 1) / PK);
   j.block_bytes = R >= PR ? PBLOCK : ((R + 7) & ~int64_t(7)) * 128;
   j.rg = R >= PR ? PR : (int32_t)((R + 7) & ~int64_t(7));
@@ -1174,12 +1631,192 @@ GemmDesc make_gemm(const ContractDesc& d, const PackJob& ja, const PackJob& jb, 
   g.slabs_per_split = (int32_t)(d.k_per_split / PK);
   g.pjob = -1;
   g.p_mn = 0;
+  g.ph = PR;
+  g.kw = PK;
+  g.bkmask = 0;
+  g.nsb = 1;
+  g.tmap = nullptr;
+  g.tmap_idx = -1;
   g.K = d.K;
   *swapped = swap;
   return g;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when the driver does not provide it.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
 }  // namespace
+
+bool plan_tma_box(const ContractDesc& d, TmaBox* box, TmaMap* map) {
+  static_assert(sizeof(TmaMap) == sizeof(CUtensorMap), "tensor map size");
+  const bool swap = p_is_b(d);
+  const float* src = swap ? d.B : d.A;
+  if (!src || (reinterpret_cast<uintptr_t>(src) & 15) || d.K <= 0) return false;
+  // device memory only (host-resident operands keep the converters' copies)
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, src) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (pa.type != cudaMemoryTypeDevice) return false;
+  // P's legs of extent > 1: free legs in the order they flatten into the row
+  // index, shared legs in the order they flatten into k (last fastest)
+  struct Leg {
+    int64_t dim, str, place;
+    bool k;
+  };
+  Leg rl[TN_MAX_RANK], kl[TN_MAX_RANK];
+  int nr = 0, nk = 0;
+  const int nfree = swap ? d.nn : d.nm;
+  const int32_t* fdim = swap ? d.ndim : d.mdim;
+  const int64_t* fstr = swap ? d.nstr : d.mstr;
+  const int64_t* kstr = swap ? d.kstrB : d.kstrA;
+  int64_t place = 1;
+  for (int q = nfree - 1; q >= 0; --q) {
+    if (fdim[q] > 1) rl[nr++] = Leg{fdim[q], fstr[q], place, false};
+    place *= fdim[q];
+  }
+  place = 1;
+  for (int q = d.nk - 1; q >= 0; --q) {
+    if (d.kdim[q] > 1) kl[nk++] = Leg{d.kdim[q], kstr[q], place, true};
+    place *= d.kdim[q];
+  }
+  // rl / kl now run fastest first
+  if (nr + nk == 0 || nr + nk > 5) return false;
+  // box extents, fastest leg first: whole legs while they fit, then the
+  // largest divisor of the next leg that fits, then 1 -- so the boxes tile
+  // the flattened index exactly, each one a run of consecutive rows (or k)
+  auto extents = [](const Leg* l, int n, int64_t cap, int64_t* b) -> int64_t {
+    int64_t e = 1;
+    int q = 0;
+    for (; q < n && e * l[q].dim <= cap; ++q) {
+      b[q] = l[q].dim;
+      e *= l[q].dim;
+    }
+    if (q < n) {
+      int64_t m = cap / e;
+      while (l[q].dim % m) --m;
+      b[q] = m;
+      e *= m;
+      for (++q; q < n; ++q) b[q] = 1;
+    }
+    return e;
+  };
+  int64_t rb[TN_MAX_RANK], kb[TN_MAX_RANK];
+  const int64_t H = extents(rl, nr, PR, rb), W = extents(kl, nk, PK, kb);
+  const int64_t RQ = swap ? d.M : d.N;
+  // narrow boxes on a long k would multiply Q's packed slabs, short ones on
+  // many rows the work units
+  const int64_t RP = swap ? d.N : d.M;
+  if ((W < 32 && W < d.K) || (H < 32 && H < RP)) return false;
+  // the unit-stride leg leads: the last shared leg (tile row-major along k)
+  // or else the last free leg (tile row-major along the rows)
+  int mode = 0;
+  if (nk && kl[0].str == 1) mode = 1;
+  else if (nr && rl[0].str == 1) mode = 2;
+  if (!mode) return false;
+  // P with few rows, staged row-major along k: one box covers nsb
+  // consecutive slabs (k extent nsb * W, a box of its own), its k-blocks
+  // stacked as nsb x ceil8(H) rows of the bf16 tile; bounded by the tile's
+  // 128 rows, the rounding's 8 loads per lane, Q's 8 KB slot and the TMA's
+  // 256 elements per dimension
+  int64_t nsb = 1;
+  if (mode == 1) {
+    const int64_t H8 = (H + 7) & ~int64_t(7), ni = (H + 15) / 16, qblk = ((RQ + 7) & ~int64_t(7)) * 128;
+    int64_t cap = std::min<int64_t>(std::min<int64_t>(PR / H8, 8 / ni), std::min<int64_t>(8192 / qblk, d.K / W));
+    for (int64_t c = cap; c > 1; --c) {
+      int64_t kb2[TN_MAX_RANK];
+      if (extents(kl, nk, c * W, kb2) != c * W) continue;
+      bool fits = true;
+      for (int q = 0; q < nk; ++q) fits = fits && kb2[q] <= 256;
+      if (!fits) continue;
+      nsb = c;
+      for (int q = 0; q < nk; ++q) kb[q] = kb2[q];
+      break;
+    }
+  }
+  // tensor-map dimensions, fastest first
+  Leg dl[5];
+  int64_t db[5];
+  int n = 0;
+  const Leg* first = mode == 1 ? kl : rl;
+  const Leg* second = mode == 1 ? rl : kl;
+  const int64_t* fb = mode == 1 ? kb : rb;
+  const int64_t* sb = mode == 1 ? rb : kb;
+  const int n1 = mode == 1 ? nk : nr, n2 = mode == 1 ? nr : nk;
+  for (int q = 0; q < n1; ++q, ++n) {
+    dl[n] = first[q];
+    db[n] = fb[q];
+  }
+  for (int q = 0; q < n2; ++q, ++n) {
+    dl[n] = second[q];
+    db[n] = sb[q];
+  }
+  // TMA: the innermost box extent a multiple of 16 bytes (so is every
+  // coordinate along it: multiples of that extent), other strides too
+  if (db[0] % 4) return false;
+  int64_t span = 1;
+  for (int q = 0; q < n; ++q) {
+    if (q > 0 && (dl[q].str % 4 || dl[q].str <= 0)) return false;
+    span += (dl[q].dim - 1) * dl[q].str;
+  }
+  cuuint64_t gdim[5], gstr[4];
+  cuuint32_t bdim[5], estr[5] = {1, 1, 1, 1, 1};
+  const int64_t pad_str = (span + 3) / 4 * 4;  // unit padding dimensions: any multiple of 16 bytes
+  box->kmask = 0;
+  for (int q = 0; q < 5; ++q) {
+    const bool real = q < n;
+    gdim[q] = real ? (cuuint64_t)dl[q].dim : 1;
+    bdim[q] = real ? (cuuint32_t)db[q] : 1;
+    if (q > 0) gstr[q - 1] = (cuuint64_t)(4 * (real ? dl[q].str : pad_str));
+    box->dim[q] = real ? (uint32_t)dl[q].dim : 1;
+    box->place[q] = real ? (uint32_t)dl[q].place : 1;
+    if (real && dl[q].k) box->kmask |= 1 << q;
+  }
+  box->ph = (int32_t)H;
+  box->kw = (int32_t)W;
+  box->nsb = (int32_t)nsb;
+  box->p_mn = mode == 2 ? 1 : 0;
+  // the shared legs' map dimensions, fastest first, and the first one whose
+  // box is not the whole leg: the next slab advances it by its box extent
+  box->k0 = box->k1 = -1;
+  box->kstep = 0;
+  for (int q = 0; q < n; ++q) {
+    if (!dl[q].k) continue;
+    box->k1 = q;
+    if (box->k0 < 0 && db[q] < dl[q].dim) {
+      box->k0 = q;
+      box->kstep = (int32_t)db[q];
+    }
+  }
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  CUtensorMap m;
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(src), gdim, gstr, bdim, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  memcpy(map->bytes, &m, sizeof(m));
+  return true;
+}
 
 // Host side: pack jobs (two per contraction), their block units, and the GEMM
 // descriptors, with block storage as offsets in the plan's packed region.
@@ -1217,14 +1854,45 @@ void fused_tables(const ContractDesc& d, std::vector<int32_t>* tab, int64_t* rta
 }
 
 int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,
-                int64_t ktab_off, PackedPlan* pp) {
-  const PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
-  const PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
+                int64_t ktab_off, const TmaBox* box, int64_t map, PackedPlan* pp) {
+  PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
+  PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
   if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
     return TN_ERR_UNSUPPORTED;
   bool swap = false;
   GemmDesc g = make_gemm(d, ja, jb, sc.q_tile, &swap);
-  fuse = fuse && prec == TN_PREC_BF16 && g.RQ <= PR / 2 && rtab_off >= 0 && ktab_off >= 0;
+  fuse = fuse && prec == TN_PREC_BF16 && g.RQ <= PR / 2 &&
+         ((rtab_off >= 0 && ktab_off >= 0) || (box && map >= 0));
+  const bool tma = fuse && box && map >= 0;
+  if (tma) {
+    // P in boxes of box->ph rows x box->kw shared indices; Q packed in
+    // slabs of the same width, so slab ks of both covers k = ks * kw ..
+    PackJob& jq = swap ? ja : jb;
+    jq.kw = box->kw;
+    jq.slabs = (int32_t)(d.K / box->kw);
+    if ((int64_t)jq.tiles * jq.slabs > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+    g.ph = box->ph;
+    g.kw = box->kw;
+    g.tiles_p = (int32_t)(g.RP / box->ph);
+    g.slabs = jq.slabs;
+    // the unit's k range: about as many shared indices as the schedule's,
+    // in whole boxes
+    int64_t per = std::max<int64_t>(1, d.k_per_split / box->kw);
+    per = (per + box->nsb - 1) / box->nsb * box->nsb;
+    g.slabs_per_split = (int32_t)std::min<int64_t>(per, g.slabs);
+    g.nsb = box->nsb;
+    g.splits = (int32_t)((g.slabs + g.slabs_per_split - 1) / g.slabs_per_split);
+    g.p_mn = box->p_mn;
+    g.bkmask = box->kmask;
+    for (int i = 0; i < 5; ++i) {
+      g.bdim[i] = box->dim[i];
+      g.bplace[i] = box->place[i];
+    }
+    g.bk0 = box->k0;
+    g.bk1 = box->k1;
+    g.bkstep = box->kstep;
+    g.tmap_idx = map;
+  }
   // a fused contraction packs Q only: P (A, or B when swapped) is read by
   // the fused GEMM's converters
   const bool pack_a = !(fuse && !swap), pack_b = !(fuse && swap);
@@ -1271,7 +1939,7 @@ int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool 
   g.P_lo = split ? (int64_t)(swap ? off_blo : off_alo) - (int64_t)g.P_off : 0;
   g.Q_lo = split ? (int64_t)(swap ? off_alo : off_blo) - (int64_t)g.Q_off : 0;
   g.pjob = fuse ? ja_idx + (swap ? 1 : 0) : -1;
-  g.p_mn = fuse && pp->jobs[(size_t)ja_idx + (swap ? 1 : 0)].vec4 == 2 ? 1 : 0;
+  if (!tma) g.p_mn = fuse && pp->jobs[(size_t)ja_idx + (swap ? 1 : 0)].vec4 == 2 ? 1 : 0;
   pp->gemms.push_back(g);
   return TN_OK;
 }

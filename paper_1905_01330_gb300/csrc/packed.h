@@ -12,11 +12,12 @@
 namespace tn {
 
 // One operand of one contraction, packed K-major: block (tile, slab) holds
-// rows tile*128 .. +127 and shared indices slab*64 .. +63 as bf16 in the
-// 128-byte-swizzled layout (8-row atoms of 1 KB), at hi + (tile * slabs +
-// slab) * block_bytes. Rows past the operand's end are not stored (a block
-// of a 1..127-row operand is ceil8(rows) * 128 bytes); shared indices past K
-// are stored as zeros.
+// rows tile*128 .. +127 and shared indices slab*kw .. +kw-1 (kw = 64 unless
+// the other operand is read by the fused TMA GEMM) as bf16 in the
+// 128-byte-swizzled layout (8-row atoms of 1 KB, 64 positions per row), at
+// hi + (tile * slabs + slab) * block_bytes. Rows past the operand's end are
+// not stored (a block of a 1..127-row operand is ceil8(rows) * 128 bytes);
+// positions past kw or past K are stored as zeros.
 struct PackJob {
   const float* src;
   uint8_t* hi;            // device: bf16(x) blocks
@@ -30,6 +31,9 @@ struct PackJob {
                           // elements from a 4-aligned index are contiguous and 16-byte
                           // aligned), 0 none
   int32_t rg, nbv;        // pack: rows per block, and blocks packed at once (nbv * rg <= 128)
+  int32_t kw;             // shared indices per slab: 64, or the width of the TMA box of the
+                          // fused TMA GEMM's P (positions kw .. 63 of a slab are zeros)
+  int32_t pad_kw;
   const int32_t* rtab;    // device (fused P only): source offset of every row, R entries
   const int32_t* ktab;    // and of every shared index, K entries (32-byte aligned, zero-padded
                           // to whole 64-wide slabs)
@@ -66,8 +70,41 @@ struct GemmDesc {
                           // and rounded inside the GEMM, never packed); -1: P is packed
   int32_t p_mn;           // fused, P contiguous along its rows: the P tile is staged
                           // MN-major (rows fastest), else K-major
-  int32_t pad2;
+  int32_t ph;             // rows of P per tile: 128, or the TMA box's height (fused TMA GEMM)
+  int32_t kw;             // shared indices per slab: 64, or the TMA box's width
+  int32_t bkmask;         // fused TMA GEMM: bit i set when dimension i of P's tensor map
+                          // walks a shared leg (else a free leg, or a unit padding dimension)
+  uint32_t bdim[5];       // extent of each tensor-map dimension, and the place value of its
+  uint32_t bplace[5];     // leg in the flattened row or shared index (coordinate i of the box
+                          // at row r0, shared index k0 = (r0 or k0) / bplace[i] % bdim[i])
+  int32_t bk0, bk1, bkstep;  // the next box: bkstep more along map dimension bk0, carries
+                             // into the dimensions up to bk1 (the shared legs)
+  int32_t nsb;            // fused TMA GEMM: slabs per box (P with few rows: the staged
+                          // tile holds nsb k-blocks of ceil8(ph) rows), else 1
+  const void* tmap;       // device: P's tensor map (fused TMA GEMM), else null
+  int64_t tmap_idx;       // host: its index in the plan's tensor-map list, -1 none
 };
+
+// The fused TMA GEMM's tiling of a contraction's P: tiles of ph rows x kw
+// shared indices, each one box of P's tensor map (the leg permutation is done
+// by the TMA unit: the box's dimensions are P's legs, ordered so that the
+// staged tile is row-major along k, or along the rows when P is contiguous
+// along them).
+struct TmaBox {
+  int32_t ph, kw, p_mn, kmask;
+  uint32_t dim[5], place[5];
+  int32_t k0, k1, kstep, nsb;
+};
+// One encoded tensor map (the driver's 128-byte CUtensorMap, 64-byte aligned).
+struct alignas(64) TmaMap {
+  uint8_t bytes[128];
+};
+// Box tiling and tensor map of d's P for the fused TMA GEMM. False when P's
+// layout does not allow one (more than five legs of extent > 1, no unit
+// stride on its last free or last shared leg, strides or the innermost box
+// extent not multiples of 16 bytes, a box narrower than 32 shared indices on
+// a longer k, or no driver entry point to encode the map).
+bool plan_tma_box(const ContractDesc& d, TmaBox* box, TmaMap* map);
 
 // Schedule of the packed GEMM for one class of contractions: the output
 // tile width (rows of Q per unit), whether a spec with many tiles keeps each
@@ -96,8 +133,10 @@ struct PackedPlan {
 // would cost 4 more bytes per element than reading it once; P is then not
 // packed, and its job (with the offset tables at rtab_off / ktab_off) is kept
 // for the fused GEMM's converters (pjob).
+// box (or null): the contraction's TMA tiling, taken when it is fused; its
+// tensor map is entry `map` of the plan's list.
 int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,
-                int64_t ktab_off, PackedPlan* pp);
+                int64_t ktab_off, const TmaBox* box, int64_t map, PackedPlan* pp);
 
 // The operand on the MMA's 128-row side of contraction d: B when it has more
 // rows and A fewer than 128, else A.
@@ -118,10 +157,19 @@ size_t packed_single_bytes(const ContractDesc& d, int prec);
 // Upper bound of packed_single_bytes for an M x K by K x N contraction.
 size_t packed_scratch_bound(int64_t M, int64_t N, int64_t K, int prec);
 int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s);
-int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, int prec, cudaStream_t s);
+// unit_ctr (or null: units assigned statically): the device counter the
+// launch's CTAs claim units from (zeroed here, before the launch, on the same
+// stream).
+int launch_packed_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, int prec, uint32_t* unit_ctr,
+                       cudaStream_t s);
 // The fused GEMM (BF16): units whose P is read as float32 through jobs[pjob]
 // and rounded to bf16 in shared memory, Q packed.
 int launch_fused_gemm(const GemmDesc* descs, const int32_t* map, const PackJob* jobs, int64_t units,
                       cudaStream_t s);
+// The fused TMA GEMM (BF16): units whose P tiles are boxes of its tensor map
+// (GemmDesc::tmap), loaded as float32 and rounded to bf16 in shared memory;
+// its CTAs claim units from the device counter unit_ctr (zeroed here, before
+// the launch, on the same stream).
+int launch_tma_gemm(const GemmDesc* descs, const int32_t* map, int64_t units, uint32_t* unit_ctr, cudaStream_t s);
 
 }  // namespace tn

@@ -93,6 +93,30 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst_smem, const void* src
       : "memory");
 }
 
+// Tiled tensor load (TMA): the box of the tensor map at `map` (a generic
+// address of a 64-byte aligned CUtensorMap in global memory) whose first
+// element has coordinates c0 .. c4 (c0, along the unit-stride dimension, a
+// multiple of 16 bytes) into shared memory at dst (128-byte aligned),
+// completing its bytes on the mbarrier.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void* map, int32_t c0, int32_t c1, int32_t c2,
+                                            int32_t c3, int32_t c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];" ::"r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory accesses by 32-bit shared address: 16 bytes in, 8 bytes out.
+__device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
 // Asynchronous global -> shared copies (cp.async; completion tracked per
 // thread with commit / wait groups): 16 bytes (both addresses 16-byte
 // aligned; L2 only) or 4 bytes.

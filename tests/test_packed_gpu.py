@@ -157,13 +157,15 @@ def test_autotune_picks_a_schedule_and_caches_it(tn, prec):
 
 
 def test_fused_gemm_access_patterns(tn):
-    """BF16 contractions whose narrower operand has at most 64 rows take the
-    fused GEMM (the wider operand rounded to bf16 inside it, never packed). Cases
-    cover its converters' paths: the wider operand unit-stride along k
-    (16-byte copies), along its rows (4-byte copies with lanes on rows), with
-    no unit stride, at an address that is not 16-byte aligned (4-byte
-    fallback), on either side (A, or B with the roles swapped), row and k
-    tails, K < 8, many units per CTA, and split k ranges."""
+    """BF16 contractions whose narrower operand has at most 64 rows take a
+    fused GEMM (the wider operand rounded to bf16 inside it, never packed):
+    the TMA one when the wider operand's layout allows whole boxes, else the
+    one whose converters copy through offset tables. Cases cover the
+    converters' paths: the wider operand unit-stride along k (16-byte
+    copies), along its rows (16-byte copies of 4 rows), with no unit stride,
+    at an address that is not 16-byte aligned (4-byte fallback), on either
+    side (A, or B with the roles swapped), row and k tails, K < 8, many units
+    per CTA, and split k ranges; the aligned ones take the TMA GEMM."""
     base = torch.from_numpy(rand(60, (1 + 700 * 96,))).cuda()
     Au = base[1:].view(700, 96)                          # 4-byte aligned only
     Aunp = Au.cpu().numpy()
@@ -171,6 +173,7 @@ def test_fused_gemm_access_patterns(tn):
     Bx = Bfull[:, ::2]                                   # (40, 300), strides (600, 2): no unit stride
     cases = [
         (rand(50, (1000, 192)), [1], rand(51, (192, 40)), [0]),         # k unit stride, P = A
+        (rand(66, (2000, 100)), [1], rand(67, (100, 30)), [0]),         # ... no 16-byte TMA box (50 wide)
         (rand(52, (72, 900)), [0], rand(53, (72, 24)), [0]),            # rows unit stride (k outer)
         (Au, [1], rand(54, (96, 33)), [0], Aunp, None),                  # misaligned rows: 4-byte copies
         (rand(55, (24, 77)), [1], rand(56, (3000, 77)), [1]),           # swapped: P = B, k tail 13
@@ -189,7 +192,7 @@ def test_fused_gemm_access_patterns(tn):
         specs.append((At, list(la), Btt, list(lb), torch.empty(tn.result_shape(At, la, Btt, lb), device="cuda")))
         host.append((np.ascontiguousarray(Ah), la, np.ascontiguousarray(Bh), lb))
     plan = tn.GroupPlan(specs, prec="bf16")
-    assert "gemm_fused" in plan.launch_names()
+    assert "gemm_fused" in plan.launch_names() and "gemm_tma" in plan.launch_names()
     for rep in range(2):   # twice: the second run reuses stale shared memory and staging
         for sp in specs:
             sp[4].fill_(float("nan"))
@@ -244,3 +247,53 @@ def test_staged_plan_from_pinned_host(tn):
             B = hi[in_offs[2 * i + 1]:in_offs[2 * i + 1] + in_sizes[2 * i + 1]].reshape(sb)
             C = host_out[out_offs[i]:out_offs[i] + int(np.prod(outs[i]))].view(outs[i])
             check(C, A, la, B, lb, "bf16")
+
+
+def test_tma_gemm_box_layouts(tn):
+    """The fused TMA GEMM: each tile of the wider operand P is one box of its
+    tensor map, the box's dimensions P's legs (whole legs from the fastest,
+    then a divisor of the next), staged row-major along k (P unit-stride
+    along its last shared leg) or along the rows (unit stride on its last
+    free leg), the map's strides in an order that is not the memory order
+    when free and shared legs interleave. Cases: boxes of 125, 100 and 96
+    rows (tiles of fewer than 128 rows, one odd), 36-, 40- and 48-wide slabs (Q packed
+    in slabs of that width), boxes spanning two and three legs, a rank-5
+    operand over all five dimensions of the map, P = B, a single-row Q,
+    split k ranges with atomically accumulated results, and many units per
+    CTA; P with few rows and a long k, whose boxes each cover several slabs
+    (the staged tile holds them as k-blocks of ceil8(rows) rows, Q's slot
+    their consecutive packed blocks). All in one plan, which then has only
+    the TMA GEMM; run twice over NaN-filled results (the second run reuses
+    stale staging)."""
+    cases = [
+        (rand(70, (1000, 192)), [1], rand(71, (192, 40)), [0]),          # 125-row boxes, k 3 x 64
+        (rand(72, (72, 900)), [0], rand(73, (72, 24)), [0]),             # rows unit stride: 100 x 36 boxes
+        (rand(74, (48, 24, 32)), [2, 0], rand(75, (32, 8, 48)), [0, 2]), # k box over two legs, strides out of order
+        (rand(76, (24, 48, 40)), [2], rand(77, (40, 16)), [0]),          # row box: 48 x 2 of (24, 48)
+        (rand(78, (64, 8, 24)), [0], rand(79, (64, 32)), [0]),           # rows fastest over two legs: 24 x 4
+        (rand(80, (16, 96)), [1], rand(81, (96, 2048)), [0]),            # P = B, rows fastest, 48-wide slabs
+        (rand(82, (100, 6000)), [1], rand(83, (6000, 50)), [0]),         # 100 slabs of 60: split k ranges
+        (rand(84, (4096,)), [0], rand(85, (4096, 200)), [0]),            # Q of one row
+        (rand(86, (8, 16, 8, 24, 8)), [4, 1], rand(87, (16, 8, 12)), [1, 0]),  # rank 5: five map dims
+        (rand(88, (20000, 64)), [1], rand(89, (64, 60)), [0]),           # 160 tiles: CTAs run several
+        # few rows of P: one box covers several slabs, stacked as k-blocks
+        (rand(90, (32, 96, 64)), [1, 2], rand(91, (96, 64, 16)), [0, 1]),  # 32 rows, 4 slabs over two k legs
+        (rand(92, (8, 4096)), [1], rand(93, (24, 4096)), [1]),           # P = B, 24 rows, 4 slabs per box
+        (rand(94, (16, 65536)), [1], rand(95, (65536,)), [0]),           # a matrix-vector product, split k
+        (rand(96, (4, 8, 2048)), [2], rand(97, (2048, 8)), [0]),         # rows over two legs
+        (rand(98, (20, 8192)), [1], rand(99, (8192, 3)), [0]),           # 20 rows: k-blocks 24 rows apart
+    ]
+    specs = []
+    for A, la, B, lb in cases:
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        specs.append((At, list(la), Bt, list(lb), torch.empty(tn.result_shape(At, la, Bt, lb), device="cuda")))
+    plan = tn.GroupPlan(specs, prec="bf16")
+    assert [n for n in plan.launch_names() if n not in ("zero", "pack")] == ["gemm_tma"]
+    for rep in range(2):
+        for sp in specs:
+            sp[4].fill_(float("nan"))
+        plan.run()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == 0
+        for (A, la, B, lb), sp in zip(cases, specs):
+            check(sp[4], A, la, B, lb, "bf16")
