@@ -158,15 +158,18 @@ void tn_group_plan_destroy(tn_group_plan* plan);
  *     fit in the 4 MiB array; larger requests return TN_ERR_UNSUPPORTED and
  *     launch nothing.
  *   The first call on a device looks up the array's device address there
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (cudaGetSymbolAddress). A call on a stream that is being captured into a
+ *   CUDA graph returns TN_ERR_UNSUPPORTED and enqueues nothing: the work list
+ *   is copied from host staging arrays that the next call overwrites, so a
+ *   captured copy would replay another call's work list.
  *   Every GPU that loads libtn.so holds the array until the process exits.
  *   All calls share the array: calls whose work overlaps on the GPU (other
  *   streams or host threads) race on it; calls on one stream are ordered.
  *   The work list goes to the array in three copies from the library's
  *   pageable host staging arrays; a copy from pageable memory may block the
  *   calling thread until the stream's earlier work has finished.
- * Errors: as tn_group_plan_create, plus TN_ERR_UNSUPPORTED (too large) and
- * TN_ERR_CUDA.
+ * Errors: as tn_group_plan_create, plus TN_ERR_UNSUPPORTED (too large, or
+ * the stream is capturing) and TN_ERR_CUDA.
  */
 int tn_contract_grouped_static(const tn_contract_spec* specs, int nspecs, int prec, void* stream);
 

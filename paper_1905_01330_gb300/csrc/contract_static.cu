@@ -60,11 +60,16 @@ extern "C" int tn_contract_grouped_static(const tn_contract_spec* specs, int nsp
   if (nspecs < 0 || (nspecs > 0 && !specs)) return TN_ERR_ARG;
   if (prec != TN_PREC_FP32 && prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
   if (nspecs > STATIC_MAX_SPECS) return TN_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The work list is copied from host staging arrays that the next call
+  // overwrites: a captured copy would replay whatever list was staged last.
+  // So a capturing stream is refused before anything is enqueued.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return TN_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> guard(h_lock);
   unsigned char* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != TN_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   int nd = 0, nz = 0;
   for (int i = 0; i < nspecs; ++i) {

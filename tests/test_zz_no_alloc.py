@@ -129,3 +129,32 @@ def test_static_grouped_rejects_work_list_larger_than_array(tn):
     torch.cuda.synchronize()
     assert tn.sync_status() == 0
     assert torch.equal(C1, torch.full_like(C1, 16.0))
+
+
+def test_static_grouped_refuses_a_capturing_stream(tn):
+    # The work list is copied from host staging arrays the next call
+    # overwrites, so a call on a capturing stream is refused with nothing
+    # enqueued; the capture itself stays valid and the stream usable.
+    fn = static_fn(tn)
+    A = torch.ones(64, 16, device="cuda")
+    B = torch.ones(16, 32, device="cuda")
+    C = torch.full((64, 32), float("nan"), device="cuda")
+    D = torch.zeros(8, device="cuda")
+    arr = spec_array(tn, [(A, [1], B, [0])], [C])
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        rc = fn(arr, 1, tn.PREC["fp32"], ctypes.c_void_p(side.cuda_stream))
+        D.add_(1.0)
+    assert rc == UNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.isnan(C).all().item()
+    assert torch.equal(D, torch.ones_like(D))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert fn(arr, 1, tn.PREC["fp32"], stream) == 0
+    torch.cuda.synchronize()
+    assert tn.sync_status() == 0
+    assert torch.equal(C, torch.full_like(C, 16.0))
