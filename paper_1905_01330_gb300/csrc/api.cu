@@ -30,7 +30,7 @@ int* status_word() {
 
 // One contraction alone should still fill the GPU when its K allows: ask for
 // at least two work units per SM.
-static int64_t min_units_single() {
+int64_t min_units_single() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;

@@ -18,6 +18,7 @@
 // 2^-e, e the binary exponent of that maximum (the contractions are linear in
 // L, so scaling T2 scales everything downstream), and adds e ln 2 to the
 // float64 log-scale.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -407,6 +408,154 @@ __global__ void __launch_bounds__(256) mpo_step_ii_kernel(const __grid_constant_
               blockIdx.x == 0 && threadIdx.x == 0);
 }
 
+// Step (ii) written straight into step (iii)'s packed operand (BF16 and
+// BF16X3 sweeps whose extended MPO has (bond) x d <= 8 on both sides of every
+// site). T2[w', s', a', b] = 2^-e sum_{w,s} W'[w, w', s, s'] T1[w, a', s, b]
+// is the first operand P of (iii) with row r = w' Db + b and shared index
+// k = s' ps + a' pa (the planner's order of the shared legs); it is rounded
+// to bf16 (and its remainder to bf16 for BF16X3) and stored as whole MN-major
+// 128-row x 64-k blocks, block (tile, slab) at hi + (tile slabs + slab) 16 KB.
+// The float32 T2 is never written to memory and no pack pass reads it back.
+// Positions past the last shared index are written as zeros (rows past R
+// are left as they are: each row of the product depends on its own row of P
+// only, and the GEMM discards those rows).
+struct StepIIPack {
+  const float* T1;          // [wa][Da][d][Db], row-major
+  const float* W;           // the site's extended MPO [wa][wb][d][d]
+  const unsigned* maxbits;  // bits of the largest |L| (null: no rescale)
+  double* lg;               // float64 log-scale: e ln 2 added
+  uint8_t* hi;
+  uint8_t* lo;              // BF16X3, else null
+  int32_t Da, Db, wa, wb, d;
+  int32_t tiles, slabs;     // of P: rows wb Db, shared indices d Da
+  int32_t ps, pa;           // place values of s' and a' in the shared index
+};
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ float bf16_lo_rest(float x) {
+  return x - __bfloat162float(__float2bfloat16_rn(x));
+}
+
+__global__ void __launch_bounds__(256) step_ii_pack_kernel(const __grid_constant__ StepIIPack q) {
+  __shared__ float Ws[8][8];  // [(w, s)][(w', s')], zero past the MPO
+  const int wad = q.wa * q.d, wbd = q.wb * q.d, d = q.d;
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+    const int k = e >> 3, m = e & 7;
+    float v = 0.0f;
+    if (k < wad && m < wbd) {
+      const int w = k / d, sk = k - w * d, w2 = m / d, s2 = m - w2 * d;
+      v = q.W[((w * q.wb + w2) * d + sk) * d + s2];
+    }
+    Ws[k][m] = v;
+  }
+  __syncthreads();
+  int e = 0;
+  if (q.maxbits) e = pow2_exponent(__uint_as_float(*q.maxbits));
+  const float inv = __int_as_float((127 - e) << 23);
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
+  if (gtid == 0 && q.maxbits) *q.lg += (double)e * 0.69314718055994530942;
+  const int32_t Da = q.Da, Db = q.Db, slabs = q.slabs;
+  const float* __restrict__ T1 = q.T1;
+  if ((Db & 7) == 0) {
+    // a thread takes 8 consecutive b at one a': one 16-byte chunk (8 rows at
+    // one shared index) per output channel (w', s'); a warp's stores fill
+    // four whole 128-byte lines
+    const int32_t groups = Db >> 3;
+    const int64_t items = (int64_t)Da * groups;
+    for (int64_t it = gtid; it < items; it += gstride) {
+      const int32_t a = (int32_t)(it / groups), b0 = (int32_t)(it - (int64_t)a * groups) * 8;
+      float t[8][8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k < wad) {
+          const int w = k / d, sk = k - w * d;
+          const float4* src = reinterpret_cast<const float4*>(T1 + ((int64_t)(w * Da + a) * d + sk) * Db + b0);
+          const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+          t[k][0] = x0.x; t[k][1] = x0.y; t[k][2] = x0.z; t[k][3] = x0.w;
+          t[k][4] = x1.x; t[k][5] = x1.y; t[k][6] = x1.z; t[k][7] = x1.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[k][j] = 0.0f;
+        }
+      }
+#pragma unroll 1
+      for (int m = 0; m < wbd; ++m) {
+        float o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = fmaf(Ws[k][m], t[k][j], acc);
+          o[j] = acc * inv;
+        }
+        const int w2 = m / d, s2 = m - w2 * d;
+        const int32_t r0 = w2 * Db + b0, kx = s2 * q.ps + a * q.pa;
+        const size_t off = ((size_t)(r0 >> 7) * slabs + (kx >> 6)) * MN_BLOCK_BYTES +
+                           mn_block_chunk((r0 & 127) >> 3, kx & 63);
+        uint4 h;
+        h.x = bf16x2_bits(o[0], o[1]);
+        h.y = bf16x2_bits(o[2], o[3]);
+        h.z = bf16x2_bits(o[4], o[5]);
+        h.w = bf16x2_bits(o[6], o[7]);
+        *reinterpret_cast<uint4*>(q.hi + off) = h;
+        if (q.lo) {
+          uint4 l;
+          l.x = bf16x2_bits(bf16_lo_rest(o[0]), bf16_lo_rest(o[1]));
+          l.y = bf16x2_bits(bf16_lo_rest(o[2]), bf16_lo_rest(o[3]));
+          l.z = bf16x2_bits(bf16_lo_rest(o[4]), bf16_lo_rest(o[5]));
+          l.w = bf16x2_bits(bf16_lo_rest(o[6]), bf16_lo_rest(o[7]));
+          *reinterpret_cast<uint4*>(q.lo + off) = l;
+        }
+      }
+    }
+  } else {
+    // small or odd bonds: a thread per column (a', b), 2-byte stores
+    const int64_t items = (int64_t)Da * Db;
+    for (int64_t it = gtid; it < items; it += gstride) {
+      const int32_t a = (int32_t)(it / Db), b = (int32_t)(it - (int64_t)a * Db);
+      float t[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        t[k] = 0.0f;
+        if (k < wad) {
+          const int w = k / d, sk = k - w * d;
+          t[k] = __ldg(T1 + ((int64_t)(w * Da + a) * d + sk) * Db + b);
+        }
+      }
+      for (int m = 0; m < wbd; ++m) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = fmaf(Ws[k][m], t[k], acc);
+        const float o = acc * inv;
+        const int w2 = m / d, s2 = m - w2 * d;
+        const int32_t r = w2 * Db + b, kx = s2 * q.ps + a * q.pa;
+        const size_t off = ((size_t)(r >> 7) * slabs + (kx >> 6)) * MN_BLOCK_BYTES +
+                           mn_block_chunk((r & 127) >> 3, kx & 63) + 2 * (r & 7);
+        const __nv_bfloat16 h = __float2bfloat16_rn(o);
+        *reinterpret_cast<__nv_bfloat16*>(q.hi + off) = h;
+        if (q.lo) *reinterpret_cast<__nv_bfloat16*>(q.lo + off) = __float2bfloat16_rn(o - __bfloat162float(h));
+      }
+    }
+  }
+  // zeros at the shared indices past K = d Da of every block of the last slab
+  const int32_t K = d * Da, kpad = slabs * 64 - K;
+  if (kpad > 0) {
+    const int64_t chunks = (int64_t)q.tiles * 16 * kpad;
+    for (int64_t it = gtid; it < chunks; it += gstride) {
+      const int32_t kk = K + (int32_t)(it % kpad);
+      const int64_t rest = it / kpad;
+      const int32_t mg = (int32_t)(rest & 15), tile = (int32_t)(rest >> 4);
+      const size_t off = ((size_t)tile * slabs + (kk >> 6)) * MN_BLOCK_BYTES + mn_block_chunk(mg, kk & 63);
+      *reinterpret_cast<uint4*>(q.hi + off) = make_uint4(0u, 0u, 0u, 0u);
+      if (q.lo) *reinterpret_cast<uint4*>(q.lo + off) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
 // Grouped form: blockIdx.y picks the chain's descriptor.
 template <int WD>
 __global__ void __launch_bounds__(256) mpo_step_ii_grouped(const StepII* __restrict__ descs) {
@@ -444,6 +593,8 @@ struct ExpectWs2 {
   double* lg;
   uint8_t* scratch;
   size_t scratch_bytes;
+  uint8_t* scratch3;  // BF16 / BF16X3 with step (ii) fused: (iii)'s packed operands
+  size_t scratch3_bytes;
   size_t bytes;
   std::vector<int64_t> woff;
 };
@@ -471,6 +622,10 @@ ExpectWs2 expect2_layout(uint8_t* base, const tn_mps* psi, const tn_mpo* H) {
   w.scratch_bytes = std::max(packed_scratch_bound(W1 * D, d * D, D, TN_PREC_BF16X3),
                              packed_scratch_bound(W1 * D, D, d * D, TN_PREC_BF16X3));
   w.scratch = take(w.scratch_bytes);
+  // step (iii) of the fused sweep: T2 in whole MN-major blocks and the core,
+  // packed while the previous contraction's operands are still in use
+  w.scratch3_bytes = packed_scratch_bound(W1 * D, D, d * D, TN_PREC_BF16X3);
+  w.scratch3 = take(w.scratch3_bytes);
   w.bytes = off;
   return w;
 }
@@ -554,6 +709,84 @@ int inner_sweep(const tn_mps* bra, const tn_mps* ket, int prec, const InnerWs& w
     std::swap(E, E2);
   }
   *final_env = E;
+  return TN_OK;
+}
+
+// The fused energy sweep's support: BF16 / BF16X3, and (extended MPO bond)
+// x d <= 8 on both sides of every site (step (ii) keeps all its channels of 8
+// columns in registers).
+bool fused_expect_ok(const tn_mps* psi, const tn_mpo* H, int prec) {
+  if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return false;
+  for (int i = 0; i <= H->n; ++i)
+    if ((H->bond[i] + 1) * psi->d > 8) return false;
+  return true;
+}
+
+// Energy sweep with step (ii) fused into the packing of step (iii)'s first
+// operand. Per site, four launches: one pack launch (L, with its largest
+// magnitude for this site's rescale, the core for (i) and the core for
+// (iii)), the GEMM of (i), step (ii) writing T2 as packed bf16 blocks, the
+// GEMM of (iii). Leaves the final environment in *final_env.
+int expect_sweep_fused(const tn_mps* psi, const tn_mpo* H, int prec, const ExpectWs2& w, float** final_env,
+                       cudaStream_t s) {
+  const int n = psi->n;
+  const int64_t d = psi->d;
+  float* L = w.L0;
+  float* L2 = w.L1;
+  int rc;
+  for (int i = 0; i < n; ++i) {
+    const int64_t Da = psi->bond[i], Db = psi->bond[i + 1], wa = H->bond[i] + 1, wb = H->bond[i + 1] + 1;
+    // (i) T1[w, a', s, b] = sum_a L[w, a, a'] A[a, s, b]
+    tn_tensor tL = tensor3(L, wa, Da, Da);
+    tn_tensor tA = tensor3(psi->cores[i], Da, d, Db);
+    tn_tensor tT1 = tensor4(w.T1, wa, Da, d, Db);
+    const int la1[1] = {1}, lb1[1] = {0};
+    ContractDesc d1;
+    if ((rc = plan_contract(&tL, la1, &tA, lb1, 1, &tT1, &d1)) != TN_OK) return rc;
+    plan_units(&d1, min_units_single());
+    SinglePacked s1;
+    if ((rc = plan_single_packed(d1, prec, false, w.scratch, w.scratch_bytes, &s1)) != TN_OK) return rc;
+    // (iii) L'[w', b, b'] = sum_{a', s'} T2[w', s', a', b] A[a', s', b'] (T2's
+    // float32 layout stands in for the planner; its blocks come from (ii))
+    tn_tensor tT2 = tensor4(w.T2, wb, d, Da, Db);
+    tn_tensor tL2 = tensor3(L2, wb, Db, Db);
+    const int la3[2] = {1, 2}, lb3[2] = {1, 0};
+    ContractDesc d3;
+    if ((rc = plan_contract(&tT2, la3, &tA, lb3, 2, &tL2, &d3)) != TN_OK) return rc;
+    plan_units(&d3, min_units_single());
+    SinglePacked s3;
+    if ((rc = plan_single_packed(d3, prec, true, w.scratch3, w.scratch3_bytes, &s3)) != TN_OK) return rc;
+    // the shared index of (iii): legs (s', a') in the planner's order; rows (w', b)
+    if (d3.nk != 2 || d3.nm != 2 || d3.M != wb * Db || d3.K != d * Da) return TN_ERR_UNSUPPORTED;
+    const bool s_inner = Da > 1 && d3.kstrA[1] == Da * Db;
+    StepIIPack q;
+    memset(&q, 0, sizeof(q));
+    q.T1 = w.T1;
+    q.W = w.Wx + w.woff[(size_t)i];
+    q.maxbits = i > 0 ? w.bits + i : nullptr;
+    q.lg = w.lg;
+    q.hi = s3.ja.hi;
+    q.lo = s3.ja.lo;
+    q.Da = (int32_t)Da;
+    q.Db = (int32_t)Db;
+    q.wa = (int32_t)wa;
+    q.wb = (int32_t)wb;
+    q.d = (int32_t)d;
+    q.tiles = s3.ja.tiles;
+    q.slabs = s3.ja.slabs;
+    q.ps = s_inner ? 1 : (int32_t)Da;
+    q.pa = s_inner ? (int32_t)d : 1;
+    // L (and its largest magnitude: this site's rescale), then both cores
+    if ((rc = launch_pack_jobs(&s1.ja, i > 0 ? w.bits + i : nullptr, &s1.jb, &s3.jb, s)) != TN_OK) return rc;
+    if ((rc = launch_gemm_single(s1.g, prec, s)) != TN_OK) return rc;
+    const int64_t items = (Db % 8 == 0 ? Da * (Db / 8) : Da * Db);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 1216));
+    step_ii_pack_kernel<<<grid, 256, 0, s>>>(q);
+    if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+    if ((rc = launch_gemm_single(s3.g, prec, s)) != TN_OK) return rc;
+    std::swap(L, L2);
+  }
+  *final_env = L;
   return TN_OK;
 }
 
@@ -707,6 +940,11 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
   if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
   float* L = w.L0;
   float* L2 = w.L1;
+  if (fused_expect_ok(psi, H, prec)) {
+    if ((rc = expect_sweep_fused(psi, H, prec, w, &L, s)) != TN_OK) return rc;
+    expect_finish_kernel<<<1, 32, 0, s>>>(L, w.lg, result);
+    return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+  }
   for (int i = 0; i < n; ++i) {
     const int64_t Da = psi->bond[i], Db = psi->bond[i + 1], wa = H->bond[i] + 1, wb = H->bond[i + 1] + 1;
     // (i) T1[w, a', s, b] = sum_a L[w, a, a'] A[a, s, b]

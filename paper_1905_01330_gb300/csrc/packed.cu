@@ -179,6 +179,16 @@ __device__ __forceinline__ void block_load(const PackJob& J, const VBlock& v, in
   }
 }
 
+// Largest magnitude among this thread's loaded values (zeros stand in for
+// positions outside the operand, so they never raise it).
+__device__ __forceinline__ float chunk_absmax(const ChunkRegs& cr, float m) {
+#pragma unroll
+  for (int c = 0; c < PACK_CPT; ++c)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(cr.v[c][j]));
+  return m;
+}
+
 // Converts and writes this thread's chunks of virtual block v (rows < ceil8(rv)).
 __device__ __forceinline__ void block_write(const PackJob& J, const VBlock& v, const ChunkRegs& cr) {
   const int rs = (v.rv + 7) & ~7;
@@ -197,7 +207,10 @@ __device__ __forceinline__ void block_write(const PackJob& J, const VBlock& v, c
 // decoded into the other slot while the loads of this one are in flight; one
 // barrier per virtual block publishes them (and orders the reuse of a slot
 // two virtual blocks later).
-__device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm) {
+// MAX: also folds the largest |value| packed into *amax (this thread's).
+template <bool MAX = false>
+__device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int count, PackSmem& sm,
+                                            float* amax = nullptr) {
   if (count <= 0) return;
   const int nbv = J.nbv;
   VBlock v = vblock(J, first, min(nbv, count));
@@ -206,6 +219,7 @@ __device__ __forceinline__ void pack_blocks(const PackJob& J, int first, int cou
   ChunkRegs cr;
   for (int j = 0, sl = 0; j < count; j += nbv, sl ^= 1) {
     block_load(J, v, sl, sm, cr);
+    if (MAX) *amax = chunk_absmax(cr, *amax);
     VBlock vn = v;
     if (j + nbv < count) {
       vn = vblock(J, first + j + nbv, min(nbv, count - j - nbv));
@@ -236,24 +250,38 @@ pack_kernel(const PackJob* __restrict__ jobs, const PackUnit* __restrict__ units
   pack_blocks(sm.job, un.first, un.count, sm);
 }
 
-// Single-contraction form: both jobs passed by value (nothing to upload, so
+// Single-contraction form: the jobs passed by value (nothing to upload, so
 // the launch can be captured in a CUDA graph). CTAs 0 .. units_a-1 pack A,
-// `per_a` slabs of one row tile each; the rest pack B, `per_b` each.
+// `per_a` blocks each; the next units_b pack B, `per_b` each; the rest pack
+// the optional third job C (an operand of a later contraction packed in the
+// same launch), `per_c` each. maxbits (or null): the bits of the largest
+// |value| of A are raised to with atomicMax (non-negative floats order as
+// their bit patterns do).
 struct PackPair {
-  PackJob a, b;
-  int32_t units_a, per_a, per_b, pad;
+  PackJob a, b, c;
+  int32_t units_a, units_b, per_a, per_b, per_c, pad;
+  unsigned* maxbits;
 };
 
 __global__ void __launch_bounds__(PACK_THREADS)
 pack_pair_kernel(const __grid_constant__ PackPair pp) {
   extern __shared__ __align__(16) uint8_t pack_smem_raw[];
   PackSmem& sm = *reinterpret_cast<PackSmem*>(pack_smem_raw);
-  const bool is_a = (int)blockIdx.x < pp.units_a;
-  stage_job(is_a ? pp.a : pp.b, sm);
+  const int blk = (int)blockIdx.x;
+  const int which = blk < pp.units_a ? 0 : (blk < pp.units_a + pp.units_b ? 1 : 2);
+  stage_job(which == 0 ? pp.a : (which == 1 ? pp.b : pp.c), sm);
   const PackJob& J = sm.job;
-  const int per = is_a ? pp.per_a : pp.per_b;
-  const int first = (is_a ? (int)blockIdx.x : (int)blockIdx.x - pp.units_a) * per;
+  const int per = which == 0 ? pp.per_a : (which == 1 ? pp.per_b : pp.per_c);
+  const int first = (blk - (which >= 1 ? pp.units_a : 0) - (which == 2 ? pp.units_b : 0)) * per;
   const int nb = J.tiles * J.slabs;
+  if (which == 0 && pp.maxbits) {
+    float m = 0.0f;
+    pack_blocks<true>(J, first, min(per, nb - first), sm, &m);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(pp.maxbits, __float_as_uint(m));
+    return;
+  }
   pack_blocks(J, first, min(per, nb - first), sm);
 }
 
@@ -985,7 +1013,8 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qleft = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
         // a 256-wide tile takes its Q rows from two consecutive 128-row blocks
-        const uint32_t pb = FUSE ? 0u : rows_bytes(d.RP - g.p0), qb = rows_bytes(qleft);
+        // an MN-major packed P block is stored whole (its two 64-row halves 8 KB apart)
+        const uint32_t pb = FUSE ? 0u : (d.p_mn ? (uint32_t)PBLOCK : rows_bytes(d.RP - g.p0)), qb = rows_bytes(qleft);
         const uint32_t qb2 = qleft > PR ? rows_bytes(qleft - PR) : 0u;
         const uint32_t tx = (pb + qb + qb2) * (SPLIT ? 2u : 1u);
         const uint8_t* pbase = d.P + ((g.p0 / PR) * d.slabs + g.ks0) * d.P_block;
@@ -1047,7 +1076,7 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
         const GUnit g = gunit(d, u - d.tile_begin);
         const int64_t qrows = d.RQ - g.q0 < d.q_tile ? d.RQ - g.q0 : d.q_tile;
         const int nmma = (int)((qrows + 15) & ~int64_t(15));
-        const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, FUSE ? d.p_mn : 0, 0);
+        const uint32_t idesc = ptx::idesc_bf16_f32(PR, nmma, d.p_mn, 0);
         const int chunk = SPLIT ? KC : g.nks;
         const int step = FUSE == 2 ? d.nsb : 1;  // slabs per stage
         // fused TMA: slab j of a stage at row j * ceil8(ph) of the P tile,
@@ -1075,13 +1104,14 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
 #pragma unroll
               for (int kk = 0; kk < PK / 16; ++kk) {
                 if (16 * kk >= d.kw) break;  // positions past kw are zeros on both sides
-                const uint64_t pd = (FUSE && d.p_mn)
-                                        ? ptx::sw128_mnmajor_desc(pj + kk * 2 * MN_KGROUP, MN_HALF, MN_KGROUP)
-                                        : ptx::sw128_kmajor_desc(pj + kk * 32);
+                const uint64_t pd = d.p_mn ? ptx::sw128_mnmajor_desc(pj + kk * 2 * MN_KGROUP, MN_HALF, MN_KGROUP)
+                                           : ptx::sw128_kmajor_desc(pj + kk * 32);
                 const uint64_t qd = ptx::sw128_kmajor_desc(qj + kk * 32);
                 ptx::mma_bf16(dt, pd, qd, idesc, (ks == c0 && j == 0 && kk == 0) ? 0u : 1u);
                 if (SPLIT) {
-                  const uint64_t pl = ptx::sw128_kmajor_desc(st + 2 * PBLOCK + kk * 32);
+                  const uint64_t pl =
+                      d.p_mn ? ptx::sw128_mnmajor_desc(st + 2 * PBLOCK + kk * 2 * MN_KGROUP, MN_HALF, MN_KGROUP)
+                             : ptx::sw128_kmajor_desc(st + 2 * PBLOCK + kk * 32);
                   const uint64_t ql = ptx::sw128_kmajor_desc(st + 3 * PBLOCK + kk * 32);
                   ptx::mma_bf16(dt, pd, ql, idesc, 1u);
                   ptx::mma_bf16(dt, pl, qd, idesc, 1u);
@@ -1958,52 +1988,103 @@ size_t packed_scratch_bound(int64_t M, int64_t N, int64_t K, int prec) {
   return planes * (align256(ra * slabs * PK * 2) + align256(rb * slabs * PK * 2));
 }
 
-int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s) {
+int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, uint8_t* base, size_t bytes,
+                       SinglePacked* sp) {
   if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
   PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
   PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
   if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
     return TN_ERR_UNSUPPORTED;
+  bool swap = false;
+  GemmDesc g = make_gemm(d, ja, jb, PR, &swap);
+  if (p_mn) {
+    // P (the first operand: never the MMA's narrower side here) written by
+    // the caller as whole MN-major blocks
+    if (swap) return TN_ERR_UNSUPPORTED;
+    ja.block_bytes = PBLOCK;
+    g.P_block = PBLOCK;
+    g.p_mn = 1;
+  }
   const bool split = prec == TN_PREC_BF16X3;
   const size_t ba = align256(job_bytes(ja)), bb = align256(job_bytes(jb));
-  if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255) || bytes < (split ? 2 : 1) * (ba + bb))
+  if (!base || (reinterpret_cast<uintptr_t>(base) & 255) || bytes < (split ? 2 : 1) * (ba + bb))
     return TN_ERR_WORKSPACE;
-  uint8_t* base = static_cast<uint8_t*>(scratch);
   ja.hi = base;
   jb.hi = base + ba;
   ja.lo = split ? base + ba + bb : nullptr;
   jb.lo = split ? base + 2 * ba + bb : nullptr;
-  PackPair pp;
-  memset(&pp, 0, sizeof(pp));
-  pp.a = ja;
-  pp.b = jb;
-  // one contraction alone on the GPU: units of fewer blocks when that is
-  // what it takes to give every SM a few (a large operand in units of 8
-  // blocks left two thirds of the SMs idle and the rest latency-bound)
-  const int64_t blocks = (int64_t)ja.tiles * ja.slabs + (int64_t)jb.tiles * jb.slabs;
-  const int32_t cap = (int32_t)std::max<int64_t>(1, blocks / (4 * (int64_t)sm_count()));
-  pp.per_a = std::min(blocks_per_unit(ja), cap);
-  pp.per_b = std::min(blocks_per_unit(jb), cap);
-  const int64_t na = (ja.tiles * (int64_t)ja.slabs + pp.per_a - 1) / pp.per_a;
-  const int64_t nb = (jb.tiles * (int64_t)jb.slabs + pp.per_b - 1) / pp.per_b;
-  if (na + nb > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
-  pp.units_a = (int32_t)na;
-  bool swap = false;
-  GemmDesc g = make_gemm(d, ja, jb, PR, &swap);
   g.P = swap ? jb.hi : ja.hi;
   g.Q = swap ? ja.hi : jb.hi;
   g.P_lo = split ? (swap ? jb.lo - jb.hi : ja.lo - ja.hi) : 0;
   g.Q_lo = split ? (swap ? ja.lo - ja.hi : jb.lo - jb.hi) : 0;
   g.tile_begin = 0;
-  if (d.splits > 1 && cudaMemsetAsync(d.C, 0, sizeof(float) * (size_t)(d.M * d.N), s) != cudaSuccess)
-    return TN_ERR_CUDA;
+  if ((int64_t)g.tiles_p * g.tiles_q * g.splits > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  sp->ja = ja;
+  sp->jb = jb;
+  sp->g = g;
+  sp->swap = swap;
+  return TN_OK;
+}
+
+size_t single_packed_bytes(const ContractDesc& d, int prec, bool p_mn) {
+  PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
+  const PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
+  if (p_mn) ja.block_bytes = PBLOCK;
+  const size_t planes = prec == TN_PREC_BF16X3 ? 2 : 1;
+  return planes * (align256(job_bytes(ja)) + align256(job_bytes(jb)));
+}
+
+int launch_pack_jobs(const PackJob* a, unsigned* maxbits, const PackJob* b, const PackJob* c, cudaStream_t s) {
+  PackPair pp;
+  memset(&pp, 0, sizeof(pp));
+  const PackJob* jobs[3] = {a, b, c};
+  int64_t blocks = 0;
+  for (const PackJob* j : jobs)
+    if (j) blocks += (int64_t)j->tiles * j->slabs;
+  // jobs alone on the GPU: units of fewer blocks when that is what it takes
+  // to give every SM a few (a large operand in units of 8 blocks left two
+  // thirds of the SMs idle and the rest latency-bound)
+  const int32_t cap = (int32_t)std::max<int64_t>(1, blocks / (4 * (int64_t)sm_count()));
+  int64_t units[3] = {0, 0, 0};
+  int32_t per[3] = {1, 1, 1};
+  for (int q = 0; q < 3; ++q) {
+    if (!jobs[q]) continue;
+    per[q] = std::min(blocks_per_unit(*jobs[q]), cap);
+    units[q] = ((int64_t)jobs[q]->tiles * jobs[q]->slabs + per[q] - 1) / per[q];
+  }
+  const int64_t total = units[0] + units[1] + units[2];
+  if (total == 0) return TN_OK;
+  if (total > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (a) pp.a = *a;
+  if (b) pp.b = *b;
+  if (c) pp.c = *c;
+  pp.units_a = (int32_t)units[0];
+  pp.units_b = (int32_t)units[1];
+  pp.per_a = per[0];
+  pp.per_b = per[1];
+  pp.per_c = per[2];
+  pp.maxbits = a ? maxbits : nullptr;
   if (!pack_attr()) return TN_ERR_CUDA;
-  pack_pair_kernel<<<(unsigned)(na + nb), PACK_THREADS, PACK_SMEM, s>>>(pp);
-  if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
+  pack_pair_kernel<<<(unsigned)total, PACK_THREADS, PACK_SMEM, s>>>(pp);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+int launch_gemm_single(const GemmDesc& g, int prec, cudaStream_t s) {
+  if (g.splits > 1 && cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)(g.RP * g.RQ), s) != cudaSuccess)
+    return TN_ERR_CUDA;
   const int64_t units = (int64_t)g.tiles_p * g.tiles_q * g.splits;
-  if (units > 0x7FFFFFFF) return TN_ERR_UNSUPPORTED;
+  if (units <= 0) return TN_OK;
   if (prec == TN_PREC_BF16) return launch_gemm<0, 0>(g, nullptr, nullptr, nullptr, units, s);
-  return launch_gemm<1, 0>(g, nullptr, nullptr, nullptr, units, s);
+  if (prec == TN_PREC_BF16X3) return launch_gemm<1, 0>(g, nullptr, nullptr, nullptr, units, s);
+  return TN_ERR_ARG;
+}
+
+int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s) {
+  SinglePacked sp;
+  int rc = plan_single_packed(d, prec, false, static_cast<uint8_t*>(scratch), bytes, &sp);
+  if (rc != TN_OK) return rc;
+  if ((rc = launch_pack_jobs(&sp.ja, nullptr, &sp.jb, nullptr, s)) != TN_OK) return rc;
+  return launch_gemm_single(sp.g, prec, s);
 }
 
 }  // namespace tn

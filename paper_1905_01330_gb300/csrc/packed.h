@@ -68,8 +68,9 @@ struct GemmDesc {
                           // (whole-sector stores) instead of one row per thread
   int32_t pjob;           // fused: index of P's job in the job list (P is read as float32
                           // and rounded inside the GEMM, never packed); -1: P is packed
-  int32_t p_mn;           // fused, P contiguous along its rows: the P tile is staged
-                          // MN-major (rows fastest), else K-major
+  int32_t p_mn;           // the P tile is MN-major (rows fastest), else K-major: fused with
+                          // P contiguous along its rows, or packed P written by the caller
+                          // as whole MN-major blocks (plan_single_packed)
   int32_t ph;             // rows of P per tile: 128, or the TMA box's height (fused TMA GEMM)
   int32_t kw;             // shared indices per slab: 64, or the TMA box's width
   int32_t bkmask;         // fused TMA GEMM: bit i set when dimension i of P's tensor map
@@ -157,6 +158,38 @@ size_t packed_single_bytes(const ContractDesc& d, int prec);
 // Upper bound of packed_single_bytes for an M x K by K x N contraction.
 size_t packed_scratch_bound(int64_t M, int64_t N, int64_t K, int prec);
 int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s);
+
+// The pieces of contract_packed_single, for callers that fuse work around
+// them (the energy sweep): d's pack jobs (A, B) and GEMM descriptor with the
+// packed blocks at `base` (256-byte aligned, `bytes` long), nothing launched.
+// p_mn: the first operand A is the GEMM's P (never its narrower side) and is
+// written by the caller as whole MN-major blocks of MN_BLOCK_BYTES (rows
+// fastest, see mn_block_chunk) at ja.hi (+ ja.lo for BF16X3) instead of being
+// packed; TN_ERR_UNSUPPORTED if A would be the narrower side.
+struct SinglePacked {
+  PackJob ja, jb;
+  GemmDesc g;
+  bool swap;
+};
+int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, uint8_t* base, size_t bytes, SinglePacked* sp);
+size_t single_packed_bytes(const ContractDesc& d, int prec, bool p_mn);
+// Packs up to three jobs in one launch (b, c: null for none); maxbits (or
+// null): raised with atomicMax to the bits of the largest |value| of job a.
+int launch_pack_jobs(const PackJob* a, unsigned* maxbits, const PackJob* b, const PackJob* c, cudaStream_t s);
+// The GEMM of a planned single contraction (its result zeroed first when its
+// shared index is split).
+int launch_gemm_single(const GemmDesc& g, int prec, cudaStream_t s);
+
+// MN-major packed block: 128 rows x 64 shared indices of bf16, 16 KB, in the
+// 128-byte-swizzled MN-major layout the MMA reads through an MN-major
+// descriptor (atoms of 8 k-rows x 64 rows, 128 bytes per k-row; the two
+// 64-row halves 8 KB apart, 8-row k groups 1 KB apart). The 16-byte chunk of
+// rows 8 mg .. 8 mg + 7 at shared index k starts at mn_block_chunk(mg, k);
+// row r within it at 2 (r % 8) bytes.
+constexpr int MN_BLOCK_BYTES = 16384;
+__host__ __device__ inline uint32_t mn_block_chunk(int mg, int k) {
+  return (uint32_t)((mg >> 3) * 8192 + (k >> 3) * 1024 + (k & 7) * 128 + (((mg & 7) ^ (k & 7)) << 4));
+}
 // unit_ctr (or null: units assigned statically): the device counter the
 // launch's CTAs claim units from (zeroed here, before the launch, on the same
 // stream).

@@ -70,6 +70,8 @@ constexpr int MAX_SLABS_PER_UNIT = 32;
 // Sets tiles_m/n, splits and k_per_split; `min_units` asks for at least that
 // many work units when K is long enough to split (keeping >= 4 slabs per unit).
 void plan_units(ContractDesc* d, int64_t min_units);
+// Work units a lone contraction asks plan_units for (two per SM).
+int64_t min_units_single();
 // The same for the packed GEMM (longer k ranges when a spec has many tiles).
 void plan_units_packed(ContractDesc* d, bool long_k);
 

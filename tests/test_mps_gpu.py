@@ -130,6 +130,28 @@ def test_left_canonical_energy_large_bond(tn, prec):
     assert abs(val(r, 1) - 1.0) <= tol(prec, 2 * n) + n * 1e-6
 
 
+@pytest.mark.parametrize("chi,n", [(20, 12), (40, 12), (100, 16)])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_energy_ragged_bonds(tn, chi, n, prec):
+    # Bonds whose step-(iii) operand (rows (w', b), shared (s', a')) ends in a
+    # ragged row tile and a ragged 64-wide shared slab -- chi 20: 80 rows and
+    # 40 shared indices, 40: 160 and 80, 100: 400 and 200 -- and bonds that
+    # are not multiples of 8 (20, 100: one output column per thread in step
+    # (ii)). The energy is bounded relative to ||H|| <psi|psi>, the norm (a
+    # sum of squares) with the one-signed bias of its c = 2n contractions.
+    cores = synth.left_canonical_mps(n, 2, chi, seed=11)
+    W = synth.tfim_mpo(n)
+    e, le = oracle.mpo_expect(cores, W)
+    nv, ln = oracle.mps_inner(cores, cores)
+    r = tn.mps_expect(to_dev(cores), to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    norm = nv * math.exp(ln)
+    h_norm = (n - 1) + n
+    assert abs(val(r, 0) - e * math.exp(le)) <= tol(prec, 2 * n) * h_norm * norm
+    bias = {"bf16x3": 2.0 ** -18, "bf16": 2.0 ** -16}[prec]
+    assert rel(val(r, 1), norm) <= tol(prec, 2 * n) + 2 * n * bias
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
 def test_grouped_energy_uneven_bonds(tn, prec):
     # config-5 batch shape at reduced size: uneven chi (one smallest, one
