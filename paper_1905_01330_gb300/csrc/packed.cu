@@ -1988,7 +1988,7 @@ size_t packed_scratch_bound(int64_t M, int64_t N, int64_t K, int prec) {
   return planes * (align256(ra * slabs * PK * 2) + align256(rb * slabs * PK * 2));
 }
 
-int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, uint8_t* base, size_t bytes,
+int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, int q_tile, uint8_t* base, size_t bytes,
                        SinglePacked* sp) {
   if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return TN_ERR_ARG;
   PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
@@ -1996,7 +1996,9 @@ int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, uint8_t* base
   if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
     return TN_ERR_UNSUPPORTED;
   bool swap = false;
-  GemmDesc g = make_gemm(d, ja, jb, PR, &swap);
+  // 256-wide tiles: BF16 only (the BF16X3 accumulator is promoted into
+  // registers, which hold 128 columns)
+  GemmDesc g = make_gemm(d, ja, jb, prec == TN_PREC_BF16 ? q_tile : PR, &swap);
   if (p_mn) {
     // P (the first operand: never the MMA's narrower side here) written by
     // the caller as whole MN-major blocks
@@ -2081,7 +2083,7 @@ int launch_gemm_single(const GemmDesc& g, int prec, cudaStream_t s) {
 
 int contract_packed_single(const ContractDesc& d, int prec, void* scratch, size_t bytes, cudaStream_t s) {
   SinglePacked sp;
-  int rc = plan_single_packed(d, prec, false, static_cast<uint8_t*>(scratch), bytes, &sp);
+  int rc = plan_single_packed(d, prec, false, PR, static_cast<uint8_t*>(scratch), bytes, &sp);
   if (rc != TN_OK) return rc;
   if ((rc = launch_pack_jobs(&sp.ja, nullptr, &sp.jb, nullptr, s)) != TN_OK) return rc;
   return launch_gemm_single(sp.g, prec, s);

@@ -171,7 +171,9 @@ struct SinglePacked {
   GemmDesc g;
   bool swap;
 };
-int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, uint8_t* base, size_t bytes, SinglePacked* sp);
+// q_tile: the output tile's width (128, or 256 for BF16).
+int plan_single_packed(const ContractDesc& d, int prec, bool p_mn, int q_tile, uint8_t* base, size_t bytes,
+                       SinglePacked* sp);
 size_t single_packed_bytes(const ContractDesc& d, int prec, bool p_mn);
 // Packs up to three jobs in one launch (b, c: null for none); maxbits (or
 // null): raised with atomicMax to the bits of the largest |value| of job a.
