@@ -60,6 +60,7 @@ struct tn_group_plan {
   std::vector<ZeroRange> zero_ranges;  // results zeroed on the device before the launch
   std::vector<int32_t> unit_desc;      // descriptor (or GEMM) index of every work unit
   tn::PackedPlan pp;                   // packed path (BF16 / BF16X3)
+  std::vector<uint8_t> ext_p;          // per descriptor: its A written by the caller (MN-major blocks)
   tn::PackedSchedule sched[3];         // packed schedules: thin (min(M, N) < 128), short k (<= 512), long k
   // list sizes and packed bytes of the largest layout (workspace offsets):
   // the schedule with the longest lists, nothing fused
@@ -239,7 +240,9 @@ int build_packed(tn_group_plan* p, bool allow_fuse = true) {
     plan_units_packed(&d, sc.long_k != 0);
     const int64_t rt = p->ctab_r.empty() ? -1 : p->ctab_r[i], kt = p->ctab_k.empty() ? -1 : p->ctab_k[i];
     const int64_t bm = p->box_map.empty() ? -1 : p->box_map[i];
-    const int rc = plan_packed(d, p->prec, sc, allow_fuse, rt, kt, bm >= 0 ? &p->boxes[i] : nullptr, bm, &p->pp);
+    const bool ext = !p->ext_p.empty() && p->ext_p[i] != 0;
+    const int rc = plan_packed(d, p->prec, sc, allow_fuse && !ext, rt, kt, bm >= 0 ? &p->boxes[i] : nullptr, bm,
+                               &p->pp, ext);
     if (rc != TN_OK) return rc;
   }
   // largest units first: tensor time plus memory time of one unit
@@ -300,7 +303,7 @@ uint64_t plan_signature(const tn_group_plan* p) {
 }  // namespace
 
 int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec, bool allow_packed,
-                             tn_group_plan** plan) {
+                             tn_group_plan** plan, const uint8_t* ext_p) {
   if (!plan) return TN_ERR_ARG;
   *plan = nullptr;
   if (nspecs < 0 || (nspecs > 0 && !specs)) return TN_ERR_ARG;
@@ -319,11 +322,18 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
     if (rc != TN_OK) { delete p; return rc; }
     if (d.M == 0 || d.N == 0) continue;
     p->bytes += 4.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
-    if (d.K == 0) { p->zeros.push_back(d); continue; }
+    if (d.K == 0) {
+      if (ext_p && ext_p[i]) { delete p; return TN_ERR_ARG; }
+      p->zeros.push_back(d);
+      continue;
+    }
     p->flops += 2.0 * (double)d.M * (double)d.N * (double)d.K;
     plan_units(&d, 1);
     p->descs.push_back(d);
+    p->ext_p.push_back(ext_p && ext_p[i] ? 1 : 0);
   }
+  const bool any_ext = std::find(p->ext_p.begin(), p->ext_p.end(), (uint8_t)1) != p->ext_p.end();
+  if (any_ext && (prec == TN_PREC_FP32 || !allow_packed)) { delete p; return TN_ERR_ARG; }
   // largest work units first, so the tail of the launch is made of small ones
   if (prec != TN_PREC_FP32 && allow_packed) {
     p->packed = true;
@@ -335,6 +345,7 @@ int tn::group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec
       p->box_map.assign(p->descs.size(), -1);
       for (size_t i = 0; i < p->descs.size(); ++i) {
         const ContractDesc& d = p->descs[i];
+        if (p->ext_p[i]) continue;  // never fused
         tn::TmaMap m;
         if (std::min(d.M, d.N) <= 64 && tn::plan_tma_box(d, &p->boxes[i], &m)) {
           p->box_map[i] = (int64_t)p->tmaps.size();
@@ -535,6 +546,25 @@ size_t tn::group_plan_packed_bytes(const tn_group_plan* plan) {
   return plan && plan->packed ? plan->reserve_packed : 0;
 }
 
+int tn::group_plan_ext_layout(const tn_group_plan* plan, int i, ExtPLayout* out) {
+  if (!plan || !out || !plan->packed || i < 0 || (size_t)i >= plan->descs.size() || !plan->ext_p[(size_t)i])
+    return TN_ERR_ARG;
+  const size_t j = 2 * (size_t)i;  // A's job: two jobs per contraction, in order
+  const tn::PackJob& job = plan->pp.jobs[j];
+  const ContractDesc& d = plan->descs[(size_t)i];
+  memset(out, 0, sizeof(*out));
+  out->hi_off = (int64_t)plan->pp.job_hi_off[j];
+  out->lo_off = plan->pp.job_lo_off[j] == SIZE_MAX ? -1 : (int64_t)plan->pp.job_lo_off[j];
+  out->tiles = job.tiles;
+  out->slabs = job.slabs;
+  out->nk = d.nk;
+  for (int q = 0; q < d.nk; ++q) {
+    out->kdim[q] = d.kdim[q];
+    out->kstrA[q] = d.kstrA[q];
+  }
+  return TN_OK;
+}
+
 int tn::group_plan_upload_shared(const tn_group_plan* plan, void* lists, size_t bytes, void* packed,
                                  cudaStream_t s) {
   if (!plan) return TN_ERR_ARG;
@@ -690,7 +720,7 @@ double tn_group_plan_launch_bytes(const tn_group_plan* plan, int index) {
     case L_PACK: {
       const double out = plan->prec == TN_PREC_BF16X3 ? 4.0 : 2.0;  // hi (+ lo) per element
       for (size_t i = 0; i < plan->pp.jobs.size(); ++i)
-        if (plan->pp.job_hi_off[i] != SIZE_MAX)
+        if (plan->pp.job_hi_off[i] != SIZE_MAX && !plan->pp.job_ext[i])
           b += (4.0 + out) * (double)plan->pp.jobs[i].R * (double)plan->pp.jobs[i].K;
       return b;
     }

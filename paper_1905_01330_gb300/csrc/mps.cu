@@ -410,27 +410,10 @@ __global__ void __launch_bounds__(256) mpo_step_ii_kernel(const __grid_constant_
 
 // Step (ii) written straight into step (iii)'s packed operand (BF16 and
 // BF16X3 sweeps whose extended MPO has (bond) x d <= 8 on both sides of every
-// site). T2[w', s', a', b] = 2^-e sum_{w,s} W'[w, w', s, s'] T1[w, a', s, b]
-// is the first operand P of (iii) with row r = w' Db + b and shared index
-// k = s' ps + a' pa (the planner's order of the shared legs); it is rounded
-// to bf16 (and its remainder to bf16 for BF16X3) and stored as whole MN-major
-// 128-row x 64-k blocks, block (tile, slab) at hi + (tile slabs + slab) 16 KB.
-// The float32 T2 is never written to memory and no pack pass reads it back.
-// Positions past the last shared index are written as zeros (rows past R
-// are left as they are: each row of the product depends on its own row of P
-// only, and the GEMM discards those rows).
-struct StepIIPack {
-  const float* T1;          // [wa][Da][d][Db], row-major
-  const float* W;           // the site's extended MPO [wa][wb][d][d]
-  const unsigned* maxbits;  // bits of the largest |L| (null: no rescale)
-  double* lg;               // float64 log-scale: e ln 2 added
-  uint8_t* hi;
-  uint8_t* lo;              // BF16X3, else null
-  int32_t Da, Db, wa, wb, d;
-  int32_t tiles, slabs;     // of P: rows wb Db, shared indices d Da
-  int32_t ps, pa;           // place values of s' and a' in the shared index
-};
-
+// site; the layout is StepIIPack's). The float32 T2 is never written to
+// memory and no pack pass reads it back. Rows past R are left as they are:
+// each row of the product depends on its own row of P only, and the GEMM
+// discards those rows.
 __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -440,7 +423,7 @@ __device__ __forceinline__ float bf16_lo_rest(float x) {
   return x - __bfloat162float(__float2bfloat16_rn(x));
 }
 
-__global__ void __launch_bounds__(256) step_ii_pack_kernel(const __grid_constant__ StepIIPack q) {
+__device__ __forceinline__ void step_ii_pack(const StepIIPack& q, int64_t gtid, int64_t gstride, bool log_thread) {
   __shared__ float Ws[8][8];  // [(w, s)][(w', s')], zero past the MPO
   const int wad = q.wa * q.d, wbd = q.wb * q.d, d = q.d;
   for (int e = threadIdx.x; e < 64; e += blockDim.x) {
@@ -456,8 +439,7 @@ __global__ void __launch_bounds__(256) step_ii_pack_kernel(const __grid_constant
   int e = 0;
   if (q.maxbits) e = pow2_exponent(__uint_as_float(*q.maxbits));
   const float inv = __int_as_float((127 - e) << 23);
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
-  if (gtid == 0 && q.maxbits) *q.lg += (double)e * 0.69314718055994530942;
+  if (log_thread && q.maxbits) *q.lg += (double)e * 0.69314718055994530942;
   const int32_t Da = q.Da, Db = q.Db, slabs = q.slabs;
   const float* __restrict__ T1 = q.T1;
   if ((Db & 7) == 0) {
@@ -555,6 +537,21 @@ __global__ void __launch_bounds__(256) step_ii_pack_kernel(const __grid_constant
     }
   }
 }
+
+__global__ void __launch_bounds__(256) step_ii_pack_kernel(const __grid_constant__ StepIIPack q) {
+  step_ii_pack(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+               blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Grouped form: blockIdx.y picks the chain's descriptor.
+__global__ void __launch_bounds__(256) step_ii_pack_grouped(const StepIIPack* __restrict__ descs) {
+  const StepIIPack q = descs[blockIdx.y];
+  step_ii_pack(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+               blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Work items of one chain's step_ii_pack (8-column groups, or columns).
+int64_t step_ii_pack_items(int64_t Da, int64_t Db) { return Db % 8 == 0 ? Da * (Db / 8) : Da * Db; }
 
 // Grouped form: blockIdx.y picks the chain's descriptor.
 template <int WD>
@@ -774,7 +771,6 @@ int expect_sweep_fused(const tn_mps* psi, const tn_mpo* H, int prec, const Expec
       return rc;
     // the shared index of (iii): legs (s', a') in the planner's order; rows (w', b)
     if (d3.nk != 2 || d3.nm != 2 || d3.M != wb * Db || d3.K != d * Da) return TN_ERR_UNSUPPORTED;
-    const bool s_inner = Da > 1 && d3.kstrA[1] == Da * Db;
     StepIIPack q;
     memset(&q, 0, sizeof(q));
     q.T1 = w.T1;
@@ -790,12 +786,11 @@ int expect_sweep_fused(const tn_mps* psi, const tn_mpo* H, int prec, const Expec
     q.d = (int32_t)d;
     q.tiles = s3.ja.tiles;
     q.slabs = s3.ja.slabs;
-    q.ps = s_inner ? 1 : (int32_t)Da;
-    q.pa = s_inner ? (int32_t)d : 1;
+    step_iii_places(Da, Db, d, d3.kstrA, &q.ps, &q.pa);
     // L (and its largest magnitude: this site's rescale), then both cores
     if ((rc = launch_pack_jobs(&s1.ja, i > 0 ? w.bits + i : nullptr, &s1.jb, &s3.jb, s)) != TN_OK) return rc;
     if ((rc = launch_gemm_single(s1.g, prec, s)) != TN_OK) return rc;
-    const int64_t items = (Db % 8 == 0 ? Da * (Db / 8) : Da * Db);
+    const int64_t items = step_ii_pack_items(Da, Db);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 1216));
     step_ii_pack_kernel<<<grid, 256, 0, s>>>(q);
     if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
@@ -819,6 +814,22 @@ int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols,
     case 16: mpo_step_ii_grouped<16><<<grid, 256, 0, s>>>(descs); break;
     default: mpo_step_ii_grouped<32><<<grid, 256, 0, s>>>(descs); break;
   }
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+void step_iii_places(int64_t Da, int64_t Db, int64_t d, const int64_t* kstrA, int32_t* ps, int32_t* pa) {
+  // the innermost shared leg is s' (stride Da Db in T2) or a' (stride Db);
+  // with Da = 1 only s' varies and either order gives k = s'
+  const bool s_inner = Da > 1 && kstrA[1] == Da * Db;
+  *ps = s_inner ? 1 : (int32_t)Da;
+  *pa = s_inner ? (int32_t)d : 1;
+}
+
+int launch_step_ii_pack_grouped(const StepIIPack* descs, int count, int64_t max_items, cudaStream_t s) {
+  if (count <= 0) return TN_OK;
+  // at most 64 blocks per chain (the small chains' blocks would mostly start and leave)
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_items + 255) / 256, 64)), (unsigned)count);
+  step_ii_pack_grouped<<<grid, 256, 0, s>>>(descs);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
 

@@ -6,7 +6,10 @@
 // count per site does not grow with the batch: (i) one grouped contraction,
 // (ii) one grouped float32 kernel that also applies the previous site's
 // deferred power-of-two rescale, (iii) one grouped contraction, then one
-// grouped max-abs pass over the count new environments.
+// grouped max-abs pass over the count new environments. BF16 / BF16X3 with
+// an extended MPO of (bond) x d <= 8: step (ii) writes each chain's T2
+// straight into the (iii) plan's packed region as its first operand (whole
+// MN-major blocks), so that plan packs only the cores.
 #include <math.h>
 #include <string.h>
 
@@ -139,11 +142,17 @@ struct GroupedSweep {
   std::vector<size_t> plan_bytes;
   std::vector<Segment> segs;          // n * count
   std::vector<StepII> steps;          // n * count
+  // fused mode (BF16 / BF16X3, extended MPO bond x d <= 8): step (ii) writes
+  // T2 straight into the (iii) plan's packed region
+  bool fused = false;
+  std::vector<StepIIPack> psteps;     // n * count (hi / lo: offsets in the packed region until laid out)
+  std::vector<int64_t> max_items;     // per site: the largest step (ii) work of a chain
   std::vector<int64_t> max_cols;      // per site: the largest Da Db of the batch
   std::vector<ChainInit> inits;
   std::vector<ChainFinal> finals;
   std::vector<int64_t> woff;          // extended MPO of every site
-  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_steps = 0, off_init = 0, off_final = 0, off_packed = 0;
+  size_t off_lg = 0, off_bits = 0, off_segs = 0, off_steps = 0, off_psteps = 0, off_init = 0, off_final = 0,
+         off_packed = 0;
   size_t off_w = 0, total = 0;
   size_t packed_bytes = 0;  // largest packed-operand region of one plan
   int64_t nbits = 0;
@@ -177,6 +186,9 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
   g->count = count;
   g->n = n;
   g->d = d;
+  g->fused = prec != TN_PREC_FP32;
+  for (int i = 0; i <= n; ++i)
+    if ((H->bond[i] + 1) * d > 8) g->fused = false;
   size_t off = 0;
   auto take = [&](size_t b) {
     uint8_t* p = base + off;
@@ -250,11 +262,43 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
     }
     g->max_cols.push_back(mc);
     const std::vector<tn_contract_spec>* stages[2] = {&s1, &s3};
+    const std::vector<uint8_t> ext((size_t)count, 1);
     for (int j = 0; j < 2; ++j) {
       tn_group_plan* p = nullptr;
-      int rc = tn_group_plan_create(stages[j]->data(), (int)stages[j]->size(), prec, &p);
+      int rc = group_plan_create_ex(stages[j]->data(), (int)stages[j]->size(), prec, true, &p,
+                                    j == 1 && g->fused ? ext.data() : nullptr);
       if (rc != TN_OK) return rc;
       g->plans.emplace_back(p);
+      if (j == 1 && g->fused) {
+        // step (ii) of every chain writes its T2 where the (iii) plan reads P
+        int64_t mi = 1;
+        for (int k = 0; k < count; ++k) {
+          ExtPLayout lay;
+          if ((rc = group_plan_ext_layout(p, k, &lay)) != TN_OK) return rc;
+          const StepII& q0 = g->steps[(size_t)count * i + k];
+          StepIIPack q;
+          memset(&q, 0, sizeof(q));
+          q.T1 = q0.T1;
+          q.W = q0.W;
+          q.maxbits = q0.maxbits;
+          q.lg = q0.lg;
+          // offsets for now; device addresses once the packed region is placed
+          q.hi = reinterpret_cast<uint8_t*>((uintptr_t)lay.hi_off);
+          q.lo = lay.lo_off < 0 ? nullptr : reinterpret_cast<uint8_t*>((uintptr_t)lay.lo_off);
+          q.Da = (int32_t)q0.Da;
+          q.Db = (int32_t)q0.Db;
+          q.wa = q0.wa;
+          q.wb = q0.wb;
+          q.d = q0.d;
+          q.tiles = lay.tiles;
+          q.slabs = lay.slabs;
+          if (lay.nk != 2) return TN_ERR_UNSUPPORTED;
+          step_iii_places(q0.Da, q0.Db, d, lay.kstrA, &q.ps, &q.pa);
+          g->psteps.push_back(q);
+          mi = std::max(mi, q0.Db % 8 == 0 ? q0.Da * (q0.Db / 8) : q0.Da * q0.Db);
+        }
+        g->max_items.push_back(mi);
+      }
       const size_t bytes = group_plan_list_bytes(p);
       g->plan_off.push_back(off);
       g->plan_bytes.push_back(bytes);
@@ -266,10 +310,16 @@ int build_sweep(const tn_mps* psis, int count, const tn_mpo* H, int prec, uint8_
   // plans run one after another on the stream)
   g->off_packed = off;
   off += align256(g->packed_bytes);
+  for (auto& q : g->psteps) {
+    q.hi = base + g->off_packed + (uintptr_t)q.hi;
+    if (q.lo) q.lo = base + g->off_packed + (uintptr_t)q.lo;
+  }
   g->off_segs = off;
   off += align256(sizeof(Segment) * g->segs.size());
   g->off_steps = off;
   off += align256(sizeof(StepII) * g->steps.size());
+  g->off_psteps = off;
+  off += align256(sizeof(StepIIPack) * g->psteps.size());
   g->inits.resize((size_t)count);
   g->finals.resize((size_t)count);
   for (int k = 0; k < count; ++k) {
@@ -334,9 +384,14 @@ int run_sweep(const tn_expect_plan* pl, double* result, cudaStream_t s) {
     if ((rc = group_plan_run_shared(g.plans[p0].get(), base + g.plan_off[p0], g.plan_bytes[p0], s)) != TN_OK)
       return rc;
     const StepII& q0 = g.steps[(size_t)count * i];
-    if ((rc = launch_mpo_step_ii_grouped(steps + (size_t)count * i, count, g.max_cols[(size_t)i],
-                                         (int64_t)q0.wa * q0.d, (int64_t)q0.wb * q0.d, s)) != TN_OK)
+    if (g.fused) {
+      const StepIIPack* psteps = reinterpret_cast<const StepIIPack*>(base + g.off_psteps);
+      if ((rc = launch_step_ii_pack_grouped(psteps + (size_t)count * i, count, g.max_items[(size_t)i], s)) != TN_OK)
+        return rc;
+    } else if ((rc = launch_mpo_step_ii_grouped(steps + (size_t)count * i, count, g.max_cols[(size_t)i],
+                                                (int64_t)q0.wa * q0.d, (int64_t)q0.wb * q0.d, s)) != TN_OK) {
       return rc;
+    }
     if ((rc = group_plan_run_shared(g.plans[p0 + 1].get(), base + g.plan_off[p0 + 1], g.plan_bytes[p0 + 1], s)) !=
         TN_OK)
       return rc;
@@ -388,6 +443,9 @@ int tn_mps_expect_grouped_plan(const tn_mps* psis, int count, const tn_mpo* H, i
                       s) != cudaSuccess ||
       cudaMemcpyAsync(base + g.off_steps, g.steps.data(), sizeof(StepII) * g.steps.size(), cudaMemcpyHostToDevice,
                       s) != cudaSuccess ||
+      (!g.psteps.empty() && cudaMemcpyAsync(base + g.off_psteps, g.psteps.data(),
+                                            sizeof(StepIIPack) * g.psteps.size(), cudaMemcpyHostToDevice,
+                                            s) != cudaSuccess) ||
       cudaMemcpyAsync(base + g.off_init, g.inits.data(), sizeof(ChainInit) * g.inits.size(),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + g.off_final, g.finals.data(), sizeof(ChainFinal) * g.finals.size(),

@@ -1884,13 +1884,19 @@ void fused_tables(const ContractDesc& d, std::vector<int32_t>* tab, int64_t* rta
 }
 
 int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,
-                int64_t ktab_off, const TmaBox* box, int64_t map, PackedPlan* pp) {
+                int64_t ktab_off, const TmaBox* box, int64_t map, PackedPlan* pp, bool ext_p) {
   PackJob ja = make_job(d, d.A, d.M, d.nm, d.mdim, d.mstr, d.kstrA);
   PackJob jb = make_job(d, d.B, d.N, d.nn, d.ndim, d.nstr, d.kstrB);
   if ((int64_t)ja.tiles * ja.slabs > 0x7FFFFFFF || (int64_t)jb.tiles * jb.slabs > 0x7FFFFFFF)
     return TN_ERR_UNSUPPORTED;
   bool swap = false;
   GemmDesc g = make_gemm(d, ja, jb, sc.q_tile, &swap);
+  if (ext_p) {
+    if (swap) return TN_ERR_UNSUPPORTED;
+    ja.block_bytes = PBLOCK;
+    g.P_block = PBLOCK;
+    fuse = false;
+  }
   fuse = fuse && prec == TN_PREC_BF16 && g.RQ <= PR / 2 &&
          ((rtab_off >= 0 && ktab_off >= 0) || (box && map >= 0));
   const bool tma = fuse && box && map >= 0;
@@ -1925,8 +1931,8 @@ int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool 
   }
   // a fused contraction packs Q only: P (A, or B when swapped) is read by
   // the fused GEMM's converters
-  const bool pack_a = !(fuse && !swap), pack_b = !(fuse && swap);
-  const size_t bytes_a = pack_a ? (size_t)ja.tiles * ja.slabs * ja.block_bytes : 0;
+  const bool pack_a = !(fuse && !swap) && !ext_p, pack_b = !(fuse && swap);
+  const size_t bytes_a = (pack_a || ext_p) ? (size_t)ja.tiles * ja.slabs * ja.block_bytes : 0;
   const size_t bytes_b = pack_b ? (size_t)jb.tiles * jb.slabs * jb.block_bytes : 0;
   const bool split = prec == TN_PREC_BF16X3;
   // storage offsets (relative to the packed region): A hi, B hi, A lo, B lo
@@ -1951,10 +1957,12 @@ int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool 
     jp.rtab_off = rtab_off;
     jp.ktab_off = ktab_off;
   }
-  pp->job_hi_off.push_back(pack_a ? off_a : SIZE_MAX);
+  pp->job_hi_off.push_back((pack_a || ext_p) ? off_a : SIZE_MAX);
   pp->job_hi_off.push_back(pack_b ? off_b : SIZE_MAX);
   pp->job_lo_off.push_back(split ? off_alo : SIZE_MAX);
   pp->job_lo_off.push_back(split ? off_blo : SIZE_MAX);
+  pp->job_ext.push_back(ext_p ? 1 : 0);
+  pp->job_ext.push_back(0);
   for (int w = 0; w < 2; ++w) {
     if (!(w == 0 ? pack_a : pack_b)) continue;
     const PackJob& j = pp->jobs[(size_t)ja_idx + w];
@@ -1969,7 +1977,7 @@ int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool 
   g.P_lo = split ? (int64_t)(swap ? off_blo : off_alo) - (int64_t)g.P_off : 0;
   g.Q_lo = split ? (int64_t)(swap ? off_alo : off_blo) - (int64_t)g.Q_off : 0;
   g.pjob = fuse ? ja_idx + (swap ? 1 : 0) : -1;
-  if (!tma) g.p_mn = fuse && pp->jobs[(size_t)ja_idx + (swap ? 1 : 0)].vec4 == 2 ? 1 : 0;
+  if (!tma) g.p_mn = (fuse && pp->jobs[(size_t)ja_idx + (swap ? 1 : 0)].vec4 == 2) || ext_p ? 1 : 0;
   pp->gemms.push_back(g);
   return TN_OK;
 }

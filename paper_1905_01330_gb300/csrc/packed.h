@@ -121,6 +121,7 @@ struct PackedPlan {
   std::vector<PackJob> jobs;       // two per contraction (A, B)
   std::vector<size_t> job_hi_off;  // offsets in the packed region
   std::vector<size_t> job_lo_off;  // SIZE_MAX when absent
+  std::vector<uint8_t> job_ext;    // written by the caller (MN-major blocks), not packed
   std::vector<PackUnit> units;
   std::vector<GemmDesc> gemms;     // one per contraction, in contraction order
   size_t packed_bytes = 0;
@@ -136,8 +137,10 @@ struct PackedPlan {
 // for the fused GEMM's converters (pjob).
 // box (or null): the contraction's TMA tiling, taken when it is fused; its
 // tensor map is entry `map` of the plan's list.
+// ext_p: A is written by the caller as whole MN-major blocks (not packed,
+// never fused); TN_ERR_UNSUPPORTED if A would be the GEMM's narrower side.
 int plan_packed(const ContractDesc& d, int prec, const PackedSchedule& sc, bool fuse, int64_t rtab_off,
-                int64_t ktab_off, const TmaBox* box, int64_t map, PackedPlan* pp);
+                int64_t ktab_off, const TmaBox* box, int64_t map, PackedPlan* pp, bool ext_p = false);
 
 // The operand on the MMA's 128-row side of contraction d: B when it has more
 // rows and A fewer than 128, else A.

@@ -91,8 +91,23 @@ int contract_internal(const tn_tensor* A, const int* legsA, const tn_tensor* B, 
 
 // tn_group_plan_create; allow_packed = false keeps BF16 / BF16X3 plans on
 // the single-launch kernel, whose workspace holds only the work list.
+// ext_p (or null): per spec, nonzero when its first operand A is written by
+// the caller straight into the plan's packed region as whole MN-major
+// blocks (BF16 / BF16X3 packed plans; A must be the GEMM's wider side): the
+// plan packs no A for it and never fuses it.
 int group_plan_create_ex(const tn_contract_spec* specs, int nspecs, int prec, bool allow_packed,
-                         tn_group_plan** plan);
+                         tn_group_plan** plan, const uint8_t* ext_p = nullptr);
+// Where a caller-written A goes: spec `i` (numbered among the specs with a
+// nonempty result), its blocks at packed + hi_off (+ lo_off for BF16X3; -1
+// none), `tiles` x `slabs` blocks of 16 KB (block (t, s) at t * slabs + s),
+// and the plan's order of its shared legs (kdim, kstrA as planned).
+struct ExtPLayout {
+  int64_t hi_off, lo_off;
+  int32_t tiles, slabs, nk, pad;
+  int32_t kdim[TN_MAX_RANK];
+  int64_t kstrA[TN_MAX_RANK];
+};
+int group_plan_ext_layout(const tn_group_plan* plan, int i, ExtPLayout* out);
 
 // Plans that run one after another on a stream can share one region for
 // their packed bf16 blocks: the lists go to `lists` (group_plan_list_bytes),
@@ -116,6 +131,31 @@ struct StepII {
   const unsigned* maxbits;
   double* lg;
 };
+// Step (ii) written straight into step (iii)'s packed operand (mps.cu):
+// T2 is the first operand P of (iii) with row r = w' Db + b and shared index
+// k = s' ps + a' pa, rounded to bf16 (and its remainder to bf16 for BF16X3)
+// and stored as whole MN-major 128-row x 64-k blocks, block (tile, slab) at
+// hi + (tile slabs + slab) 16 KB; positions past the last shared index are
+// written as zeros. (Extended MPO bond) x d <= 8 on both sides.
+struct StepIIPack {
+  const float* T1;          // [wa][Da][d][Db], row-major
+  const float* W;           // the site's extended MPO [wa][wb][d][d]
+  const unsigned* maxbits;  // bits of the largest |L| (null: no rescale)
+  double* lg;               // float64 log-scale: e ln 2 added
+  uint8_t* hi;
+  uint8_t* lo;              // BF16X3, else null
+  int32_t Da, Db, wa, wb, d;
+  int32_t tiles, slabs;     // of P: rows wb Db, shared indices d Da
+  int32_t ps, pa;           // place values of s' and a' in the shared index
+  int32_t pad;
+};
+// One launch for `count` chains (blockIdx.y: the chain); max_items: the
+// largest work of one chain (Da Db / 8 columns groups, or Da Db).
+int launch_step_ii_pack_grouped(const StepIIPack* descs, int count, int64_t max_items, cudaStream_t s);
+// The place values (ps, pa) of s' and a' in the shared index of step (iii),
+// from the planner's order of its two shared legs (kstrA of T2[w', s', a', b]).
+void step_iii_places(int64_t Da, int64_t Db, int64_t d, const int64_t* kstrA, int32_t* ps, int32_t* pa);
+
 // wad, wbd: (extended MPO bond) x d on either side of the site.
 int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, int64_t wad, int64_t wbd,
                                cudaStream_t s);
