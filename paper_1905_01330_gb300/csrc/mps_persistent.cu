@@ -1,0 +1,611 @@
+// Persistent energy sweep: <psi|H|psi> and <psi|psi> of one MPS (Sec. II,
+// Fig. 3a) in ONE cooperative launch for the whole chain. Every CTA stays
+// resident from the first site to the last; the environment, its packed bf16
+// image and the per-site intermediates stay in device memory that the 129 MB
+// L2 holds at these bonds, and the sites' four phases are separated by
+// device-wide barriers instead of kernel launches:
+//   (A) pack L (with its largest magnitude, the site's exact rescale) and
+//       the site's core in the two operand layouts of (i) and (iii);
+//   (B) tcgen05 GEMM  T1[(w, a'), (s, b)] = sum_a L[(w, a'), a] A[a, (s, b)];
+//   (C) step (ii) into (iii)'s packed operand (mpo_step.cuh);
+//   (D) tcgen05 GEMM  L'[(w', b), b'] = sum_{(a', s')} T2 A[(a', s'), b'].
+// A GEMM phase: CTA c takes output tiles c, c + grid, ... (128 x 128); one
+// thread streams the packed blocks of each 64-wide shared slab into a ring of
+// shared-memory stages (1-D bulk copies) and issues the MMAs, eight warps
+// drain the TMEM accumulator (double-buffered across tiles) and store the
+// float32 result. BF16X3 issues hi*hi, hi*lo, lo*hi per step and promotes the
+// accumulator into registers every 512 shared indices, as the grouped GEMM.
+// Every wait (mbarriers and the device-wide barrier) is bounded; on expiry
+// the status word records TN_ERR_TIMEOUT and every CTA winds down.
+#include <string.h>
+
+#include <algorithm>
+
+#include "mpo_step.cuh"
+#include "packed.h"
+#include "ptx.cuh"
+#include "tn_internal.h"
+
+namespace tn {
+namespace {
+
+constexpr int PS_THREADS = 384;  // 12 warps: warp 0 copies + MMAs, warp 1 TMEM, warps 4..11 drain TMEM
+constexpr int PS_EPI0 = 4;       // first draining warp
+constexpr int PS_EPI = 8;        // draining warps: two per TMEM lane quadrant, 64 columns each
+constexpr int PS_KC = 8;         // BF16X3: slabs between promotions (512 shared indices)
+constexpr int PS_BLOCK = 16384;  // one packed block: 128 rows x 64 shared indices of bf16
+constexpr int PS_MAX_SITES = 512;
+constexpr uint32_t PS_TMEM_COLS = 256;  // two 128-column accumulators
+
+template <int SPLIT>
+struct PsCfg {
+  // BF16: P and Q hi (32 KB) per stage; BF16X3: hi and lo of both (64 KB)
+  static constexpr int OPS = SPLIT ? 4 : 2;
+  static constexpr int STAGES = SPLIT ? 3 : 6;
+  static constexpr int STAGE_BYTES = OPS * PS_BLOCK;
+};
+
+struct PsSite {
+  const float* A;  // core (Da, d, Db), row-major
+  int32_t Da, Db, wa, wb;
+  int32_t woff, pad;  // the site's extended MPO at Wx + woff
+};
+
+struct PsParams {
+  int32_t n, d;
+  const float* Wx;       // extended MPO of every site
+  float* L[2];           // environments, (wa, Da, Da) / (wb, Db, Db) row-major
+  float* T1;             // (wa, Da, d, Db)
+  uint8_t* Lp;           // packed L: rows (w, a'), shared a (K-major blocks)
+  uint8_t* A1p;          // packed core for (i): rows (s, b), shared a
+  uint8_t* T2p;          // packed T2 for (iii): rows (w', b), shared a' d + s' (MN-major blocks)
+  uint8_t* A3p;          // packed core for (iii): rows b', shared a' d + s'
+  int64_t Lp_lo, A1p_lo, T2p_lo, A3p_lo;  // byte distance from a hi block to its lo block (BF16X3)
+  unsigned* bits;        // per site: bits of the largest |L| entering it
+  double* lg;            // float64 log-scale
+  unsigned* bar;         // device-wide barrier counter (zero at launch)
+  double* result;        // {energy, log-scale, norm, log-scale}
+  int* status;
+  PsSite site[PS_MAX_SITES];
+};
+
+struct __align__(8) PsAux {
+  uint64_t full[8];       // stage s holds its blocks
+  uint64_t empty[8];      // the MMAs that read stage s are complete
+  uint64_t acc_full[2];   // accumulator b holds a finished chunk
+  uint64_t acc_empty[2];  // the draining warps have read accumulator b
+  uint64_t final_bar;     // every MMA of the launch is complete
+  uint32_t tmem_base;
+  volatile int32_t abort;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const unsigned* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Device-wide barrier of the cooperative grid (all threads of every CTA).
+// Writes before it are visible after it to every CTA's generic loads and to
+// the bulk copies (async proxy) that read packed blocks. Bounded: on expiry
+// the status word records TN_ERR_TIMEOUT and false is returned everywhere in
+// this CTA (the CTAs that did arrive time out too and wind down).
+__device__ bool grid_sync(const PsParams& p, uint32_t& epoch, PsAux& x) {
+  fence_proxy_async_global();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t target = (epoch + 1) * gridDim.x;
+    atomicAdd(p.bar, 1u);
+    if (ld_acquire_gpu(p.bar) < target) {
+      const uint64_t t0 = ptx::globaltimer();
+      for (uint32_t i = 1;; ++i) {
+        if (ld_acquire_gpu(p.bar) >= target) break;
+        if ((i & 63u) == 0u && ptx::globaltimer() - t0 > ptx::kWaitLimitNs) {
+          ptx::set_status(p.status, TN_ERR_TIMEOUT);
+          x.abort = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  ++epoch;
+  __syncthreads();
+  fence_proxy_async_global();
+  return x.abort == 0;
+}
+
+__device__ __forceinline__ uint32_t ps_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// One K-major packed operand written by the pack phase: element (r, k) of
+// an R x K matrix at src[r_off(r) + k_off(k)], stored in whole 16 KB blocks
+// of 128 rows x 64 shared indices (128-byte swizzle, as the grouped GEMM's
+// packed blocks), zeros at every position past R or K.
+struct PsPack {
+  const float* src;
+  uint8_t* hi;
+  int64_t lo;       // byte distance to the lo plane, 0: none
+  int32_t R, K, tiles, slabs;
+  // row r = r1 * rd0 + r0 (r0 < rd0): offset r1 * rs1 + r0 * rs0; shared k likewise
+  int32_t rd0, ks0_div;
+  int64_t rs1, rs0, kq1, kq0;
+};
+
+__device__ __forceinline__ int32_t ceil_div(int32_t a, int32_t b) { return (a + b - 1) / b; }
+
+// Chunks of one packed operand: (tile, 8-wide k group of the slab, row in the
+// tile), rows fastest, so consecutive threads read consecutive rows at one
+// shared index (the row digit r0 is the source's unit-stride one).
+__device__ __forceinline__ int64_t pack_chunks(const PsPack& q) { return (int64_t)q.tiles * q.slabs * 8 * 128; }
+
+__device__ __forceinline__ float pack_chunk(const PsPack& q, int64_t e, float amax) {
+  const int32_t rr = (int32_t)(e & 127);
+  int64_t rest = e >> 7;
+  const int32_t g = (int32_t)(rest & 7);
+  rest >>= 3;
+  const int32_t sl = (int32_t)(rest % q.slabs), t = (int32_t)(rest / q.slabs);
+  const int32_t r = t * 128 + rr, k0 = sl * 64 + g * 8;
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+  if (r < q.R) {
+    const int32_t r1 = r / q.rd0, r0 = r - r1 * q.rd0;
+    const float* row = q.src + r1 * q.rs1 + r0 * q.rs0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int32_t k = k0 + j;
+      if (k < q.K) {
+        const int32_t k1 = k / q.ks0_div, kk = k - k1 * q.ks0_div;
+        v[j] = __ldg(row + k1 * q.kq1 + kk * q.kq0);
+      }
+    }
+  }
+  uint4 h;
+  h.x = ps_bf16x2(v[0], v[1]);
+  h.y = ps_bf16x2(v[2], v[3]);
+  h.z = ps_bf16x2(v[4], v[5]);
+  h.w = ps_bf16x2(v[6], v[7]);
+  const size_t off = ((size_t)t * q.slabs + sl) * PS_BLOCK +
+                     (size_t)((rr >> 3) * 1024 + (rr & 7) * 128 + ((g ^ (rr & 7)) << 4));
+  *reinterpret_cast<uint4*>(q.hi + off) = h;
+  if (q.lo) {
+    const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
+    uint4 l;
+    l.x = ps_bf16x2(v[0] - __low2float(hb[0]), v[1] - __high2float(hb[0]));
+    l.y = ps_bf16x2(v[2] - __low2float(hb[1]), v[3] - __high2float(hb[1]));
+    l.z = ps_bf16x2(v[4] - __low2float(hb[2]), v[5] - __high2float(hb[2]));
+    l.w = ps_bf16x2(v[6] - __low2float(hb[3]), v[7] - __high2float(hb[3]));
+    *reinterpret_cast<uint4*>(q.hi + q.lo + off) = l;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) amax = fmaxf(amax, fabsf(v[j]));
+  return amax;
+}
+
+// One GEMM phase: C[r, c] = sum_k P[r, k] Q[c, k] over whole packed blocks
+// (P K-major, or MN-major when p_mn; Q K-major), output tiles of 128 x 128.
+struct PsGemm {
+  const uint8_t* P;
+  const uint8_t* Q;
+  int64_t P_lo, Q_lo;  // byte distance from a hi block to its lo block (BF16X3)
+  float* C;
+  int32_t ldc, R, N;   // C row stride; rows of P (result rows) and of Q (result columns)
+  int32_t tp, tq, slabs, p_mn;
+};
+
+// Pipeline positions kept across the phases of the launch: slabs through the
+// stage ring (producer), accumulator chunks (producer and draining warps).
+struct PsPipe {
+  uint32_t issued, consumed, gc;
+};
+
+// Producer and MMA issuer of a GEMM phase (one thread). Keeps STAGES - 1
+// slabs of copies in flight ahead of the slab being multiplied; a slab's
+// MMAs are queued before the thread waits to refill a stage.
+template <int SPLIT>
+__device__ bool gemm_issue(const PsGemm& g, uint32_t stage0, PsAux& x, uint32_t tmem, PsPipe& pp, int* status) {
+  using C = PsCfg<SPLIT>;
+  constexpr int S = C::STAGES;
+  const uint32_t idesc = ptx::idesc_bf16_f32(128, 128, g.p_mn, 0);
+  const int nks = g.slabs, chunk = SPLIT ? PS_KC : nks;
+  for (int u = blockIdx.x; u < g.tp * g.tq; u += gridDim.x) {
+    const int tpi = u / g.tq, tqi = u - tpi * g.tq;
+    const uint8_t* pb = g.P + (size_t)tpi * g.slabs * PS_BLOCK;
+    const uint8_t* qb = g.Q + (size_t)tqi * g.slabs * PS_BLOCK;
+    const uint32_t first = pp.consumed;  // this unit's slab ks is global slab first + ks
+    auto issue = [&](int ks) -> bool {
+      const uint32_t gsl = first + (uint32_t)ks, st = gsl % S;
+      // the stage's previous contents: read by MMAs that must be complete
+      if (gsl >= (uint32_t)S && !ptx::mbar_wait(ptx::smem_addr(&x.empty[st]), ((gsl / S) - 1u) & 1u, status))
+        return false;
+      const uint32_t full = ptx::smem_addr(&x.full[st]), dst = stage0 + st * C::STAGE_BYTES;
+      ptx::mbar_arrive_expect_tx(full, (uint32_t)C::STAGE_BYTES);
+      ptx::bulk_copy_g2s(dst, pb + (size_t)ks * PS_BLOCK, PS_BLOCK, full);
+      ptx::bulk_copy_g2s(dst + PS_BLOCK, qb + (size_t)ks * PS_BLOCK, PS_BLOCK, full);
+      if (SPLIT) {
+        ptx::bulk_copy_g2s(dst + 2 * PS_BLOCK, pb + g.P_lo + (size_t)ks * PS_BLOCK, PS_BLOCK, full);
+        ptx::bulk_copy_g2s(dst + 3 * PS_BLOCK, qb + g.Q_lo + (size_t)ks * PS_BLOCK, PS_BLOCK, full);
+      }
+      ++pp.issued;
+      return true;
+    };
+    for (int ks = 0; ks < S - 1 && ks < nks; ++ks)
+      if (!issue(ks)) return false;
+    uint32_t b = 0;
+    for (int ks = 0; ks < nks; ++ks) {
+      const bool start = ks % chunk == 0;
+      if (start) {
+        // the accumulator this chunk overwrites has been drained
+        b = pp.gc & 1u;
+        if (!ptx::mbar_wait(ptx::smem_addr(&x.acc_empty[b]), ((pp.gc >> 1) & 1u) ^ 1u, status)) return false;
+      }
+      const uint32_t gsl = first + (uint32_t)ks, st = gsl % S;
+      if (!ptx::mbar_wait(ptx::smem_addr(&x.full[st]), (gsl / S) & 1u, status)) return false;
+      ptx::tc_fence_after();
+      const uint32_t sa = stage0 + st * C::STAGE_BYTES, dt = tmem + b * 128u;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t pd = g.p_mn ? ptx::sw128_mnmajor_desc(sa + kk * 2048, 8192, 1024)
+                                   : ptx::sw128_kmajor_desc(sa + kk * 32);
+        const uint64_t qd = ptx::sw128_kmajor_desc(sa + PS_BLOCK + kk * 32);
+        ptx::mma_bf16(dt, pd, qd, idesc, (start && kk == 0) ? 0u : 1u);
+        if (SPLIT) {
+          const uint64_t pl = g.p_mn ? ptx::sw128_mnmajor_desc(sa + 2 * PS_BLOCK + kk * 2048, 8192, 1024)
+                                     : ptx::sw128_kmajor_desc(sa + 2 * PS_BLOCK + kk * 32);
+          const uint64_t ql = ptx::sw128_kmajor_desc(sa + 3 * PS_BLOCK + kk * 32);
+          ptx::mma_bf16(dt, pd, ql, idesc, 1u);
+          ptx::mma_bf16(dt, pl, qd, idesc, 1u);
+        }
+      }
+      ptx::mma_commit(ptx::smem_addr(&x.empty[st]));
+      ++pp.consumed;
+      if (ks % chunk == chunk - 1 || ks == nks - 1) {
+        ptx::mma_commit(ptx::smem_addr(&x.acc_full[b]));
+        ++pp.gc;
+      }
+      // the next copies go to the stage of slab ks - 1, whose MMAs complete
+      // while this slab's, queued behind them, keep the tensor pipe busy
+      if (ks + S - 1 < nks && !issue(ks + S - 1)) return false;
+    }
+  }
+  return true;
+}
+
+// Draining warps of a GEMM phase: warp (PS_EPI0 + 4 grp + quad) reads TMEM
+// lanes quad * 32 .. + 31 (one result row per thread), columns grp * 64 ..
+// + 63; BF16X3 adds each chunk's partial sums into float32 registers.
+template <int SPLIT>
+__device__ bool gemm_drain(const PsGemm& g, PsAux& x, uint32_t tmem, PsPipe& pp, int* status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quad = warp & 3, grp = (warp - PS_EPI0) >> 2;
+  const int nks = g.slabs, nchunks = SPLIT ? (nks + PS_KC - 1) / PS_KC : 1;
+  const bool vec = (g.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0;
+  for (int u = blockIdx.x; u < g.tp * g.tq; u += gridDim.x) {
+    const int tpi = u / g.tq, tqi = u - tpi * g.tq;
+    const int row = tpi * 128 + quad * 32 + lane, col0 = tqi * 128 + grp * 64;
+    float* dst = g.C + (size_t)row * g.ldc + col0;
+    const int ncol = g.N - col0;  // valid columns of this thread's 64
+    auto store = [&](int h, const float* v) {
+      if (row >= g.R || ncol <= 32 * h) return;
+      if (vec && ncol >= 32 * h + 32) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4*>(dst + 32 * h + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (32 * h + j < ncol) dst[32 * h + j] = v[j];
+      }
+    };
+    float acc[SPLIT ? 64 : 1];
+#pragma unroll
+    for (int j = 0; j < (SPLIT ? 64 : 1); ++j) acc[j] = 0.0f;
+    for (int c = 0; c < nchunks; ++c) {
+      const uint32_t b = pp.gc & 1u;
+      const bool w = ptx::mbar_wait(ptx::smem_addr(&x.acc_full[b]), (pp.gc >> 1) & 1u, status);
+      if (!__all_sync(0xffffffffu, w)) return false;
+      ptx::tc_fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + b * 128u + (uint32_t)(grp * 64);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t r[32];
+        ptx::tmem_ld_32x32b_x32(ta + 32u * h, r);
+        ptx::tmem_ld_wait();
+        if (SPLIT) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[32 * h + j] += __uint_as_float(r[j]);
+        } else {
+          float v[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+          store(h, v);
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ptx::smem_addr(&x.acc_empty[b]));
+      ++pp.gc;
+    }
+    if (SPLIT) {
+      store(0, acc);
+      store(1, acc + 32);
+    }
+  }
+  return true;
+}
+
+template <int SPLIT>
+__device__ bool gemm_phase(const PsGemm& g, uint32_t stage0, PsAux& x, uint32_t tmem, PsPipe& pp, int* status) {
+  const int warp = threadIdx.x >> 5;
+  bool ok = true;
+  if (threadIdx.x == 0) ok = gemm_issue<SPLIT>(g, stage0, x, tmem, pp, status);
+  else if (warp >= PS_EPI0) ok = gemm_drain<SPLIT>(g, x, tmem, pp, status);
+  if (!ok) x.abort = 1;
+  return ok;
+}
+
+// The whole sweep. Grid: one CTA per SM (cooperative launch).
+template <int SPLIT>
+__global__ void __launch_bounds__(PS_THREADS, 1) expect_persistent_kernel(const __grid_constant__ PsParams p) {
+  using C = PsCfg<SPLIT>;
+  extern __shared__ uint8_t ps_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ps_smem_raw) + 1023) & ~uintptr_t(1023));
+  PsAux& x = *reinterpret_cast<PsAux*>(smem + (size_t)C::STAGES * C::STAGE_BYTES);
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < C::STAGES; ++st) {
+      ptx::mbar_init(ptx::smem_addr(&x.full[st]), 1);   // the producer's transaction arrival
+      ptx::mbar_init(ptx::smem_addr(&x.empty[st]), 1);  // the MMA issuer's commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(ptx::smem_addr(&x.acc_full[b]), 1);
+      ptx::mbar_init(ptx::smem_addr(&x.acc_empty[b]), PS_EPI);
+    }
+    ptx::mbar_init(ptx::smem_addr(&x.final_bar), 1);
+    x.abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_addr(&x.tmem_base), PS_TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = x.tmem_base, stage0 = ptx::smem_addr(smem);
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
+  const int32_t d = p.d;
+  PsPipe pp{0u, 0u, 0u};
+  uint32_t epoch = 0;
+  int cur = 0;
+  bool ok = true;
+  for (int i = 0; i < p.n && ok; ++i) {
+    const PsSite& st = p.site[i];
+    const int32_t Da = st.Da, Db = st.Db, wa = st.wa, wb = st.wb;
+    // (A) L and the core, packed; L's largest magnitude (the site's rescale)
+    PsPack q[3];
+    // L[w, a, a'] as rows (w, a'), shared a
+    q[0].src = p.L[cur];
+    q[0].hi = p.Lp;
+    q[0].lo = SPLIT ? p.Lp_lo : 0;
+    q[0].R = wa * Da;
+    q[0].K = Da;
+    q[0].rd0 = Da;
+    q[0].rs1 = (int64_t)Da * Da;
+    q[0].rs0 = 1;
+    q[0].ks0_div = Da;
+    q[0].kq1 = 0;
+    q[0].kq0 = Da;
+    // A[a, s, b] as rows (s, b), shared a
+    q[1].src = st.A;
+    q[1].hi = p.A1p;
+    q[1].lo = SPLIT ? p.A1p_lo : 0;
+    q[1].R = d * Db;
+    q[1].K = Da;
+    q[1].rd0 = Db;
+    q[1].rs1 = Db;
+    q[1].rs0 = 1;
+    q[1].ks0_div = Da;
+    q[1].kq1 = 0;
+    q[1].kq0 = (int64_t)d * Db;
+    // A[a', s', b'] as rows b', shared a' d + s' (offset (a' d + s') Db)
+    q[2].src = st.A;
+    q[2].hi = p.A3p;
+    q[2].lo = SPLIT ? p.A3p_lo : 0;
+    q[2].R = Db;
+    q[2].K = d * Da;
+    q[2].rd0 = Db;
+    q[2].rs1 = 0;
+    q[2].rs0 = 1;
+    q[2].ks0_div = d * Da;
+    q[2].kq1 = 0;
+    q[2].kq0 = Db;
+    int64_t c[3];
+    for (int j = 0; j < 3; ++j) {
+      q[j].tiles = ceil_div(q[j].R, 128);
+      q[j].slabs = ceil_div(q[j].K, 64);
+      c[j] = pack_chunks(q[j]);
+    }
+    float m = 0.0f;
+    for (int64_t e = gtid; e < c[0] + c[1] + c[2]; e += gstride) {
+      if (e < c[0]) m = pack_chunk(q[0], e, m);
+      else if (e < c[0] + c[1]) pack_chunk(q[1], e - c[0], 0.0f);
+      else pack_chunk(q[2], e - c[0] - c[1], 0.0f);
+    }
+    if (i > 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(p.bits + i, __float_as_uint(m));
+    }
+    if (!(ok = grid_sync(p, epoch, x))) break;
+    // (B) T1[(w, a'), (s, b)] = sum_a L[(w, a'), a] A[a, (s, b)]
+    PsGemm g;
+    g.P = p.Lp;
+    g.Q = p.A1p;
+    g.P_lo = p.Lp_lo;
+    g.Q_lo = p.A1p_lo;
+    g.C = p.T1;
+    g.ldc = d * Db;
+    g.R = wa * Da;
+    g.N = d * Db;
+    g.tp = q[0].tiles;
+    g.tq = q[1].tiles;
+    g.slabs = q[0].slabs;
+    g.p_mn = 0;
+    gemm_phase<SPLIT>(g, stage0, x, tmem, pp, p.status);
+    if (!(ok = grid_sync(p, epoch, x))) break;
+    // (C) T2 = 2^-e W' T1, straight into (iii)'s packed first operand
+    StepIIPack q2;
+    q2.T1 = p.T1;
+    q2.W = p.Wx + st.woff;
+    q2.maxbits = i > 0 ? p.bits + i : nullptr;
+    q2.lg = p.lg;
+    q2.hi = p.T2p;
+    q2.lo = SPLIT ? p.T2p + p.T2p_lo : nullptr;
+    q2.Da = Da;
+    q2.Db = Db;
+    q2.wa = wa;
+    q2.wb = wb;
+    q2.d = d;
+    q2.tiles = ceil_div(wb * Db, 128);
+    q2.slabs = q[2].slabs;
+    q2.ps = 1;
+    q2.pa = d;
+    q2.pad = 0;
+    step_ii_pack(q2, gtid, gstride, blockIdx.x == 0 && threadIdx.x == 0);
+    if (!(ok = grid_sync(p, epoch, x))) break;
+    // (D) L'[(w', b), b'] = sum_{(a', s')} T2[(w', b), (a', s')] A[(a', s'), b']
+    g.P = p.T2p;
+    g.Q = p.A3p;
+    g.P_lo = p.T2p_lo;
+    g.Q_lo = p.A3p_lo;
+    g.C = p.L[cur ^ 1];
+    g.ldc = Db;
+    g.R = wb * Db;
+    g.N = Db;
+    g.tp = q2.tiles;
+    g.tq = q[2].tiles;
+    g.slabs = q[2].slabs;
+    g.p_mn = 1;
+    gemm_phase<SPLIT>(g, stage0, x, tmem, pp, p.status);
+    if (!(ok = grid_sync(p, epoch, x))) break;
+    cur ^= 1;
+  }
+  if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
+    const float* L = p.L[cur];
+    p.result[0] = (double)L[0];
+    p.result[1] = *p.lg;
+    p.result[2] = (double)L[1];
+    p.result[3] = *p.lg;
+  }
+  // wind down: copies still in flight land, every MMA completes, then TMEM is freed
+  if (threadIdx.x == 0) {
+    for (uint32_t q = pp.consumed; q < pp.issued; ++q)
+      ptx::mbar_wait(ptx::smem_addr(&x.full[q % C::STAGES]), (q / C::STAGES) & 1u, p.status);
+    ptx::mma_commit(ptx::smem_addr(&x.final_bar));
+    ptx::mbar_wait(ptx::smem_addr(&x.final_bar), 0u, p.status);
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, PS_TMEM_COLS);
+  }
+}
+
+}  // namespace
+
+bool expect_persistent_ok(const tn_mps* psi, const tn_mpo* H, int prec) {
+  if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return false;
+  if (psi->n > PS_MAX_SITES) return false;
+  for (int i = 0; i <= H->n; ++i)
+    if ((H->bond[i] + 1) * psi->d > 8) return false;
+  return true;
+}
+
+int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const ExpectBuffers& w, double* result,
+                      cudaStream_t s) {
+  if (!expect_persistent_ok(psi, H, prec)) return TN_ERR_UNSUPPORTED;
+  const bool split = prec == TN_PREC_BF16X3;
+  PsParams p;
+  memset(&p, 0, sizeof(p));
+  p.n = psi->n;
+  p.d = (int32_t)psi->d;
+  p.Wx = w.Wx;
+  p.L[0] = w.L0;
+  p.L[1] = w.L1;
+  p.T1 = w.T1;
+  // packed regions, laid out for the largest bond: [L hi | core(i) hi | L lo | core(i) lo]
+  // and [T2 hi | core(iii) hi | T2 lo | core(iii) lo]
+  int64_t Wm = 1, D = 1;
+  for (int i = 0; i <= H->n; ++i) Wm = std::max(Wm, H->bond[i]);
+  for (int i = 0; i <= psi->n; ++i) D = std::max(D, psi->bond[i]);
+  const int64_t W1 = Wm + 1, d = psi->d;
+  auto blocks = [](int64_t R, int64_t K) { return (size_t)((R + 127) / 128) * (size_t)((K + 63) / 64) * PS_BLOCK; };
+  const size_t bl = align256(blocks(W1 * D, D)), ba1 = align256(blocks(d * D, D));
+  const size_t bt = align256(blocks(W1 * D, d * D)), ba3 = align256(blocks(D, d * D));
+  if (w.scratch_bytes < 2 * (bl + ba1) || w.scratch3_bytes < 2 * (bt + ba3)) return TN_ERR_WORKSPACE;
+  p.Lp = w.scratch;
+  p.A1p = w.scratch + bl;
+  p.Lp_lo = p.A1p_lo = (int64_t)(bl + ba1);
+  p.T2p = w.scratch3;
+  p.A3p = w.scratch3 + bt;
+  p.T2p_lo = p.A3p_lo = (int64_t)(bt + ba3);
+  p.bits = w.bits;
+  p.lg = w.lg;
+  p.bar = w.bar;
+  p.result = result;
+  p.status = status_word();
+  for (int i = 0; i < psi->n; ++i) {
+    PsSite& st = p.site[i];
+    st.A = psi->cores[i];
+    st.Da = (int32_t)psi->bond[i];
+    st.Db = (int32_t)psi->bond[i + 1];
+    st.wa = (int32_t)(H->bond[i] + 1);
+    st.wb = (int32_t)(H->bond[i + 1] + 1);
+    st.woff = (int32_t)w.woff[(size_t)i];
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess)
+    return TN_ERR_CUDA;
+  const size_t smem = 1024 + (size_t)(split ? PsCfg<1>::STAGES * PsCfg<1>::STAGE_BYTES
+                                            : PsCfg<0>::STAGES * PsCfg<0>::STAGE_BYTES) +
+                      sizeof(PsAux);
+  const void* fn = split ? (const void*)expect_persistent_kernel<1> : (const void*)expect_persistent_kernel<0>;
+  static bool attr[2] = {false, false};
+  if (!attr[split ? 1 : 0]) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return TN_ERR_CUDA;
+    attr[split ? 1 : 0] = true;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PS_THREADS, smem) != cudaSuccess || per_sm < 1)
+    return TN_ERR_UNSUPPORTED;
+  // the device-wide barrier counts arrivals from zero
+  if (cudaMemsetAsync(w.bar, 0, sizeof(unsigned), s) != cudaSuccess) return TN_ERR_CUDA;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)sms);
+  cfg.blockDim = dim3(PS_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = split ? cudaLaunchKernelEx(&cfg, expect_persistent_kernel<1>, p)
+                              : cudaLaunchKernelEx(&cfg, expect_persistent_kernel<0>, p);
+  return e == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+}
+
+}  // namespace tn

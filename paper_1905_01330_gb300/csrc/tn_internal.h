@@ -156,6 +156,28 @@ int launch_step_ii_pack_grouped(const StepIIPack* descs, int count, int64_t max_
 // from the planner's order of its two shared legs (kstrA of T2[w', s', a', b]).
 void step_iii_places(int64_t Da, int64_t Db, int64_t d, const int64_t* kstrA, int32_t* ps, int32_t* pa);
 
+// The energy sweep as one persistent cooperative launch (mps_persistent.cu):
+// BF16 / BF16X3, at most 512 sites, (extended MPO bond) x d <= 8. Buffers
+// from the energy sweep's workspace: environments L0 / L1 (with the first
+// site's L0 = 1 in its channels), T1, the extended MPO Wx (site i at
+// woff[i]), per-site max slots `bits` and the log-scale `lg` (zeroed), the
+// barrier counter `bar` (4 bytes), and the packed regions `scratch` / `scratch3`.
+struct ExpectBuffers {
+  float *L0, *L1, *T1;
+  const float* Wx;
+  const int64_t* woff;
+  unsigned* bits;
+  double* lg;
+  unsigned* bar;
+  uint8_t* scratch;
+  size_t scratch_bytes;
+  uint8_t* scratch3;
+  size_t scratch3_bytes;
+};
+bool expect_persistent_ok(const tn_mps* psi, const tn_mpo* H, int prec);
+int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const ExpectBuffers& w, double* result,
+                      cudaStream_t s);
+
 // wad, wbd: (extended MPO bond) x d on either side of the site.
 int launch_mpo_step_ii_grouped(const StepII* descs, int count, int64_t max_cols, int64_t wad, int64_t wbd,
                                cudaStream_t s);
