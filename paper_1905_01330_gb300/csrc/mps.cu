@@ -32,6 +32,7 @@ namespace tn {
 namespace {
 
 constexpr int SMALL_D = 64;      // largest bond of the one-CTA sweep
+constexpr int64_t PERSISTENT_MAX_BOND = 512;  // largest bond of the persistent energy sweep
 constexpr int SMALL_PHYS = 4;    // largest physical dim of the one-CTA sweep
 constexpr int SMALL_MAXN = 1024; // sites passed by value to the one-CTA sweep
 constexpr int SMALL_THREADS = 256;
@@ -458,6 +459,8 @@ struct ExpectWs2 {
   size_t scratch_bytes;
   uint8_t* scratch3;  // BF16 / BF16X3 with step (ii) fused: (iii)'s packed operands
   size_t scratch3_bytes;
+  uint8_t* cores;     // the persistent sweep: every site's packed cores
+  size_t cores_bytes;
   size_t bytes;
   std::vector<int64_t> woff;
 };
@@ -490,6 +493,8 @@ ExpectWs2 expect2_layout(uint8_t* base, const tn_mps* psi, const tn_mpo* H) {
   // packed while the previous contraction's operands are still in use
   w.scratch3_bytes = packed_scratch_bound(W1 * D, D, d * D, TN_PREC_BF16X3);
   w.scratch3 = take(w.scratch3_bytes);
+  w.cores_bytes = D <= PERSISTENT_MAX_BOND ? expect_persistent_cores_bytes(psi) : 0;
+  w.cores = take(w.cores_bytes);
   w.bytes = off;
   return w;
 }
@@ -594,7 +599,7 @@ bool fused_expect_ok(const tn_mps* psi, const tn_mpo* H, int prec) {
 // warp-specialised GEMM and 256-wide BF16 tiles, are faster (BF16X3 11.5
 // against 13.6 ms).
 bool use_persistent(const tn_mps* psi, const tn_mpo* H, int prec) {
-  return max_bond(psi) <= 512 && expect_persistent_ok(psi, H, prec);
+  return max_bond(psi) <= PERSISTENT_MAX_BOND && expect_persistent_ok(psi, H, prec);
 }
 
 // Output tile width of a sweep contraction on the BF16 GEMM: 256 columns
@@ -859,6 +864,8 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
     b.scratch_bytes = w.scratch_bytes;
     b.scratch3 = w.scratch3;
     b.scratch3_bytes = w.scratch3_bytes;
+    b.cores = w.cores;
+    b.cores_bytes = w.cores_bytes;
     return expect_persistent(psi, H, prec, b, result, s);
   }
   if (fused_expect_ok(psi, H, prec)) {

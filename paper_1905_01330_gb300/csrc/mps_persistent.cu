@@ -49,6 +49,9 @@ struct PsSite {
   const float* A;  // core (Da, d, Db), row-major
   int32_t Da, Db, wa, wb;
   int32_t woff, pad;  // the site's extended MPO at Wx + woff
+  // the core packed once per launch: for (i) at Cp + a1_off, for (iii) at
+  // Cp + a3_off (bytes); its first pack chunk in the launch's numbering
+  int64_t a1_off, a3_off, chunk0;
 };
 
 struct PsParams {
@@ -56,11 +59,11 @@ struct PsParams {
   const float* Wx;       // extended MPO of every site
   float* L[2];           // environments, (wa, Da, Da) / (wb, Db, Db) row-major
   float* T1;             // (wa, Da, d, Db)
-  uint8_t* Lp;           // packed L: rows (w, a'), shared a (K-major blocks)
-  uint8_t* A1p;          // packed core for (i): rows (s, b), shared a
+  uint8_t* Lp;           // packed L: rows (w, a'), shared a (MN-major blocks)
   uint8_t* T2p;          // packed T2 for (iii): rows (w', b), shared a' d + s' (MN-major blocks)
-  uint8_t* A3p;          // packed core for (iii): rows b', shared a' d + s'
-  int64_t Lp_lo, A1p_lo, T2p_lo, A3p_lo;  // byte distance from a hi block to its lo block (BF16X3)
+  uint8_t* Cp;           // every site's packed cores (K-major blocks)
+  int64_t Lp_lo, T2p_lo, Cp_lo;  // byte distance from a hi block to its lo block (BF16X3)
+  int64_t chunks;        // pack chunks of all the cores
   unsigned* bits;        // per site: bits of the largest |L| entering it
   double* lg;            // float64 log-scale
   unsigned* bar;         // device-wide barrier counter (zero at launch)
@@ -190,6 +193,77 @@ __device__ __forceinline__ float pack_chunk(const PsPack& q, int64_t e, float am
   return amax;
 }
 
+// The pack jobs of a site's core: q1 for (i) (rows (s, b), shared a: A[a, s,
+// b] at (a d + s) Db + b) and q3 for (iii) (rows b', shared a' d + s': at
+// (a' d + s') Db + b'), at their places in the cores region.
+__device__ __forceinline__ void core_packs(const PsParams& p, const PsSite& st, int32_t d, PsPack* q1, PsPack* q3) {
+  if (q1) {
+    q1->src = st.A;
+    q1->hi = p.Cp + st.a1_off;
+    q1->lo = p.Cp_lo;
+    q1->R = d * st.Db;
+    q1->K = st.Da;
+    q1->rd0 = st.Db;
+    q1->rs1 = st.Db;
+    q1->rs0 = 1;
+    q1->ks0_div = st.Da;
+    q1->kq1 = 0;
+    q1->kq0 = (int64_t)d * st.Db;
+    q1->tiles = ceil_div(q1->R, 128);
+    q1->slabs = ceil_div(q1->K, 64);
+  }
+  if (q3) {
+    q3->src = st.A;
+    q3->hi = p.Cp + st.a3_off;
+    q3->lo = p.Cp_lo;
+    q3->R = st.Db;
+    q3->K = d * st.Da;
+    q3->rd0 = st.Db;
+    q3->rs1 = 0;
+    q3->rs0 = 1;
+    q3->ks0_div = q3->K;
+    q3->kq1 = 0;
+    q3->kq0 = st.Db;
+    q3->tiles = ceil_div(q3->R, 128);
+    q3->slabs = ceil_div(q3->K, 64);
+  }
+}
+
+// One 16-byte chunk (8 rows at one shared index) of the first environment
+// L[w, a, a'] as an MN-major operand (row w Da + a', shared a), zeros past R
+// or K; chunks numbered (tile, slab, row group, k), k fastest.
+__device__ __forceinline__ void pack_mn_chunk(const float* L, int32_t Da, int32_t R, int32_t K, int32_t slabs,
+                                              uint8_t* hi, int64_t lo, int64_t e) {
+  const int32_t kk = (int32_t)(e & 63);
+  int64_t rest = e >> 6;
+  const int32_t mg = (int32_t)(rest & 15);
+  rest >>= 4;
+  const int32_t sl = (int32_t)(rest % slabs), t = (int32_t)(rest / slabs);
+  const int32_t k = sl * 64 + kk;
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int32_t r = t * 128 + mg * 8 + j;
+    v[j] = 0.0f;
+    if (r < R && k < K) {
+      const int32_t w = r / Da, a2 = r - w * Da;
+      v[j] = L[((int64_t)w * Da + k) * Da + a2];
+    }
+  }
+  uint4 h, l;
+  uint32_t* hp = reinterpret_cast<uint32_t*>(&h);
+  uint32_t* lp = reinterpret_cast<uint32_t*>(&l);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    hp[j] = ps_bf16x2(v[2 * j], v[2 * j + 1]);
+    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&hp[j]);
+    lp[j] = ps_bf16x2(v[2 * j] - __low2float(hb), v[2 * j + 1] - __high2float(hb));
+  }
+  const size_t off = ((size_t)t * slabs + sl) * PS_BLOCK + mn_block_chunk(mg, kk);
+  *reinterpret_cast<uint4*>(hi + off) = h;
+  if (lo) *reinterpret_cast<uint4*>(hi + lo + off) = l;
+}
+
 // One GEMM phase: C[r, c] = sum_k P[r, k] Q[c, k] over whole packed blocks
 // (P K-major, or MN-major when p_mn; Q K-major), output tiles of 128 x 128.
 struct PsGemm {
@@ -199,6 +273,13 @@ struct PsGemm {
   float* C;
   int32_t ldc, R, N;   // C row stride; rows of P (result rows) and of Q (result columns)
   int32_t tp, tq, slabs, p_mn;
+  // (iii): the result is also the next site's first operand of (i), written
+  // here as whole MN-major blocks (row w' Db + b', shared index b), and its
+  // largest magnitude goes to *maxbits; Pn null: none
+  uint8_t* Pn;
+  int64_t Pn_lo;
+  int32_t Db, pn_slabs;
+  unsigned* maxbits;
 };
 
 // Pipeline positions kept across the phases of the launch: slabs through the
@@ -288,6 +369,7 @@ __device__ bool gemm_drain(const PsGemm& g, PsAux& x, uint32_t tmem, PsPipe& pp,
   const int quad = warp & 3, grp = (warp - PS_EPI0) >> 2;
   const int nks = g.slabs, nchunks = SPLIT ? (nks + PS_KC - 1) / PS_KC : 1;
   const bool vec = (g.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0;
+  float mx = 0.0f;  // largest |value| written to the next site's operand
   for (int u = blockIdx.x; u < g.tp * g.tq; u += gridDim.x) {
     const int tpi = u / g.tq, tqi = u - tpi * g.tq;
     const int row = tpi * 128 + quad * 32 + lane, col0 = tqi * 128 + grp * 64;
@@ -303,6 +385,50 @@ __device__ bool gemm_drain(const PsGemm& g, PsAux& x, uint32_t tmem, PsPipe& pp,
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (32 * h + j < ncol) dst[32 * h + j] = v[j];
+      }
+    };
+    // 32 result columns of this thread's row into the next site's packed
+    // operand: row (w', b) of L' at shared index b, columns b' as rows
+    auto pack_out = [&](int h, const float* v) {
+      if (!g.Pn || row >= g.R) return;
+      const int cb = col0 + 32 * h;
+      if (cb >= g.N) return;
+      const int wq = row / g.Db, b = row - wq * g.Db, kk = b & 63;
+      const size_t slab_off = (size_t)(b >> 6) * PS_BLOCK;
+      if ((g.Db & 63) == 0) {
+        // rows r0 .. r0 + 31 of one tile: four 16-byte chunks
+        const int r0 = wq * g.Db + cb;
+        const size_t base = (size_t)(r0 >> 7) * g.pn_slabs * PS_BLOCK + slab_off;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const size_t off = base + mn_block_chunk(((r0 & 127) >> 3) + c, kk);
+          uint4 hv, lv;
+          uint32_t* hp = reinterpret_cast<uint32_t*>(&hv);
+          uint32_t* lp = reinterpret_cast<uint32_t*>(&lv);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float a = v[8 * c + 2 * j], e2 = v[8 * c + 2 * j + 1];
+            hp[j] = ps_bf16x2(a, e2);
+            const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&hp[j]);
+            lp[j] = ps_bf16x2(a - __low2float(hb), e2 - __high2float(hb));
+            mx = fmaxf(mx, fmaxf(fabsf(a), fabsf(e2)));
+          }
+          *reinterpret_cast<uint4*>(g.Pn + off) = hv;
+          if (g.Pn_lo) *reinterpret_cast<uint4*>(g.Pn + g.Pn_lo + off) = lv;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (cb + j >= g.N) continue;
+          const int r = wq * g.Db + cb + j;
+          const size_t off = (size_t)(r >> 7) * g.pn_slabs * PS_BLOCK + slab_off +
+                             mn_block_chunk((r & 127) >> 3, kk) + 2 * (r & 7);
+          const __nv_bfloat16 hb = __float2bfloat16_rn(v[j]);
+          *reinterpret_cast<__nv_bfloat16*>(g.Pn + off) = hb;
+          if (g.Pn_lo)
+            *reinterpret_cast<__nv_bfloat16*>(g.Pn + g.Pn_lo + off) = __float2bfloat16_rn(v[j] - __bfloat162float(hb));
+          mx = fmaxf(mx, fabsf(v[j]));
+        }
       }
     };
     float acc[SPLIT ? 64 : 1];
@@ -327,6 +453,7 @@ __device__ bool gemm_drain(const PsGemm& g, PsAux& x, uint32_t tmem, PsPipe& pp,
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
           store(h, v);
+          pack_out(h, v);
         }
       }
       ptx::tc_fence_before();
@@ -337,7 +464,14 @@ __device__ bool gemm_drain(const PsGemm& g, PsAux& x, uint32_t tmem, PsPipe& pp,
     if (SPLIT) {
       store(0, acc);
       store(1, acc + 32);
+      pack_out(0, acc);
+      pack_out(1, acc + 32);
     }
+  }
+  if (g.maxbits) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx > 0.0f) atomicMax(g.maxbits, __float_as_uint(mx));
   }
   return true;
 }
@@ -386,83 +520,56 @@ __global__ void __launch_bounds__(PS_THREADS, 1) expect_persistent_kernel(const 
   PsPipe pp{0u, 0u, 0u};
   uint32_t epoch = 0;
   int cur = 0;
-  bool ok = true;
+  // (0) every site's core in the two operand layouts, and the first
+  // environment (1 in each channel) as the first site's MN-major operand
+  for (int64_t e = gtid; e < p.chunks; e += gstride) {
+    int lo = 0, hi = p.n - 1;  // the site whose chunks hold e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.site[mid].chunk0 <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const PsSite& st = p.site[lo];
+    PsPack q;
+    core_packs(p, st, d, &q, nullptr);
+    const int64_t c1 = pack_chunks(q);
+    int64_t k = e - st.chunk0;
+    if (k >= c1) {
+      core_packs(p, st, d, nullptr, &q);
+      k -= c1;
+    }
+    pack_chunk(q, k, 0.0f);
+  }
+  {
+    const PsSite& s0 = p.site[0];
+    const int32_t R = s0.wa * s0.Da, K = s0.Da, tiles = ceil_div(R, 128), slabs = ceil_div(K, 64);
+    for (int64_t e = gtid; e < (int64_t)tiles * slabs * 16 * 64; e += gstride)
+      pack_mn_chunk(p.L[0], s0.Da, R, K, slabs, p.Lp, SPLIT ? p.Lp_lo : 0, e);
+  }
+  bool ok = grid_sync(p, epoch, x);
   for (int i = 0; i < p.n && ok; ++i) {
     const PsSite& st = p.site[i];
     const int32_t Da = st.Da, Db = st.Db, wa = st.wa, wb = st.wb;
-    // (A) L and the core, packed; L's largest magnitude (the site's rescale)
-    PsPack q[3];
-    // L[w, a, a'] as rows (w, a'), shared a
-    q[0].src = p.L[cur];
-    q[0].hi = p.Lp;
-    q[0].lo = SPLIT ? p.Lp_lo : 0;
-    q[0].R = wa * Da;
-    q[0].K = Da;
-    q[0].rd0 = Da;
-    q[0].rs1 = (int64_t)Da * Da;
-    q[0].rs0 = 1;
-    q[0].ks0_div = Da;
-    q[0].kq1 = 0;
-    q[0].kq0 = Da;
-    // A[a, s, b] as rows (s, b), shared a
-    q[1].src = st.A;
-    q[1].hi = p.A1p;
-    q[1].lo = SPLIT ? p.A1p_lo : 0;
-    q[1].R = d * Db;
-    q[1].K = Da;
-    q[1].rd0 = Db;
-    q[1].rs1 = Db;
-    q[1].rs0 = 1;
-    q[1].ks0_div = Da;
-    q[1].kq1 = 0;
-    q[1].kq0 = (int64_t)d * Db;
-    // A[a', s', b'] as rows b', shared a' d + s' (offset (a' d + s') Db)
-    q[2].src = st.A;
-    q[2].hi = p.A3p;
-    q[2].lo = SPLIT ? p.A3p_lo : 0;
-    q[2].R = Db;
-    q[2].K = d * Da;
-    q[2].rd0 = Db;
-    q[2].rs1 = 0;
-    q[2].rs0 = 1;
-    q[2].ks0_div = d * Da;
-    q[2].kq1 = 0;
-    q[2].kq0 = Db;
-    int64_t c[3];
-    for (int j = 0; j < 3; ++j) {
-      q[j].tiles = ceil_div(q[j].R, 128);
-      q[j].slabs = ceil_div(q[j].K, 64);
-      c[j] = pack_chunks(q[j]);
-    }
-    float m = 0.0f;
-    for (int64_t e = gtid; e < c[0] + c[1] + c[2]; e += gstride) {
-      if (e < c[0]) m = pack_chunk(q[0], e, m);
-      else if (e < c[0] + c[1]) pack_chunk(q[1], e - c[0], 0.0f);
-      else pack_chunk(q[2], e - c[0] - c[1], 0.0f);
-    }
-    if (i > 0) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(p.bits + i, __float_as_uint(m));
-    }
-    if (!(ok = grid_sync(p, epoch, x))) break;
+    const int32_t slabs1 = ceil_div(Da, 64), slabs3 = ceil_div(d * Da, 64);
     // (B) T1[(w, a'), (s, b)] = sum_a L[(w, a'), a] A[a, (s, b)]
     PsGemm g;
+    memset(&g, 0, sizeof(g));
     g.P = p.Lp;
-    g.Q = p.A1p;
+    g.Q = p.Cp + st.a1_off;
     g.P_lo = p.Lp_lo;
-    g.Q_lo = p.A1p_lo;
+    g.Q_lo = p.Cp_lo;
     g.C = p.T1;
     g.ldc = d * Db;
     g.R = wa * Da;
     g.N = d * Db;
-    g.tp = q[0].tiles;
-    g.tq = q[1].tiles;
-    g.slabs = q[0].slabs;
-    g.p_mn = 0;
+    g.tp = ceil_div(g.R, 128);
+    g.tq = ceil_div(g.N, 128);
+    g.slabs = slabs1;
+    g.p_mn = 1;
     gemm_phase<SPLIT>(g, stage0, x, tmem, pp, p.status);
     if (!(ok = grid_sync(p, epoch, x))) break;
-    // (C) T2 = 2^-e W' T1, straight into (iii)'s packed first operand
+    // (C) T2 = 2^-e W' T1, straight into (iii)'s packed first operand; zeros
+    // at the shared indices past Db of the next site's operand of (i)
     StepIIPack q2;
     q2.T1 = p.T1;
     q2.W = p.Wx + st.woff;
@@ -476,25 +583,45 @@ __global__ void __launch_bounds__(PS_THREADS, 1) expect_persistent_kernel(const 
     q2.wb = wb;
     q2.d = d;
     q2.tiles = ceil_div(wb * Db, 128);
-    q2.slabs = q[2].slabs;
+    q2.slabs = slabs3;
     q2.ps = 1;
     q2.pa = d;
     q2.pad = 0;
     step_ii_pack(q2, gtid, gstride, blockIdx.x == 0 && threadIdx.x == 0);
+    const int32_t nslabs = ceil_div(Db, 64), npad = nslabs * 64 - Db;
+    if (i + 1 < p.n && npad > 0) {
+      const int64_t nz = (int64_t)ceil_div(wb * Db, 128) * 16 * npad;
+      for (int64_t e = gtid; e < nz; e += gstride) {
+        const int32_t kk = Db + (int32_t)(e % npad);
+        const int64_t rest = e / npad;
+        const int32_t mg = (int32_t)(rest & 15), t = (int32_t)(rest >> 4);
+        const size_t off = ((size_t)t * nslabs + (kk >> 6)) * PS_BLOCK + mn_block_chunk(mg, kk & 63);
+        *reinterpret_cast<uint4*>(p.Lp + off) = make_uint4(0u, 0u, 0u, 0u);
+        if (SPLIT) *reinterpret_cast<uint4*>(p.Lp + p.Lp_lo + off) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
     if (!(ok = grid_sync(p, epoch, x))) break;
-    // (D) L'[(w', b), b'] = sum_{(a', s')} T2[(w', b), (a', s')] A[(a', s'), b']
+    // (D) L'[(w', b), b'] = sum_{(a', s')} T2[(w', b), (a', s')] A[(a', s'), b'];
+    // L' also packed as the next site's operand of (i), with its largest magnitude
     g.P = p.T2p;
-    g.Q = p.A3p;
+    g.Q = p.Cp + st.a3_off;
     g.P_lo = p.T2p_lo;
-    g.Q_lo = p.A3p_lo;
+    g.Q_lo = p.Cp_lo;
     g.C = p.L[cur ^ 1];
     g.ldc = Db;
     g.R = wb * Db;
     g.N = Db;
     g.tp = q2.tiles;
-    g.tq = q[2].tiles;
-    g.slabs = q[2].slabs;
+    g.tq = ceil_div(Db, 128);
+    g.slabs = slabs3;
     g.p_mn = 1;
+    if (i + 1 < p.n) {
+      g.Pn = p.Lp;
+      g.Pn_lo = SPLIT ? p.Lp_lo : 0;
+      g.Db = Db;
+      g.pn_slabs = nslabs;
+      g.maxbits = p.bits + i + 1;
+    }
     gemm_phase<SPLIT>(g, stage0, x, tmem, pp, p.status);
     if (!(ok = grid_sync(p, epoch, x))) break;
     cur ^= 1;
@@ -523,6 +650,19 @@ __global__ void __launch_bounds__(PS_THREADS, 1) expect_persistent_kernel(const 
 
 }  // namespace
 
+size_t ps_blocks(int64_t R, int64_t K) { return (size_t)((R + 127) / 128) * (size_t)((K + 63) / 64) * PS_BLOCK; }
+
+// One plane (hi or lo) of every site's packed cores: the core as (i)'s
+// second operand (d Db rows, Da shared) then as (iii)'s (Db rows, d Da shared).
+size_t cores_plane_bytes(const tn_mps* psi) {
+  size_t b = 0;
+  for (int i = 0; i < psi->n; ++i)
+    b += ps_blocks(psi->d * psi->bond[i + 1], psi->bond[i]) + ps_blocks(psi->bond[i + 1], psi->d * psi->bond[i]);
+  return align256(b);
+}
+
+size_t expect_persistent_cores_bytes(const tn_mps* psi) { return 2 * cores_plane_bytes(psi); }
+
 bool expect_persistent_ok(const tn_mps* psi, const tn_mpo* H, int prec) {
   if (prec != TN_PREC_BF16 && prec != TN_PREC_BF16X3) return false;
   if (psi->n > PS_MAX_SITES) return false;
@@ -543,22 +683,21 @@ int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const Expect
   p.L[0] = w.L0;
   p.L[1] = w.L1;
   p.T1 = w.T1;
-  // packed regions, laid out for the largest bond: [L hi | core(i) hi | L lo | core(i) lo]
-  // and [T2 hi | core(iii) hi | T2 lo | core(iii) lo]
+  // packed regions, laid out for the largest bond: L (hi, lo) in scratch,
+  // T2 (hi, lo) in scratch3; every site's cores (hi plane, then lo) in cores
   int64_t Wm = 1, D = 1;
   for (int i = 0; i <= H->n; ++i) Wm = std::max(Wm, H->bond[i]);
   for (int i = 0; i <= psi->n; ++i) D = std::max(D, psi->bond[i]);
   const int64_t W1 = Wm + 1, d = psi->d;
-  auto blocks = [](int64_t R, int64_t K) { return (size_t)((R + 127) / 128) * (size_t)((K + 63) / 64) * PS_BLOCK; };
-  const size_t bl = align256(blocks(W1 * D, D)), ba1 = align256(blocks(d * D, D));
-  const size_t bt = align256(blocks(W1 * D, d * D)), ba3 = align256(blocks(D, d * D));
-  if (w.scratch_bytes < 2 * (bl + ba1) || w.scratch3_bytes < 2 * (bt + ba3)) return TN_ERR_WORKSPACE;
+  const size_t bl = align256(ps_blocks(W1 * D, D)), bt = align256(ps_blocks(W1 * D, d * D));
+  const size_t bc = cores_plane_bytes(psi);
+  if (w.scratch_bytes < 2 * bl || w.scratch3_bytes < 2 * bt || w.cores_bytes < 2 * bc) return TN_ERR_WORKSPACE;
   p.Lp = w.scratch;
-  p.A1p = w.scratch + bl;
-  p.Lp_lo = p.A1p_lo = (int64_t)(bl + ba1);
+  p.Lp_lo = split ? (int64_t)bl : 0;
   p.T2p = w.scratch3;
-  p.A3p = w.scratch3 + bt;
-  p.T2p_lo = p.A3p_lo = (int64_t)(bt + ba3);
+  p.T2p_lo = split ? (int64_t)bt : 0;
+  p.Cp = w.cores;
+  p.Cp_lo = split ? (int64_t)bc : 0;
   p.bits = w.bits;
   p.lg = w.lg;
   p.bar = w.bar;
@@ -573,6 +712,20 @@ int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const Expect
     st.wb = (int32_t)(H->bond[i + 1] + 1);
     st.woff = (int32_t)w.woff[(size_t)i];
   }
+  // the cores' places and pack chunks, site by site
+  size_t off = 0;
+  int64_t chunks = 0;
+  for (int i = 0; i < psi->n; ++i) {
+    PsSite& st = p.site[i];
+    const int64_t Da = st.Da, Db = st.Db;
+    st.a1_off = (int64_t)off;
+    off += ps_blocks(d * Db, Da);
+    st.a3_off = (int64_t)off;
+    off += ps_blocks(Db, d * Da);
+    st.chunk0 = chunks;
+    chunks += (int64_t)(ps_blocks(d * Db, Da) + ps_blocks(Db, d * Da)) / PS_BLOCK * 1024;
+  }
+  p.chunks = chunks;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                 cudaSuccess)

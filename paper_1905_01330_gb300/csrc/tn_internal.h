@@ -161,7 +161,8 @@ void step_iii_places(int64_t Da, int64_t Db, int64_t d, const int64_t* kstrA, in
 // from the energy sweep's workspace: environments L0 / L1 (with the first
 // site's L0 = 1 in its channels), T1, the extended MPO Wx (site i at
 // woff[i]), per-site max slots `bits` and the log-scale `lg` (zeroed), the
-// barrier counter `bar` (4 bytes), and the packed regions `scratch` / `scratch3`.
+// barrier counter `bar` (4 bytes), the packed regions `scratch` / `scratch3`
+// and `cores` (every site's core packed once per call).
 struct ExpectBuffers {
   float *L0, *L1, *T1;
   const float* Wx;
@@ -173,8 +174,11 @@ struct ExpectBuffers {
   size_t scratch_bytes;
   uint8_t* scratch3;
   size_t scratch3_bytes;
+  uint8_t* cores;  // every site's packed cores (expect_persistent_cores_bytes)
+  size_t cores_bytes;
 };
 bool expect_persistent_ok(const tn_mps* psi, const tn_mpo* H, int prec);
+size_t expect_persistent_cores_bytes(const tn_mps* psi);
 int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const ExpectBuffers& w, double* result,
                       cudaStream_t s);
 
