@@ -303,6 +303,19 @@ int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace
  * The MPO's bonds must satisfy (bond + 1) * d <= 32, n <= 1024 and
  * (bond + 1) * D * d * D < 2^31 for the largest MPS bond D (else
  * TN_ERR_UNSUPPORTED).
+ * Launch forms (results the same up to the order of float32 sums):
+ *   - BF16 / BF16X3 with (bond + 1) * d <= 8 on every MPO bond, n <= 512 and
+ *     D <= 512: ONE persistent cooperative launch for the whole chain (one
+ *     CTA per SM, the sites' GEMM (i) / step (ii) / GEMM (iii) phases
+ *     separated by device-wide barriers; the cores packed to bf16 once per
+ *     call, step (ii) and GEMM (iii) writing the next contraction's packed
+ *     operand). Its barriers are bounded: on expiry TN_ERR_TIMEOUT is
+ *     recorded in the status word (tn_sync_status) and the launch ends.
+ *   - BF16 / BF16X3 otherwise with (bond + 1) * d <= 8: four launches per
+ *     site (a pack of L and the core, the GEMM of (i), step (ii) written
+ *     straight into (iii)'s packed operand, the GEMM of (iii)).
+ *   - FP32 and wider MPOs: three contractions, a float32 step (ii) and a
+ *     max-abs pass per site.
  *   result: DEVICE pointer to 4 doubles {e_value, e_log_scale, n_value,
  *           n_log_scale}: <psi|H|psi> = e_value * exp(e_log_scale) and
  *           <psi|psi> = n_value * exp(n_log_scale); the energy per the
