@@ -829,7 +829,7 @@ def main():
         serial_ms = e2e_time(serial)
         e2e = {"value": tndist.weak_scaling_value(flops, e_ms, world) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "api": "StagedGroupPlan.run(host_in, host_out), 32 chunks",
+               "api": "StagedGroupPlan.run(host_in, host_out) = tn_staged_plan_run, 32 chunks",
                "serial_ms_per_step": serial_ms,
                "serial_value": tndist.weak_scaling_value(flops, serial_ms, world) / 1e12}
         del staged, host_in, host_out

@@ -241,6 +241,56 @@ int tn_group_plan_schedule(const tn_group_plan* plan, int cls, int* tile_width, 
  * Errors: TN_ERR_ARG, TN_ERR_UNSUPPORTED (256 on a BF16X3 plan). */
 int tn_group_plan_set_schedule(tn_group_plan* plan, int cls, int tile_width, int long_k, int store16);
 
+/*
+ * A grouped contraction staged from and to HOST memory: the end-to-end form
+ * of the plan above, for operands that start in host memory and results
+ * that must end there. (The paper's contractions start and end in the
+ * backend's memory; this is a convenience of the library.)
+ *   specs: as tn_group_plan_create; every A and B a view into the device
+ *     buffer dev_in (in_bytes long), every C a view into dev_out (out_bytes),
+ *     laid out in spec order (a later spec's tensors never start before an
+ *     earlier spec's end), so each run of consecutive specs owns one byte
+ *     range of each buffer.
+ *   chunks: the specs are cut into at most this many runs of about equal
+ *     bytes (tn_chunk_bounds), each with its own group plan.
+ *   tn_staged_plan_create: host validation and planning; creates three
+ *     non-blocking streams and two events per chunk on the current device
+ *     (released by _destroy).
+ *   tn_staged_plan_set_schedule: tn_group_plan_set_schedule on every chunk's
+ *     plan (before _upload).
+ *   tn_staged_plan_workspace_bytes / _upload: one DEVICE workspace (256-byte
+ *     aligned) holding every chunk plan's work lists and one packed region
+ *     they share (they run one after another); upload on `stream`.
+ *   tn_staged_plan_run: host_in (HOST, laid out like dev_in; pinned for the
+ *     copies to overlap) and host_out (HOST, laid out like dev_out). Chunk c's
+ *     byte range of host_in is copied to dev_in on one library stream while
+ *     chunk c - 1 is contracted on a second and chunk c - 2's range of
+ *     dev_out goes to host_out on a third; the library streams start after
+ *     `stream`'s earlier work and `stream` waits for all of them, so host_out
+ *     is complete once `stream` is.
+ * Errors: as tn_group_plan_create and _run, plus TN_ERR_ARG when a tensor
+ * lies outside its buffer or the layout is not in spec order.
+ */
+typedef struct tn_staged_plan tn_staged_plan;
+int tn_staged_plan_create(const tn_contract_spec* specs, int nspecs, int prec, const void* dev_in, size_t in_bytes,
+                          void* dev_out, size_t out_bytes, int chunks, tn_staged_plan** plan);
+int tn_staged_plan_chunks(const tn_staged_plan* plan);
+double tn_staged_plan_flops(const tn_staged_plan* plan);
+int tn_staged_plan_set_schedule(tn_staged_plan* plan, int cls, int tile_width, int long_k, int store16);
+size_t tn_staged_plan_workspace_bytes(const tn_staged_plan* plan);
+int tn_staged_plan_upload(const tn_staged_plan* plan, void* workspace, size_t bytes, void* stream);
+int tn_staged_plan_run(const tn_staged_plan* plan, void* workspace, size_t bytes, const void* host_in,
+                       void* host_out, void* stream);
+void tn_staged_plan_destroy(tn_staged_plan* plan);
+/* Cuts n items with the given (host) weights into at most `chunks` runs of
+ * consecutive items of about equal total weight: bounds (HOST, room for
+ * chunks + 1 ints) receives the run boundaries 0 = b_0 < b_1 < ... = n (0, 0
+ * for n = 0), *nbounds their count. Boundary k goes where the running weight
+ * comes closest to k/chunks of the total, strictly after the previous one and
+ * before the end; a run never splits an item, so heavy items make fewer,
+ * unequal runs. Host only. Errors: TN_ERR_ARG. */
+int tn_chunk_bounds(const double* weights, int n, int chunks, int* bounds, int* nbounds);
+
 /* ------------------------------------------------------------------------ */
 /* Matrix product states and operators (Sec. II, Fig. 3a)                    */
 /* ------------------------------------------------------------------------ */

@@ -6,7 +6,6 @@ built, or no GPU is present, the calls raise.
 """
 from __future__ import annotations
 
-import bisect
 import ctypes
 import os
 
@@ -100,6 +99,17 @@ def _signatures():
         "tn_group_plan_autotune": (i32, [vp, vp, ctypes.c_size_t, vp]),
         "tn_group_plan_schedule": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "tn_group_plan_set_schedule": (i32, [vp, i32, i32, i32, i32]),
+        "tn_staged_plan_create": (i32, [ctypes.POINTER(TnContractSpec), i32, i32, vp, ctypes.c_size_t, vp,
+                                        ctypes.c_size_t, i32, ctypes.POINTER(vp)]),
+        "tn_staged_plan_chunks": (i32, [vp]),
+        "tn_staged_plan_flops": (ctypes.c_double, [vp]),
+        "tn_staged_plan_set_schedule": (i32, [vp, i32, i32, i32, i32]),
+        "tn_staged_plan_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "tn_staged_plan_upload": (i32, [vp, vp, ctypes.c_size_t, vp]),
+        "tn_staged_plan_run": (i32, [vp, vp, ctypes.c_size_t, vp, vp, vp]),
+        "tn_staged_plan_destroy": (None, [vp]),
+        "tn_chunk_bounds": (i32, [ctypes.POINTER(ctypes.c_double), i32, i32, ctypes.POINTER(i32),
+                                  ctypes.POINTER(i32)]),
         "tn_mps_inner_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
         "tn_mps_inner": (i32, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain), i32, vp, ctypes.c_size_t, vp, vp]),
         "tn_mps_expect_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(TnChain), ctypes.POINTER(TnChain)]),
@@ -592,95 +602,80 @@ class GroupPlan:
 
 def chunk_bounds(weights, chunks: int):
     """Cuts a sequence of items with the given weights into at most `chunks`
-    runs of consecutive items of about equal total weight: returns the run
-    boundaries [0, ..., len(weights)]. Boundary k goes where the running
-    weight comes closest to k/chunks of the total (strictly after the
-    previous boundary and before the end); a run never splits an item, so
-    heavy items make fewer, unequal runs."""
-    n, cum, acc = len(weights), [], 0
-    for w in weights:
-        acc += w
-        cum.append(acc)
-    bounds = [0]
-    for k in range(1, chunks):
-        t = acc * k / chunks
-        j = bisect.bisect_left(cum, t)  # first item whose running weight reaches t
-        cands = list(range(max(bounds[-1] + 1, j), min(j + 2, n)))
-        if not cands and bounds[-1] + 1 < n:
-            cands = [bounds[-1] + 1]
-        if cands:
-            bounds.append(min(cands, key=lambda b: abs(cum[b - 1] - t)))
-    bounds.append(n)
-    return bounds
+    runs of consecutive items of about equal total weight (tn_chunk_bounds,
+    host code in the library): returns the run boundaries [0, ..., len(weights)]."""
+    lib = load(require_gpu=False)
+    n = len(weights)
+    w = (ctypes.c_double * max(n, 1))(*[float(x) for x in weights])
+    out = (ctypes.c_int32 * (chunks + 1))()
+    m = ctypes.c_int32()
+    _check(lib.tn_chunk_bounds(w, n, chunks, out, ctypes.byref(m)), "tn_chunk_bounds")
+    return [out[i] for i in range(m.value)]
+
+
+def _spec_array(specs):
+    arr = (TnContractSpec * max(len(specs), 1))()
+    for i, (A, la, B, lb, C) in enumerate(specs):
+        arr[i].A = tensor_desc(A)
+        arr[i].B = tensor_desc(B)
+        arr[i].C = tensor_desc(C)
+        arr[i].nshared = len(la)
+        for j in range(len(la)):
+            arr[i].legsA[j] = la[j]
+            arr[i].legsB[j] = lb[j]
+    return arr
 
 
 class StagedGroupPlan:
     """A grouped contraction fed from pinned host memory and drained back to it
-    in chunks. The specs' operands must fill one device buffer `dev_in` and
-    their results another, `dev_out`, in spec order (each chunk of consecutive
-    specs then owns one contiguous range of each). run(host_in, host_out)
-    copies chunk c's operands host -> device on one stream while chunk c-1 is
-    contracted (its own GroupPlan) on a second and chunk c-2's results go
-    device -> host on a third, so the two copy directions and the kernels
-    overlap; the caller's stream waits for the last copy. host_in / host_out
-    are pinned tensors laid out like dev_in / dev_out."""
+    in chunks (tn_staged_plan_*). The specs' operands must fill one device
+    buffer `dev_in` and their results another, `dev_out`, in spec order (each
+    chunk of consecutive specs then owns one contiguous range of each).
+    run(host_in, host_out): the library copies chunk c's operands host ->
+    device on one of its streams while chunk c-1 is contracted on a second and
+    chunk c-2's results go device -> host on a third; the caller's stream
+    waits for the last copy. host_in / host_out are pinned tensors laid out
+    like dev_in / dev_out."""
 
     def __init__(self, specs, dev_in: torch.Tensor, dev_out: torch.Tensor, chunks: int = 8, prec: str = "bf16",
-                 schedule=None):
+                 schedule=None, stream=None):
         if dev_in.dim() != 1 or dev_out.dim() != 1:
             raise ValueError("dev_in and dev_out must be 1-D buffers")
-        esz = dev_in.element_size()
-        base_in, base_out = dev_in.data_ptr(), dev_out.data_ptr()
-
-        def span(t, base, n):
-            lo = (t.data_ptr() - base) // esz
-            if t.data_ptr() < base or lo + t.numel() > n:
-                raise ValueError("a spec tensor lies outside its buffer")
-            return lo, lo + t.numel()
-        bounds = chunk_bounds([A.numel() + B.numel() + C.numel() for A, _, B, _, C in specs], chunks)
+        lib = load()
+        arr = _spec_array(specs)
+        h = ctypes.c_void_p()
+        _check(lib.tn_staged_plan_create(arr, len(specs), PREC[prec], ctypes.c_void_p(dev_in.data_ptr()),
+                                         dev_in.numel() * dev_in.element_size(),
+                                         ctypes.c_void_p(dev_out.data_ptr()),
+                                         dev_out.numel() * dev_out.element_size(), chunks, ctypes.byref(h)),
+               "tn_staged_plan_create")
+        self._h = h
+        self._keep = (specs, dev_in, dev_out)
         self.dev_in, self.dev_out = dev_in, dev_out
-        self.parts = []
-        prev_in = prev_out = 0
-        for c in range(len(bounds) - 1):
-            sp = specs[bounds[c]:bounds[c + 1]]
-            if not sp:
-                continue
-            ins = [span(t, base_in, dev_in.numel()) for A, _, B, _, _ in sp for t in (A, B)]
-            outs = [span(C, base_out, dev_out.numel()) for *_, C in sp]
-            lo_in, hi_in = min(a for a, _ in ins), max(b for _, b in ins)
-            lo_out, hi_out = min(a for a, _ in outs), max(b for _, b in outs)
-            if lo_in < prev_in or lo_out < prev_out:
-                raise ValueError("operands and results must be laid out in spec order")
-            prev_in, prev_out = hi_in, hi_out
-            plan = GroupPlan(sp, prec=prec)
-            if schedule:
-                for cls, (w, lk, s16) in schedule.items():
-                    plan.set_schedule(cls, w, bool(lk), bool(s16))
-            self.parts.append((plan, lo_in, hi_in, lo_out, hi_out))
-        self.flops = sum(p[0].flops for p in self.parts)
-        dev = dev_in.device
-        self.streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+        self.chunks = lib.tn_staged_plan_chunks(h)
+        self.flops = lib.tn_staged_plan_flops(h)
+        if schedule:
+            for cls, (w, lk, s16) in schedule.items():
+                _check(lib.tn_staged_plan_set_schedule(h, GroupPlan.SCHEDULE_CLASSES.index(cls), w, int(bool(lk)),
+                                                       int(bool(s16))), "tn_staged_plan_set_schedule")
+        nbytes = lib.tn_staged_plan_workspace_bytes(h)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev_in.device)
+        self.ws_bytes = self.workspace.numel()
+        _check(lib.tn_staged_plan_upload(h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                         _stream(stream)), "tn_staged_plan_upload")
 
-    def run(self, host_in: torch.Tensor, host_out: torch.Tensor):
-        h2d, comp, d2h = self.streams
-        cur = torch.cuda.current_stream(self.dev_in.device)
-        for st in self.streams:
-            st.wait_stream(cur)
-        for plan, lo_in, hi_in, lo_out, hi_out in self.parts:
-            with torch.cuda.stream(h2d):
-                self.dev_in[lo_in:hi_in].copy_(host_in[lo_in:hi_in], non_blocking=True)
-                ready = torch.cuda.Event()
-                ready.record(h2d)
-            comp.wait_event(ready)
-            with torch.cuda.stream(comp):
-                plan.run()
-                done = torch.cuda.Event()
-                done.record(comp)
-            d2h.wait_event(done)
-            with torch.cuda.stream(d2h):
-                host_out[lo_out:hi_out].copy_(self.dev_out[lo_out:hi_out], non_blocking=True)
-        for st in self.streams:
-            cur.wait_stream(st)
+    def run(self, host_in: torch.Tensor, host_out: torch.Tensor, stream=None):
+        if host_in.numel() * host_in.element_size() < self.dev_in.numel() * self.dev_in.element_size() or \
+                host_out.numel() * host_out.element_size() < self.dev_out.numel() * self.dev_out.element_size():
+            raise ValueError("host buffers must be laid out like dev_in / dev_out")
+        _check(load().tn_staged_plan_run(self._h, ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                                         ctypes.c_void_p(host_in.data_ptr()), ctypes.c_void_p(host_out.data_ptr()),
+                                         _stream(stream)), "tn_staged_plan_run")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.tn_staged_plan_destroy(self._h)
+            self._h = None
 
 
 def classifier_workspace(cores, label_site: int, n_labels: int, batch: int, ckpt_every: int) -> torch.Tensor:

@@ -1,4 +1,4 @@
-"""Host logic without a GPU: the chunking of StagedGroupPlan and the bench's
+"""Host logic without a GPU: the chunking of the staged plan (tn_chunk_bounds) and the bench's
 JSON line of the reference arm (the FP64 oracle on the host cores)."""
 import json
 import os
@@ -10,6 +10,12 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+@pytest.fixture(scope="module")
+def built():
+    from paper_1905_01330_gb300 import build
+    return build.build()
+
+
 @pytest.mark.parametrize("weights,chunks,bounds", [
     ([1] * 8, 4, [0, 2, 4, 6, 8]),
     ([1] * 7, 3, [0, 2, 5, 7]),
@@ -19,9 +25,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     ([5], 8, [0, 1]),
     ([], 4, [0, 0]),
 ])
-def test_chunk_bounds(weights, chunks, bounds):
+def test_chunk_bounds(built, weights, chunks, bounds):
     from paper_1905_01330_gb300.tn import chunk_bounds
-    got = chunk_bounds(weights, chunks)
+    got = chunk_bounds(weights, chunks)  # tn_chunk_bounds, host code of libtn.so
     assert got == bounds
     assert all(a < b for a, b in zip(got, got[1:])) or not weights
 

@@ -232,7 +232,7 @@ def test_staged_plan_from_pinned_host(tn):
         C = dev_out[out_offs[i]:out_offs[i] + int(np.prod(outs[i]))].view(outs[i])
         specs.append((A, list(la), B, list(lb), C))
     staged = tn.StagedGroupPlan(specs, dev_in, dev_out, chunks=3, prec="bf16")
-    assert len(staged.parts) == 3
+    assert staged.chunks == 3
     host_in = torch.empty(n_in, dtype=torch.float32, pin_memory=True)
     host_out = torch.empty(n_out, dtype=torch.float32, pin_memory=True)
     for seed in (1, 2):
