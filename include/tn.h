@@ -511,6 +511,13 @@ int tn_mps_classify_loss(const float* ftilde, const int64_t* labels, int batch, 
  * Errors: TN_ERR_CUDA (launch failed).
  */
 int tn_check_wait_timeout(uint64_t limit_ns, void* stream);
+/* Failure-path check of the persistent energy sweep's device-wide barrier: a
+ * two-CTA cooperative launch in which one CTA leaves without arriving, so the
+ * other's bounded wait gives up after limit_ns (clamped to 10 ms .. 2 s) and
+ * records TN_ERR_TIMEOUT in the status word. counter: 4 bytes of DEVICE memory
+ * the barrier counts in (zeroed here, on `stream`). No GPU fault is involved;
+ * the context stays usable. Errors: TN_ERR_ARG, TN_ERR_CUDA. */
+int tn_check_grid_barrier_timeout(uint64_t limit_ns, void* counter, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Classifier with one MPS per label (Sec. IV.A)                              */

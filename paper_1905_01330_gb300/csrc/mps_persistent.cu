@@ -92,25 +92,27 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Device-wide barrier of the cooperative grid (all threads of every CTA).
-// Writes before it are visible after it to every CTA's generic loads and to
-// the bulk copies (async proxy) that read packed blocks. Bounded: on expiry
-// the status word records TN_ERR_TIMEOUT and false is returned everywhere in
-// this CTA (the CTAs that did arrive time out too and wind down).
-__device__ bool grid_sync(const PsParams& p, uint32_t& epoch, PsAux& x) {
+// Device-wide barrier of the cooperative grid (all threads of every CTA):
+// arrival `epoch` completes when the counter at `bar` reaches (epoch + 1) *
+// gridDim.x. Writes before it are visible after it to every CTA's generic
+// loads and to the bulk copies (async proxy) that read packed blocks.
+// Bounded: after limit_ns of waiting the status word records TN_ERR_TIMEOUT,
+// *abort is set and false is returned everywhere in this CTA (the CTAs that
+// did arrive time out too and wind down).
+__device__ bool grid_barrier(unsigned* bar, uint32_t& epoch, int* status, uint64_t limit_ns, volatile int32_t* abort) {
   fence_proxy_async_global();
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const uint32_t target = (epoch + 1) * gridDim.x;
-    atomicAdd(p.bar, 1u);
-    if (ld_acquire_gpu(p.bar) < target) {
+    atomicAdd(bar, 1u);
+    if (ld_acquire_gpu(bar) < target) {
       const uint64_t t0 = ptx::globaltimer();
       for (uint32_t i = 1;; ++i) {
-        if (ld_acquire_gpu(p.bar) >= target) break;
-        if ((i & 63u) == 0u && ptx::globaltimer() - t0 > ptx::kWaitLimitNs) {
-          ptx::set_status(p.status, TN_ERR_TIMEOUT);
-          x.abort = 1;
+        if (ld_acquire_gpu(bar) >= target) break;
+        if ((i & 63u) == 0u && ptx::globaltimer() - t0 > limit_ns) {
+          ptx::set_status(status, TN_ERR_TIMEOUT);
+          *abort = 1;
           break;
         }
       }
@@ -120,7 +122,22 @@ __device__ bool grid_sync(const PsParams& p, uint32_t& epoch, PsAux& x) {
   ++epoch;
   __syncthreads();
   fence_proxy_async_global();
-  return x.abort == 0;
+  return *abort == 0;
+}
+
+__device__ __forceinline__ bool grid_sync(const PsParams& p, uint32_t& epoch, PsAux& x) {
+  return grid_barrier(p.bar, epoch, p.status, ptx::kWaitLimitNs, &x.abort);
+}
+
+// Failure-path check of the device-wide barrier: CTA 1 of a two-CTA
+// cooperative launch leaves without arriving, so CTA 0's wait runs out.
+__global__ void grid_barrier_timeout_kernel(unsigned* bar, int* status, uint64_t limit_ns) {
+  __shared__ volatile int32_t abort;
+  if (threadIdx.x == 0) abort = 0;
+  __syncthreads();
+  if (blockIdx.x != 0) return;
+  uint32_t epoch = 0;
+  grid_barrier(bar, epoch, status, limit_ns, &abort);
 }
 
 __device__ __forceinline__ uint32_t ps_bf16x2(float a, float b) {
@@ -762,3 +779,25 @@ int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const Expect
 }
 
 }  // namespace tn
+
+extern "C" int tn_check_grid_barrier_timeout(uint64_t limit_ns, void* counter, void* stream) {
+  if (!counter || (reinterpret_cast<uintptr_t>(counter) & 3)) return TN_ERR_ARG;
+  const uint64_t lo = 10000000ull, hi = 2000000000ull;
+  uint64_t lim = limit_ns < lo ? lo : (limit_ns > hi ? hi : limit_ns);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return TN_ERR_CUDA;
+  unsigned* bar = static_cast<unsigned*>(counter);
+  int* status = tn::status_word();
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tn::grid_barrier_timeout_kernel, bar, status, lim) == cudaSuccess ? TN_OK
+                                                                                                   : TN_ERR_CUDA;
+}

@@ -140,6 +140,7 @@ def _signatures():
         "tn_mps_classify_separate_backward": (i32, [ctypes.POINTER(TnChain), i32, vp, i32, i32, i32, vp,
                                                     ctypes.POINTER(ctypes.c_void_p), vp, ctypes.c_size_t, vp]),
         "tn_check_wait_timeout": (i32, [ctypes.c_uint64, vp]),
+        "tn_check_grid_barrier_timeout": (i32, [ctypes.c_uint64, vp, vp]),
         "tn_sync_status": (i32, [vp]),
         "tn_status_string": (ctypes.c_char_p, [i32]),
     }
@@ -235,6 +236,13 @@ def sync_status(stream=None) -> int:
 def check_wait_timeout(limit_ns: int = 20_000_000, stream=None) -> None:
     """Launches the failure-path check kernel (tn_check_wait_timeout)."""
     _check(load().tn_check_wait_timeout(limit_ns, _stream(stream)), "tn_check_wait_timeout")
+
+
+def check_grid_barrier_timeout(limit_ns: int = 20_000_000, stream=None) -> None:
+    """Launches the device-wide barrier's failure-path check (tn_check_grid_barrier_timeout)."""
+    counter = torch.zeros(64, dtype=torch.int32, device="cuda")
+    _check(load().tn_check_grid_barrier_timeout(limit_ns, ctypes.c_void_p(counter.data_ptr()), _stream(stream)),
+           "tn_check_grid_barrier_timeout")
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
