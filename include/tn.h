@@ -128,7 +128,10 @@ typedef struct tn_contract_spec {
  *     returns TN_OK and *plan, or the first spec's error (*plan = NULL).
  *   tn_group_plan_workspace_bytes: device bytes the plan's work list needs.
  *   tn_group_plan_upload: copies the work list into `workspace` (device,
- *     256-byte aligned, at least the size above) on `stream`.
+ *     256-byte aligned, at least the size above) on `stream`, from host
+ *     lists that a captured copy could not replay: on a stream being
+ *     captured into a CUDA graph it returns TN_ERR_UNSUPPORTED (upload
+ *     before capturing; tn_group_plan_run itself only launches).
  *   tn_group_plan_run: launches the contractions; `workspace` must hold the
  *     uploaded work list (uploads and runs are ordered on the stream).
  *   tn_group_plan_destroy: frees the host plan (never device memory).
@@ -390,7 +393,9 @@ int tn_mps_expect(const tn_mps* psi, const tn_mpo* H, int prec, void* workspace,
  *           bytes, 256-byte aligned: the environments and intermediates of
  *           every state plus the uploaded launch tables. The call uploads
  *           those tables (host -> device copies on `stream`) and then
- *           launches; it is not meant for stream capture.
+ *           launches; on a stream being captured into a CUDA graph it
+ *           returns TN_ERR_UNSUPPORTED (as does _plan below; _run only
+ *           launches).
  * Errors: as tn_mps_expect, plus TN_ERR_ARG when count < 1 or the states
  * differ in length or physical dimension.
  */
@@ -473,7 +478,9 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
  * accumulates every step's dW (the products over the segment's samples on
  * tcgen05, float32 reductions into a workspace buffer, then one scatter);
  * TN_PREC_FP32 runs the float32 adjoint sweep and one grouped tensordot over
- * the batch per segment.
+ * the batch per segment (their plans built and uploaded in the call, so the
+ * FP32 backward returns TN_ERR_UNSUPPORTED on a stream being captured into a
+ * CUDA graph; BF16 / BF16X3 only launch).
  *   dcores: host table of n DEVICE pointers, each shaped like its core
  *           (overwritten).
  *   prec:   arithmetic of the sweeps and of the gradient products (the label

@@ -498,7 +498,8 @@ static int upload_tables(const tn_group_plan* plan, uint8_t* base, cudaStream_t 
 static int upload_impl(const tn_group_plan* plan, void* workspace, uint8_t* packed, cudaStream_t s,
                        bool with_tables = true) {
   // pageable sources: each call returns once the bytes are staged, so the
-  // plan may be destroyed right after it
+  // plan may be destroyed right after it -- and a capturing stream is refused
+  if (stream_capturing(s)) return TN_ERR_UNSUPPORTED;
   uint8_t* base = static_cast<uint8_t*>(workspace);
   if (plan->packed) {
     // device addresses of the packed blocks, patched into copies of the lists

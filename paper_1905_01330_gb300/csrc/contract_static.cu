@@ -64,8 +64,7 @@ extern "C" int tn_contract_grouped_static(const tn_contract_spec* specs, int nsp
   // The work list is copied from host staging arrays that the next call
   // overwrites: a captured copy would replay whatever list was staged last.
   // So a capturing stream is refused before anything is enqueued.
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return TN_ERR_UNSUPPORTED;
+  if (stream_capturing(s)) return TN_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> guard(h_lock);
   unsigned char* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);

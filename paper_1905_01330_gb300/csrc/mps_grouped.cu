@@ -418,6 +418,8 @@ int tn_mps_expect_grouped_plan(const tn_mps* psis, int count, const tn_mpo* H, i
   if (!plan) return TN_ERR_ARG;
   *plan = nullptr;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return TN_ERR_WORKSPACE;
+  // its tables are copied from host lists that live in the plan: not from a capture
+  if (stream_capturing(static_cast<cudaStream_t>(stream))) return TN_ERR_UNSUPPORTED;
   std::unique_ptr<tn_expect_plan> pl(new tn_expect_plan());
   uint8_t* base = static_cast<uint8_t*>(workspace);
   GroupedSweep& g = pl->g;

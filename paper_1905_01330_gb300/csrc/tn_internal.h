@@ -197,4 +197,17 @@ int* status_word();
 // Bytes rounded up to the 256-byte alignment every workspace region keeps.
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// True when `s` is being captured into a CUDA graph (or the query fails, as
+// it does on the legacy stream while another stream captures). Calls that
+// copy host lists which do not outlive them (plan uploads) refuse such a
+// stream: a captured copy would replay from freed host memory.
+inline bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
 }  // namespace tn

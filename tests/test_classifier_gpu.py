@@ -265,3 +265,52 @@ def test_backward_fp32_chi128(tn):
     for i, (g, r) in enumerate(zip(grads, g_ref)):
         err = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
         assert err <= 1e-4, (i, err)
+
+
+def test_backward_under_graph_capture(tn):
+    # BF16 / BF16X3 only launch: the training step replays from a CUDA graph
+    # with the eager gradients. The FP32 backward builds and uploads its
+    # grouped plans in the call, from host lists a captured copy could not
+    # replay, so it refuses a capturing stream (TN_ERR_UNSUPPORTED) with
+    # nothing enqueued.
+    n, chi, ls, L, B = 16, 8, 7, 4, 48
+    cores = synth.classifier_mps(n, chi, ls, L, seed=71, eps_std=0.2)
+    px, y = dev(synth.pixels(B, n, seed=72)), torch.from_numpy(synth.labels(B, L, seed=73)).cuda()
+    dc = [dev(c) for c in cores]
+    for prec in ("bf16", "bf16x3"):
+        ws = tn.classifier_workspace(dc, ls, L, B, 4)
+
+        def step():
+            ft, lam, _ = tn.mps_classify(dc, ls, px, prec=prec, ckpt_every=4, workspace=ws)
+            _, dft = tn.mps_classify_loss(ft, y)
+            return tn.mps_classify_backward(dc, ls, px, dft, ws, prec=prec, ckpt_every=4)
+        eager = [g.clone() for g in step()]
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            out = step()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == 0
+        for a, b in zip(eager, out):
+            # float32 atomics in the gradient reductions: equal to rounding
+            assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(a.abs().max()))
+    ws = tn.classifier_workspace(dc, ls, L, B, 4)
+    ft, lam, _ = tn.mps_classify(dc, ls, px, prec="fp32", ckpt_every=4, workspace=ws)
+    _, dft = tn.mps_classify_loss(ft, y)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with pytest.raises(tn.TnError) as err:
+        with torch.cuda.graph(graph):
+            tn.mps_classify_backward(dc, ls, px, dft, ws, prec="fp32", ckpt_every=4)
+    assert err.value.code == 3
+    torch.cuda.synchronize()
+    assert tn.sync_status() == 0
+    grads = tn.mps_classify_backward(dc, ls, px, dft, ws, prec="fp32", ckpt_every=4)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == 0 and all(bool(torch.isfinite(g).all()) for g in grads)
