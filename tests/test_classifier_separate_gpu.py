@@ -128,3 +128,47 @@ def test_empty_batch_and_errors(tn):
     short = [mps_d[0], mps_d[1][:5]]
     with pytest.raises(tn.TnError):
         tn.mps_classify_separate(short, torch.rand((3, 6), device="cuda"), ckpt_every=0)
+
+
+def test_under_graph_capture(tn):
+    # the L sweeps run on library streams forked from and joined into the
+    # caller's stream, so forward (every precision) and the BF16 / BF16X3
+    # training step replay from a CUDA graph with the eager results
+    n, chi, L, B = 24, 16, 4, 64
+    mps = [[dev(c) for c in cores] for cores in synth.classifier_separate_mps(n, chi, L, seed=81, eps_std=0.1)]
+    px = dev(synth.pixels(B, n, seed=82))
+    y = torch.from_numpy(synth.labels(B, L, seed=83)).cuda()
+
+    def capture(fn):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            out = fn()
+        graph.replay()
+        torch.cuda.synchronize()
+        return out
+    for prec in ("fp32", "bf16", "bf16x3"):
+        ws = tn.classifier_separate_workspace(mps, B, 0)
+        fwd = lambda: tn.mps_classify_separate(mps, px, prec=prec, ckpt_every=0, workspace=ws)[:2]
+        eager = [t.clone() for t in fwd()]
+        got = capture(fwd)
+        assert tn.sync_status() == 0
+        for a, b in zip(eager, got):
+            assert torch.allclose(a, b, rtol=1e-6, atol=0.0), prec
+    for prec in ("bf16", "bf16x3"):
+        ws = tn.classifier_separate_workspace(mps, B, 3)
+
+        def step():
+            ft, lam, _ = tn.mps_classify_separate(mps, px, prec=prec, ckpt_every=3, workspace=ws)
+            _, dft = tn.mps_classify_loss(ft, y)
+            return tn.mps_classify_separate_backward(mps, px, dft, ws, prec=prec, ckpt_every=3)
+        eager = [[g.clone() for g in m] for m in step()]
+        got = capture(step)
+        assert tn.sync_status() == 0
+        for em, gm in zip(eager, got):
+            for a, b in zip(em, gm):
+                assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(a.abs().max())), prec
