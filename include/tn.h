@@ -270,7 +270,10 @@ int tn_group_plan_set_schedule(tn_group_plan* plan, int cls, int tile_width, int
  *     chunk c - 1 is contracted on a second and chunk c - 2's range of
  *     dev_out goes to host_out on a third; the library streams start after
  *     `stream`'s earlier work and `stream` waits for all of them, so host_out
- *     is complete once `stream` is.
+ *     is complete once `stream` is. Runs of one plan must not overlap (one
+ *     host thread, one stream at a time): they share its streams and events.
+ *     The run only launches and copies, so it can be captured in a CUDA
+ *     graph (host_in / host_out must then outlive the graph).
  * Errors: as tn_group_plan_create and _run, plus TN_ERR_ARG when a tensor
  * lies outside its buffer or the layout is not in spec order.
  */
@@ -373,7 +376,9 @@ int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace
  *           n_log_scale}: <psi|H|psi> = e_value * exp(e_log_scale) and
  *           <psi|psi> = n_value * exp(n_log_scale); the energy per the
  *           normalised state is their ratio.
- *   workspace: DEVICE scratch of tn_mps_expect_workspace_bytes() bytes.
+ *   workspace: DEVICE scratch of tn_mps_expect_workspace_bytes() bytes
+ *           (for chains with bonds <= 512 it includes room for every
+ *           site's core packed once per call, as the persistent form needs).
  * Errors: as tn_mps_inner, plus TN_ERR_UNSUPPORTED.
  */
 size_t tn_mps_expect_workspace_bytes(const tn_mps* psi, const tn_mpo* H);

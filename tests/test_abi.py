@@ -274,3 +274,37 @@ def test_separate_classifier_validation_without_gpu(libpath):
     # backward: checkpoints every >= 1 site required
     table = (ctypes.c_void_p * (2 * n))(*[0x9000] * (2 * n))
     assert lib.tn_mps_classify_separate_backward(two, 2, px, 8, 0, 0, ft, table, None, 0, None) == 1
+
+
+def test_staged_plan_validation_without_gpu(libpath):
+    """tn_staged_plan_create checks, on the host before any CUDA call, that
+    every tensor lies in its buffer and that the buffers are laid out in spec
+    order; the failure-path check wants a 256-byte aligned counter."""
+    lib, tn = _bound(libpath)
+
+    def desc(shape, addr):
+        t = tn.TnTensor()
+        t.data, t.rank = addr, len(shape)
+        for i, n in enumerate(shape):
+            t.shape[i] = n
+        return t
+    base_in, base_out = 0x100000, 0x900000
+    # two 8 x 8 by 8 x 8 specs: operands at base_in + 0, 256, 512, 768 bytes
+    def specs(order):
+        arr = (tn.TnContractSpec * 2)()
+        for i, k in enumerate(order):
+            arr[i].A = desc((8, 8), base_in + 512 * k)
+            arr[i].B = desc((8, 8), base_in + 512 * k + 256)
+            arr[i].C = desc((8, 8), base_out + 256 * k)
+            arr[i].nshared = 1
+            arr[i].legsA[0], arr[i].legsB[0] = 1, 0
+        return arr
+    h = ctypes.c_void_p()
+    vin, vout = ctypes.c_void_p(base_in), ctypes.c_void_p(base_out)
+    assert lib.tn_staged_plan_create(specs([0, 1]), 2, 0, vin, 1024, vout, 512, 0, ctypes.byref(h)) == 1  # chunks
+    assert lib.tn_staged_plan_create(specs([0, 1]), 2, 0, vin, 1000, vout, 512, 2, ctypes.byref(h)) == 1  # outside
+    assert lib.tn_staged_plan_create(specs([0, 1]), 2, 0, vin, 1024, vout, 500, 2, ctypes.byref(h)) == 1  # outside
+    assert lib.tn_staged_plan_create(specs([1, 0]), 2, 0, vin, 1024, vout, 512, 2, ctypes.byref(h)) == 1  # order
+    assert not h.value
+    assert lib.tn_check_grid_barrier_timeout(10_000_000, ctypes.c_void_p(0x1002), None) == 1
+    assert lib.tn_check_grid_barrier_timeout(10_000_000, None, None) == 1
