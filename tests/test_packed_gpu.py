@@ -235,10 +235,23 @@ def test_staged_plan_from_pinned_host(tn):
     assert staged.chunks == 3
     host_in = torch.empty(n_in, dtype=torch.float32, pin_memory=True)
     host_out = torch.empty(n_out, dtype=torch.float32, pin_memory=True)
-    for seed in (1, 2):
+    graph = None
+    for seed in (1, 2, 3):
         host_in.copy_(torch.from_numpy(np.random.default_rng(seed).standard_normal(n_in).astype(np.float32)))
         host_out.fill_(float("nan"))
-        staged.run(host_in, host_out)
+        if seed < 3:
+            staged.run(host_in, host_out)
+        else:
+            # the run only launches and copies: it replays from a CUDA graph
+            # (its library streams fork from and join the capturing stream)
+            graph = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=side):
+                staged.run(host_in, host_out, stream=side)
+            host_out.fill_(float("nan"))
+            graph.replay()
         torch.cuda.synchronize()
         assert tn.sync_status() == 0
         hi = host_in.numpy()
