@@ -445,7 +445,8 @@ void tn_mps_expect_grouped_destroy(tn_expect_plan* plan);
  * site (float32 path: divided by their largest magnitude; tensor-core paths:
  * multiplied by 2^-e, e the binary exponent of that magnitude, exactly), the
  * logs of the factors summed in float64, and met at the label core (a
- * float32 contraction over the batch).
+ * contraction over the batch: float32 for TN_PREC_FP32, the split BF16X3
+ * tensor-core contraction for the BF16 / BF16X3 modes).
  *   pixels:  DEVICE [batch, n] float32, row-major.
  *   ftilde:  DEVICE [batch, n_labels] float32; log_scale: DEVICE [batch]
  *            float64. score_l(b) = ftilde[b, l] * exp(log_scale[b]).
@@ -489,7 +490,8 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
  *   dcores: host table of n DEVICE pointers, each shaped like its core
  *           (overwritten).
  *   prec:   arithmetic of the sweeps and of the gradient products (the label
- *           core's contractions run in float32). TN_PREC_BF16X3 needs chi <=
+ *           core's contractions run in float32 for TN_PREC_FP32, split BF16X3
+ *           otherwise). TN_PREC_BF16X3 needs chi <=
  *           64 (its staging at chi = 128 does not fit in shared memory).
  * Errors: as tn_mps_classify, plus TN_ERR_UNSUPPORTED for TN_PREC_BF16X3 at
  * chi = 128. The gradient reductions are float32 atomics: results agree

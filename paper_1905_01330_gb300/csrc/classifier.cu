@@ -545,8 +545,14 @@ LabelParams label_params(const tn_mps* W, const ClsLayout& w, const float* pixel
   return lp;
 }
 
-// G[b, a, s, l] = sum_c vR[b, c] C[a, s, l, c] (float32).
-int label_G(const tn_mps* W, const ClsLayout& w, cudaStream_t s) {
+// The label core's contractions: float32 for an FP32 classifier; the split
+// BF16X3 tensor-core contraction for BF16 / BF16X3 (relative error ~2^-16 of
+// |A||B| per element, below either mode's own sweep error, at a fraction of
+// the float32 kernel's time).
+int label_prec(int prec) { return prec == TN_PREC_FP32 ? TN_PREC_FP32 : TN_PREC_BF16X3; }
+
+// G[b, a, s, l] = sum_c vR[b, c] C[a, s, l, c].
+int label_G(const tn_mps* W, const ClsLayout& w, int prec, cudaStream_t s) {
   const int64_t DL = W->bond[w.ls], DR = W->bond[w.ls + 1], B = w.batch, L = w.L;
   const int64_t shv[2] = {B, DR}, stv[2] = {w.chi, 1};
   const int64_t shc[4] = {DL, 2, L, DR}, stc[4] = {0, 0, 0, 0};
@@ -555,7 +561,7 @@ int label_G(const tn_mps* W, const ClsLayout& w, cudaStream_t s) {
   tn_tensor tc = strided(const_cast<float*>(W->cores[w.ls]), 4, shc, stc);
   tn_tensor tg = strided(w.labG, 4, shg, stg);
   const int lv[1] = {1}, lc[1] = {3};
-  return contract_internal(&tv, lv, &tc, lc, 1, &tg, TN_PREC_FP32, s);
+  return contract_internal(&tv, lv, &tc, lc, 1, &tg, label_prec(prec), s);
 }
 
 }  // namespace
@@ -620,7 +626,7 @@ int tn_mps_classify(const tn_mps* W, int label_site, int n_labels, const float* 
     q.store_every = ckpt_every > 0 ? ckpt_every : 1;
     if ((rc = cls_fwd_tc_launch(w.chi, split, q, s)) != TN_OK) return rc;
   }
-  if ((rc = label_G(W, w, s)) != TN_OK) return rc;
+  if ((rc = label_G(W, w, prec, s)) != TN_OK) return rc;
   LabelParams lp = label_params(W, w, pixels);
   lp.ftilde = ftilde;
   lp.log_scale = log_scale;
@@ -653,7 +659,7 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
 
   // label core: the adjoints entering both half-chains, and dC
   {
-    if ((rc = label_G(W, w, s)) != TN_OK) return rc;
+    if ((rc = label_G(W, w, prec, s)) != TN_OK) return rc;
     LabelParams lp = label_params(W, w, pixels);
     lp.dft = dftilde;
     lp.gL = w.g[0];
@@ -669,14 +675,14 @@ int tn_mps_classify_backward(const tn_mps* W, int label_site, int n_labels, cons
     tn_tensor tc = strided(const_cast<float*>(W->cores[ls]), 4, shc, stc);
     tn_tensor tr = strided(w.gR, 2, shr, str);
     const int lh[3] = {1, 2, 3}, lc[3] = {0, 1, 2};
-    if ((rc = contract_internal(&th, lh, &tc, lc, 3, &tr, TN_PREC_FP32, s)) != TN_OK) return rc;
+    if ((rc = contract_internal(&th, lh, &tc, lc, 3, &tr, label_prec(prec), s)) != TN_OK) return rc;
     const int64_t nvec = B * chi;
     cls_pad_rows<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(w.gR, (int)DR, w.g[1], batch, chi);
     if (cudaGetLastError() != cudaSuccess) return TN_ERR_CUDA;
     tn_tensor tv = strided(w.state[1], 2, shv, stv);
     tn_tensor td = strided(dcores[ls], 4, shc, stc);
     const int l0[1] = {0};
-    if ((rc = contract_internal(&th, l0, &tv, l0, 1, &td, TN_PREC_FP32, s)) != TN_OK) return rc;
+    if ((rc = contract_internal(&th, l0, &tv, l0, 1, &td, label_prec(prec), s)) != TN_OK) return rc;
   }
 
   const int seg = ckpt_every <= 1 ? std::max(std::max(w.T[0], w.T[1]), 1) : ckpt_every;
