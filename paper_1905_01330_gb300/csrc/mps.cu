@@ -596,7 +596,7 @@ bool fused_expect_ok(const tn_mps* psi, const tn_mpo* H, int prec) {
 // short and a launch boundary per phase costs more than a device-wide
 // barrier (measured, N = 100: chi = 512 BF16X3 4.7 -> 4.1 ms, BF16 3.35 ->
 // 3.2 ms; chi = 256 even). At chi = 1024 the per-site launches, with their
-// warp-specialised GEMM and 256-wide BF16 tiles, are faster (BF16X3 11.5
+// warp-specialised GEMM and 256-wide BF16 tiles, are faster (BF16X3 10.8
 // against 13.6 ms).
 bool use_persistent(const tn_mps* psi, const tn_mpo* H, int prec) {
   return max_bond(psi) <= PERSISTENT_MAX_BOND && expect_persistent_ok(psi, H, prec);
