@@ -82,6 +82,20 @@ def test_tfim_closed_forms_via_mpo(n):
     assert abs(v * math.exp(lg) - (-n)) < 1e-12         # |+..+>: E = -h N
 
 
+@pytest.mark.parametrize("n,seed", [(1, 11), (2, 12), (3, 13), (8, 14)])
+def test_tfim_product_state_closed_form(n, seed):
+    # site i in cos(t_i)|0> + sin(t_i)|1>: <Z_i> = cos 2t_i, <X_i> = sin 2t_i, and
+    # a product state factorises <Z_i Z_i+1>, so
+    # E = -J sum_i cos 2t_i cos 2t_i+1 - h sum_i sin 2t_i
+    t = np.random.default_rng(seed).uniform(-math.pi, math.pi, n)
+    J, h = 0.75, 1.25   # exact in float32, so the MPO holds them exactly
+    cores = [np.array([math.cos(a), math.sin(a)]).reshape(1, 2, 1) for a in t]
+    v, lg = oracle.mpo_expect(cores, synth.tfim_mpo(n, J=J, h=h))
+    ref = -J * sum(math.cos(2 * t[i]) * math.cos(2 * t[i + 1]) for i in range(n - 1)) \
+        - h * sum(math.sin(2 * a) for a in t)
+    assert abs(v * math.exp(lg) - ref) < 1e-12
+
+
 @pytest.mark.parametrize("n,chi,seed", [(6, 4, 1), (10, 8, 2), (12, 16, 3)])
 def test_mpo_energy_against_dense_hamiltonian(n, chi, seed):
     cores = synth.random_mps(n, 2, chi, seed=seed)
