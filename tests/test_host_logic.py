@@ -1,5 +1,5 @@
-"""Host logic without a GPU: the chunking of the staged plan (tn_chunk_bounds) and the bench's
-JSON line of the reference arm (the FP64 oracle on the host cores)."""
+"""Host logic without a GPU: the chunking of the staged plan (tn_chunk_bounds), the bench's
+JSON line of the reference arm (the FP64 oracle on the host cores) and its clock record."""
 import json
 import os
 import subprocess
@@ -44,3 +44,34 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_clock_sampler_keeps_samples_of_the_timed_region(tmp_path, monkeypatch):
+    """The bench's clock record: samples taken between start() and stop()
+    only, with the throttle reasons parsed from nvidia-smi's CSV. A stand-in
+    nvidia-smi on PATH prints one CSV line every 50 ms."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nwhile true; do\n"
+                    "  echo '0, 2070, 2070, 512.3, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.05\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    import time
+    s = bench.ClockSampler(0)
+    s.start()
+    time.sleep(0.4)
+    c = s.stop()
+    assert c is not None
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    assert 3 <= c["samples"] <= 12
+    # without nvidia-smi there is no record (and no error)
+    monkeypatch.setenv("PATH", str(tmp_path / "none"))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop() is None
