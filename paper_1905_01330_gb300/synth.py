@@ -224,6 +224,37 @@ def tfim_mpo(n_sites: int, J: float = 1.0, h: float = 1.0):
     return cores
 
 
+def spin1_xz_mpo(n_sites: int, h: float = 0.5):
+    """MPO of H = sum (Sz_i Sz_{i+1} + Sx_i Sx_{i+1}) - h sum Sz_i for spin-1
+    sites (d = 3, basis m = +1, 0, -1) on an open chain, bond dim 4.
+
+    Bulk tensor (w_left, w_right, s, s') = [[I,0,0,0],[Sz,0,0,0],[Sx,0,0,0],
+    [-h Sz, Sz, Sx, I]]; the first site keeps row 3, the last site keeps
+    column 0. Every operator is real symmetric. float32.
+    """
+    I = np.eye(3)
+    r = 1.0 / np.sqrt(2.0)
+    Sx = np.array([[0.0, r, 0.0], [r, 0.0, r], [0.0, r, 0.0]])
+    Sz = np.diag([1.0, 0.0, -1.0])
+    W = np.zeros((4, 4, 3, 3))
+    W[0, 0] = I
+    W[1, 0] = Sz
+    W[2, 0] = Sx
+    W[3, 0] = -h * Sz
+    W[3, 1] = Sz
+    W[3, 2] = Sx
+    W[3, 3] = I
+    cores = []
+    for i in range(n_sites):
+        w = W
+        if i == 0:
+            w = w[3:4]
+        if i == n_sites - 1:
+            w = w[:, 0:1]
+        cores.append(np.ascontiguousarray(w).astype(np.float32))
+    return cores
+
+
 # ---------------------------------------------------------------------------
 # MPS classifier inputs
 # ---------------------------------------------------------------------------

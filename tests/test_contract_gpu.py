@@ -174,6 +174,23 @@ def test_degenerate_shapes(tn, prec):
         check(C, A, la, B, lb, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
+def test_maximum_rank(tn, prec):
+    # rank 8 (the most a tensor may have): a rank-8 operand with four shared
+    # legs in scattered positions, and a rank-8 result
+    cases = [((2, 3, 2, 3, 2, 3, 2, 2), [1, 3, 5, 7], (3, 4, 3, 3, 2), [0, 2, 3, 4]),
+             ((3, 4, 5, 6, 7), [2], (5, 2, 3, 2, 2), [0]),
+             ((2, 2, 2, 2, 2, 2, 2, 9), [7, 0, 3], (2, 9, 2), [1, 2, 0])]
+    for i, (sa, la, sb, lb) in enumerate(cases):
+        A, B = rand(130 + i, sa), rand(140 + i, sb)
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        C = tn.contract(At, la, Bt, lb, prec=prec)
+        assert C.dim() == len(sa) + len(sb) - 2 * len(la)
+        check(C, A, la, B, lb, prec)
+        if prec != "fp32":   # and the single-pass kernel (no scratch)
+            check(tn.contract(At, la, Bt, lb, prec=prec, packed=False), A, la, B, lb, prec)
+
+
 def test_paper_examples_on_gpu(tn):
     # ones(2) . ones(2) = 2 (Sec. III.B.4); ncon example equals matmul (App. B)
     o = torch.ones(2, device="cuda")

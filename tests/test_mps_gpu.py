@@ -152,6 +152,44 @@ def test_energy_ragged_bonds(tn, chi, n, prec):
     assert rel(val(r, 1), norm) <= tol(prec, 2 * n) + 2 * n * bias
 
 
+@pytest.mark.parametrize("n", [512, 600])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_energy_long_chain_both_launch_forms(tn, n, prec):
+    # 512 sites: the most the one-launch persistent sweep takes (its site
+    # table is a launch parameter); 600 sites: past it, so the sweep runs as
+    # per-site launches. Same bound as the ragged-bond test.
+    cores = synth.left_canonical_mps(n, 2, 16, seed=12)
+    W = synth.tfim_mpo(n)
+    e, le = oracle.mpo_expect(cores, W)
+    nv, ln = oracle.mps_inner(cores, cores)
+    r = tn.mps_expect(to_dev(cores), to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    norm = nv * math.exp(ln)
+    h_norm = (n - 1) + n
+    assert abs(val(r, 0) - e * math.exp(le)) <= tol(prec, 2 * n) * h_norm * norm
+    bias = {"bf16x3": 2.0 ** -18, "bf16": 2.0 ** -16}[prec]
+    assert rel(val(r, 1), norm) <= tol(prec, 2 * n) + 2 * n * bias
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_energy_three_level_sites(tn, prec):
+    # spin-1 sites (d = 3) with a bond-4 MPO: (bond + 1) d = 15, so the sweep
+    # takes its general per-site launches. Bound as in the ragged-bond test,
+    # with ||H|| <= 2 (n - 1) + h n (||Sz Sz|| = ||Sx Sx|| = 1, ||Sz|| = 1).
+    n, d, chi, h = 8, 3, 12, 0.5
+    cores = synth.random_mps(n, d, chi, seed=21)
+    W = synth.spin1_xz_mpo(n, h=h)
+    e, le = oracle.mpo_expect(cores, W)
+    nv, ln = oracle.mps_inner(cores, cores)
+    norm = nv * math.exp(ln)
+    r = tn.mps_expect(to_dev(cores), to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    assert abs(val(r, 0) - e * math.exp(le)) <= tol(prec, 2 * n) * (2 * (n - 1) + h * n) * norm
+    assert rel(val(r, 1), norm) <= tol(prec, 2 * n)
+    ri = tn.mps_inner(to_dev(cores), to_dev(cores), prec=prec).cpu().numpy()
+    assert rel(ri[0] * math.exp(ri[1]), norm) <= tol(prec, 2 * n)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
 def test_grouped_energy_uneven_bonds(tn, prec):
     # config-5 batch shape at reduced size: uneven chi (one smallest, one
@@ -176,6 +214,25 @@ def test_grouped_energy_uneven_bonds(tn, prec):
         err = abs(r[k, 0] * math.exp(r[k, 1]) - e * math.exp(le))
         assert err <= tol(prec, 2 * n) * h_norm * norm, (k, chis[k])
         assert rel(r[k, 2] * math.exp(r[k, 3]), norm) <= tol(prec, 2 * n), (k, chis[k])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_grouped_energy_three_level_sites(tn, prec):
+    # spin-1 chains of uneven bonds in one grouped sweep (general step (ii):
+    # (bond + 1) d = 15); bound as in the single-chain spin-1 test
+    n, h = 8, 0.5
+    states = [synth.random_mps(n, 3, chi, seed=90 + chi) for chi in (5, 12, 27)]
+    W = synth.spin1_xz_mpo(n, h=h)
+    r = tn.mps_expect_grouped([to_dev(c) for c in states], to_dev(W), prec=prec)
+    assert tn.sync_status() == 0
+    r = r.cpu().numpy()
+    for k, cores in enumerate(states):
+        e, le = oracle.mpo_expect(cores, W)
+        nv, ln = oracle.mps_inner(cores, cores)
+        norm = nv * math.exp(ln)
+        err = abs(r[k, 0] * math.exp(r[k, 1]) - e * math.exp(le))
+        assert err <= tol(prec, 2 * n) * (2 * (n - 1) + h * n) * norm, k
+        assert rel(r[k, 2] * math.exp(r[k, 3]), norm) <= tol(prec, 2 * n), k
 
 
 def test_grouped_energy_matches_single_sweeps(tn):

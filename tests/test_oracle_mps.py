@@ -96,6 +96,36 @@ def test_tfim_product_state_closed_form(n, seed):
     assert abs(v * math.exp(lg) - ref) < 1e-12
 
 
+@pytest.mark.parametrize("n,seed", [(2, 31), (5, 32)])
+def test_spin1_mpo_energy_against_dense_hamiltonian(n, seed):
+    # d = 3: the state by explicit matrix products (numpy einsum) and H as a
+    # dense sum of Kronecker products, with the MPO's float32 entries
+    cores = synth.random_mps(n, 3, 6, seed=seed)
+    psi = cores[0].astype(np.float64)[0]                      # (s1, D1)
+    for c in cores[1:]:
+        psi = np.einsum("xa,asb->xsb", psi, c.astype(np.float64)).reshape(-1, c.shape[2])
+    psi = psi[:, 0]
+    r = float(np.float32(1.0 / math.sqrt(2.0)))
+    Sx = np.array([[0.0, r, 0.0], [r, 0.0, r], [0.0, r, 0.0]])
+    Sz = np.diag([1.0, 0.0, -1.0])
+    h = 0.5
+
+    def site_op(ops):   # {site: operator} as a 3^n x 3^n matrix
+        m = np.eye(1)
+        for i in range(n):
+            m = np.kron(m, ops.get(i, np.eye(3)))
+        return m
+
+    H = -h * sum(site_op({i: Sz}) for i in range(n))
+    for i in range(n - 1):
+        H = H + site_op({i: Sz, i + 1: Sz}) + site_op({i: Sx, i + 1: Sx})
+    ref = float(psi @ H @ psi)
+    v, lg = oracle.mpo_expect(cores, synth.spin1_xz_mpo(n, h=h))
+    assert abs(v * math.exp(lg) - ref) <= 1e-10 * max(1.0, abs(ref))
+    nv, ln = oracle.mps_inner(cores, cores)
+    assert abs(nv * math.exp(ln) - float(psi @ psi)) <= 1e-10 * float(psi @ psi)
+
+
 @pytest.mark.parametrize("n,chi,seed", [(6, 4, 1), (10, 8, 2), (12, 16, 3)])
 def test_mpo_energy_against_dense_hamiltonian(n, chi, seed):
     cores = synth.random_mps(n, 2, chi, seed=seed)
