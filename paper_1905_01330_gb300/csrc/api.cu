@@ -36,7 +36,7 @@ int64_t min_units_single() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
+      sms = 152;
   }
   return 2 * (int64_t)sms;
 }

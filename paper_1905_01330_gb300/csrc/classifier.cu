@@ -190,13 +190,8 @@ size_t sweep_smem() {
 template <int CHI>
 int launch_sweep_chi(const SweepParams& p, cudaStream_t s) {
   const size_t smem = sweep_smem<CHI>();
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(cls_sweep_simt<CHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return TN_ERR_CUDA;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  if (!smem_limit_once((const void*)cls_sweep_simt<CHI>, smem, &attr)) return TN_ERR_CUDA;
   cls_sweep_simt<CHI><<<(p.batch + BT - 1) / BT, 2 * CHI, smem, s>>>(p);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }

@@ -727,13 +727,8 @@ __global__ void cls_scatter_kernel(const __grid_constant__ ClsScatterParams p) {
 template <int CHI, int SPLIT>
 int launch_fwd(const ClsTcParams& p, cudaStream_t s) {
   const size_t smem = fwd_smem_bytes<CHI, SPLIT>();
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(cls_fwd_tc<CHI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return TN_ERR_CUDA;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  if (!smem_limit_once((const void*)cls_fwd_tc<CHI, SPLIT>, smem, &attr)) return TN_ERR_CUDA;
   cls_fwd_tc<CHI, SPLIT><<<2 * p.ntiles, NTHREADS, smem, s>>>(p);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
 }
@@ -744,13 +739,8 @@ int launch_adj(const ClsTcParams& p, cudaStream_t s) {
     return TN_ERR_UNSUPPORTED;
   } else {
     const size_t smem = adj_smem_bytes<CHI, SPLIT>();
-    static bool attr = false;
-    if (!attr) {
-      if (cudaFuncSetAttribute(cls_adj_tc<CHI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-        return TN_ERR_CUDA;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if (!smem_limit_once((const void*)cls_adj_tc<CHI, SPLIT>, smem, &attr)) return TN_ERR_CUDA;
     cls_adj_tc<CHI, SPLIT><<<2 * p.ntiles, NTHREADS, smem, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
   }

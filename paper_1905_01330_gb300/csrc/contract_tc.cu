@@ -559,7 +559,7 @@ int sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
+      sms = 152;
   }
   return sms;
 }
@@ -568,13 +568,8 @@ template <int SPLIT>
 int launch_tc(const ContractDesc& single, const ContractDesc* group, const int32_t* unit_desc, int64_t units,
               cudaStream_t stream) {
   const size_t smem = tc_smem_bytes<SPLIT>();
-  static bool attr_set = false;  // per process; every device gets the same attribute value
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(tc_contract_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return TN_ERR_CUDA;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  if (!smem_limit_once((const void*)tc_contract_kernel<SPLIT>, smem, &attr)) return TN_ERR_CUDA;
   const int64_t resident = (int64_t)sm_count();
   const unsigned grid = (unsigned)(units < resident ? units : resident);
   tc_contract_kernel<SPLIT><<<grid, Cfg<SPLIT>::NT, smem, stream>>>(single, group, unit_desc, units, status_word());

@@ -609,10 +609,10 @@ bool use_persistent(const tn_mps* psi, const tn_mpo* H, int prec) {
 int wide_tile(const ContractDesc& d) {
   const int64_t rp = p_is_b(d) ? d.N : d.M, rq = p_is_b(d) ? d.M : d.N;
   const int64_t units = (rp + 127) / 128 * ((rq + 255) / 256) * d.splits;
-  int dev = 0, sms = 148;
+  int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                  cudaSuccess)
-    sms = 148;
+    sms = 152;
   return rq >= 256 && units >= sms ? 256 : 128;
 }
 
@@ -789,24 +789,14 @@ int tn_mps_inner(const tn_mps* bra, const tn_mps* ket, int prec, void* workspace
     const size_t staged = sizeof(float) * (2 * (size_t)z.emax + z.tmax + 4 * (size_t)z.cmax);
     constexpr size_t STAGED_MAX = 200 * 1024;
     if (staged <= STAGED_MAX) {
-      static bool attr2 = false;
-      if (!attr2) {
-        if (cudaFuncSetAttribute(mps_inner_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)STAGED_MAX) != cudaSuccess)
-          return TN_ERR_CUDA;
-        attr2 = true;
-      }
+      static std::atomic<uint64_t> attr2{0};
+      if (!smem_limit_once((const void*)mps_inner_staged_kernel, STAGED_MAX, &attr2)) return TN_ERR_CUDA;
       mps_inner_staged_kernel<<<1, SMALL_THREADS, staged, s>>>(c, z, result);
       return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
     }
     const size_t smem = sizeof(float) * (2 * SMALL_D * SMALL_D + SMALL_D * SMALL_PHYS * SMALL_D);
-    static bool attr = false;
-    if (!attr) {
-      if (cudaFuncSetAttribute(mps_inner_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem) != cudaSuccess)
-        return TN_ERR_CUDA;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if (!smem_limit_once((const void*)mps_inner_small_kernel, smem, &attr)) return TN_ERR_CUDA;
     mps_inner_small_kernel<<<1, SMALL_THREADS, smem, s>>>(c, result);
     return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ERR_CUDA;
   }

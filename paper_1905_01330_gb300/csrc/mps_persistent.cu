@@ -751,12 +751,8 @@ int expect_persistent(const tn_mps* psi, const tn_mpo* H, int prec, const Expect
                                             : PsCfg<0>::STAGES * PsCfg<0>::STAGE_BYTES) +
                       sizeof(PsAux);
   const void* fn = split ? (const void*)expect_persistent_kernel<1> : (const void*)expect_persistent_kernel<0>;
-  static bool attr[2] = {false, false};
-  if (!attr[split ? 1 : 0]) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return TN_ERR_CUDA;
-    attr[split ? 1 : 0] = true;
-  }
+  static std::atomic<uint64_t> attr[2];
+  if (!smem_limit_once(fn, smem, &attr[split ? 1 : 0])) return TN_ERR_CUDA;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PS_THREADS, smem) != cudaSuccess || per_sm < 1)
     return TN_ERR_UNSUPPORTED;

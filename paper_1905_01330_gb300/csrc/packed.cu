@@ -1497,17 +1497,12 @@ packed_gemm_kernel(const __grid_constant__ GemmDesc single, const GemmDesc* __re
 }
 
 // Both pack kernels take PACK_SMEM of dynamic shared memory (above the 48 KB
-// default); set once per process.
+// default); set once per device.
 bool pack_attr() {
-  static bool done = false;
-  if (!done) {
-    if (cudaFuncSetAttribute(pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PACK_SMEM) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(pack_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PACK_SMEM) !=
-            cudaSuccess)
-      return false;
-    done = true;
-  }
+  static std::atomic<uint64_t> done_pack{0}, done_pair{0};
+  if (!smem_limit_once((const void*)pack_kernel, PACK_SMEM, &done_pack) ||
+      !smem_limit_once((const void*)pack_pair_kernel, PACK_SMEM, &done_pair))
+    return false;
   return true;
 }
 
@@ -1517,7 +1512,7 @@ int sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
+      sms = 152;
   }
   return sms;
 }
@@ -1526,13 +1521,8 @@ template <int SPLIT, int FUSE>
 int launch_gemm(const GemmDesc& single, const GemmDesc* descs, const int32_t* map, const PackJob* jobs,
                 int64_t units, cudaStream_t s, uint32_t* unit_ctr = nullptr) {
   const size_t smem = gemm_smem_bytes<SPLIT, FUSE>();
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(packed_gemm_kernel<SPLIT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return TN_ERR_CUDA;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  if (!smem_limit_once((const void*)packed_gemm_kernel<SPLIT, FUSE>, smem, &attr)) return TN_ERR_CUDA;
   const int64_t sms = sm_count();
   const unsigned grid = (unsigned)(units < sms ? units : sms);
   packed_gemm_kernel<SPLIT, FUSE>

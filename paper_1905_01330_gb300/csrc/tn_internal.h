@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/tn.h"
 
 namespace tn {
@@ -201,6 +203,20 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // it does on the legacy stream while another stream captures). Calls that
 // copy host lists which do not outlive them (plan uploads) refuse such a
 // stream: a captured copy would replay from freed host memory.
+// Raises kernel fn's dynamic shared-memory limit to `bytes` the first time it
+// is launched on the current device: the attribute belongs to the function as
+// loaded on each device, so `done` (one per kernel, static at the call site)
+// keeps one bit per device. False when the device or the call fails.
+inline bool smem_limit_once(const void* fn, size_t bytes, std::atomic<uint64_t>* done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  const uint64_t bit = uint64_t(1) << dev;
+  if (done->load(std::memory_order_acquire) & bit) return true;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+  done->fetch_or(bit, std::memory_order_acq_rel);
+  return true;
+}
+
 inline bool stream_capturing(cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
