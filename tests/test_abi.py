@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -308,3 +309,38 @@ def test_staged_plan_validation_without_gpu(libpath):
     assert not h.value
     assert lib.tn_check_grid_barrier_timeout(10_000_000, ctypes.c_void_p(0x1002), None) == 1
     assert lib.tn_check_grid_barrier_timeout(10_000_000, None, None) == 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
+def test_workload_plan_counts_the_algorithmic_work(libpath, prec):
+    """The bench's headline divides the plan's flops and bytes by the step
+    time: for the 2048-spec workload they are sum 2 M N K (about 2.0 TFLOP)
+    and sum 4 (|A| + |B| + |C|) bytes (about 31.9 GB), counted here from the
+    spec shapes alone, in every precision (planning runs on the host)."""
+    from paper_1905_01330_gb300 import synth
+    lib, tn = _bound(libpath)
+    specs = synth.contraction_specs(2048, seed=2)
+    arr = (tn.TnContractSpec * len(specs))()
+    flops = nbytes = 0.0
+    addr = 1 << 20
+    for i, (sha, la, shb, lb) in enumerate(specs):
+        M, N, K = synth.spec_sizes((sha, la, shb, lb))
+        flops += 2.0 * M * N * K
+        nbytes += 4.0 * (M * K + K * N + M * N)
+        shc = [n for j, n in enumerate(sha) if j not in la] + [n for j, n in enumerate(shb) if j not in lb]
+        for t, sh in ((arr[i].A, sha), (arr[i].B, shb), (arr[i].C, shc)):
+            t.data, t.rank = addr, len(sh)
+            for j, n in enumerate(sh):
+                t.shape[j] = n
+            addr += 256 * ((4 * int(np.prod(sh)) + 255) // 256)
+        arr[i].nshared = len(la)
+        for j in range(len(la)):
+            arr[i].legsA[j], arr[i].legsB[j] = la[j], lb[j]
+    h = ctypes.c_void_p()
+    assert lib.tn_group_plan_create(arr, len(specs), tn.PREC[prec], ctypes.byref(h)) == 0
+    try:
+        assert lib.tn_group_plan_flops(h) == pytest.approx(flops, rel=1e-12)
+        assert lib.tn_group_plan_bytes(h) == pytest.approx(nbytes, rel=1e-12)
+        assert 1.9e12 < flops < 2.1e12 and 31e9 < nbytes < 33e9
+    finally:
+        lib.tn_group_plan_destroy(h)
