@@ -32,6 +32,28 @@ def test_chunk_bounds(built, weights, chunks, bounds):
     assert all(a < b for a, b in zip(got, got[1:])) or not weights
 
 
+def test_chunk_bounds_properties_on_random_weights(built):
+    """On random weights (zeros and heavy items included): the bounds start at
+    0, end at n, rise strictly, give at most `chunks` runs, and no run of more
+    than one item exceeds the ideal share by more than twice the largest item
+    (each cut lands within one item of its ideal place)."""
+    import random
+    from paper_1905_01330_gb300.tn import chunk_bounds
+    rnd = random.Random(5)
+    for _ in range(300):
+        n = rnd.randint(1, 60)
+        w = [rnd.choice([0.0, rnd.random(), 10 * rnd.random(), 1000 * rnd.random()]) for _ in range(n)]
+        chunks = rnd.randint(1, 12)
+        b = chunk_bounds(w, chunks)
+        assert b[0] == 0 and b[-1] == n
+        assert all(x < y for x, y in zip(b, b[1:]))
+        assert len(b) - 1 <= chunks
+        share, big = sum(w) / chunks, max(w)
+        for lo, hi in zip(b, b[1:]):
+            if hi - lo > 1:
+                assert sum(w[lo:hi]) <= share + 2 * big + 1e-9, (w, chunks, b)
+
+
 def test_reference_arm_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
